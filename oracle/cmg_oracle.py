@@ -1,0 +1,525 @@
+"""Plain FP64 CPU oracle of the collective multigrid method.
+
+TEST INFRASTRUCTURE ONLY.  This module exists to check the CUDA path: only
+the tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import it.  It shares no code with the CUDA
+library and imports nothing from the product package.
+
+It computes, slowly and in the order the paper states them:
+
+* the discrete linear-quadratic problem under uncertainty (Sec. 2, the
+  full-space optimality system), in its symmetric form: the N state
+  block rows and the N adjoint block rows carry the quadrature weight
+  1/N on the mass block only, i.e.
+      (h^2/N) y_j + A_j p_j        = (h^2/N) y_d          (state-row block)
+      nu h^2 u   - h^2 sum_j p_j   = 0                     (control row)
+      A_j y_j    - h^2 u           = h^2 f                 (adjoint-row block)
+  which is the generic block form of Eq. (2) with C_j = M/N, G = nu M,
+  D_j = E_j = -M, M = h^2 I (lumped mass), A_j the integrated 5-point
+  stiffness of -div(kappa_j grad) with harmonic-mean face coefficients;
+* the node-collected reduced systems (Eq. 12) and their O(N) solution by
+  a Schur complement on u_i (Eq. 13);
+* collective smoothing: damped collective Jacobi (Eq. 11), lexicographic
+  and red-black collective Gauss-Seidel (the variants named after Eq. 11);
+* transfers: bilinear prolongation P and restriction R = P^T, coarse
+  operators rediscretised on each grid (the alternative the paper names
+  beside its Galerkin choice, Sec. 3);
+* the coarsest-grid direct solve and the V/W-cycle of Algorithm 1;
+* the V-cycle used stationary and as right preconditioner of flexible
+  GMRES, stopped on the relative unpreconditioned residual (Sec. 3.2).
+
+Readings where the paper is silent are listed in the design doc under
+"Readings of the paper"; the code follows them.
+
+Storage: node arrays are [n, n, ...] indexed [iy, ix]; y and p carry a
+trailing sample axis [n, n, N]; u is [n, n].  The lexicographic node index
+is i = iy * n + ix (x fastest), so reshape(n*n, N) gives the [node][sample]
+layout of the CUDA path.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# Random diffusion field and grid levels
+# ---------------------------------------------------------------------------
+
+def sine_mode_field(xi: np.ndarray, amp: float):
+    """kappa_j(x, y) = exp(amp * sum_k xi[j,k] sin(k pi x) sin(pi y) / k).
+
+    The sine-mode stand-in for the log-normal field of Eq. (15) (Sec. 3.2):
+    a log-Gaussian field whose modes vanish on the boundary, so kappa = 1
+    there.  Returns a function of coordinate arrays X, Y (same shape S)
+    giving an array of shape S + (N,).
+    """
+    xi = np.asarray(xi, dtype=np.float64)
+    N, K = xi.shape
+
+    def kappa(X, Y):
+        g = np.zeros(X.shape + (N,))
+        for k in range(1, K + 1):
+            mode = np.sin(k * np.pi * X) * np.sin(np.pi * Y) / k
+            g += mode[..., None] * xi[:, k - 1]
+        return np.exp(amp * g)
+
+    return kappa
+
+
+def harmonic_mean(ka, kb):
+    """Face coefficient between two nodes with nodal values ka, kb."""
+    return 2.0 * ka * kb / (ka + kb)
+
+
+@dataclass
+class Level:
+    """One grid of the hierarchy with its rediscretised operator.
+
+    n     interior nodes per side, h = 1/(n+1)
+    kx    [n, n+1, N]  face coefficients on vertical faces; kx[iy, f] lies
+          between interior columns f-1 and f (f = 0 and f = n touch the
+          boundary x = 0 and x = 1)
+    ky    [n+1, n, N]  the same for horizontal faces
+    a     [n, n, N]    diag(A_j) at each node (sum of its four faces)
+    c, G, d, e        the scalar diagonal blocks of Eq. (12) on this grid:
+          c = h^2/N, G = nu h^2, d = e = -h^2
+    """
+
+    n: int
+    N: int
+    nu: float
+    h: float
+    kx: np.ndarray
+    ky: np.ndarray
+    a: np.ndarray
+    c: float
+    G: float
+    d: float
+    e: float
+
+    @property
+    def sigma(self) -> np.ndarray:
+        """Schur denominator of Eq. (13): G + d^T diag(a)^-1 diag(c) diag(a)^-1 e."""
+        return self.G + np.sum(self.d * self.c * self.e / self.a ** 2, axis=-1)
+
+
+def make_level(n: int, N: int, nu: float, kappa_fn) -> Level:
+    """Rediscretise the operator on the n x n interior grid."""
+    h = 1.0 / (n + 1)
+    t = np.arange(n + 2, dtype=np.float64) * h          # includes boundary coordinates
+    X, Y = np.meshgrid(t, t, indexing="xy")             # [n+2, n+2]
+    kap = kappa_fn(X, Y)                                # [n+2, n+2, N]
+    kx = harmonic_mean(kap[1:-1, :-1], kap[1:-1, 1:])   # [n, n+1, N]
+    ky = harmonic_mean(kap[:-1, 1:-1], kap[1:, 1:-1])   # [n+1, n, N]
+    a = kx[:, :-1] + kx[:, 1:] + ky[:-1, :] + ky[1:, :]
+    return Level(n=n, N=N, nu=nu, h=h, kx=kx, ky=ky, a=a,
+                 c=h * h / N, G=nu * h * h, d=-h * h, e=-h * h)
+
+
+def make_hierarchy(n: int, N: int, nu: float, kappa_fn, coarsest_n: int = 3):
+    """Nested grids n_l = 2^l - 1 from n down to coarsest_n (finest first)."""
+    if n < coarsest_n or (n + 1) & n or (coarsest_n + 1) & coarsest_n:
+        raise ValueError("grid sizes must be 2^l - 1 with n >= coarsest_n")
+    levels = []
+    m = n
+    while True:
+        levels.append(make_level(m, N, nu, kappa_fn))
+        if m == coarsest_n:
+            break
+        m = (m - 1) // 2
+    return levels
+
+
+def fine_rhs(level: Level, yd: np.ndarray, f: np.ndarray | None = None):
+    """Right-hand side of the symmetric full-space system: ((h^2/N) y_d, 0, h^2 f)."""
+    n, N, h = level.n, level.N, level.h
+    fy = np.repeat((h * h / N * yd)[:, :, None], N, axis=2)
+    fu = np.zeros((n, n))
+    fp = np.zeros((n, n, N)) if f is None else np.repeat((h * h * f)[:, :, None], N, axis=2)
+    return fy, fu, fp
+
+
+# ---------------------------------------------------------------------------
+# Operator
+# ---------------------------------------------------------------------------
+
+def _pad(v):
+    """Zero Dirichlet ghosts around the [n, n, ...] node array."""
+    width = [(1, 1), (1, 1)] + [(0, 0)] * (v.ndim - 2)
+    return np.pad(v, width)
+
+
+def offdiag_sum(level: Level, v: np.ndarray) -> np.ndarray:
+    """sum over the four faces of node i of k_f * v_neighbour (zero outside)."""
+    vp = _pad(v)
+    return (level.kx[:, :-1] * vp[1:-1, :-2] + level.kx[:, 1:] * vp[1:-1, 2:]
+            + level.ky[:-1, :] * vp[:-2, 1:-1] + level.ky[1:, :] * vp[2:, 1:-1])
+
+
+def apply_A(level: Level, v: np.ndarray) -> np.ndarray:
+    """(A_j v_j)_i = sum_faces k_f (v_i - v_nbr): the integrated 5-point stencil."""
+    return level.a * v - offdiag_sum(level, v)
+
+
+def apply_S(level: Level, y, u, p):
+    """S x for the block matrix of Eq. (2) with the blocks of this problem."""
+    sy = level.c * y + apply_A(level, p)
+    su = level.G * u + level.d * np.sum(p, axis=-1)
+    sp = apply_A(level, y) + level.e * u[:, :, None]
+    return sy, su, sp
+
+
+def residual(level: Level, x, f):
+    """r = f - S x, block by block."""
+    sy, su, sp = apply_S(level, *x)
+    return f[0] - sy, f[1] - su, f[2] - sp
+
+
+def norm(v) -> float:
+    """Euclidean norm over all (2N+1) n^2 entries of a full-space vector."""
+    return float(np.sqrt(sum(np.sum(np.asarray(b) ** 2) for b in v)))
+
+
+# ---------------------------------------------------------------------------
+# Local solve, Eq. (13)
+# ---------------------------------------------------------------------------
+
+def local_solve(b_p, b_u, b_y, a, c, G, d, e):
+    """Solve the reduced node system S~_i x_i = b_i of Eq. (12) by Eq. (13).
+
+    b_p: rhs of the first block row (diag(c) y~ + diag(a) p~ = b_p)
+    b_u: rhs of the control row     (G u + d^T p~ = b_u)
+    b_y: rhs of the last block row  (diag(a) y~ + e u = b_y)
+    a: diag entries of A_j at the node.  c, d, e are vectors over samples
+    (scalars broadcast).  Leading axes of b_p, b_y, a are batch axes; the
+    last axis is the sample axis; b_u has the batch axes only.
+    Returns (y~, u, p~).
+    """
+    ainv = 1.0 / a
+    num = b_u + np.sum(d * (ainv * c * ainv * b_y - ainv * b_p), axis=-1)
+    den = G + np.sum(d * ainv * c * ainv * e, axis=-1)
+    u = num / den
+    y = ainv * (b_y - e * u[..., None])
+    p = ainv * (b_p - c * y)
+    return y, u, p
+
+
+# ---------------------------------------------------------------------------
+# Collective smoothers
+# ---------------------------------------------------------------------------
+
+def colour_mask(n: int, colour: int) -> np.ndarray:
+    """Red = colour 0 = (ix + iy) even; black = colour 1."""
+    iy, ix = np.indices((n, n))
+    return (ix + iy) % 2 == colour
+
+
+def rbgs_half_sweep(level: Level, x, f, colour: int):
+    """Collective GS on all nodes of one colour.
+
+    Nodes of one colour couple only to nodes of the other colour, so each
+    node's local system uses the current values of its neighbours and
+    replaces (y~_i, u_i, p~_i) by S~_i^{-1}(f_i - off-diagonal couplings).
+    """
+    y, u, p = (np.array(b, copy=True) for b in x)
+    fy, fu, fp = f
+    m = colour_mask(level.n, colour)
+    b_p = (fy + offdiag_sum(level, p))[m]      # first block row: c y + A p = f_y
+    b_y = (fp + offdiag_sum(level, y))[m]      # last block row:  A y + e u = f_p
+    b_u = fu[m]                                # control row has no neighbour coupling
+    yn, un, pn = local_solve(b_p, b_u, b_y, level.a[m], level.c, level.G, level.d, level.e)
+    y[m], u[m], p[m] = yn, un, pn
+    return y, u, p
+
+
+def rbgs_sweep(level: Level, x, f):
+    """One red-black collective GS sweep: red (ix+iy even) first, then black."""
+    x = rbgs_half_sweep(level, x, f, 0)
+    return rbgs_half_sweep(level, x, f, 1)
+
+
+def lexgs_sweep(level: Level, x, f):
+    """One lexicographic collective GS sweep, node order i = iy*n + ix.
+
+    Pure-Python node loop: for small grids only.
+    """
+    y, u, p = (np.array(b, copy=True) for b in x)
+    fy, fu, fp = f
+    n = level.n
+    kx, ky = level.kx, level.ky
+    for iy in range(n):
+        for ix in range(n):
+            off_p = np.zeros(level.N)
+            off_y = np.zeros(level.N)
+            if ix > 0:
+                off_p += kx[iy, ix] * p[iy, ix - 1]
+                off_y += kx[iy, ix] * y[iy, ix - 1]
+            if ix < n - 1:
+                off_p += kx[iy, ix + 1] * p[iy, ix + 1]
+                off_y += kx[iy, ix + 1] * y[iy, ix + 1]
+            if iy > 0:
+                off_p += ky[iy, ix] * p[iy - 1, ix]
+                off_y += ky[iy, ix] * y[iy - 1, ix]
+            if iy < n - 1:
+                off_p += ky[iy + 1, ix] * p[iy + 1, ix]
+                off_y += ky[iy + 1, ix] * y[iy + 1, ix]
+            yi, ui, pi = local_solve(fy[iy, ix] + off_p, fu[iy, ix], fp[iy, ix] + off_y,
+                                     level.a[iy, ix], level.c, level.G, level.d, level.e)
+            y[iy, ix], u[iy, ix], p[iy, ix] = yi, ui, pi
+    return y, u, p
+
+
+def jacobi_sweep(level: Level, x, f, theta: float):
+    """Damped collective Jacobi, Eq. (11): x <- x + theta sum_i P_i S~_i^{-1} R_i (f - S x)."""
+    ry, ru, rp = residual(level, x, f)
+    dy, du, dp = local_solve(ry, ru, rp, level.a, level.c, level.G, level.d, level.e)
+    return x[0] + theta * dy, x[1] + theta * du, x[2] + theta * dp
+
+
+@dataclass
+class CycleOptions:
+    smoother: str = "rbgs"        # "rbgs" | "lexgs" | "jacobi"
+    theta: float = 0.5            # Jacobi damping (the paper's value)
+    n1: int = 2                   # pre-smoothing steps
+    n2: int = 2                   # post-smoothing steps
+    gamma: int = 1                # 1 = V-cycle, 2 = W-cycle
+
+
+def smooth(level: Level, x, f, steps: int, opts: CycleOptions):
+    for _ in range(steps):
+        if opts.smoother == "rbgs":
+            x = rbgs_sweep(level, x, f)
+        elif opts.smoother == "lexgs":
+            x = lexgs_sweep(level, x, f)
+        elif opts.smoother == "jacobi":
+            x = jacobi_sweep(level, x, f, opts.theta)
+        else:
+            raise ValueError(opts.smoother)
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Grid transfers
+# ---------------------------------------------------------------------------
+
+def prolongation_1d(nf: int) -> np.ndarray:
+    """Linear interpolation from (nf-1)/2 coarse to nf fine interior nodes.
+
+    Coarse node I sits on fine node 2I+1; fine nodes 2I and 2I+2 receive
+    half of it.  Shape [nf, nc].
+    """
+    nc = (nf - 1) // 2
+    P = np.zeros((nf, nc))
+    for I in range(nc):
+        P[2 * I + 1, I] = 1.0
+        P[2 * I, I] = 0.5
+        P[2 * I + 2, I] = 0.5
+    return P
+
+
+def prolong(nf: int, e):
+    """Bilinear prolongation P e of a coarse full-space vector (all three blocks)."""
+    P1 = prolongation_1d(nf)
+    ey, eu, ep = e
+    return (np.einsum("aJ,bI,JIj->abj", P1, P1, ey),
+            np.einsum("aJ,bI,JI->ab", P1, P1, eu),
+            np.einsum("aJ,bI,JIj->abj", P1, P1, ep))
+
+
+def restrict(nf: int, r):
+    """Restriction R = P^T of a fine full-space vector (all three blocks).
+
+    Every block row is in integrated (h^2-scaled) form, so the transpose
+    of the bilinear prolongation (weights 1, 1/2, 1/4, i.e. 4x the 1/16
+    full-weighting stencil) is the consistent restriction.
+    """
+    P1 = prolongation_1d(nf)
+    ry, ru, rp = r
+    return (np.einsum("aJ,bI,abj->JIj", P1, P1, ry),
+            np.einsum("aJ,bI,ab->JI", P1, P1, ru),
+            np.einsum("aJ,bI,abj->JIj", P1, P1, rp))
+
+
+# ---------------------------------------------------------------------------
+# Coarsest-grid direct solve
+# ---------------------------------------------------------------------------
+
+def dense_A(level: Level, j: int) -> np.ndarray:
+    """A_j assembled column by column from its action (small grids)."""
+    n = level.n
+    m = n * n
+    A = np.zeros((m, m))
+    for col in range(m):
+        v = np.zeros((n, n, level.N))
+        v.reshape(m, level.N)[col, j] = 1.0
+        A[:, col] = apply_A(level, v)[:, :, j].reshape(m)
+    return A
+
+
+def coarse_solve(level: Level, f):
+    """Exact S^{-1} f by block elimination of the per-sample PDE blocks.
+
+    From the adjoint-row block y_j = A_j^{-1}(f_p,j - e u); from the
+    state-row block p_j = A_j^{-1}(f_y,j - c y_j); substituting into the
+    control row gives the n^2 x n^2 system
+        (G I + d c e sum_j A_j^{-2}) u = f_u - d sum_j (A_j^{-1} f_y,j - c A_j^{-2} f_p,j).
+    """
+    n, N = level.n, level.N
+    m = n * n
+    fy, fu, fp = (np.asarray(b).reshape(m, -1) if np.asarray(b).ndim == 3 else np.asarray(b).reshape(m) for b in f)
+    c, G, d, e = level.c, level.G, level.d, level.e
+    Ainv = [np.linalg.inv(dense_A(level, j)) for j in range(N)]
+    schur = G * np.eye(m)
+    rhs = fu.copy()
+    for j in range(N):
+        A2 = Ainv[j] @ Ainv[j]
+        schur += d * c * e * A2
+        rhs -= d * (Ainv[j] @ fy[:, j] - c * (A2 @ fp[:, j]))
+    u = np.linalg.solve(schur, rhs)
+    y = np.zeros((m, N))
+    p = np.zeros((m, N))
+    for j in range(N):
+        y[:, j] = Ainv[j] @ (fp[:, j] - e * u)
+        p[:, j] = Ainv[j] @ (fy[:, j] - c * y[:, j])
+    return y.reshape(n, n, N), u.reshape(n, n), p.reshape(n, n, N)
+
+
+def dense_S(level: Level) -> np.ndarray:
+    """The full (2N+1) n^2 system matrix in the ordering (y, u, p), each block
+    flattened [node][sample] (small grids only)."""
+    n, N = level.n, level.N
+    m = n * n
+    dim = (2 * N + 1) * m
+    S = np.zeros((dim, dim))
+    for col in range(dim):
+        z = np.zeros(dim)
+        z[col] = 1.0
+        S[:, col] = pack(apply_S(level, *unpack(z, n, N)))
+    return S
+
+
+def pack(x) -> np.ndarray:
+    y, u, p = x
+    return np.concatenate([np.ravel(y), np.ravel(u), np.ravel(p)])
+
+
+def unpack(z, n: int, N: int):
+    m = n * n
+    y = z[: m * N].reshape(n, n, N)
+    u = z[m * N: m * N + m].reshape(n, n)
+    p = z[m * N + m:].reshape(n, n, N)
+    return y, u, p
+
+
+# ---------------------------------------------------------------------------
+# Cycles and outer iterations
+# ---------------------------------------------------------------------------
+
+def zeros_like_level(level: Level):
+    n, N = level.n, level.N
+    return np.zeros((n, n, N)), np.zeros((n, n)), np.zeros((n, n, N))
+
+
+def cycle(levels, l: int, x, f, opts: CycleOptions):
+    """Algorithm 1 (V-cycle; gamma = 2 recursive calls gives the W-cycle)."""
+    level = levels[l]
+    if l == len(levels) - 1:
+        return coarse_solve(level, f)
+    x = smooth(level, x, f, opts.n1, opts)
+    r = residual(level, x, f)
+    fc = restrict(level.n, r)
+    ec = zeros_like_level(levels[l + 1])
+    for _ in range(opts.gamma):
+        ec = cycle(levels, l + 1, ec, fc, opts)
+    e = prolong(level.n, ec)
+    x = (x[0] + e[0], x[1] + e[1], x[2] + e[2])
+    return smooth(level, x, f, opts.n2, opts)
+
+
+@dataclass
+class SolveResult:
+    x: tuple
+    iters: int
+    relres: float
+    history: list
+
+
+def solve_stationary(levels, f, opts: CycleOptions, tol: float = 1e-10, maxit: int = 100, x0=None):
+    """Repeat the cycle until ||f - S x|| / ||f|| <= tol."""
+    x = zeros_like_level(levels[0]) if x0 is None else tuple(np.array(b, copy=True) for b in x0)
+    fnorm = norm(f)
+    hist = [norm(residual(levels[0], x, f)) / fnorm]
+    it = 0
+    while hist[-1] > tol and it < maxit:
+        x = cycle(levels, 0, x, f, opts)
+        it += 1
+        hist.append(norm(residual(levels[0], x, f)) / fnorm)
+    return SolveResult(x=x, iters=it, relres=hist[-1], history=hist)
+
+
+def fgmres(levels, f, opts: CycleOptions, tol: float = 1e-10, maxit: int = 100,
+           restart: int = 50, x0=None, precondition=True):
+    """Right-preconditioned flexible GMRES(restart) with the cycle as preconditioner.
+
+    Arnoldi with classical Gram-Schmidt applied twice (CGS2), Givens
+    rotations for the least-squares problem, stopping test on the
+    recurrence estimate of ||f - S x|| / ||f||, true residual recomputed at
+    every restart and at exit.
+    """
+    lev = levels[0]
+    n, N = lev.n, lev.N
+    x = pack(zeros_like_level(lev)) if x0 is None else pack(x0)
+    fv = pack(f)
+    fnorm = np.linalg.norm(fv)
+    S = lambda z: pack(apply_S(lev, *unpack(z, n, N)))
+    if precondition:
+        M = lambda v: pack(cycle(levels, 0, zeros_like_level(lev), unpack(v, n, N), opts))
+    else:
+        M = lambda v: v.copy()
+    r = fv - S(x)
+    beta = np.linalg.norm(r)
+    hist = [beta / fnorm]
+    total = 0
+    while hist[-1] > tol and total < maxit:
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        k_done = 0
+        for k in range(restart):
+            z = M(V[k])
+            Z.append(z)
+            w = S(z)
+            Vk = np.array(V)
+            h1 = Vk @ w
+            w = w - Vk.T @ h1
+            h2 = Vk @ w
+            w = w - Vk.T @ h2
+            H[: k + 1, k] = h1 + h2
+            H[k + 1, k] = np.linalg.norm(w)
+            V.append(w / H[k + 1, k] if H[k + 1, k] != 0 else w)
+            for i in range(k):
+                t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+                H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
+                H[i, k] = t
+            rho = np.hypot(H[k, k], H[k + 1, k])
+            cs[k], sn[k] = H[k, k] / rho, H[k + 1, k] / rho
+            H[k, k] = rho
+            H[k + 1, k] = 0.0
+            g[k + 1] = -sn[k] * g[k]
+            g[k] = cs[k] * g[k]
+            total += 1
+            k_done = k + 1
+            hist.append(abs(g[k + 1]) / fnorm)
+            if hist[-1] <= tol or total >= maxit:
+                break
+        yk = np.linalg.solve(np.triu(H[:k_done, :k_done]), g[:k_done])
+        x = x + np.array(Z).T @ yk
+        r = fv - S(x)
+        beta = np.linalg.norm(r)
+        hist[-1] = beta / fnorm
+    return SolveResult(x=unpack(x, n, N), iters=total, relres=hist[-1], history=hist)
