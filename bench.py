@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Benchmark of the collective multigrid solver on one GB300 (per rank).
+
+Workload (default): n = 255 interior nodes per side (65,025 nodes), N = 64
+samples, 16 field modes of amplitude 1.0, nu = 1e-6, y_d = sin(pi x)
+sin(pi y), f = 0, V(2,2) red-black collective Gauss-Seidel cycles down to
+3 x 3, solved to a relative residual of 1e-10 (paper's system, see
+include/cmg.h).  One step is the whole path on one synthetic instance:
+coefficients of every grid from the field draws (device), right-hand side,
+and the solve from a zero initial guess.
+
+Forms timed: plain FP64 (FGMRES with an FP64 V-cycle, and FP64 stationary
+cycles) and mixed precision (FP32 V-cycle inside FP64 iterative refinement
+or FP64 FGMRES).  The fastest form to the tolerance is the chosen form; its
+throughput in unknowns*cycles/s, (2N+1) n^2 * fine-grid cycles / time, is
+`value`.
+
+--impl reference times the CPU oracle (FP64 numpy) on the same workload:
+each step is one oracle V(2,2) cycle on the full grid.
+"""
+from __future__ import annotations
+
+import os
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+METRIC = "time-to-1e-10 residual & unknowns*cycles/s: chosen form vs plain FP64 GPU MG"
+UNIT = "unknowns*cycles/s"
+TOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cmg", choices=["cmg", "reference"])
+    ap.add_argument("--config", default="n255_N64", choices=sorted(inputs.CONFIGS))
+    ap.add_argument("--form", default="auto", choices=["auto", "fp64-fgmres", "fp64-cycle", "fp32-ir",
+                                                        "fp32-fgmres"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(name, n_gpus):
+    c = dict(inputs.CONFIGS[name])
+    return {"workload": f"collective MG, n={c['n']} ({c['n'] ** 2} nodes), N={c['N']}, K={c['K']}, "
+                        f"amp={c['amp']}, nu={c['nu']:g}, V(2,2) red-black to 3x3, tol {TOL:g}",
+            "n": c["n"], "N": c["N"], "K": c["K"], "nu": c["nu"], "amp": c["amp"],
+            "unknowns": (2 * c["N"] + 1) * c["n"] ** 2, "instances_per_gpu": 1,
+            "parallelism": f"replicas x{n_gpus} (independent instances, no collective)",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"cmg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+class OracleWorkload:
+    """The oracle's hierarchy and right side for one workload (built once)."""
+
+    def __init__(self, cfg_name: str):
+        import oracle.cmg_oracle as O
+
+        self.O = O
+        pr = inputs.make_problem(**inputs.CONFIGS[cfg_name])
+        self.levels = O.make_hierarchy(pr.n, pr.N, pr.nu, O.sine_mode_field(pr.xi, pr.amp))
+        self.f = O.fine_rhs(self.levels[0], pr.yd)
+        self.x = O.zeros_like_level(self.levels[0])
+        self.unknowns = (2 * pr.N + 1) * pr.n ** 2
+
+    def cycles(self, seconds: float, max_cycles: int):
+        """Run V(2,2) red-black oracle cycles until `seconds` have passed or
+        max_cycles are done; returns (cycles, seconds)."""
+        opts = self.O.CycleOptions()
+        t0 = time.perf_counter()
+        done = 0
+        while done < max_cycles:
+            self.x = self.O.cycle(self.levels, 0, self.x, self.f, opts)
+            done += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+        return done, time.perf_counter() - t0
+
+
+def oracle_cycle_rate(cfg_name: str, seconds: float = 12.0, max_cycles: int = 100):
+    """unknowns*cycles/s of the oracle on the full workload over a bounded
+    sample of about `seconds`; returns (rate, cycles, seconds)."""
+    w = OracleWorkload(cfg_name)
+    cyc, dt = w.cycles(seconds, max_cycles)
+    return w.unknowns * cyc / dt, cyc, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cfg = workload_config(args.config, args.gpus)
+    w = OracleWorkload(args.config)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        _, dt = w.cycles(0.0, 1)
+        if i >= args.warmup:
+            per_step.append(dt)
+    unknowns = cfg["unknowns"]
+    value = unknowns * len(per_step) / sum(per_step)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / len(per_step), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one FP64 V(2,2) red-black oracle cycle on the full grid per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+FORMS = {
+    "fp64-fgmres": dict(precision=0, method=1),
+    "fp64-cycle": dict(precision=0, method=0),
+    "fp32-ir": dict(precision=1, method=0),
+    "fp32-fgmres": dict(precision=1, method=1),
+}
+
+
+def algorithmic_bytes(kind: int, n: int, N: int, s: int) -> float:
+    """Minimum DRAM bytes one launch of `kind` must move on an n x n grid
+    with N samples and element size s (per-unit figures in the design doc)."""
+    nodes = n * n
+    faces = 2 * n * (n + 1) * N * s
+    if kind == 1:   # red-black half-sweep (average of the red and black launches)
+        act = nodes / 2.0
+        inact = nodes / 2.0
+        inva = act * N * 8 if s == 8 else 0.0
+        return (faces + act * N * (2 * s + 2 * s) + inact * N * 2 * s + inva + act * (8 + 8 + s))
+    if kind == 2:   # residual: read x, f, faces; write r
+        return 6 * s * nodes * N + faces + 3 * s * nodes
+    if kind == 4:   # restriction
+        nc = (n - 1) // 2
+        return 2 * s * nodes * N + 2 * s * nc * nc * N + s * (nodes + nc * nc)
+    if kind == 8:   # prolongation + correction
+        nc = (n - 1) // 2
+        return 4 * s * nodes * N + 2 * s * nc * nc * N + s * (2 * nodes + nc * nc)
+    raise ValueError(kind)
+
+
+KIND_NAMES = {1: "rbgs_half_kernel", 2: "residual_kernel", 4: "restrict_kernel", 8: "prolong_add_kernel"}
+
+
+def traffic_record(kernel: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2302_13680_gb300", "csrc", "cmg_stencil.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    entry = rec.get(f"{kernel}:{precision}")
+    if not entry or entry.get("source_sha") != sha:
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+def run_cmg(args, world, rank, local):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2302_13680_gb300 as P
+    from paper_2302_13680_gb300 import cmg as C
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    base = dict(inputs.CONFIGS[args.config])
+    base["seed"] = base["seed"] + 1000 * rank          # one independent instance per rank
+    pr = inputs.make_problem(**base)
+    n, N = pr.n, pr.N
+    unknowns = (2 * N + 1) * n * n
+    stream = torch.cuda.current_stream()
+    H = P.Hierarchy(n, N, pr.xi, pr.nu, pr.amp, stream=stream)
+    dev = torch.device("cuda", local)
+    xi_d = torch.tensor(pr.xi, device=dev)
+    yd_d = torch.tensor(pr.yd.reshape(-1), device=dev)
+    f = H.zeros(0)
+    x = H.zeros(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(form):
+        spec = FORMS[form]
+        H.set_samples(xi_d)
+        fr = H.rhs(yd_d)
+        for a, b in zip(f, fr):
+            a.copy_(b)
+        for t in x:
+            t.zero_()
+        st, status = H.solve(P.CycleOptions(precision=spec["precision"]), f, x, method=spec["method"],
+                             tol=TOL, maxit=200, restart=30, raise_on_fail=False)
+        if status != 0:
+            raise RuntimeError(f"form {form} did not reach {TOL}: status {status}, relres {st.relres:.3e}")
+        return st
+
+    def timed_steps(form, k, profile_kind=None):
+        times, cycles = [], []
+        prof = (0.0, 0)
+        if profile_kind:
+            H.profile_begin(profile_kind, 0)
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step(form)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            cycles.append(st.cycles)
+        if profile_kind:
+            prof = H.profile_end()
+        return times, cycles, prof, st
+
+    # --- compare forms (untimed for the result line, reported as context)
+    forms = list(FORMS) if args.form == "auto" else [args.form]
+    survey = {}
+    for form in forms:
+        for _ in range(2):
+            step(form)
+        t, c, _, st = timed_steps(form, 3)
+        survey[form] = {"time_to_tol_ms": statistics.median(t), "cycles": c[-1], "iters": st.iters,
+                        "relres": st.relres}
+    chosen = min(survey, key=lambda k: survey[k]["time_to_tol_ms"])
+    plain = "fp64-fgmres" if "fp64-fgmres" in survey else chosen
+    prec = "f32" if FORMS[chosen]["precision"] == 1 else "f64"
+    s_bytes = 4 if prec == "f32" else 8
+
+    # --- dominant level-0 kernel kind of the chosen form (one profiled step per kind)
+    kind_time = {}
+    for kind in (1, 2, 4, 8):
+        H.profile_begin(kind, 0)
+        step(chosen)
+        ms, cnt = H.profile_end()
+        kind_time[kind] = (ms, cnt)
+    dom = max(kind_time, key=lambda k: kind_time[k][0])
+
+    # --- warm-up and timed region
+    for _ in range(args.warmup):
+        step(chosen)
+    clocks = ClockSampler(local)
+    launches0 = C.kernel_launches()
+    barrier()
+    clocks.start()
+    times, cycles, (dom_ms, dom_cnt), st = timed_steps(chosen, args.steps, profile_kind=dom)
+    barrier()
+    clk = clocks.stop()
+    launches = C.kernel_launches() - launches0
+    total_s = sum(times) / 1e3
+    t_local = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    units_local = torch.tensor([float(unknowns * sum(cycles))], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(units_local, op=dist.ReduceOp.SUM)
+    total_s = float(t_local.item())
+    value = float(units_local.item()) / total_s
+
+    # --- end to end through the public API with host buffers
+    xi_h = torch.tensor(pr.xi).pin_memory()
+    yd_h = torch.tensor(pr.yd.reshape(-1)).pin_memory()
+    x_h = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in x]
+    e2e_times, e2e_cycles = [], []
+    h2d = xi_h.numel() * 8 + yd_h.numel() * 8
+    d2h = sum(t.numel() * 8 for t in x)
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xi_d.copy_(xi_h, non_blocking=True)
+        yd_d.copy_(yd_h, non_blocking=True)
+        st2 = step(chosen)
+        for hbuf, dbuf in zip(x_h, x):
+            hbuf.copy_(dbuf, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+        e2e_cycles.append(st2.cycles)
+    e2e_value = unknowns * sum(e2e_cycles) / (sum(e2e_times) / 1e3)
+
+    # --- roofline of the dominant kernel (algorithmic bytes / in-region launch time)
+    import json as _json
+
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _json.load(open(pk))
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    alg = algorithmic_bytes(dom, n, N, s_bytes)
+    avg_ms = dom_ms / max(dom_cnt, 1)
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    kname = KIND_NAMES[dom]
+    roofline = {"bound": "hbm", "kernel": f"{kname} ({prec}, finest grid)", "achieved": achieved,
+                "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_record(kname, prec), "algorithmic_bytes_per_launch": alg,
+                "avg_launch_ms": avg_ms, "launches_timed": dom_cnt}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cyc, dt = oracle_cycle_rate(args.config, seconds=12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{cyc} FP64 V(2,2) red-black oracle cycles on the full grid ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == "f32" else "f64",
+                "data": "synthetic", "config": workload_config(args.config, world),
+                "form": chosen,
+                "time_to_tol_ms": {"chosen": statistics.median(times), "plain_fp64": survey[plain]["time_to_tol_ms"]},
+                "speedup_vs_plain_fp64": survey[plain]["time_to_tol_ms"] / statistics.median(times),
+                "forms": survey, "cycles_per_step": statistics.mean(cycles),
+                "roofline": roofline,
+                "kernel_time_share_level0": {KIND_NAMES[k]: v[0] for k, v in kind_time.items()},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    H.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_cmg(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,244 @@
+/*
+ * cmg.h — C ABI of the collective multigrid solver for the saddle-point
+ * optimality system S x = f of a linear-quadratic elliptic optimal control
+ * problem under uncertainty (Ciaramella, Nobile, Vanzan, arXiv 2302.13680).
+ *
+ * Discrete problem (Sec. 2, full-space optimality system, in its symmetric
+ * scaling; generic block form Eq. (2)): on the unit square with n x n
+ * interior nodes, h = 1/(n+1), N samples of the diffusion field,
+ *     (h^2/N) y_j + A_j p_j        = f_y,j      (state-row block, C_j = M/N)
+ *     nu h^2 u   - h^2 sum_j p_j   = f_u        (control row,  G = nu M, D_j = -M)
+ *     A_j y_j    - h^2 u           = f_p,j      (adjoint-row block, E_j = -M)
+ * with M = h^2 I (lumped mass) and A_j the integrated 5-point stiffness of
+ * -div(kappa_j grad), face coefficients the harmonic mean of the two nodal
+ * values, zero Dirichlet data.  kappa_j(x,y) = exp(amp sum_k xi_jk
+ * sin(k pi x) sin(pi y) / k), the sine-mode stand-in for the log-normal
+ * field of Eq. (15).
+ *
+ * Vector layout (all levels): a full-space vector is three arrays
+ *     y [n*n][N]   state, node-major, sample index fastest
+ *     u [n*n]      control
+ *     p [n*n][N]   adjoint
+ * node index i = iy*n + ix (x fastest).  Level 0 is the finest grid; level
+ * l has n_l = (n_{l-1} - 1)/2 nodes per side.
+ *
+ * Memory and streams: every vector argument is a DEVICE pointer, borrowed
+ * for the duration of the call, 16-byte aligned.  The handle owns the
+ * device memory it allocates (hierarchy coefficients, coarse factors,
+ * work vectors) and frees it in cmg_destroy.  All work is enqueued on the
+ * stream given to cmg_create; calls return after enqueueing except those
+ * documented as synchronising (cmg_solve, cmg_norm).
+ *
+ * Errors: every call returns a cmg_status; on failure a message is kept in
+ * the handle (cmg_last_error).  No call aborts the process; a failed call
+ * leaves the handle usable.  Invalid sizes, null pointers or a level out of
+ * range give CMG_ERR_INVALID_ARG before anything is enqueued.
+ */
+#ifndef CMG_H_
+#define CMG_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cmg_handle cmg_handle;
+
+typedef enum {
+  CMG_OK = 0,
+  CMG_ERR_INVALID_ARG = 1,
+  CMG_ERR_CUDA = 2,
+  CMG_ERR_OOM = 3,
+  CMG_ERR_NOT_CONVERGED = 4,
+  CMG_ERR_NONFINITE = 5,
+  CMG_ERR_TIMEOUT = 6,
+  CMG_ERR_UNSUPPORTED = 7
+} cmg_status;
+
+enum { CMG_SMOOTH_RBGS = 0, CMG_SMOOTH_JACOBI = 1 };
+enum { CMG_FP64 = 0, CMG_FP32 = 1 };
+enum { CMG_METHOD_CYCLE = 0, CMG_METHOD_FGMRES = 1 };
+
+/* Problem description (Sec. 2; field of Sec. 3.2). */
+typedef struct {
+  int n;            /* interior nodes per side, finest grid: 2^L - 1, 3 <= n <= 4095 */
+  int N;            /* samples (quadrature nodes, Monte Carlo weights 1/N): 1 <= N <= 512 */
+  int K;            /* field modes, 0 <= K <= 64 */
+  double nu;        /* control cost nu > 0 */
+  double amp;       /* field amplitude */
+  int coarsest_n;   /* nodes per side of the coarsest grid: 1, 3 or 7 (<= n) */
+} cmg_problem;
+
+/* Cycle options (Algorithm 1). */
+typedef struct {
+  int smoother;     /* CMG_SMOOTH_RBGS (red = (ix+iy) even first) | CMG_SMOOTH_JACOBI */
+  double theta;     /* damping of collective Jacobi, Eq. (11); the paper uses 0.5 */
+  int n1, n2;       /* pre- and post-smoothing sweeps */
+  int gamma;        /* recursive calls per level: 1 = V-cycle, 2 = W-cycle */
+  int precision;    /* arithmetic of the cycle: CMG_FP64, or CMG_FP32 (single-precision
+                       smoothing, residual and transfers; Schur scalar for u and the
+                       coarsest solve in FP64) */
+} cmg_cycle;
+
+/* Solve statistics filled by cmg_solve. */
+typedef struct {
+  int iters;        /* outer iterations: cycles (CMG_METHOD_CYCLE) or FGMRES steps */
+  int cycles;       /* fine-grid cycles applied */
+  double relres0;   /* ||W (f - S x0)||_2 / ||W f||_2 (see cmg_solve) */
+  double relres;    /* final ||W (f - S x)||_2 / ||W f||_2, recomputed from x */
+} cmg_stats;
+
+/* ---- hierarchy ------------------------------------------------------- */
+
+/* Build the grid hierarchy n, (n-1)/2, ..., coarsest_n and, on the device,
+ * the nodal field, face coefficients, diag(A_j) and the Schur denominators
+ * of Eq. (13) on every grid (coarse operators rediscretised, Sec. 3), plus
+ * the coarsest-grid factors used by the direct solve of Algorithm 1.
+ * xi_host: host array [N][K] of field coefficients (copied).  stream: a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns all
+ * device memory it allocated.  Synchronises the stream once.
+ * Errors: INVALID_ARG (sizes), UNSUPPORTED (N above the kernels' limit),
+ * OOM, CUDA. */
+cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stream,
+                      cmg_handle** out);
+
+/* Recompute every level's coefficients and the coarsest factors from new
+ * field coefficients xi_dev (DEVICE [N][K]), same sizes.  Enqueued only. */
+cmg_status cmg_set_samples(cmg_handle* h, const double* xi_dev);
+
+void cmg_destroy(cmg_handle* h);
+const char* cmg_last_error(const cmg_handle* h);
+int cmg_num_levels(const cmg_handle* h);
+int cmg_level_n(const cmg_handle* h, int level);   /* -1 if out of range */
+
+/* ---- right-hand side -------------------------------------------------- */
+
+/* f = ((h^2/N) y_d, 0, h^2 f_src) on the finest grid (right side of the
+ * full-space system, Sec. 2).  yd, fsrc: device [n*n] (fsrc may be NULL
+ * for zero forcing). */
+cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc,
+                   double* fy, double* fu, double* fp);
+
+/* ---- level operators (FP64; *_f32 take float vectors) ------------------ */
+
+/* r = f - S x on grid `level` (Eq. (2) with this problem's blocks).  With
+ * fy, fu, fp all NULL the call computes r = S x (operator apply). */
+cmg_status cmg_residual(cmg_handle* h, int level,
+                        const double* y, const double* u, const double* p,
+                        const double* fy, const double* fu, const double* fp,
+                        double* ry, double* ru, double* rp);
+cmg_status cmg_residual_f32(cmg_handle* h, int level,
+                            const float* y, const float* u, const float* p,
+                            const float* fy, const float* fu, const float* fp,
+                            float* ry, float* ru, float* rp);
+
+/* `sweeps` collective smoothing steps in place on grid `level`:
+ * red-black collective Gauss-Seidel (each node solves its reduced system
+ * Eq. (12) by Eq. (13) with current neighbour values; all red nodes, then
+ * all black) or damped collective Jacobi Eq. (11).  Only opts->smoother and
+ * opts->theta are read. */
+cmg_status cmg_smooth(cmg_handle* h, int level, const cmg_cycle* opts, int sweeps,
+                      double* y, double* u, double* p,
+                      const double* fy, const double* fu, const double* fp);
+cmg_status cmg_smooth_f32(cmg_handle* h, int level, const cmg_cycle* opts, int sweeps,
+                          float* y, float* u, float* p,
+                          const float* fy, const float* fu, const float* fp);
+
+/* Coarse right side c = P^T r from grid `level` to `level`+1, P the
+ * bilinear prolongation (Algorithm 1, restriction step; weights 1, 1/2,
+ * 1/4, i.e. four times the 1/16 full-weighting stencil because every block
+ * row is in integrated form). */
+cmg_status cmg_restrict(cmg_handle* h, int level,
+                        const double* ry, const double* ru, const double* rp,
+                        double* cy, double* cu, double* cp);
+cmg_status cmg_restrict_f32(cmg_handle* h, int level,
+                            const float* ry, const float* ru, const float* rp,
+                            float* cy, float* cu, float* cp);
+
+/* x += P e: bilinear prolongation of the correction e on grid `level`+1
+ * added to x on grid `level` (Algorithm 1, coarse correction step). */
+cmg_status cmg_prolong_add(cmg_handle* h, int level,
+                           const double* ey, const double* eu, const double* ep,
+                           double* y, double* u, double* p);
+cmg_status cmg_prolong_add_f32(cmg_handle* h, int level,
+                               const float* ey, const float* eu, const float* ep,
+                               float* y, float* u, float* p);
+
+/* x = S^{-1} f on the coarsest grid (Algorithm 1, direct solver): the
+ * per-sample PDE blocks are eliminated with precomputed A_j^{-1} and the
+ * n_c^2 x n_c^2 Schur system for u is solved with its precomputed inverse.
+ * Always computed in FP64 (the f32 variant converts on load and store). */
+cmg_status cmg_coarse_solve(cmg_handle* h, const double* fy, const double* fu, const double* fp,
+                            double* y, double* u, double* p);
+cmg_status cmg_coarse_solve_f32(cmg_handle* h, const float* fy, const float* fu, const float* fp,
+                                float* y, float* u, float* p);
+
+/* ---- cycles and solves ------------------------------------------------ */
+
+/* One cycle of Algorithm 1 on the finest grid, in place on x, for rhs f.
+ * opts->precision must match the vector type (cmg_cycle_f32 for FP32). */
+cmg_status cmg_cycle_apply(cmg_handle* h, const cmg_cycle* opts,
+                           double* y, double* u, double* p,
+                           const double* fy, const double* fu, const double* fp);
+cmg_status cmg_cycle_apply_f32(cmg_handle* h, const cmg_cycle* opts,
+                               float* y, float* u, float* p,
+                               const float* fy, const float* fu, const float* fp);
+
+/* Solve S x = f on the finest grid to ||W (f - S x)||_2 <= tol ||W f||_2,
+ * x in/out (initial guess in, solution out), FP64 vectors.  This is the
+ * relative unpreconditioned residual of Sec. 3.2 measured on the paper's
+ * own form of the system (Sec. 2), whose state rows are N times the
+ * symmetric ones used here: W = diag(N I, 1, 1) on the (y, u, p) rows.
+ * (In the symmetric scaling the FP64 rounding floor of ||f - S x|| / ||f||
+ * grows like N (n+1)^2 eps and lies above 1e-10 for n = 255, N = 64.)
+ * method CMG_METHOD_CYCLE: repeated cycles (stationary iteration, Algorithm 1
+ *   repeated); with opts->precision == CMG_FP32 each step is FP64 iterative
+ *   refinement: r = f - S x in FP64, e = cycle_FP32(0; r), x += e.
+ * method CMG_METHOD_FGMRES: right-preconditioned flexible GMRES(restart)
+ *   on W S x = W f with one cycle (FP64 or FP32) applied to W^{-1} v as
+ *   preconditioner; Arnoldi by classical Gram-Schmidt applied twice, all
+ *   Krylov vectors FP64.
+ * Synchronises once per outer iteration to test convergence.  Returns
+ * CMG_ERR_NOT_CONVERGED if maxit is reached (x holds the last iterate),
+ * CMG_ERR_NONFINITE if a residual norm is not finite. */
+cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method, double tol,
+                     int maxit, int restart,
+                     const double* fy, const double* fu, const double* fp,
+                     double* y, double* u, double* p, cmg_stats* stats);
+
+/* ||(y,u,p)||_2 over all (2N+1) n_l^2 entries of a level vector, written to
+ * *out_host.  Synchronises. */
+cmg_status cmg_norm(cmg_handle* h, int level, const double* y, const double* u,
+                    const double* p, double* out_host);
+
+/* Wait for all work enqueued on the handle's stream. */
+cmg_status cmg_sync(cmg_handle* h);
+
+/* ---- measurement ------------------------------------------------------- */
+
+/* Kernel kinds for cmg_profile_begin. */
+enum {
+  CMG_KERNEL_SMOOTH = 1,     /* red-black half-sweep or Jacobi update */
+  CMG_KERNEL_RESIDUAL = 2,   /* residual / operator apply */
+  CMG_KERNEL_RESTRICT = 4,
+  CMG_KERNEL_PROLONG = 8,
+  CMG_KERNEL_COARSE = 16
+};
+
+/* Bracket every subsequent launch of the kernel kinds in `kinds` (a bit
+ * mask) on grid `level` with CUDA events on the handle's stream (at most
+ * 16384 launches are recorded).  Not part of the algorithm: used to time a
+ * kernel inside a longer run. */
+cmg_status cmg_profile_begin(cmg_handle* h, int kinds, int level);
+
+/* Stop recording, synchronise, and return the summed device time (ms) and
+ * the number of recorded launches since cmg_profile_begin. */
+cmg_status cmg_profile_end(cmg_handle* h, double* total_ms, int* launches);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+long long cmg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMG_H_ */

@@ -26,7 +26,8 @@ It computes, slowly and in the order the paper states them:
   beside its Galerkin choice, Sec. 3);
 * the coarsest-grid direct solve and the V/W-cycle of Algorithm 1;
 * the V-cycle used stationary and as right preconditioner of flexible
-  GMRES, stopped on the relative unpreconditioned residual (Sec. 3.2).
+  GMRES, stopped on the relative unpreconditioned residual of the paper's
+  own (unsymmetric) system (Sec. 3.2; see paper_norm).
 
 Readings where the paper is silent are listed in the design doc under
 "Readings of the paper"; the code follows them.
@@ -181,6 +182,20 @@ def norm(v) -> float:
     return float(np.sqrt(sum(np.sum(np.asarray(b) ** 2) for b in v)))
 
 
+def paper_norm(v, N: int) -> float:
+    """Euclidean norm of the vector in the scaling of the paper's system.
+
+    The paper writes the full-space optimality system (Sec. 2) with the
+    state rows M y_j + A_j^T p_j = M y_d, i.e. N times the symmetric state
+    rows used here (its adjoint is N times ours; the control and adjoint
+    rows coincide).  Its relative residual (Sec. 3.2) is therefore
+    ||W r|| / ||W f|| with W = diag(N I, 1, 1) on (y, u, p) rows.
+    """
+    y, u, p = v
+    return float(np.sqrt(N * N * np.sum(np.asarray(y) ** 2) + np.sum(np.asarray(u) ** 2)
+                         + np.sum(np.asarray(p) ** 2)))
+
+
 # ---------------------------------------------------------------------------
 # Local solve, Eq. (13)
 # ---------------------------------------------------------------------------
@@ -318,13 +333,20 @@ def prolongation_1d(nf: int) -> np.ndarray:
     return P
 
 
+def _apply_2d(P1, v, transpose: bool):
+    """(P1 (x) P1) v, or its transpose, on a node array [rows, cols, ...]:
+    the 2D operator is the tensor product of the 1D one, applied along y
+    (first axis) and then along x (second axis)."""
+    A = P1.T if transpose else P1
+    t = np.tensordot(A, v, axes=(1, 0))                 # along y
+    t = np.tensordot(A, t, axes=(1, 1))                 # along x -> [x, y, ...]
+    return np.swapaxes(t, 0, 1)
+
+
 def prolong(nf: int, e):
     """Bilinear prolongation P e of a coarse full-space vector (all three blocks)."""
     P1 = prolongation_1d(nf)
-    ey, eu, ep = e
-    return (np.einsum("aJ,bI,JIj->abj", P1, P1, ey),
-            np.einsum("aJ,bI,JI->ab", P1, P1, eu),
-            np.einsum("aJ,bI,JIj->abj", P1, P1, ep))
+    return tuple(_apply_2d(P1, np.asarray(b), transpose=False) for b in e)
 
 
 def restrict(nf: int, r):
@@ -335,10 +357,7 @@ def restrict(nf: int, r):
     full-weighting stencil) is the consistent restriction.
     """
     P1 = prolongation_1d(nf)
-    ry, ru, rp = r
-    return (np.einsum("aJ,bI,abj->JIj", P1, P1, ry),
-            np.einsum("aJ,bI,ab->JI", P1, P1, ru),
-            np.einsum("aJ,bI,abj->JIj", P1, P1, rp))
+    return tuple(_apply_2d(P1, np.asarray(b), transpose=True) for b in r)
 
 
 # ---------------------------------------------------------------------------
@@ -446,15 +465,17 @@ class SolveResult:
 
 
 def solve_stationary(levels, f, opts: CycleOptions, tol: float = 1e-10, maxit: int = 100, x0=None):
-    """Repeat the cycle until ||f - S x|| / ||f|| <= tol."""
+    """Repeat the cycle until the relative residual of the paper's system,
+    ||W (f - S x)|| / ||W f|| (see paper_norm), is <= tol."""
+    N = levels[0].N
     x = zeros_like_level(levels[0]) if x0 is None else tuple(np.array(b, copy=True) for b in x0)
-    fnorm = norm(f)
-    hist = [norm(residual(levels[0], x, f)) / fnorm]
+    fnorm = paper_norm(f, N)
+    hist = [paper_norm(residual(levels[0], x, f), N) / fnorm]
     it = 0
     while hist[-1] > tol and it < maxit:
         x = cycle(levels, 0, x, f, opts)
         it += 1
-        hist.append(norm(residual(levels[0], x, f)) / fnorm)
+        hist.append(paper_norm(residual(levels[0], x, f), N) / fnorm)
     return SolveResult(x=x, iters=it, relres=hist[-1], history=hist)
 
 
@@ -462,21 +483,26 @@ def fgmres(levels, f, opts: CycleOptions, tol: float = 1e-10, maxit: int = 100,
            restart: int = 50, x0=None, precondition=True):
     """Right-preconditioned flexible GMRES(restart) with the cycle as preconditioner.
 
-    Arnoldi with classical Gram-Schmidt applied twice (CGS2), Givens
-    rotations for the least-squares problem, stopping test on the
-    recurrence estimate of ||f - S x|| / ||f||, true residual recomputed at
-    every restart and at exit.
+    GMRES runs on the paper's system W S x = W f (W = diag(N I, 1, 1), see
+    paper_norm) so that it minimises the residual the paper reports; the
+    preconditioner is one cycle applied to W^{-1} v.  Arnoldi with
+    classical Gram-Schmidt applied twice (CGS2), Givens rotations for the
+    least-squares problem, stopping test on the recurrence estimate of
+    ||W (f - S x)|| / ||W f||, true residual recomputed at every restart
+    and at exit.
     """
     lev = levels[0]
     n, N = lev.n, lev.N
+    m = n * n * N
+    wvec = np.concatenate([np.full(m, float(N)), np.ones(n * n), np.ones(m)])
     x = pack(zeros_like_level(lev)) if x0 is None else pack(x0)
-    fv = pack(f)
+    fv = wvec * pack(f)
     fnorm = np.linalg.norm(fv)
-    S = lambda z: pack(apply_S(lev, *unpack(z, n, N)))
+    S = lambda z: wvec * pack(apply_S(lev, *unpack(z, n, N)))
     if precondition:
-        M = lambda v: pack(cycle(levels, 0, zeros_like_level(lev), unpack(v, n, N), opts))
+        M = lambda v: pack(cycle(levels, 0, zeros_like_level(lev), unpack(v / wvec, n, N), opts))
     else:
-        M = lambda v: v.copy()
+        M = lambda v: v / wvec
     r = fv - S(x)
     beta = np.linalg.norm(r)
     hist = [beta / fnorm]

@@ -1,0 +1,282 @@
+"""Python binding of libcmg (include/cmg.h): argument marshalling only.
+
+Every numerical step runs in the CUDA kernels of libcmg.so.  Tensors are
+PyTorch CUDA tensors (device memory and streams only); this module checks
+their dtype, shape, device and contiguity and passes raw pointers through
+the C ABI.  There is no CPU fallback: if the library is missing or no GPU
+is present, calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcmg.so")
+
+CMG_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE",
+          6: "TIMEOUT", 7: "UNSUPPORTED"}
+SMOOTH_RBGS, SMOOTH_JACOBI = 0, 1
+FP64, FP32 = 0, 1
+METHOD_CYCLE, METHOD_FGMRES = 0, 1
+
+
+class CMGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cmg {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int), ("nu", ctypes.c_double),
+                ("amp", ctypes.c_double), ("coarsest_n", ctypes.c_int)]
+
+
+class Cycle(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("theta", ctypes.c_double), ("n1", ctypes.c_int),
+                ("n2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("relres0", ctypes.c_double),
+                ("relres", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libcmg.so (built by paper_2302_13680_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcmg.so not found at {path}: run paper_2302_13680_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    sig = {
+        "cmg_create": (_I, [ctypes.POINTER(Problem), _P, _P, ctypes.POINTER(H)]),
+        "cmg_set_samples": (_I, [H, _P]),
+        "cmg_destroy": (None, [H]),
+        "cmg_last_error": (ctypes.c_char_p, [H]),
+        "cmg_num_levels": (_I, [H]),
+        "cmg_level_n": (_I, [H, _I]),
+        "cmg_rhs": (_I, [H, _P, _P, _P, _P, _P]),
+        "cmg_norm": (_I, [H, _I, _P, _P, _P, ctypes.POINTER(_D)]),
+        "cmg_sync": (_I, [H]),
+        "cmg_profile_begin": (_I, [H, _I, _I]),
+        "cmg_profile_end": (_I, [H, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+        "cmg_kernel_launches": (ctypes.c_longlong, []),
+        "cmg_solve": (_I, [H, ctypes.POINTER(Cycle), _I, _D, _I, _I, _P, _P, _P, _P, _P, _P,
+                           ctypes.POINTER(Stats)]),
+    }
+    for suf in ("", "_f32"):
+        sig["cmg_residual" + suf] = (_I, [H, _I] + [_P] * 9)
+        sig["cmg_smooth" + suf] = (_I, [H, _I, ctypes.POINTER(Cycle), _I] + [_P] * 6)
+        sig["cmg_restrict" + suf] = (_I, [H, _I] + [_P] * 6)
+        sig["cmg_prolong_add" + suf] = (_I, [H, _I] + [_P] * 6)
+        sig["cmg_coarse_solve" + suf] = (_I, [H] + [_P] * 6)
+        sig["cmg_cycle_apply" + suf] = (_I, [H, ctypes.POINTER(Cycle)] + [_P] * 6)
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+@dataclass
+class CycleOptions:
+    smoother: int = SMOOTH_RBGS
+    theta: float = 0.5
+    n1: int = 2
+    n2: int = 2
+    gamma: int = 1
+    precision: int = FP64
+
+    def c(self) -> Cycle:
+        return Cycle(self.smoother, self.theta, self.n1, self.n2, self.gamma, self.precision)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Hierarchy:
+    """One problem instance: grid hierarchy and coefficients on the GPU.
+
+    Vectors are triples (y, u, p) of CUDA tensors with y, p of shape
+    [n_l*n_l, N] and u of shape [n_l*n_l] on grid l, contiguous, dtype
+    float64 (or float32 for the *_f32 calls).
+    """
+
+    def __init__(self, n: int, N: int, xi, nu: float, amp: float, coarsest_n: int = 3, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libcmg needs a CUDA GPU; none is available")
+        self._lib = load_library()
+        xi = np.ascontiguousarray(np.asarray(xi, dtype=np.float64))
+        if xi.ndim != 2 or xi.shape[0] != N:
+            raise ValueError("xi must have shape [N, K]")
+        self.n, self.N, self.K = int(n), int(N), int(xi.shape[1])
+        self.nu, self.amp = float(nu), float(amp)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        prob = Problem(self.n, self.N, self.K, self.nu, self.amp, coarsest_n)
+        h = ctypes.c_void_p()
+        st = self._lib.cmg_create(ctypes.byref(prob), xi.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != CMG_OK:
+            raise CMGError(st, "cmg_create failed")
+        self._h = h
+        self.levels = self._lib.cmg_num_levels(h)
+        self.level_n = [self._lib.cmg_level_n(h, l) for l in range(self.levels)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- helpers ----
+    def _check(self, st: int):
+        if st != CMG_OK:
+            msg = self._lib.cmg_last_error(self._h)
+            raise CMGError(st, msg.decode() if msg else "")
+
+    def _vec(self, v, level: int, dtype, name: str):
+        import torch
+
+        if v is None:
+            return [None, None, None]
+        y, u, p = v
+        if not 0 <= level < self.levels:
+            # out-of-range level: let the C ABI reject the call
+            return [_ptr(y), _ptr(u), _ptr(p)]
+        m = self.level_n[level] ** 2
+        for t, shape in ((y, (m, self.N)), (u, (m,)), (p, (m, self.N))):
+            if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != dtype:
+                raise TypeError(f"{name}: expected CUDA {dtype} tensors")
+            if tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"{name}: expected contiguous shape {shape}, got {tuple(t.shape)}")
+        return [_ptr(y), _ptr(u), _ptr(p)]
+
+    def zeros(self, level: int = 0, dtype=None):
+        import torch
+
+        dtype = dtype or torch.float64
+        m = self.level_n[level] ** 2
+        return (torch.zeros(m, self.N, dtype=dtype, device=self.device),
+                torch.zeros(m, dtype=dtype, device=self.device),
+                torch.zeros(m, self.N, dtype=dtype, device=self.device))
+
+    @staticmethod
+    def _suffix(dtype):
+        import torch
+
+        return "_f32" if dtype == torch.float32 else ""
+
+    # ---- C ABI calls ----
+    def set_samples(self, xi_dev):
+        self._check(self._lib.cmg_set_samples(self._h, _ptr(xi_dev)))
+
+    def rhs(self, yd, fsrc=None):
+        import torch
+
+        f = self.zeros(0)
+        self._check(self._lib.cmg_rhs(self._h, _ptr(yd), _ptr(fsrc), *[_ptr(t) for t in f]))
+        return f
+
+    def residual(self, level, x, f, r):
+        dt = x[0].dtype
+        fn = getattr(self._lib, "cmg_residual" + self._suffix(dt))
+        self._check(fn(self._h, level, *self._vec(x, level, dt, "x"), *self._vec(f, level, dt, "f"),
+                       *self._vec(r, level, dt, "r")))
+
+    def smooth(self, level, opts: CycleOptions, sweeps, x, f):
+        dt = x[0].dtype
+        fn = getattr(self._lib, "cmg_smooth" + self._suffix(dt))
+        c = opts.c()
+        self._check(fn(self._h, level, ctypes.byref(c), sweeps, *self._vec(x, level, dt, "x"),
+                       *self._vec(f, level, dt, "f")))
+
+    def restrict(self, level, r, c):
+        if not 0 <= level < self.levels - 1:
+            raise CMGError(1, "level out of range")
+        dt = r[0].dtype
+        fn = getattr(self._lib, "cmg_restrict" + self._suffix(dt))
+        self._check(fn(self._h, level, *self._vec(r, level, dt, "r"), *self._vec(c, level + 1, dt, "c")))
+
+    def prolong_add(self, level, e, x):
+        if not 0 <= level < self.levels - 1:
+            raise CMGError(1, "level out of range")
+        dt = e[0].dtype
+        fn = getattr(self._lib, "cmg_prolong_add" + self._suffix(dt))
+        self._check(fn(self._h, level, *self._vec(e, level + 1, dt, "e"), *self._vec(x, level, dt, "x")))
+
+    def coarse_solve(self, f, x):
+        dt = f[0].dtype
+        L = self.levels - 1
+        fn = getattr(self._lib, "cmg_coarse_solve" + self._suffix(dt))
+        self._check(fn(self._h, *self._vec(f, L, dt, "f"), *self._vec(x, L, dt, "x")))
+
+    def cycle(self, opts: CycleOptions, x, f):
+        dt = x[0].dtype
+        fn = getattr(self._lib, "cmg_cycle_apply" + self._suffix(dt))
+        c = opts.c()
+        self._check(fn(self._h, ctypes.byref(c), *self._vec(x, 0, dt, "x"), *self._vec(f, 0, dt, "f")))
+
+    def solve(self, opts: CycleOptions, f, x, method=METHOD_CYCLE, tol=1e-10, maxit=100, restart=30,
+              raise_on_fail=True):
+        import torch
+
+        c = opts.c()
+        st = Stats()
+        status = self._lib.cmg_solve(self._h, ctypes.byref(c), method, tol, maxit, restart,
+                                     *self._vec(f, 0, torch.float64, "f"), *self._vec(x, 0, torch.float64, "x"),
+                                     ctypes.byref(st))
+        if raise_on_fail:
+            self._check(status)
+        return st, status
+
+    def norm(self, level, v):
+        import torch
+
+        out = ctypes.c_double()
+        self._check(self._lib.cmg_norm(self._h, level, *self._vec(v, level, torch.float64, "v"),
+                                       ctypes.byref(out)))
+        return out.value
+
+    def sync(self):
+        self._check(self._lib.cmg_sync(self._h))
+
+    def profile_begin(self, kinds: int, level: int = 0):
+        self._check(self._lib.cmg_profile_begin(self._h, kinds, level))
+
+    def profile_end(self):
+        ms, cnt = ctypes.c_double(), ctypes.c_int()
+        self._check(self._lib.cmg_profile_end(self._h, ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
+
+KERNEL_SMOOTH, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_COARSE = 1, 2, 4, 8, 16
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libcmg in this process so far."""
+    return int(load_library().cmg_kernel_launches())

@@ -1,0 +1,733 @@
+// C ABI of libcmg (include/cmg.h): handle, grid hierarchy, cycles and
+// outer solvers.  All device work is enqueued on the handle's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <atomic>
+
+#include "cmg_common.cuh"
+
+using namespace cmg;
+
+namespace cmg {
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace cmg
+
+namespace {
+
+struct Lev {
+  int n = 0;
+  double h = 0, c = 0, G = 0, d = 0, e = 0;
+  size_t nodes = 0;                      // n*n
+  double *kx64 = nullptr, *ky64 = nullptr, *inva = nullptr, *sigma = nullptr;
+  float *kx32 = nullptr, *ky32 = nullptr;
+  double* x64[3] = {nullptr, nullptr, nullptr};
+  double* f64[3] = {nullptr, nullptr, nullptr};
+  double* r64[3] = {nullptr, nullptr, nullptr};
+  float* x32[3] = {nullptr, nullptr, nullptr};
+  float* f32[3] = {nullptr, nullptr, nullptr};
+  float* r32[3] = {nullptr, nullptr, nullptr};
+};
+
+template <typename T> struct Work;
+template <> struct Work<double> {
+  static Vec3<double> x(Lev& l) { return {l.x64[0], l.x64[1], l.x64[2]}; }
+  static Vec3<double> f(Lev& l) { return {l.f64[0], l.f64[1], l.f64[2]}; }
+  static Vec3<double> r(Lev& l) { return {l.r64[0], l.r64[1], l.r64[2]}; }
+};
+template <> struct Work<float> {
+  static Vec3<float> x(Lev& l) { return {l.x32[0], l.x32[1], l.x32[2]}; }
+  static Vec3<float> f(Lev& l) { return {l.f32[0], l.f32[1], l.f32[2]}; }
+  static Vec3<float> r(Lev& l) { return {l.r32[0], l.r32[1], l.r32[2]}; }
+};
+
+constexpr int kMaxRestart = 60;
+constexpr int kMaxProf = 4096;   // event pairs recorded per profiling window
+
+}  // namespace
+
+struct cmg_handle {
+  cmg_problem prob{};
+  cudaStream_t stream = nullptr;
+  int L = 0;
+  Lev lv[kMaxLevels];
+  CoarseData coarse{};
+  double* xi = nullptr;       // [N][K] device
+  double* kap = nullptr;      // setup scratch
+  double* red = nullptr;      // reduction partials
+  double* dsc = nullptr;      // device scalars
+  double* hsc = nullptr;      // pinned host scalars
+  // FGMRES workspace
+  int gm_cap = 0;
+  double* gm = nullptr;       // [2*cap + 2][nt_pad]
+  size_t nt = 0, nt_pad = 0;
+  std::vector<void*> allocs;
+  std::string err;
+  // kernel timing window (cmg_profile_begin / end)
+  int prof_kinds = 0, prof_level = -1, prof_n = 0;
+  std::vector<cudaEvent_t> prof_ev;
+};
+
+namespace {
+
+cmg_status fail(cmg_handle* h, cmg_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+cmg_status cuda_fail(cmg_handle* h, cudaError_t e, const char* what) {
+  const cmg_status st = (e == cudaErrorMemoryAllocation) ? CMG_ERR_OOM : CMG_ERR_CUDA;
+  (void)cudaGetLastError();  // clear a sticky launch error so the handle stays usable
+  return fail(h, st, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(cmg_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (count ? count : 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+// Brackets one launch of `kind` on grid `level` with CUDA events when the
+// profiling window asks for it.
+struct ProfScope {
+  cmg_handle* h;
+  int idx = -1;
+  ProfScope(cmg_handle* hh, int kind, int level) : h(hh) {
+    if ((h->prof_kinds & kind) && level == h->prof_level && h->prof_n < kMaxProf) {
+      idx = h->prof_n++;
+      (void)cudaEventRecord(h->prof_ev[2 * idx], h->stream);
+    }
+  }
+  ~ProfScope() {
+    if (idx >= 0) (void)cudaEventRecord(h->prof_ev[2 * idx + 1], h->stream);
+  }
+};
+
+template <typename T>
+LevelView<T> view(const cmg_handle* h, int l);
+template <>
+LevelView<double> view<double>(const cmg_handle* h, int l) {
+  const Lev& v = h->lv[l];
+  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.sigma, v.c, v.G, v.d, v.e};
+}
+template <>
+LevelView<float> view<float>(const cmg_handle* h, int l) {
+  const Lev& v = h->lv[l];
+  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.sigma, v.c, v.G, v.d, v.e};
+}
+
+bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
+
+template <typename T>
+bool vec_ok(const T* y, const T* u, const T* p) { return y && u && p; }
+
+cudaError_t setup_coefficients(cmg_handle* h) {
+  const cmg_problem& P = h->prob;
+  for (int l = 0; l < h->L; ++l) {
+    Lev& v = h->lv[l];
+    cudaError_t e = launch_level_setup(v.n, P.N, P.K, P.amp, h->xi, h->kap, v.kx64, v.ky64, v.kx32, v.ky32, v.inva,
+                                       v.sigma, v.c, v.G, v.d, v.e, h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  const Lev& cl = h->lv[h->L - 1];
+  return launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
+}
+
+// ---- smoothing and cycles --------------------------------------------------
+
+template <typename T>
+cudaError_t smooth(cmg_handle* h, const cmg_cycle& o, int l, int sweeps, Vec3<T> x, Vec3c<T> f) {
+  const LevelView<T> L = view<T>(h, l);
+  for (int s = 0; s < sweeps; ++s) {
+    if (o.smoother == CMG_SMOOTH_RBGS) {
+      for (int colour = 0; colour < 2; ++colour) {
+        ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+        const cudaError_t e = launch_rbgs_half<T>(L, x, f, colour, h->stream);
+        if (e != cudaSuccess) return e;
+      }
+    } else {
+      Vec3<T> r = Work<T>::r(h->lv[l]);
+      cudaError_t e;
+      {
+        ProfScope ps(h, CMG_KERNEL_RESIDUAL, l);
+        e = launch_residual<T>(L, cview(x), f, r, h->stream);
+      }
+      if (e != cudaSuccess) return e;
+      ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+      e = launch_jacobi_update<T>(L, x, cview(r), o.theta, h->stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t zero_vec(cmg_handle* h, int l, Vec3<T> x) {
+  const size_t nodes = h->lv[l].nodes, N = (size_t)h->prob.N;
+  cudaError_t e = cudaMemsetAsync(x.y, 0, nodes * N * sizeof(T), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x.u, 0, nodes * sizeof(T), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x.p, 0, nodes * N * sizeof(T), h->stream);
+  return e;
+}
+
+// Algorithm 1 on grid l: smoothing, residual, restriction, gamma recursive
+// calls from a zero guess, prolongation, smoothing; direct solve on the
+// coarsest grid.
+template <typename T>
+cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> f) {
+  Lev& v = h->lv[l];
+  const int N = h->prob.N;
+  if (l == h->L - 1) {
+    ProfScope ps(h, CMG_KERNEL_COARSE, l);
+    return launch_coarse_solve<T>(h->coarse, v.c, v.d, v.e, f, x, h->stream);
+  }
+  cudaError_t e = smooth<T>(h, o, l, o.n1, x, f);
+  if (e != cudaSuccess) return e;
+  Vec3<T> r = Work<T>::r(v);
+  {
+    ProfScope ps(h, CMG_KERNEL_RESIDUAL, l);
+    e = launch_residual<T>(view<T>(h, l), cview(x), f, r, h->stream);
+  }
+  if (e != cudaSuccess) return e;
+  Lev& cl = h->lv[l + 1];
+  Vec3<T> fc = Work<T>::f(cl), xc = Work<T>::x(cl);
+  {
+    ProfScope ps(h, CMG_KERNEL_RESTRICT, l);
+    e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream);
+  }
+  if (e == cudaSuccess) e = zero_vec<T>(h, l + 1, xc);
+  for (int g = 0; g < o.gamma && e == cudaSuccess; ++g) e = cycle<T>(h, o, l + 1, xc, cview(fc));
+  if (e == cudaSuccess) {
+    ProfScope ps(h, CMG_KERNEL_PROLONG, l);
+    e = launch_prolong_add<T>(v.n, N, cview(xc), x, h->stream);
+  }
+  if (e == cudaSuccess) e = smooth<T>(h, o, l, o.n2, x, f);
+  return e;
+}
+
+cmg_status check_cycle(cmg_handle* h, const cmg_cycle* o) {
+  if (!o) return fail(h, CMG_ERR_INVALID_ARG, "null cycle options");
+  if (o->smoother != CMG_SMOOTH_RBGS && o->smoother != CMG_SMOOTH_JACOBI)
+    return fail(h, CMG_ERR_INVALID_ARG, "unknown smoother");
+  if (o->n1 < 0 || o->n2 < 0 || o->n1 > 64 || o->n2 > 64) return fail(h, CMG_ERR_INVALID_ARG, "n1/n2 out of range");
+  if (o->gamma < 1 || o->gamma > 2) return fail(h, CMG_ERR_INVALID_ARG, "gamma must be 1 or 2");
+  if (o->precision != CMG_FP64 && o->precision != CMG_FP32) return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");
+  if (o->smoother == CMG_SMOOTH_JACOBI && !(o->theta > 0.0 && o->theta <= 1.0))
+    return fail(h, CMG_ERR_INVALID_ARG, "theta must be in (0, 1]");
+  return CMG_OK;
+}
+
+// ---- norms -------------------------------------------------------------------
+
+// wy2 * ||y||^2 + ||u||^2 + ||p||^2 of a level vector into *out (device), not
+// synchronised.  wy2 = N^2 gives the norm in the paper's row scaling.
+cudaError_t sumsq3(cmg_handle* h, int l, const double* y, const double* u, const double* p, double* out,
+                   double wy2 = 1.0) {
+  const size_t nodes = h->lv[l].nodes, N = (size_t)h->prob.N;
+  cudaError_t e = launch_sumsq(y, nodes * N, h->red, 0, wy2, h->stream);
+  if (e == cudaSuccess) e = launch_sumsq(u, nodes, h->red, 1, 1.0, h->stream);
+  if (e == cudaSuccess) e = launch_sumsq(p, nodes * N, h->red, 1, 1.0, h->stream);
+  if (e == cudaSuccess) e = launch_finish_sum(h->red, kRedBlocks, out, h->stream);
+  return e;
+}
+
+cudaError_t fetch(cmg_handle* h, const double* dev, int count) {
+  cudaError_t e = cudaMemcpyAsync(h->hsc, dev, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stream, cmg_handle** out) {
+  if (!out) return CMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!prob) return CMG_ERR_INVALID_ARG;
+  const cmg_problem P = *prob;
+  const auto pow2m1 = [](int v) { return v >= 1 && ((v + 1) & v) == 0; };
+  if (!pow2m1(P.n) || P.n < 3 || P.n > 4095) return CMG_ERR_INVALID_ARG;
+  if (!(P.coarsest_n == 1 || P.coarsest_n == 3 || P.coarsest_n == 7) || P.coarsest_n > P.n) return CMG_ERR_INVALID_ARG;
+  if (P.N < 1 || P.K < 0 || P.K > 64 || !(P.nu > 0.0) || !std::isfinite(P.amp)) return CMG_ERR_INVALID_ARG;
+  if (P.K > 0 && !xi_host) return CMG_ERR_INVALID_ARG;
+  const SampleMap m64 = choose_map(P.N, 8), m32 = choose_map(P.N, 4);
+  if (m64.spl > kMaxSPL || m32.spl > kMaxSPL) return CMG_ERR_UNSUPPORTED;
+
+  cmg_handle* h = new (std::nothrow) cmg_handle();
+  if (!h) return CMG_ERR_OOM;
+  h->prob = P;
+  h->stream = static_cast<cudaStream_t>(stream);
+  int n = P.n, L = 0;
+  while (true) {
+    Lev& v = h->lv[L];
+    v.n = n;
+    v.h = 1.0 / (n + 1);
+    v.nodes = (size_t)n * n;
+    v.c = v.h * v.h / P.N;
+    v.G = P.nu * v.h * v.h;
+    v.d = -v.h * v.h;
+    v.e = -v.h * v.h;
+    ++L;
+    if (n == P.coarsest_n) break;
+    n = (n - 1) / 2;
+  }
+  h->L = L;
+  const size_t N = (size_t)P.N;
+  cudaError_t e = cudaSuccess;
+#define AL(ptr, cnt)                        \
+  do {                                      \
+    if (e == cudaSuccess) e = dalloc(h, &(ptr), (cnt)); \
+  } while (0)
+  for (int l = 0; l < L; ++l) {
+    Lev& v = h->lv[l];
+    const size_t faces = (size_t)v.n * (v.n + 1) * N;
+    AL(v.kx64, faces); AL(v.ky64, faces); AL(v.kx32, faces); AL(v.ky32, faces);
+    AL(v.inva, v.nodes * N); AL(v.sigma, v.nodes);
+    for (int b = 0; b < 3; ++b) {
+      const size_t cnt = (b == 1) ? v.nodes : v.nodes * N;
+      AL(v.r64[b], cnt); AL(v.x32[b], cnt); AL(v.f32[b], cnt); AL(v.r32[b], cnt); AL(v.f64[b], cnt);
+      if (l > 0) AL(v.x64[b], cnt);
+    }
+  }
+  const size_t g = (size_t)P.n + 2;
+  AL(h->kap, g * g * N + g * N);
+  AL(h->xi, (size_t)N * (P.K > 0 ? P.K : 1));
+  AL(h->red, (size_t)kRedBlocks * 8 * 16);
+  AL(h->dsc, 1024);
+  const int cn = h->lv[L - 1].n;
+  h->coarse.n = cn;
+  h->coarse.m = cn * cn;
+  h->coarse.N = P.N;
+  h->coarse.blocks = (P.N + 31) / 32;
+  AL(h->coarse.Ainv, N * h->coarse.m * h->coarse.m);
+  AL(h->coarse.Minv, (size_t)h->coarse.m * h->coarse.m);
+  AL(h->coarse.wz, std::max(2 * N * h->coarse.m, (size_t)h->coarse.m * h->coarse.m));
+  AL(h->coarse.partial, (size_t)h->coarse.blocks * h->coarse.m);
+#undef AL
+  if (e == cudaSuccess) {
+    void* hp = nullptr;
+    e = cudaMallocHost(&hp, 1024 * sizeof(double));
+    h->hsc = static_cast<double*>(hp);
+  }
+  if (e == cudaSuccess && P.K > 0)
+    e = cudaMemcpyAsync(h->xi, xi_host, N * P.K * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = setup_coefficients(h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    const cmg_status st = (e == cudaErrorMemoryAllocation) ? CMG_ERR_OOM : CMG_ERR_CUDA;
+    (void)cudaGetLastError();
+    cmg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return CMG_OK;
+}
+
+cmg_status cmg_set_samples(cmg_handle* h, const double* xi_dev) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  if (h->prob.K > 0) {
+    if (!xi_dev) return fail(h, CMG_ERR_INVALID_ARG, "null xi");
+    CK(cudaMemcpyAsync(h->xi, xi_dev, (size_t)h->prob.N * h->prob.K * sizeof(double), cudaMemcpyDeviceToDevice,
+                       h->stream));
+  }
+  CK(setup_coefficients(h));
+  return CMG_OK;
+}
+
+void cmg_destroy(cmg_handle* h) {
+  if (!h) return;
+  if (h->stream) (void)cudaStreamSynchronize(h->stream);
+  else (void)cudaDeviceSynchronize();
+  for (void* p : h->allocs) (void)cudaFree(p);
+  for (auto& ev : h->prof_ev) (void)cudaEventDestroy(ev);
+  if (h->gm) (void)cudaFree(h->gm);
+  if (h->hsc) (void)cudaFreeHost(h->hsc);
+  delete h;
+}
+
+const char* cmg_last_error(const cmg_handle* h) { return h ? h->err.c_str() : "null handle"; }
+int cmg_num_levels(const cmg_handle* h) { return h ? h->L : 0; }
+int cmg_level_n(const cmg_handle* h, int level) { return level_ok(h, level) ? h->lv[level].n : -1; }
+
+cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* fy, double* fu, double* fp) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  if (!yd || !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");
+  CK(launch_rhs(h->prob.n, h->prob.N, h->lv[0].h, yd, fsrc, fy, fu, fp, h->stream));
+  return CMG_OK;
+}
+
+#define CMG_LEVEL_OPS(SUF, T)                                                                                  \
+  cmg_status cmg_residual##SUF(cmg_handle* h, int level, const T* y, const T* u, const T* p, const T* fy,       \
+                               const T* fu, const T* fp, T* ry, T* ru, T* rp) {                                 \
+    if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
+    if (!level_ok(h, level)) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");                        \
+    if (!vec_ok(y, u, p) || !vec_ok(ry, ru, rp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
+    if ((fy || fu || fp) && !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "partial rhs");           \
+    CK(launch_residual<T>(view<T>(h, level), Vec3c<T>{y, u, p}, Vec3c<T>{fy, fu, fp}, Vec3<T>{ry, ru, rp},     \
+                          h->stream));                                                                          \
+    return CMG_OK;                                                                                              \
+  }                                                                                                             \
+  cmg_status cmg_smooth##SUF(cmg_handle* h, int level, const cmg_cycle* opts, int sweeps, T* y, T* u, T* p,     \
+                             const T* fy, const T* fu, const T* fp) {                                           \
+    if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
+    if (!level_ok(h, level)) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");                        \
+    if (!vec_ok(y, u, p) || !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
+    if (sweeps < 0) return fail(h, CMG_ERR_INVALID_ARG, "negative sweeps");                                    \
+    cmg_cycle o = *opts;                                                                                        \
+    o.n1 = o.n2 = 0; o.gamma = 1; o.precision = sizeof(T) == 8 ? CMG_FP64 : CMG_FP32;                           \
+    const cmg_status st = check_cycle(h, &o);                                                                   \
+    if (st != CMG_OK) return st;                                                                                \
+    CK(smooth<T>(h, o, level, sweeps, Vec3<T>{y, u, p}, Vec3c<T>{fy, fu, fp}));                                \
+    return CMG_OK;                                                                                              \
+  }                                                                                                             \
+  cmg_status cmg_restrict##SUF(cmg_handle* h, int level, const T* ry, const T* ru, const T* rp, T* cy, T* cu,   \
+                               T* cp) {                                                                         \
+    if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
+    if (!level_ok(h, level) || level == h->L - 1) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");   \
+    if (!vec_ok(ry, ru, rp) || !vec_ok(cy, cu, cp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");       \
+    CK(launch_restrict<T>(h->lv[level].n, h->prob.N, Vec3c<T>{ry, ru, rp}, Vec3<T>{cy, cu, cp}, h->stream));   \
+    return CMG_OK;                                                                                              \
+  }                                                                                                             \
+  cmg_status cmg_prolong_add##SUF(cmg_handle* h, int level, const T* ey, const T* eu, const T* ep, T* y, T* u,  \
+                                  T* p) {                                                                       \
+    if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
+    if (!level_ok(h, level) || level == h->L - 1) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");   \
+    if (!vec_ok(ey, eu, ep) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
+    CK(launch_prolong_add<T>(h->lv[level].n, h->prob.N, Vec3c<T>{ey, eu, ep}, Vec3<T>{y, u, p}, h->stream));   \
+    return CMG_OK;                                                                                              \
+  }                                                                                                             \
+  cmg_status cmg_coarse_solve##SUF(cmg_handle* h, const T* fy, const T* fu, const T* fp, T* y, T* u, T* p) {    \
+    if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
+    if (!vec_ok(fy, fu, fp) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
+    const Lev& v = h->lv[h->L - 1];                                                                             \
+    CK(launch_coarse_solve<T>(h->coarse, v.c, v.d, v.e, Vec3c<T>{fy, fu, fp}, Vec3<T>{y, u, p}, h->stream));   \
+    return CMG_OK;                                                                                              \
+  }                                                                                                             \
+  cmg_status cmg_cycle_apply##SUF(cmg_handle* h, const cmg_cycle* opts, T* y, T* u, T* p, const T* fy,          \
+                                  const T* fu, const T* fp) {                                                   \
+    if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
+    const cmg_status st = check_cycle(h, opts);                                                                 \
+    if (st != CMG_OK) return st;                                                                                \
+    if (opts->precision != (sizeof(T) == 8 ? CMG_FP64 : CMG_FP32))                                              \
+      return fail(h, CMG_ERR_INVALID_ARG, "precision does not match the vector type");                         \
+    if (!vec_ok(y, u, p) || !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
+    CK(cycle<T>(h, *opts, 0, Vec3<T>{y, u, p}, Vec3c<T>{fy, fu, fp}));                                          \
+    return CMG_OK;                                                                                              \
+  }
+
+CMG_LEVEL_OPS(, double)
+CMG_LEVEL_OPS(_f32, float)
+
+cmg_status cmg_norm(cmg_handle* h, int level, const double* y, const double* u, const double* p, double* out_host) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  if (!level_ok(h, level)) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");
+  if (!vec_ok(y, u, p) || !out_host) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");
+  CK(sumsq3(h, level, y, u, p, h->dsc));
+  CK(fetch(h, h->dsc, 1));
+  *out_host = std::sqrt(h->hsc[0]);
+  return CMG_OK;
+}
+
+cmg_status cmg_sync(cmg_handle* h) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  return CMG_OK;
+}
+
+cmg_status cmg_profile_begin(cmg_handle* h, int kinds, int level) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  if (!level_ok(h, level)) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");
+  if (h->prof_ev.empty()) {
+    h->prof_ev.resize(2 * kMaxProf);
+    for (auto& ev : h->prof_ev) CK(cudaEventCreate(&ev));
+  }
+  h->prof_kinds = kinds;
+  h->prof_level = level;
+  h->prof_n = 0;
+  return CMG_OK;
+}
+
+cmg_status cmg_profile_end(cmg_handle* h, double* total_ms, int* launches) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  h->prof_kinds = 0;
+  CK(cudaStreamSynchronize(h->stream));
+  double tot = 0.0;
+  for (int i = 0; i < h->prof_n; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = h->prof_n;
+  h->prof_n = 0;
+  return CMG_OK;
+}
+
+long long cmg_kernel_launches(void) { return cmg::g_launches.load(); }
+
+}  // extern "C"
+
+// ============================================================================
+// Outer solvers
+namespace {
+
+// Row weight of the state block in the paper's scaling of the system (its
+// state rows are N times the symmetric ones used here).
+inline double paper_wy(const cmg_handle* h) { return (double)h->prob.N; }
+
+// ||W (f - S x)||_2 into *rho (host), residual r = f - S x (unweighted) left
+// in level-0 r64.
+cmg_status true_residual(cmg_handle* h, Vec3c<double> f, Vec3c<double> x, double* rho) {
+  Lev& v = h->lv[0];
+  Vec3<double> r = Work<double>::r(v);
+  CK(launch_residual<double>(view<double>(h, 0), x, f, r, h->stream));
+  CK(sumsq3(h, 0, r.y, r.u, r.p, h->dsc, paper_wy(h) * paper_wy(h)));
+  CK(fetch(h, h->dsc, 1));
+  *rho = std::sqrt(h->hsc[0]);
+  return CMG_OK;
+}
+
+// One preconditioner application z = M^{-1} W^{-1} v (zero initial guess),
+// FP64 in/out: one cycle on the right side whose state block is divided
+// by wy (undoing the paper's row scaling of the Krylov vector).
+cmg_status precondition(cmg_handle* h, const cmg_cycle& o, Vec3c<double> v, Vec3<double> z, double wy) {
+  Lev& l0 = h->lv[0];
+  const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes;
+  if (o.precision == CMG_FP64) {
+    double* fy = l0.f64[0];
+    CK((launch_scale_cast<double, double>(1.0 / wy, v.y, fy, ny, h->stream)));
+    CK(zero_vec<double>(h, 0, z));
+    CK(cycle<double>(h, o, 0, z, Vec3c<double>{fy, v.u, v.p}));
+    return CMG_OK;
+  }
+  // FP32 cycle on the right side (Krylov vectors have unit norm, no scaling
+  // is needed for the FP32 range), result converted into FP64.
+  const double vscale = 1.0;
+  Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
+  CK((launch_scale_cast<double, float>(vscale / wy, v.y, f32.y, ny, h->stream)));
+  CK((launch_scale_cast<double, float>(vscale, v.u, f32.u, nu, h->stream)));
+  CK((launch_scale_cast<double, float>(vscale, v.p, f32.p, ny, h->stream)));
+  CK(zero_vec<float>(h, 0, x32));
+  CK(cycle<float>(h, o, 0, x32, cview(f32)));
+  CK((launch_scale_cast<float, double>(1.0 / vscale, x32.y, z.y, ny, h->stream)));
+  CK((launch_scale_cast<float, double>(1.0 / vscale, x32.u, z.u, nu, h->stream)));
+  CK((launch_scale_cast<float, double>(1.0 / vscale, x32.p, z.p, ny, h->stream)));
+  return CMG_OK;
+}
+
+cmg_status solve_cycle(cmg_handle* h, const cmg_cycle& o, double tol, int maxit, Vec3c<double> f, Vec3<double> x,
+                       double fnorm, cmg_stats* st) {
+  Lev& l0 = h->lv[0];
+  const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes;
+  double rho = 0;
+  cmg_status s = true_residual(h, f, cview(x), &rho);
+  if (s != CMG_OK) return s;
+  st->relres0 = rho / fnorm;
+  int it = 0;
+  while (std::isfinite(rho) && rho > tol * fnorm && it < maxit) {
+    if (o.precision == CMG_FP64) {
+      CK(cycle<double>(h, o, 0, x, f));
+    } else {
+      // iterative refinement: e = cycle_FP32(0; r), x += e; r is in level-0 r64
+      Vec3<double> r = Work<double>::r(l0);
+      Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
+      const double sc = 1.0 / rho;
+      CK((launch_scale_cast<double, float>(sc, r.y, f32.y, ny, h->stream)));
+      CK((launch_scale_cast<double, float>(sc, r.u, f32.u, nu, h->stream)));
+      CK((launch_scale_cast<double, float>(sc, r.p, f32.p, ny, h->stream)));
+      CK(zero_vec<float>(h, 0, x32));
+      CK(cycle<float>(h, o, 0, x32, cview(f32)));
+      CK((launch_axpy<float, double>(rho, x32.y, x.y, ny, h->stream)));
+      CK((launch_axpy<float, double>(rho, x32.u, x.u, nu, h->stream)));
+      CK((launch_axpy<float, double>(rho, x32.p, x.p, ny, h->stream)));
+    }
+    ++it;
+    s = true_residual(h, f, cview(x), &rho);
+    if (s != CMG_OK) return s;
+  }
+  st->iters = it;
+  st->cycles = it;
+  st->relres = rho / fnorm;
+  if (!std::isfinite(rho)) return fail(h, CMG_ERR_NONFINITE, "residual norm is not finite");
+  if (rho > tol * fnorm) return fail(h, CMG_ERR_NOT_CONVERGED, "maximum iterations reached");
+  return CMG_OK;
+}
+
+// Flat [y | pad | u | pad | p | pad] Krylov vector: every segment starts on a
+// 256-byte boundary (the node kernels use 16-byte vector loads); the pads
+// are zeroed once at allocation and stay zero under every vector operation.
+inline size_t pad32(size_t v) { return (v + 31) & ~(size_t)31; }
+Vec3<double> flat3(double* base, size_t ny, size_t nu) {
+  return {base, base + pad32(ny), base + pad32(ny) + pad32(nu)};
+}
+
+cmg_status solve_fgmres(cmg_handle* h, const cmg_cycle& o, double tol, int maxit, int restart, Vec3c<double> f,
+                        Vec3<double> x, double fnorm, cmg_stats* st) {
+  Lev& l0 = h->lv[0];
+  const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes, nt = 2 * pad32(ny) + pad32(nu);
+  const size_t pad = nt;
+  if (restart > h->gm_cap || h->nt != nt) {
+    if (h->gm) {
+      CK(cudaStreamSynchronize(h->stream));
+      CK(cudaFree(h->gm));
+      h->gm = nullptr;
+      h->gm_cap = 0;
+    }
+    void* q = nullptr;
+    CK(cudaMalloc(&q, (size_t)(2 * restart + 2) * pad * sizeof(double)));
+    h->gm = static_cast<double*>(q);
+    CK(cudaMemsetAsync(q, 0, (size_t)(2 * restart + 2) * pad * sizeof(double), h->stream));
+    h->gm_cap = restart;
+    h->nt = nt;
+    h->nt_pad = pad;
+  }
+  double* V = h->gm;                                   // restart+1 vectors
+  double* Z = h->gm + (size_t)(restart + 1) * pad;     // restart vectors
+  double* X = h->gm + (size_t)(2 * restart + 1) * pad; // flat iterate
+  const Vec3<double> Xv = flat3(X, ny, nu);
+  CK(cudaMemcpyAsync(Xv.y, x.y, ny * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(Xv.u, x.u, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(Xv.p, x.p, ny * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+
+  double* d_h1 = h->dsc + 64;
+  double* d_h2 = h->dsc + 192;
+  double* d_nrm = h->dsc + 320;
+  double* d_y = h->dsc + 384;
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), yk(restart);
+  auto Hat = [&](int i, int k) -> double& { return H[(size_t)i * restart + k]; };
+
+  auto residual_to_v0 = [&](double* beta) -> cmg_status {
+    Vec3<double> r0 = flat3(V, ny, nu);
+    CK(launch_residual<double>(view<double>(h, 0), cview(Xv), f, r0, h->stream, paper_wy(h)));
+    CK(launch_sumsq(V, nt, h->red, 0, 1.0, h->stream));
+    CK(launch_finish_sum(h->red, kRedBlocks, d_nrm, h->stream));
+    CK(fetch(h, d_nrm, 1));
+    *beta = std::sqrt(h->hsc[0]);
+    return CMG_OK;
+  };
+
+  double beta = 0;
+  cmg_status s = residual_to_v0(&beta);
+  if (s != CMG_OK) return s;
+  st->relres0 = beta / fnorm;
+  double relres = st->relres0;
+  int total = 0;
+  bool breakdown = false;
+  while (std::isfinite(relres) && relres > tol && total < maxit && !breakdown) {
+    CK(launch_scale_by(V, d_nrm, V, nt, h->stream));    // v0 = r0 / ||r0||
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kd = 0;
+    for (int k = 0; k < restart; ++k) {
+      double* vk = V + (size_t)k * pad;
+      double* zk = Z + (size_t)k * pad;
+      double* w = V + (size_t)(k + 1) * pad;
+      s = precondition(h, o, cview(flat3(vk, ny, nu)), flat3(zk, ny, nu), paper_wy(h));
+      if (s != CMG_OK) return s;
+      ++st->cycles;
+      CK(launch_residual<double>(view<double>(h, 0), cview(flat3(zk, ny, nu)), Vec3c<double>{nullptr, nullptr, nullptr},
+                                 flat3(w, ny, nu), h->stream, paper_wy(h)));   // w = W S z_k
+      // classical Gram-Schmidt, twice
+      CK(launch_mdot(V, pad, k + 1, w, nt, h->red, d_h1, h->stream));
+      CK(launch_maxpy(V, pad, k + 1, d_h1, -1.0, w, nt, h->stream));
+      CK(launch_mdot(V, pad, k + 1, w, nt, h->red, d_h2, h->stream));
+      CK(launch_maxpy(V, pad, k + 1, d_h2, -1.0, w, nt, h->stream));
+      CK(launch_sumsq(w, nt, h->red, 0, 1.0, h->stream));
+      CK(launch_finish_sum(h->red, kRedBlocks, d_nrm, h->stream));
+      CK(cudaMemcpyAsync(h->hsc, d_h1, 256 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(h->hsc + 256, d_h2, 256 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(h->hsc + 512, d_nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int i = 0; i <= k; ++i) Hat(i, k) = h->hsc[i] + h->hsc[256 + i];
+      const double hn = std::sqrt(h->hsc[512]);
+      Hat(k + 1, k) = hn;
+      if (!std::isfinite(hn)) return fail(h, CMG_ERR_NONFINITE, "Arnoldi norm is not finite");
+      if (hn > 0) CK(launch_scale_by(w, d_nrm, w, nt, h->stream));
+      else breakdown = true;
+      for (int i = 0; i < k; ++i) {
+        const double t = cs[i] * Hat(i, k) + sn[i] * Hat(i + 1, k);
+        Hat(i + 1, k) = -sn[i] * Hat(i, k) + cs[i] * Hat(i + 1, k);
+        Hat(i, k) = t;
+      }
+      const double rr = std::hypot(Hat(k, k), Hat(k + 1, k));
+      cs[k] = Hat(k, k) / rr;
+      sn[k] = Hat(k + 1, k) / rr;
+      Hat(k, k) = rr;
+      Hat(k + 1, k) = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      ++total;
+      kd = k + 1;
+      relres = std::fabs(g[k + 1]) / fnorm;
+      if (relres <= tol || total >= maxit || breakdown) break;
+    }
+    for (int i = kd - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int j = i + 1; j < kd; ++j) t -= Hat(i, j) * yk[j];
+      yk[i] = t / Hat(i, i);
+    }
+    std::memcpy(h->hsc, yk.data(), kd * sizeof(double));
+    CK(cudaMemcpyAsync(d_y, h->hsc, kd * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(launch_maxpy(Z, pad, kd, d_y, 1.0, X, nt, h->stream));
+    s = residual_to_v0(&beta);
+    if (s != CMG_OK) return s;
+    relres = beta / fnorm;
+  }
+  CK(cudaMemcpyAsync(x.y, Xv.y, ny * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(x.u, Xv.u, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(x.p, Xv.p, ny * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  st->iters = total;
+  st->relres = relres;
+  if (!std::isfinite(relres)) return fail(h, CMG_ERR_NONFINITE, "residual norm is not finite");
+  if (relres > tol) return fail(h, CMG_ERR_NOT_CONVERGED, "maximum iterations reached");
+  return CMG_OK;
+}
+
+}  // namespace
+
+extern "C" cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method, double tol, int maxit, int restart,
+                                const double* fy, const double* fu, const double* fp, double* y, double* u, double* p,
+                                cmg_stats* stats) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  cmg_status s = check_cycle(h, opts);
+  if (s != CMG_OK) return s;
+  if (!vec_ok(fy, fu, fp) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");
+  if (!(tol > 0.0) || maxit < 0) return fail(h, CMG_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 0");
+  if (method != CMG_METHOD_CYCLE && method != CMG_METHOD_FGMRES) return fail(h, CMG_ERR_INVALID_ARG, "unknown method");
+  if (method == CMG_METHOD_FGMRES && (restart < 1 || restart > kMaxRestart))
+    return fail(h, CMG_ERR_INVALID_ARG, "restart must be in [1, 60]");
+  cmg_stats local{};
+  cmg_stats* st = stats ? stats : &local;
+  *st = cmg_stats{};
+  CK(sumsq3(h, 0, fy, fu, fp, h->dsc, paper_wy(h) * paper_wy(h)));
+  CK(fetch(h, h->dsc, 1));
+  const double fnorm = std::sqrt(h->hsc[0]);   // ||W f||
+  if (!std::isfinite(fnorm)) return fail(h, CMG_ERR_NONFINITE, "right-hand side is not finite");
+  const Vec3c<double> f{fy, fu, fp};
+  const Vec3<double> x{y, u, p};
+  if (fnorm == 0.0) {
+    CK(zero_vec<double>(h, 0, x));
+    CK(cudaStreamSynchronize(h->stream));
+    return CMG_OK;
+  }
+  if (method == CMG_METHOD_CYCLE) return solve_cycle(h, *opts, tol, maxit, f, x, fnorm, st);
+  return solve_fgmres(h, *opts, tol, maxit, restart, f, x, fnorm, st);
+}

@@ -1,0 +1,254 @@
+// Coarsest-grid direct solve (Algorithm 1, "direct solver"), FP64.
+//
+// Block elimination of the saddle system on the coarsest grid (m = n_c^2
+// nodes): with the per-sample stiffness inverses A_j^{-1}
+//     y_j = A_j^{-1} (f_p,j - e u),   p_j = A_j^{-1} (f_y,j - c y_j),
+// and the control row becomes the m x m system
+//     (G I + d c e sum_j A_j^{-2}) u = f_u - d sum_j (A_j^{-1} f_y,j - c A_j^{-2} f_p,j).
+// Setup inverts every A_j (Gauss-Jordan, SPD so no pivoting) and the control
+// Schur matrix once per hierarchy; each solve is two launches: per-sample
+// products with a fixed-order reduction of the control right side, then the
+// control solve and per-sample back substitution.
+#include "cmg_common.cuh"
+
+namespace cmg {
+
+namespace {
+
+// Gauss-Jordan inverse of the m x m matrix in aug[:, 0:m] into aug[:, m:2m].
+__device__ void gauss_jordan(double* aug, double* fac, int m) {
+  const int w = 2 * m;
+  for (int col = 0; col < m; ++col) {
+    __syncthreads();
+    const double piv = aug[col * w + col];
+    __syncthreads();
+    for (int c = threadIdx.x; c < w; c += blockDim.x) aug[col * w + c] /= piv;
+    __syncthreads();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) fac[r] = aug[r * w + col];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * w; idx += blockDim.x) {
+      const int r = idx / w, c = idx - r * w;
+      if (r != col) aug[idx] -= fac[r] * aug[col * w + c];
+    }
+  }
+  __syncthreads();
+}
+
+// One CTA per sample: assemble A_j from the face coefficients and invert it.
+__global__ void coarse_inv_kernel(int n, int N, const double* __restrict__ kx, const double* __restrict__ ky,
+                                  double* __restrict__ Ainv) {
+  __shared__ double aug[kMaxCoarseM * 2 * kMaxCoarseM];
+  __shared__ double fac[kMaxCoarseM];
+  const int j = blockIdx.x;
+  const int m = n * n, w = 2 * m;
+  for (int idx = threadIdx.x; idx < m * w; idx += blockDim.x) {
+    const int r = idx / w, c = idx - r * w;
+    double v = 0.0;
+    if (c >= m) {
+      v = (c - m == r) ? 1.0 : 0.0;
+    } else {
+      const int iy = r / n, ix = r - iy * n;
+      const double kW = kx[((size_t)iy * (n + 1) + ix) * N + j];
+      const double kE = kx[((size_t)iy * (n + 1) + ix + 1) * N + j];
+      const double kS = ky[((size_t)iy * n + ix) * N + j];
+      const double kN = ky[((size_t)(iy + 1) * n + ix) * N + j];
+      if (c == r) v = (kW + kE) + (kS + kN);
+      else if (ix > 0 && c == r - 1) v = -kW;
+      else if (ix < n - 1 && c == r + 1) v = -kE;
+      else if (iy > 0 && c == r - n) v = -kS;
+      else if (iy < n - 1 && c == r + n) v = -kN;
+    }
+    aug[idx] = v;
+  }
+  gauss_jordan(aug, fac, m);
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx / m, c = idx - r * m;
+    Ainv[(size_t)j * m * m + idx] = aug[r * w + m + c];
+  }
+}
+
+// One CTA per entry (r, c) of the control Schur matrix:
+// M[r][c] = G delta_rc + d c e sum_j (A_j^{-1} A_j^{-1})[r][c], fixed-order reduction.
+__global__ void coarse_schur_kernel(int m, int N, const double* __restrict__ Ainv, double G, double dce,
+                                    double* __restrict__ M) {
+  __shared__ double red[128];
+  const int r = blockIdx.x / m, c = blockIdx.x - (blockIdx.x / m) * m;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double* A = Ainv + (size_t)j * m * m;
+    double t = 0.0;
+    for (int k = 0; k < m; ++k) t += A[r * m + k] * A[k * m + c];
+    s += t;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) M[blockIdx.x] = (r == c ? G : 0.0) + dce * red[0];
+}
+
+__global__ void invert_kernel(int m, const double* __restrict__ M, double* __restrict__ Minv) {
+  __shared__ double aug[kMaxCoarseM * 2 * kMaxCoarseM];
+  __shared__ double fac[kMaxCoarseM];
+  const int w = 2 * m;
+  for (int idx = threadIdx.x; idx < m * w; idx += blockDim.x) {
+    const int r = idx / w, c = idx - r * w;
+    aug[idx] = c < m ? M[r * m + c] : (c - m == r ? 1.0 : 0.0);
+  }
+  gauss_jordan(aug, fac, m);
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx / m, c = idx - r * m;
+    Minv[idx] = aug[r * w + m + c];
+  }
+}
+
+constexpr int kCoarseThreads = 32;   // one warp per CTA: samples spread over SMs
+
+// Per sample j: w = A_j^{-1} f_y,j, z = A_j^{-1} f_p,j, v = A_j^{-1} z;
+// per-warp partial sums of q = w - c v for the control right side.
+template <typename T, int MM>
+__global__ void __launch_bounds__(kCoarseThreads) coarse_solve_a(int m, int N, const double* __restrict__ Ainv,
+                                                                double c, const T* __restrict__ fy,
+                                                                const T* __restrict__ fp, double* __restrict__ wz,
+                                                                double* __restrict__ partial) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = j < N;
+  double q[MM];
+#pragma unroll
+  for (int r = 0; r < MM; ++r) q[r] = 0.0;
+  if (valid) {
+    const double* A = Ainv + (size_t)j * m * m;
+    double by[MM], bp[MM], z[MM];
+#pragma unroll
+    for (int r = 0; r < MM; ++r) {
+      by[r] = r < m ? (double)fy[(size_t)r * N + j] : 0.0;
+      bp[r] = r < m ? (double)fp[(size_t)r * N + j] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < MM; ++r) {
+      double sw = 0.0, sz = 0.0;
+      if (r < m) {
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+          if (k < m) {
+            sw += A[r * m + k] * by[k];
+            sz += A[r * m + k] * bp[k];
+          }
+        wz[(size_t)j * m + r] = sw;
+        wz[(size_t)N * m + (size_t)j * m + r] = sz;
+      }
+      q[r] = sw;
+      z[r] = sz;
+    }
+#pragma unroll
+    for (int r = 0; r < MM; ++r) {
+      if (r < m) {
+        double sv = 0.0;
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+          if (k < m) sv += A[r * m + k] * z[k];
+        q[r] -= c * sv;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < MM; ++r) {
+    double v = q[r];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0 && r < m) partial[(size_t)blockIdx.x * m + r] = v;
+  }
+}
+
+// Control solve (every CTA redundantly, fixed order) and back substitution.
+template <typename T, int MM>
+__global__ void __launch_bounds__(kCoarseThreads) coarse_solve_b(int m, int N, int nblk,
+                                                                const double* __restrict__ Ainv,
+                                                                const double* __restrict__ Minv, double c, double d,
+                                                                double e, const T* __restrict__ fu,
+                                                                const double* __restrict__ wz,
+                                                                const double* __restrict__ partial, T* __restrict__ y,
+                                                                T* __restrict__ u, T* __restrict__ p) {
+  __shared__ double rhs[MM], us[MM];
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * m + r];
+    rhs[r] = (double)fu[r] - d * s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += Minv[r * m + k] * rhs[k];
+    us[r] = s;
+    if (blockIdx.x == 0) u[r] = (T)s;
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const double* A = Ainv + (size_t)j * m * m;
+  double yv[MM];
+#pragma unroll
+  for (int r = 0; r < MM; ++r) {
+    if (r < m) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < MM; ++k)
+        if (k < m) t += A[r * m + k] * us[k];
+      yv[r] = wz[(size_t)N * m + (size_t)j * m + r] - e * t;
+      y[(size_t)r * N + j] = (T)yv[r];
+    } else {
+      yv[r] = 0.0;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < MM; ++r) {
+    if (r < m) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < MM; ++k)
+        if (k < m) t += A[r * m + k] * yv[k];
+      p[(size_t)r * N + j] = (T)(wz[(size_t)j * m + r] - c * t);
+    }
+  }
+}
+
+template <typename T, int MM>
+cudaError_t coarse_solve_mm(const CoarseData& C, double c, double d, double e, Vec3c<T> f, Vec3<T> x,
+                            cudaStream_t s) {
+  const int nblk = (C.N + kCoarseThreads - 1) / kCoarseThreads;
+  coarse_solve_a<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, C.Ainv, c, f.y, f.p, C.wz, C.partial);
+  coarse_solve_b<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, nblk, C.Ainv, C.Minv, c, d, e, f.u, C.wz,
+                                                         C.partial, x.y, x.u, x.p);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_coarse_solve(const CoarseData& C, double c, double d, double e, Vec3c<T> f, Vec3<T> x,
+                                cudaStream_t s) {
+  if (C.m == 1) return coarse_solve_mm<T, 1>(C, c, d, e, f, x, s);
+  if (C.m == 9) return coarse_solve_mm<T, 9>(C, c, d, e, f, x, s);
+  if (C.m == 49) return coarse_solve_mm<T, 49>(C, c, d, e, f, x, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const double* ky, double c, double G,
+                                double d, double e, cudaStream_t s) {
+  coarse_inv_kernel<<<C.N, 64, 0, s>>>(C.n, C.N, kx, ky, C.Ainv);
+  // M is staged in the wz scratch (2 N m >= m^2 is not guaranteed, so use partial-free space):
+  double* M = C.wz;   // wz holds at least max(2 N m, m m) doubles (allocated so)
+  coarse_schur_kernel<<<C.m * C.m, 128, 0, s>>>(C.m, C.N, C.Ainv, G, d * c * e, M);
+  invert_kernel<<<1, 256, 0, s>>>(C.m, M, C.Minv);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_coarse_solve<double>(const CoarseData&, double, double, double, Vec3c<double>,
+                                                 Vec3<double>, cudaStream_t);
+template cudaError_t launch_coarse_solve<float>(const CoarseData&, double, double, double, Vec3c<float>,
+                                                Vec3<float>, cudaStream_t);
+
+}  // namespace cmg

@@ -1,0 +1,66 @@
+// Device helpers shared by the node-sample kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "cmg_internal.h"
+
+namespace cmg {
+
+// V contiguous elements moved with one vector load/store (16 bytes for
+// double2 / float4).
+template <typename T, int V>
+struct alignas(sizeof(T) * V) vec {
+  T v[V];
+};
+
+template <typename T, int V>
+__device__ __forceinline__ vec<T, V> ldv(const T* p) {
+  return *reinterpret_cast<const vec<T, V>*>(p);
+}
+template <typename T, int V>
+__device__ __forceinline__ void stv(T* p, const vec<T, V>& x) {
+  *reinterpret_cast<vec<T, V>*>(p) = x;
+}
+template <typename T, int V>
+__device__ __forceinline__ vec<T, V> vzero() {
+  vec<T, V> r;
+#pragma unroll
+  for (int k = 0; k < V; ++k) r.v[k] = T(0);
+  return r;
+}
+template <typename T, int V>
+__device__ __forceinline__ vec<T, V> ldv_if(bool ok, const T* p) {
+  return ok ? ldv<T, V>(p) : vzero<T, V>();
+}
+
+// Sum over the lpn lanes that share a node (aligned groups inside a warp).
+// Every lane of the warp must call this.
+__device__ __forceinline__ double group_sum(double v, int lpn) {
+  for (int o = lpn >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Red-black ordering: map the g-th node of colour `colour` (red = (ix+iy)
+// even = 0) to (iy, ix).  Rows are paired: row 2P holds the first count0
+// nodes of pair P, row 2P+1 the remaining n - count0.
+__device__ __forceinline__ void colour_node(long g, int n, int colour, int& iy, int& ix) {
+  const long P = g / n;
+  const int q = (int)(g - P * n);
+  const int s0 = colour & 1;
+  const int count0 = (n - s0 + 1) >> 1;
+  if (q < count0) {
+    iy = (int)(2 * P);
+    ix = s0 + 2 * q;
+  } else {
+    iy = (int)(2 * P + 1);
+    ix = (1 - s0) + 2 * (q - count0);
+  }
+}
+
+__host__ __device__ inline long colour_count(int n, int colour) {
+  const long nn = (long)n * n;
+  return colour == 0 ? (nn + 1) / 2 : nn / 2;
+}
+
+}  // namespace cmg

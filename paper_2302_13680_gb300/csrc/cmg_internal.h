@@ -1,0 +1,123 @@
+// Internal declarations shared by the CUDA translation units of libcmg.
+// Nothing here is part of the C ABI (include/cmg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/cmg.h"
+
+namespace cmg {
+
+// Process-wide count of kernels launched by this library.
+void count_launches(int k);
+
+constexpr int kBlock = 256;        // threads per CTA of the node-sample kernels
+constexpr int kMaxLevels = 16;
+constexpr int kMaxSPL = 8;         // chunks of V samples per lane
+constexpr int kMaxCoarseM = 49;    // nodes of the coarsest grid (7 x 7)
+
+template <typename T>
+struct Vec3 {
+  T* y;
+  T* u;
+  T* p;
+};
+template <typename T>
+struct Vec3c {
+  const T* y;
+  const T* u;
+  const T* p;
+};
+template <typename T>
+inline Vec3c<T> cview(const Vec3<T>& v) { return {v.y, v.u, v.p}; }
+
+// Read-only view of one grid's operator for the kernels.  Face arrays:
+// kx[iy][f][j], f = 0..n (face f separates columns f-1 and f; f = 0 and n
+// touch the boundary); ky[f][ix][j], f = 0..n likewise for rows.
+template <typename T>
+struct LevelView {
+  int n;            // nodes per side
+  int N;            // samples
+  int ld;           // sample stride of node arrays (elements)
+  const T* kx;
+  const T* ky;
+  const double* inva;   // 1/diag(A_j) per node-sample (FP64 path only)
+  const double* sigma;  // Schur denominator of Eq. (13) per node
+  double c, G, d, e;    // scalar blocks of Eq. (12): C_j = c I, G, D_j = d I, E_j = e I
+};
+
+// Sample mapping of a node's N samples: lanes-per-node (power of two <= 32),
+// vector width V (elements per 16-byte or narrower load), chunks per lane.
+struct SampleMap {
+  int lpn;
+  int V;
+  int spl;
+};
+SampleMap choose_map(int N, int elem_bytes);
+
+// Coarsest-grid factors (FP64).
+struct CoarseData {
+  int n, m, N;
+  double* Ainv;      // [N][m][m]
+  double* Minv;      // [m][m]   inverse of the control Schur system
+  double* wz;        // scratch [2][N][m] (A_j^{-1} f_y,j and A_j^{-1} f_p,j)
+  double* partial;   // scratch [blocks][m]
+  int blocks;
+};
+
+// ---- stencil kernels (cmg_stencil.cu) ----
+// r = f - S x (or r = S x when f.y == nullptr); the y block of r is then
+// multiplied by wy (wy = N gives the paper's row scaling).
+template <typename T>
+cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r, cudaStream_t s,
+                            double wy = 1.0);
+template <typename T>
+cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t s);
+template <typename T>
+cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, double theta, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t s);
+
+// ---- coarsest grid (cmg_coarse.cu) ----
+template <typename T>
+cudaError_t launch_coarse_solve(const CoarseData& C, double c, double d, double e,
+                                Vec3c<T> f, Vec3<T> x, cudaStream_t s);
+cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const double* ky,
+                                double c, double G, double d, double e, cudaStream_t s);
+
+// ---- coefficients (cmg_setup.cu) ----
+// Nodal field on the (n+2)^2 grid including boundary points, then faces,
+// 1/diag and Schur denominators.  kap: scratch [(n+2)^2][N] doubles.
+cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi, double* kap,
+                               double* kx64, double* ky64, float* kx32, float* ky32,
+                               double* inva, double* sigma, double c, double G, double d,
+                               double e, cudaStream_t s);
+
+// ---- vector kernels (cmg_blas.cu) ----
+constexpr int kRedBlocks = 304;    // fixed partial count: deterministic reductions
+// partial[0..kRedBlocks) (+)= w2 * per-block sums of squares; call finish to combine.
+cudaError_t launch_sumsq(const double* a, size_t n, double* partial, int accumulate, double w2, cudaStream_t s);
+cudaError_t launch_finish_sum(const double* partial, int count, double* out, cudaStream_t s);
+// out[i] = sum_k V_i[k] w[k], i < nv; V_i = V + i*stride.  partial: [nv][kRedBlocks]
+cudaError_t launch_mdot(const double* V, size_t stride, int nv, const double* w, size_t n,
+                        double* partial, double* out, cudaStream_t s);
+// w += sign * sum_i coef[i] V_i  (coef on device)
+cudaError_t launch_maxpy(const double* V, size_t stride, int nv, const double* coef, double sign,
+                         double* w, size_t n, cudaStream_t s);
+// y = alpha * x (alpha read from device scalar: y = x / *den if inv)
+cudaError_t launch_scale_by(const double* x, const double* den, double* y, size_t n, cudaStream_t s);
+// y += a * x (host scalar)
+template <typename Tx, typename Ty>
+cudaError_t launch_axpy(double a, const Tx* x, Ty* y, size_t n, cudaStream_t s);
+// y = (Ty)(a * x)
+template <typename Tx, typename Ty>
+cudaError_t launch_scale_cast(double a, const Tx* x, Ty* y, size_t n, cudaStream_t s);
+// y = (h^2/N) yd broadcast over samples, u = 0, p = h^2 f broadcast
+cudaError_t launch_rhs(int n, int N, double h, const double* yd, const double* fsrc, double* fy,
+                       double* fu, double* fp, cudaStream_t s);
+
+}  // namespace cmg

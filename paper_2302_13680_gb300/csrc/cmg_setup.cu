@@ -1,0 +1,102 @@
+// Coefficient setup on one grid (FP64 arithmetic):
+//   nodal field kappa_j at the (n+2)^2 grid points including the boundary
+//   (the sine-mode log-Gaussian stand-in for Eq. (15): kappa = exp(amp *
+//   sin(pi y) * sum_k xi_jk sin(k pi x) / k), which is separable in x and y),
+//   harmonic-mean face coefficients, 1/diag(A_j) and the Schur denominators
+//   sigma_i = G + sum_j d c e / a_ij^2 of Eq. (13).
+#include "cmg_common.cuh"
+
+namespace cmg {
+
+namespace {
+
+// gx[ix][j] = sum_k xi[j][k] sin(k pi x_ix) / k, x_ix = ix h, ix = 0..n+1.
+__global__ void field_x_kernel(int n, int N, int K, const double* __restrict__ xi, double* __restrict__ gx) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)(n + 2) * N) return;
+  const int ix = (int)(t / N), j = (int)(t - (long)ix * N);
+  const double x = (double)ix / (double)(n + 1);
+  double g = 0.0;
+  for (int k = 1; k <= K; ++k) g += xi[(size_t)j * K + (k - 1)] * sinpi((double)k * x) / (double)k;
+  gx[t] = g;
+}
+
+// kap[iy][ix][j] = exp(amp * sin(pi y_iy) * gx[ix][j]) on the (n+2)^2 grid.
+__global__ void field_kernel(int n, int N, double amp, const double* __restrict__ gx, double* __restrict__ kap) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)(n + 2) * (n + 2) * N;
+  if (t >= total) return;
+  const long node = t / N;
+  const int j = (int)(t - node * N);
+  const int iy = (int)(node / (n + 2)), ix = (int)(node - (long)iy * (n + 2));
+  const double sy = sinpi((double)iy / (double)(n + 1));
+  kap[t] = exp(amp * sy * gx[(size_t)ix * N + j]);
+}
+
+__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+// kx[iy][f][j] between grid columns f and f+1 of interior row iy (grid row iy+1);
+// ky[f][ix][j] between grid rows f and f+1 of interior column ix.
+__global__ void faces_kernel(int n, int N, const double* __restrict__ kap, double* __restrict__ kx64,
+                             double* __restrict__ ky64, float* __restrict__ kx32, float* __restrict__ ky32) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per = (long)n * (n + 1) * N;
+  if (t >= 2 * per) return;
+  const size_t g = (size_t)(n + 2);
+  if (t < per) {
+    const long face = t / N;
+    const int j = (int)(t - face * N);
+    const int iy = (int)(face / (n + 1)), f = (int)(face - (long)iy * (n + 1));
+    const double v = harmonic(kap[((iy + 1) * g + f) * N + j], kap[((iy + 1) * g + f + 1) * N + j]);
+    kx64[t] = v;
+    kx32[t] = (float)v;
+  } else {
+    const long tt = t - per;
+    const long face = tt / N;
+    const int j = (int)(tt - face * N);
+    const int f = (int)(face / n), ix = (int)(face - (long)f * n);
+    const double v = harmonic(kap[((size_t)f * g + ix + 1) * N + j], kap[((size_t)(f + 1) * g + ix + 1) * N + j]);
+    ky64[tt] = v;
+    ky32[tt] = (float)v;
+  }
+}
+
+// inva[node][j] = 1 / (sum of the node's four faces); sigma[node] reduced
+// over samples by one warp per node in a fixed order.
+__global__ void diag_kernel(int n, int N, const double* __restrict__ kx, const double* __restrict__ ky,
+                            double* __restrict__ inva, double* __restrict__ sigma, double dce, double G) {
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (long)n * n) return;
+  const int iy = (int)(warp / n), ix = (int)(warp - (long)iy * n);
+  const double* kW = kx + ((size_t)iy * (n + 1) + ix) * N;
+  const double* kS = ky + ((size_t)iy * n + ix) * N;
+  double s = 0.0;
+  for (int j = lane; j < N; j += 32) {
+    const double a = (kW[j] + kW[N + j]) + (kS[j] + kS[(size_t)n * N + j]);
+    const double ia = 1.0 / a;
+    inva[(size_t)warp * N + j] = ia;
+    s += ia * ia;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) sigma[warp] = G + dce * s;
+}
+
+inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi, double* kap, double* kx64,
+                               double* ky64, float* kx32, float* ky32, double* inva, double* sigma, double c,
+                               double G, double d, double e, cudaStream_t s) {
+  // gx lives in the tail of kap's scratch: (n+2)*N doubles after the field.
+  double* gx = kap + (size_t)(n + 2) * (n + 2) * N;
+  field_x_kernel<<<blocks_for((long)(n + 2) * N, 256), 256, 0, s>>>(n, N, K, xi, gx);
+  field_kernel<<<blocks_for((long)(n + 2) * (n + 2) * N, 256), 256, 0, s>>>(n, N, amp, gx, kap);
+  faces_kernel<<<blocks_for(2L * n * (n + 1) * N, 256), 256, 0, s>>>(n, N, kap, kx64, ky64, kx32, ky32);
+  diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, sigma, d * c * e, G);
+  count_launches(4);
+  return cudaGetLastError();
+}
+
+}  // namespace cmg

@@ -1,0 +1,101 @@
+"""Error paths of the C ABI on the GPU: each returns a status, leaves the
+handle usable, and never faults the device (the failures are made on the
+host side of the call: bad arguments, a non-finite right side, too few
+iterations)."""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2302_13680_gb300 import build
+
+    build.build()
+    import paper_2302_13680_gb300 as P
+
+    pr = inputs.make_problem(**inputs.CONFIGS["n31_N8"])
+    h = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp)
+    yield h, P, pr
+    h.close()
+
+
+def rhs(h, pr):
+    yd = torch.tensor(pr.yd.reshape(-1), dtype=torch.float64, device="cuda")
+    return h.rhs(yd)
+
+
+def test_not_converged_then_usable(H):
+    h, P, pr = H
+    f = rhs(h, pr)
+    x = h.zeros(0)
+    st, status = h.solve(P.CycleOptions(), f, x, maxit=1, raise_on_fail=False)
+    assert status == 4 and st.iters == 1
+    st, status = h.solve(P.CycleOptions(), f, x, maxit=50)
+    assert status == 0 and st.relres <= 1e-10
+
+
+def test_nonfinite_rhs_reported(H):
+    h, P, pr = H
+    f = rhs(h, pr)
+    f[0][5, 3] = float("nan")
+    x = h.zeros(0)
+    st, status = h.solve(P.CycleOptions(), f, x, raise_on_fail=False)
+    assert status == 5
+    f = rhs(h, pr)
+    st, status = h.solve(P.CycleOptions(), f, x, maxit=50)
+    assert status == 0
+
+
+def test_invalid_arguments(H):
+    h, P, pr = H
+    f = rhs(h, pr)
+    x = h.zeros(0)
+    r = h.zeros(0)
+    with pytest.raises(P.CMGError) as e:
+        h.residual(h.levels, x, f, r)
+    assert e.value.status == 1
+    with pytest.raises(P.CMGError):
+        h.solve(P.CycleOptions(gamma=3), f, x)
+    with pytest.raises(P.CMGError):
+        h.solve(P.CycleOptions(smoother=P.SMOOTH_JACOBI, theta=0.0), f, x)
+    with pytest.raises(P.CMGError):
+        h.solve(P.CycleOptions(), f, x, method=P.METHOD_FGMRES, restart=0)
+    with pytest.raises(P.CMGError):
+        h.cycle(P.CycleOptions(precision=P.FP32), x, f)        # FP64 vectors, FP32 cycle
+    with pytest.raises(TypeError):
+        h.residual(0, tuple(t.float() for t in x), f, r)       # mixed dtypes
+    st, status = h.solve(P.CycleOptions(), f, x, maxit=50)
+    assert status == 0
+
+
+def test_zero_rhs_gives_zero(H):
+    h, P, pr = H
+    f = h.zeros(0)
+    x = tuple(torch.ones_like(t) for t in h.zeros(0))
+    st, status = h.solve(P.CycleOptions(), f, x)
+    assert status == 0
+    assert all(float(t.abs().max()) == 0.0 for t in x)
+
+
+def test_set_samples_recomputes_coefficients(H):
+    """New field draws through the device entry point give the same operator
+    as a fresh hierarchy built from them."""
+    h, P, pr = H
+    xi2 = inputs.draw_xi(99, pr.N, pr.K)
+    h2 = P.Hierarchy(pr.n, pr.N, xi2, pr.nu, pr.amp)
+    rng = np.random.default_rng(1)
+    x = tuple(torch.tensor(rng.standard_normal(t.shape), device="cuda") for t in h.zeros(0))
+    r1, r2 = h.zeros(0), h2.zeros(0)
+    h.set_samples(torch.tensor(xi2, device="cuda"))
+    h.residual(0, x, None, r1)
+    h2.residual(0, x, None, r2)
+    torch.cuda.synchronize()
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+    h.set_samples(torch.tensor(pr.xi, device="cuda"))
+    h2.close()

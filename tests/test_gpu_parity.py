@@ -1,0 +1,255 @@
+"""GPU parity: every kernel of libcmg against the CPU oracle, through the C ABI.
+
+FP64 bar (the solver's own acceptance rule): single kernels, sweeps and
+cycle iterates within 1e-12 relative (max-norm per block, scaled by the
+block's max magnitude); converged solutions within 1e-9 relative.  The
+FP32 kernels are held to 2e-5 relative against the FP64 oracle on
+FP32-representable inputs: each output is a short sum (<= 10 terms) of
+products of O(1)-conditioned values, so its rounding error is a few units
+of 2^-24 ~ 6e-8 times the largest term; sweeps and the control Schur
+quotient amplify it by at most the local condition, which stays below
+~100 on these grids.
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+import oracle.cmg_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def cmg():
+    from paper_2302_13680_gb300 import build
+
+    build.build()
+    import paper_2302_13680_gb300 as P
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return P
+
+
+def relerr(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = max(np.abs(ref).max(), 1e-300)
+    return float(np.abs(got - ref).max() / scale)
+
+
+def to_dev(v, dtype=torch.float64):
+    y, u, p = v
+    n = u.shape[0]
+    return (torch.tensor(np.asarray(y).reshape(n * n, -1), dtype=dtype, device="cuda").contiguous(),
+            torch.tensor(np.asarray(u).reshape(n * n), dtype=dtype, device="cuda").contiguous(),
+            torch.tensor(np.asarray(p).reshape(n * n, -1), dtype=dtype, device="cuda").contiguous())
+
+
+def to_host(v, n):
+    y, u, p = (t.double().cpu().numpy() for t in v)
+    return y.reshape(n, n, -1), u.reshape(n, n), p.reshape(n, n, -1)
+
+
+def assert_close(got, ref, tol, what=""):
+    for name, g, r in zip("yup", got, ref):
+        e = relerr(g, r)
+        assert e <= tol, f"{what} block {name}: rel err {e:.3e} > {tol:.1e}"
+
+
+def rand_level_vec(n, N, seed, dtype=np.float64):
+    rng = np.random.default_rng(seed)
+    v = (rng.standard_normal((n, n, N)), rng.standard_normal((n, n)), rng.standard_normal((n, n, N)))
+    return tuple(np.asarray(b, dtype=dtype).astype(np.float64) for b in v)
+
+
+# (n, N, K, nu, amp, seed, coarsest): the small configuration, ragged sample
+# counts (scalar and 2-wide vector paths, partial lane groups), all three
+# coarsest grids, and a sample count that spans several chunks per lane.
+CASES = [
+    (31, 8, 4, 1e-4, 0.5, 1, 3),
+    (15, 5, 3, 1e-3, 0.8, 7, 3),
+    (15, 6, 3, 1e-3, 0.8, 8, 1),
+    (31, 3, 2, 1e-5, 1.0, 9, 7),
+    (15, 1, 2, 1e-2, 0.6, 10, 3),
+    (63, 64, 16, 1e-6, 1.0, 2, 3),
+    (15, 130, 4, 1e-4, 1.0, 11, 3),
+]
+IDS = [f"n{c[0]}_N{c[1]}_c{c[6]}" for c in CASES]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=IDS)
+def case(request, cmg):
+    n, N, K, nu, amp, seed, coarsest = request.param
+    xi = inputs.draw_xi(seed, N, K)
+    H = cmg.Hierarchy(n, N, xi, nu, amp, coarsest_n=coarsest)
+    levels = O.make_hierarchy(n, N, nu, O.sine_mode_field(xi, amp), coarsest_n=coarsest)
+    yield H, levels
+    H.close()
+
+
+def test_hierarchy_shape(case):
+    H, levels = case
+    assert H.level_n == [lv.n for lv in levels]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_residual_every_level(case, prec):
+    H, levels = case
+    dt, tol = (torch.float64, TOL64) if prec == "f64" else (torch.float32, TOL32)
+    npdt = np.float64 if prec == "f64" else np.float32
+    for l, lv in enumerate(levels):
+        x = rand_level_vec(lv.n, lv.N, 100 + l, npdt)
+        f = rand_level_vec(lv.n, lv.N, 200 + l, npdt)
+        r = H.zeros(l, dt)
+        H.residual(l, to_dev(x, dt), to_dev(f, dt), r)
+        assert_close(to_host(r, lv.n), O.residual(lv, x, f), tol, f"residual level {l}")
+        # operator apply (f = NULL)
+        H.residual(l, to_dev(x, dt), None, r)
+        assert_close(to_host(r, lv.n), O.apply_S(lv, *x), tol, f"apply level {l}")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
+def test_one_sweep(case, prec, smoother):
+    H, levels = case
+    dt, tol = (torch.float64, TOL64) if prec == "f64" else (torch.float32, TOL32)
+    npdt = np.float64 if prec == "f64" else np.float32
+    import paper_2302_13680_gb300 as P
+
+    opts = P.CycleOptions(smoother=P.SMOOTH_RBGS if smoother == "rbgs" else P.SMOOTH_JACOBI, theta=0.5)
+    for l in (0, len(levels) - 2):
+        if l < 0:
+            continue
+        lv = levels[l]
+        # f of the size a cycle sees, x a random iterate
+        x = rand_level_vec(lv.n, lv.N, 300 + l, npdt)
+        f = rand_level_vec(lv.n, lv.N, 400 + l, npdt)
+        f = tuple(b * s for b, s in zip(f, (lv.c, lv.G, lv.h ** 2)))
+        f = tuple(np.asarray(b, dtype=npdt).astype(np.float64) for b in f)
+        xd = to_dev(x, dt)
+        H.smooth(l, opts, 1, xd, to_dev(f, dt))
+        if smoother == "rbgs":
+            ref = O.rbgs_sweep(lv, x, f)
+        else:
+            ref = O.jacobi_sweep(lv, x, f, 0.5)
+        assert_close(to_host(xd, lv.n), ref, tol, f"{smoother} level {l}")
+
+
+def test_red_half_sweep_leaves_black_nodes(case):
+    H, levels = case
+    lv = levels[0]
+    import paper_2302_13680_gb300 as P
+
+    x = rand_level_vec(lv.n, lv.N, 7)
+    f = rand_level_vec(lv.n, lv.N, 8)
+    xd = to_dev(x)
+    H.smooth(0, P.CycleOptions(), 2, xd, to_dev(f))
+    ref = O.rbgs_sweep(lv, O.rbgs_sweep(lv, x, f), f)
+    assert_close(to_host(xd, lv.n), ref, TOL64, "two sweeps")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_transfers(case, prec):
+    H, levels = case
+    dt, tol = (torch.float64, 1e-14) if prec == "f64" else (torch.float32, 1e-6)
+    npdt = np.float64 if prec == "f64" else np.float32
+    for l in range(len(levels) - 1):
+        nf, nc = levels[l].n, levels[l + 1].n
+        N = levels[l].N
+        r = rand_level_vec(nf, N, 500 + l, npdt)
+        c = H.zeros(l + 1, dt)
+        H.restrict(l, to_dev(r, dt), c)
+        assert_close(to_host(c, nc), O.restrict(nf, r), tol, f"restrict {l}")
+        e = rand_level_vec(nc, N, 600 + l, npdt)
+        x = rand_level_vec(nf, N, 700 + l, npdt)
+        xd = to_dev(x, dt)
+        H.prolong_add(l, to_dev(e, dt), xd)
+        pe = O.prolong(nf, e)
+        assert_close(to_host(xd, nf), tuple(a + b for a, b in zip(x, pe)), tol, f"prolong {l}")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_coarse_solve(case, prec):
+    H, levels = case
+    dt, tol = (torch.float64, TOL64) if prec == "f64" else (torch.float32, TOL32)
+    npdt = np.float64 if prec == "f64" else np.float32
+    lv = levels[-1]
+    f = rand_level_vec(lv.n, lv.N, 800, npdt)
+    x = H.zeros(len(levels) - 1, dt)
+    H.coarse_solve(to_dev(f, dt), x)
+    assert_close(to_host(x, lv.n), O.coarse_solve(lv, f), tol, "coarse")
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+@pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
+def test_cycle_iterates(case, gamma, smoother):
+    """Cycle k of the GPU from the oracle's iterate k-1 matches the oracle's cycle k.
+
+    Red-black iterates are held to 1e-12.  Damped Jacobi forms the explicit
+    residual f - S x before each update; its rounding is relative to |f| +
+    |S x| while the update scales with |r|, which after the first sweeps is
+    up to ~5x smaller, so its iterates are held to 5e-12."""
+    H, levels = case
+    import paper_2302_13680_gb300 as P
+
+    lv = levels[0]
+    yd = inputs.target_modes(lv.n, 3)
+    f = O.fine_rhs(lv, yd)
+    oopts = O.CycleOptions(smoother=smoother, gamma=gamma)
+    gopts = P.CycleOptions(smoother=P.SMOOTH_RBGS if smoother == "rbgs" else P.SMOOTH_JACOBI, gamma=gamma)
+    x = O.zeros_like_level(lv)
+    fd = to_dev(f)
+    for k in range(3):
+        xd = to_dev(x)
+        H.cycle(gopts, xd, fd)
+        x = O.cycle(levels, 0, x, f, oopts)
+        assert_close(to_host(xd, lv.n), x, TOL64 if smoother == "rbgs" else 5 * TOL64, f"cycle {k}")
+
+
+@pytest.mark.parametrize("method", ["cycle", "fgmres"])
+def test_converged_solution(case, method):
+    H, levels = case
+    import paper_2302_13680_gb300 as P
+
+    lv = levels[0]
+    yd = inputs.target_sinsin(lv.n)
+    f = O.fine_rhs(lv, yd)
+    opts = O.CycleOptions()
+    if method == "cycle":
+        ref = O.solve_stationary(levels, f, opts, tol=1e-11, maxit=60)
+        m = P.METHOD_CYCLE
+    else:
+        ref = O.fgmres(levels, f, opts, tol=1e-11)
+        m = P.METHOD_FGMRES
+    fd = to_dev(f)
+    xd = H.zeros(0)
+    st, _ = H.solve(P.CycleOptions(), fd, xd, method=m, tol=1e-11, maxit=60, restart=30)
+    assert st.relres <= 1e-11
+    assert ref.relres <= 1e-11
+    assert abs(st.iters - ref.iters) <= 1
+    assert_close(to_host(xd, lv.n), ref.x, 1e-9, "solution")
+
+
+@pytest.mark.parametrize("method", ["cycle", "fgmres"])
+def test_mixed_precision_solve(case, method):
+    """FP32 cycles inside FP64 refinement / FGMRES reach the FP64 residual
+    tolerance; the solution error against the FP64 oracle is then bounded
+    by the problem's conditioning times the tolerance."""
+    H, levels = case
+    import paper_2302_13680_gb300 as P
+
+    lv = levels[0]
+    f = O.fine_rhs(lv, inputs.target_sinsin(lv.n))
+    ref = O.fgmres(levels, f, O.CycleOptions(), tol=1e-12)
+    fd = to_dev(f)
+    xd = H.zeros(0)
+    m = P.METHOD_CYCLE if method == "cycle" else P.METHOD_FGMRES
+    st, _ = H.solve(P.CycleOptions(precision=P.FP32), fd, xd, method=m, tol=1e-10, maxit=60, restart=30)
+    assert st.relres <= 1e-10
+    got = to_host(xd, lv.n)
+    for name, g, r in zip("yup", got, ref.x):
+        assert relerr(g, r) <= 1e-6, name

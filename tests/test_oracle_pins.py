@@ -482,3 +482,41 @@ def test_cycle_counts_are_h_and_N_robust():
     vals = list(counts.values())
     assert max(vals) - min(vals) <= 3, counts
     assert max(vals) <= 16, counts
+
+
+def test_paper_system_is_row_and_column_scaling_of_symmetric_form():
+    """The paper's full-space system (Sec. 2): rows M y_j + A_j^T p_j = M y_d,
+    nu M u - sum_j zeta_j M p_j = 0, A_j y_j - M u = M f, with zeta_j = 1/N.
+    In the variables (y, u, N p) it equals W S with W = diag(N I, 1, 1), so
+    its relative residual is the W-weighted one (paper_norm)."""
+    L = small_level(n=3, N=3)
+    n, N, h = L.n, L.N, L.h
+    m = n * n
+    M = h * h * np.eye(m)
+    dim = (2 * N + 1) * m
+    Sp = np.zeros((dim, dim))
+    for j in range(N):
+        A = assemble_A_by_faces(L, j)
+        ys = slice(j * m, (j + 1) * m)
+        ps = slice(N * m + m + j * m, N * m + m + (j + 1) * m)
+        us = slice(N * m, N * m + m)
+        Sp[ys, ys] = M
+        Sp[ys, ps] = A.T
+        Sp[us, ps] = -(1.0 / N) * M
+        Sp[ps, ys] = A
+        Sp[ps, us] = -M
+    Sp[N * m:N * m + m, N * m:N * m + m] = L.nu * M
+    # sample-major ordering of the paper -> node-major ordering used here
+    perm = np.empty(dim, dtype=int)
+    for i in range(m):
+        for j in range(N):
+            perm[i * N + j] = j * m + i
+            perm[N * m + m + i * N + j] = N * m + m + j * m + i
+    perm[N * m:N * m + m] = np.arange(N * m, N * m + m)
+    Sp = Sp[np.ix_(perm, perm)]
+    S = assemble_S_blocks(L)
+    W = np.diag(np.concatenate([np.full(m * N, float(N)), np.ones(m), np.ones(m * N)]))
+    D = np.diag(np.concatenate([np.ones(m * N), np.ones(m), np.full(m * N, 1.0 / N)]))
+    assert np.allclose(W @ S @ D, Sp, rtol=1e-13, atol=1e-16)
+    r = rand_vec(L, 12)
+    assert np.isclose(O.paper_norm(r, N), np.linalg.norm(W @ O.pack(r)), rtol=1e-14)
