@@ -237,6 +237,35 @@ cmg_status cmg_profile_end(cmg_handle* h, double* total_ms, int* launches);
 /* Number of CUDA kernels this library has launched in the process so far. */
 long long cmg_kernel_launches(void);
 
+/* ---- allocation-free entry point ---------------------------------------- */
+
+/* For callers that cannot call cudaMalloc where they need a norm (code
+ * running under a host application that owns every device allocation, or
+ * a loop that must not allocate between steps).  The paper has no
+ * counterpart; this is a service of the library.
+ *
+ * Writes sqrt(wy^2 ||y||^2 + ||u||^2 + ||p||^2) to out[0] (DEVICE pointer,
+ * one double), y and p of length ny, u of length nu (DEVICE, FP64).  With
+ * wy = 1 and the level-0 sizes (ny = n*n*N, nu = n*n) it equals cmg_norm;
+ * with wy = N it is the norm of the paper's scaling used by cmg_solve.
+ * Needs no handle and allocates nothing: the per-block partial sums live in
+ * a file-scope device array of 3 x 65536 doubles (1.5 MiB) that every GPU
+ * loading this library holds until the process exits.  Its device address
+ * is looked up on the FIRST call made on each device (with that device
+ * current); make that first call before any stream capture.  Enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and not
+ * synchronised.
+ * Every call on a device shares that one array: calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and give
+ * wrong results; order them on one stream.  Each call writes every partial
+ * it reads, so nothing needs clearing between calls.
+ * Errors: CMG_ERR_INVALID_ARG for a null pointer, negative length or
+ * non-finite / negative wy; CMG_ERR_UNSUPPORTED if ny or nu exceeds 2^28
+ * (268,435,456) elements, the size the array covers (nothing is enqueued);
+ * CMG_ERR_CUDA if the launch fails. */
+cmg_status cmg_norm_noalloc(const double* y, const double* u, const double* p, long long ny,
+                            long long nu, double wy, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
