@@ -57,6 +57,7 @@ typedef enum {
 enum { CMG_SMOOTH_RBGS = 0, CMG_SMOOTH_JACOBI = 1 };
 enum { CMG_FP64 = 0, CMG_FP32 = 1 };
 enum { CMG_METHOD_CYCLE = 0, CMG_METHOD_FGMRES = 1 };
+enum { CMG_COARSE_AVERAGED = 0, CMG_COARSE_NODAL = 1 };
 
 /* Problem description (Sec. 2; field of Sec. 3.2). */
 typedef struct {
@@ -66,6 +67,12 @@ typedef struct {
   double nu;        /* control cost nu > 0 */
   double amp;       /* field amplitude */
   int coarsest_n;   /* nodes per side of the coarsest grid: 1, 3 or 7 (<= n) */
+  int coarse_coeff; /* face coefficients of the rediscretised coarse grids:
+                       CMG_COARSE_AVERAGED (default): each coarse face averages the finer
+                       grid's faces, harmonic along it (two fine faces in series) and
+                       arithmetic across it (weights 1/4, 1/2, 1/4);
+                       CMG_COARSE_NODAL: the field is sampled at each grid's own nodes and
+                       faces are harmonic means of the two endpoint values */
 } cmg_problem;
 
 /* Cycle options (Algorithm 1). */
@@ -91,7 +98,8 @@ typedef struct {
 
 /* Build the grid hierarchy n, (n-1)/2, ..., coarsest_n and, on the device,
  * the nodal field, face coefficients, diag(A_j) and the Schur denominators
- * of Eq. (13) on every grid (coarse operators rediscretised, Sec. 3), plus
+ * of Eq. (13) on every grid (coarse operators rediscretised, Sec. 3, with
+ * faces per prob->coarse_coeff), plus
  * the coarsest-grid factors used by the direct solve of Algorithm 1.
  * xi_host: host array [N][K] of field coefficients (copied).  stream: a
  * cudaStream_t (NULL = legacy default stream).  On success *out owns all

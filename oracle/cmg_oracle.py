@@ -23,7 +23,8 @@ It computes, slowly and in the order the paper states them:
   and red-black collective Gauss-Seidel (the variants named after Eq. 11);
 * transfers: bilinear prolongation P and restriction R = P^T, coarse
   operators rediscretised on each grid (the alternative the paper names
-  beside its Galerkin choice, Sec. 3);
+  beside its Galerkin choice, Sec. 3) with face coefficients harmonically
+  averaged from the next finer grid;
 * the coarsest-grid direct solve and the V/W-cycle of Algorithm 1;
 * the V-cycle used stationary and as right preconditioner of flexible
   GMRES, stopped on the relative unpreconditioned residual of the paper's
@@ -118,17 +119,55 @@ def make_level(n: int, N: int, nu: float, kappa_fn) -> Level:
                  c=h * h / N, G=nu * h * h, d=-h * h, e=-h * h)
 
 
-def make_hierarchy(n: int, N: int, nu: float, kappa_fn, coarsest_n: int = 3):
-    """Nested grids n_l = 2^l - 1 from n down to coarsest_n (finest first)."""
+def level_from_faces(n: int, N: int, nu: float, kx, ky) -> Level:
+    """The rediscretised operator on an n x n grid with given face coefficients."""
+    h = 1.0 / (n + 1)
+    a = kx[:, :-1] + kx[:, 1:] + ky[:-1, :] + ky[1:, :]
+    return Level(n=n, N=N, nu=nu, h=h, kx=kx, ky=ky, a=a,
+                 c=h * h / N, G=nu * h * h, d=-h * h, e=-h * h)
+
+
+def averaged_coarse_level(fine: Level) -> Level:
+    """Coarse grid (n-1)/2 whose face coefficients average the fine ones.
+
+    A coarse face spans two fine faces in series along its direction
+    (harmonic mean, the effective coefficient of two layers) and three
+    fine lines across it, combined in parallel with the full-weighting
+    weights 1/4, 1/2, 1/4 (arithmetic mean).  Coarse node (J, I) sits on
+    fine node (2J+1, 2I+1); the coarse vertical face I (between coarse
+    columns I-1 and I) spans the fine vertical faces 2I and 2I+1.
+    """
+    nf, N = fine.n, fine.N
+    nc = (nf - 1) // 2
+    w = (0.25, 0.5, 0.25)
+    kx = np.zeros((nc, nc + 1, N))
+    for J in range(nc):
+        for t, row in enumerate((2 * J, 2 * J + 1, 2 * J + 2)):
+            kx[J] += w[t] * harmonic_mean(fine.kx[row, 0:2 * nc + 1:2], fine.kx[row, 1:2 * nc + 2:2])
+    ky = np.zeros((nc + 1, nc, N))
+    for I in range(nc):
+        for t, col in enumerate((2 * I, 2 * I + 1, 2 * I + 2)):
+            ky[:, I] += w[t] * harmonic_mean(fine.ky[0:2 * nc + 1:2, col], fine.ky[1:2 * nc + 2:2, col])
+    return level_from_faces(nc, N, fine.nu, kx, ky)
+
+
+def make_hierarchy(n: int, N: int, nu: float, kappa_fn, coarsest_n: int = 3, coarse: str = "averaged"):
+    """Nested grids n_l = 2^l - 1 from n down to coarsest_n (finest first).
+
+    coarse = "averaged": coarse face coefficients from the next finer grid
+    (averaged_coarse_level); "nodal": every grid samples the field at its
+    own nodes and takes harmonic means of endpoint values (make_level)."""
     if n < coarsest_n or (n + 1) & n or (coarsest_n + 1) & coarsest_n:
         raise ValueError("grid sizes must be 2^l - 1 with n >= coarsest_n")
-    levels = []
-    m = n
-    while True:
-        levels.append(make_level(m, N, nu, kappa_fn))
-        if m == coarsest_n:
-            break
-        m = (m - 1) // 2
+    if coarse not in ("averaged", "nodal"):
+        raise ValueError(coarse)
+    levels = [make_level(n, N, nu, kappa_fn)]
+    while levels[-1].n != coarsest_n:
+        m = (levels[-1].n - 1) // 2
+        if coarse == "nodal":
+            levels.append(make_level(m, N, nu, kappa_fn))
+        else:
+            levels.append(averaged_coarse_level(levels[-1]))
     return levels
 
 

@@ -23,6 +23,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5:
 SMOOTH_RBGS, SMOOTH_JACOBI = 0, 1
 FP64, FP32 = 0, 1
 METHOD_CYCLE, METHOD_FGMRES = 0, 1
+COARSE = {"averaged": 0, "nodal": 1}
 
 
 class CMGError(RuntimeError):
@@ -33,7 +34,7 @@ class CMGError(RuntimeError):
 
 class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int), ("nu", ctypes.c_double),
-                ("amp", ctypes.c_double), ("coarsest_n", ctypes.c_int)]
+                ("amp", ctypes.c_double), ("coarsest_n", ctypes.c_int), ("coarse_coeff", ctypes.c_int)]
 
 
 class Cycle(ctypes.Structure):
@@ -119,7 +120,8 @@ class Hierarchy:
     float64 (or float32 for the *_f32 calls).
     """
 
-    def __init__(self, n: int, N: int, xi, nu: float, amp: float, coarsest_n: int = 3, stream=None):
+    def __init__(self, n: int, N: int, xi, nu: float, amp: float, coarsest_n: int = 3, stream=None,
+                 coarse: str = "averaged"):
         import torch
 
         if not torch.cuda.is_available():
@@ -132,7 +134,9 @@ class Hierarchy:
         self.nu, self.amp = float(nu), float(amp)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        prob = Problem(self.n, self.N, self.K, self.nu, self.amp, coarsest_n)
+        if coarse not in COARSE:
+            raise ValueError(f"coarse must be one of {sorted(COARSE)}")
+        prob = Problem(self.n, self.N, self.K, self.nu, self.amp, coarsest_n, COARSE[coarse])
         h = ctypes.c_void_p()
         st = self._lib.cmg_create(ctypes.byref(prob), xi.ctypes.data_as(ctypes.c_void_p),
                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))

@@ -140,8 +140,15 @@ cudaError_t setup_coefficients(cmg_handle* h) {
   const cmg_problem& P = h->prob;
   for (int l = 0; l < h->L; ++l) {
     Lev& v = h->lv[l];
-    cudaError_t e = launch_level_setup(v.n, P.N, P.K, P.amp, h->xi, h->kap, v.kx64, v.ky64, v.kx32, v.ky32, v.inva,
-                                       v.sigma, v.c, v.G, v.d, v.e, h->stream);
+    cudaError_t e;
+    if (l == 0 || P.coarse_coeff == CMG_COARSE_NODAL) {
+      e = launch_level_setup(v.n, P.N, P.K, P.amp, h->xi, h->kap, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.sigma,
+                             v.c, v.G, v.d, v.e, h->stream);
+    } else {
+      const Lev& f = h->lv[l - 1];
+      e = launch_coarse_level_setup(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.sigma, v.c,
+                                    v.G, v.d, v.e, h->stream);
+    }
     if (e != cudaSuccess) return e;
   }
   const Lev& cl = h->lv[h->L - 1];
@@ -266,6 +273,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   if (!pow2m1(P.n) || P.n < 3 || P.n > 4095) return CMG_ERR_INVALID_ARG;
   if (!(P.coarsest_n == 1 || P.coarsest_n == 3 || P.coarsest_n == 7) || P.coarsest_n > P.n) return CMG_ERR_INVALID_ARG;
   if (P.N < 1 || P.K < 0 || P.K > 64 || !(P.nu > 0.0) || !std::isfinite(P.amp)) return CMG_ERR_INVALID_ARG;
+  if (P.coarse_coeff != CMG_COARSE_AVERAGED && P.coarse_coeff != CMG_COARSE_NODAL) return CMG_ERR_INVALID_ARG;
   if (P.K > 0 && !xi_host) return CMG_ERR_INVALID_ARG;
   const SampleMap m64 = choose_map(P.N, 8), m32 = choose_map(P.N, 4);
   if (m64.spl > kMaxSPL || m32.spl > kMaxSPL) return CMG_ERR_UNSUPPORTED;

@@ -97,6 +97,12 @@ cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi
                                double* inva, double* sigma, double c, double G, double d,
                                double e, cudaStream_t s);
 
+// Coarse grid (nf-1)/2 with faces averaged from the finer grid's faces, then
+// 1/diag and Schur denominators.
+cudaError_t launch_coarse_level_setup(int nf, int N, const double* kxf, const double* kyf, double* kx64,
+                                      double* ky64, float* kx32, float* ky32, double* inva, double* sigma,
+                                      double c, double G, double d, double e, cudaStream_t s);
+
 // ---- vector kernels (cmg_blas.cu) ----
 constexpr int kRedBlocks = 304;    // fixed partial count: deterministic reductions
 // partial[0..kRedBlocks) (+)= w2 * per-block sums of squares; call finish to combine.

@@ -1,9 +1,12 @@
-// Coefficient setup on one grid (FP64 arithmetic):
+// Coefficient setup (FP64 arithmetic).  Finest grid (and every grid in the
+// nodal variant):
 //   nodal field kappa_j at the (n+2)^2 grid points including the boundary
 //   (the sine-mode log-Gaussian stand-in for Eq. (15): kappa = exp(amp *
 //   sin(pi y) * sum_k xi_jk sin(k pi x) / k), which is separable in x and y),
 //   harmonic-mean face coefficients, 1/diag(A_j) and the Schur denominators
 //   sigma_i = G + sum_j d c e / a_ij^2 of Eq. (13).
+// Coarse grids (averaged variant): faces averaged from the next finer grid,
+// then the same 1/diag and sigma.
 #include "cmg_common.cuh"
 
 namespace cmg {
@@ -82,9 +85,56 @@ __global__ void diag_kernel(int n, int N, const double* __restrict__ kx, const d
   if (lane == 0) sigma[warp] = G + dce * s;
 }
 
+// Coarse faces averaged from the next finer grid (nf = 2 nc + 1): a coarse
+// face spans two fine faces in series (harmonic mean) on each of three fine
+// lines across it, combined with weights 1/4, 1/2, 1/4.
+__global__ void coarse_faces_kernel(int nf, int N, const double* __restrict__ kxf, const double* __restrict__ kyf,
+                                    double* __restrict__ kx64, double* __restrict__ ky64, float* __restrict__ kx32,
+                                    float* __restrict__ ky32) {
+  const int nc = (nf - 1) / 2;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per = (long)nc * (nc + 1) * N;
+  if (t >= 2 * per) return;
+  const double w[3] = {0.25, 0.5, 0.25};
+  double v = 0.0;
+  if (t < per) {
+    const long face = t / N;
+    const int j = (int)(t - face * N);
+    const int J = (int)(face / (nc + 1)), I = (int)(face - (long)J * (nc + 1));
+    for (int k = 0; k < 3; ++k) {
+      const size_t row = (size_t)(2 * J + k) * (nf + 1);
+      v += w[k] * harmonic(kxf[(row + 2 * I) * N + j], kxf[(row + 2 * I + 1) * N + j]);
+    }
+    kx64[t] = v;
+    kx32[t] = (float)v;
+  } else {
+    const long tt = t - per;
+    const long face = tt / N;
+    const int j = (int)(tt - face * N);
+    const int J = (int)(face / nc), I = (int)(face - (long)J * nc);
+    for (int k = 0; k < 3; ++k) {
+      const size_t col = (size_t)(2 * I + k);
+      v += w[k] * harmonic(kyf[((size_t)(2 * J) * nf + col) * N + j], kyf[((size_t)(2 * J + 1) * nf + col) * N + j]);
+    }
+    ky64[tt] = v;
+    ky32[tt] = (float)v;
+  }
+}
+
 inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
 }  // namespace
+
+cudaError_t launch_coarse_level_setup(int nf, int N, const double* kxf, const double* kyf, double* kx64,
+                                      double* ky64, float* kx32, float* ky32, double* inva, double* sigma, double c,
+                                      double G, double d, double e, cudaStream_t s) {
+  const int nc = (nf - 1) / 2;
+  coarse_faces_kernel<<<blocks_for(2L * nc * (nc + 1) * N, 256), 256, 0, s>>>(nf, N, kxf, kyf, kx64, ky64, kx32,
+                                                                              ky32);
+  diag_kernel<<<blocks_for((long)nc * nc * 32, 256), 256, 0, s>>>(nc, N, kx64, ky64, inva, sigma, d * c * e, G);
+  count_launches(2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi, double* kap, double* kx64,
                                double* ky64, float* kx32, float* ky32, double* inva, double* sigma, double c,

@@ -45,13 +45,14 @@ def test_binding_loads_and_rejects_bad_sizes(lib):
 
     L = cmg.load_library()
     h = ctypes.c_void_p()
-    for bad in [cmg.Problem(30, 8, 4, 1e-4, 0.5, 3),      # n not 2^l - 1
-                cmg.Problem(31, 0, 4, 1e-4, 0.5, 3),      # N < 1
-                cmg.Problem(31, 8, 4, -1.0, 0.5, 3),      # nu <= 0
-                cmg.Problem(31, 8, 4, 1e-4, 0.5, 5),      # coarsest not 1, 3, 7
-                cmg.Problem(3, 8, 4, 1e-4, 0.5, 7)]:      # coarsest > n
+    for bad in [cmg.Problem(30, 8, 4, 1e-4, 0.5, 3, 0),      # n not 2^l - 1
+                cmg.Problem(31, 0, 4, 1e-4, 0.5, 3, 0),      # N < 1
+                cmg.Problem(31, 8, 4, -1.0, 0.5, 3, 0),      # nu <= 0
+                cmg.Problem(31, 8, 4, 1e-4, 0.5, 5, 0),      # coarsest not 1, 3, 7
+                cmg.Problem(3, 8, 4, 1e-4, 0.5, 7, 0),       # coarsest > n
+                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 2)]:     # unknown coarse-coefficient rule
         assert L.cmg_create(ctypes.byref(bad), None, None, ctypes.byref(h)) == 1
-    assert L.cmg_create(ctypes.byref(cmg.Problem(31, 4096, 0, 1e-4, 0.5, 3)), None, None,
+    assert L.cmg_create(ctypes.byref(cmg.Problem(31, 4096, 0, 1e-4, 0.5, 3, 0)), None, None,
                         ctypes.byref(h)) == 7        # N above the kernels' limit
     assert L.cmg_num_levels(None) == 0
     assert L.cmg_level_n(None, 0) == -1

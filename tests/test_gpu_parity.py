@@ -66,27 +66,29 @@ def rand_level_vec(n, N, seed, dtype=np.float64):
     return tuple(np.asarray(b, dtype=dtype).astype(np.float64) for b in v)
 
 
-# (n, N, K, nu, amp, seed, coarsest): the small configuration, ragged sample
-# counts (scalar and 2-wide vector paths, partial lane groups), all three
-# coarsest grids, and a sample count that spans several chunks per lane.
+# (n, N, K, nu, amp, seed, coarsest, coarse rule): the small configuration,
+# ragged sample counts (scalar and 2-wide vector paths, partial lane
+# groups), all three coarsest grids, a sample count that spans several
+# chunks per lane, and both coarse-coefficient rules.
 CASES = [
-    (31, 8, 4, 1e-4, 0.5, 1, 3),
-    (15, 5, 3, 1e-3, 0.8, 7, 3),
-    (15, 6, 3, 1e-3, 0.8, 8, 1),
-    (31, 3, 2, 1e-5, 1.0, 9, 7),
-    (15, 1, 2, 1e-2, 0.6, 10, 3),
-    (63, 64, 16, 1e-6, 1.0, 2, 3),
-    (15, 130, 4, 1e-4, 1.0, 11, 3),
+    (31, 8, 4, 1e-4, 0.5, 1, 3, "averaged"),
+    (31, 8, 4, 1e-4, 0.5, 1, 3, "nodal"),
+    (15, 5, 3, 1e-3, 0.8, 7, 3, "averaged"),
+    (15, 6, 3, 1e-3, 0.8, 8, 1, "averaged"),
+    (31, 3, 2, 1e-5, 1.0, 9, 7, "nodal"),
+    (15, 1, 2, 1e-2, 0.6, 10, 3, "averaged"),
+    (63, 64, 16, 1e-6, 1.0, 2, 3, "averaged"),
+    (15, 130, 4, 1e-4, 1.0, 11, 3, "averaged"),
 ]
-IDS = [f"n{c[0]}_N{c[1]}_c{c[6]}" for c in CASES]
+IDS = [f"n{c[0]}_N{c[1]}_c{c[6]}_{c[7][:3]}" for c in CASES]
 
 
 @pytest.fixture(scope="module", params=CASES, ids=IDS)
 def case(request, cmg):
-    n, N, K, nu, amp, seed, coarsest = request.param
+    n, N, K, nu, amp, seed, coarsest, coarse = request.param
     xi = inputs.draw_xi(seed, N, K)
-    H = cmg.Hierarchy(n, N, xi, nu, amp, coarsest_n=coarsest)
-    levels = O.make_hierarchy(n, N, nu, O.sine_mode_field(xi, amp), coarsest_n=coarsest)
+    H = cmg.Hierarchy(n, N, xi, nu, amp, coarsest_n=coarsest, coarse=coarse)
+    levels = O.make_hierarchy(n, N, nu, O.sine_mode_field(xi, amp), coarsest_n=coarsest, coarse=coarse)
     yield H, levels
     H.close()
 

@@ -520,3 +520,58 @@ def test_paper_system_is_row_and_column_scaling_of_symmetric_form():
     assert np.allclose(W @ S @ D, Sp, rtol=1e-13, atol=1e-16)
     r = rand_vec(L, 12)
     assert np.isclose(O.paper_norm(r, N), np.linalg.norm(W @ O.pack(r)), rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Averaged coarse coefficients
+# --------------------------------------------------------------------------
+
+def test_averaged_coarsening_constant_and_layered_media():
+    """A coarse face of length 2h_f spans two fine faces: in a medium layered
+    across the face direction they conduct in series (1/k_c is the mean of
+    1/k), in a medium layered along it in parallel (k_c is the weighted mean
+    over the three fine lines).  Constant media are reproduced exactly."""
+    nf, N = 15, 2
+    eta = np.array([0.7, 2.0])
+    fine = O.make_level(nf, N, 1e-3, const_field(eta))
+    c = O.averaged_coarse_level(fine)
+    assert np.allclose(c.kx, eta) and np.allclose(c.ky, eta)
+    # kappa depends on x only: vertical faces in series, horizontal faces parallel
+    kx_only = lambda X, Y: np.stack([1.0 + 3.0 * (X > 0.4) + X, 2.0 + np.sin(5 * X)], axis=-1)
+    fine = O.make_level(nf, N, 1e-3, kx_only)
+    c = O.averaged_coarse_level(fine)
+    nc = c.n
+    for J in range(nc):
+        for I in range(nc + 1):
+            a, b = fine.kx[2 * J + 1, 2 * I], fine.kx[2 * J + 1, 2 * I + 1]
+            assert np.allclose(1.0 / c.kx[J, I], 0.5 * (1.0 / a + 1.0 / b))
+    for J in range(nc + 1):
+        for I in range(nc):
+            cols = fine.ky[2 * J, 2 * I:2 * I + 3]           # equal along y for kappa(x)
+            assert np.allclose(c.ky[J, I], 0.25 * cols[0] + 0.5 * cols[1] + 0.25 * cols[2])
+    # kappa depends on y only: the roles swap
+    ky_only = lambda X, Y: kx_only(Y, X)
+    fine = O.make_level(nf, N, 1e-3, ky_only)
+    c = O.averaged_coarse_level(fine)
+    for J in range(nc + 1):
+        for I in range(nc):
+            a, b = fine.ky[2 * J, 2 * I + 1], fine.ky[2 * J + 1, 2 * I + 1]
+            assert np.allclose(1.0 / c.ky[J, I], 0.5 * (1.0 / a + 1.0 / b))
+
+
+def test_averaged_coarsening_improves_contraction_on_rough_fields():
+    """With a rough field (16 modes, amp 1) and small nu, sampling kappa on
+    each coarse grid aliases the field; averaging the fine faces keeps the
+    V-cycle contraction near the smooth-field rate (Sec. 3.2 robustness)."""
+    n, N = 31, 8
+    xi = inputs.draw_xi(2, N, 16)
+    rates = {}
+    for mode in ("nodal", "averaged"):
+        levels = O.make_hierarchy(n, N, 1e-6, O.sine_mode_field(xi, 1.0), coarse=mode)
+        f = O.fine_rhs(levels[0], inputs.target_sinsin(n))
+        res = O.solve_stationary(levels, f, O.CycleOptions(), tol=1e-10, maxit=60)
+        h = res.history
+        rates[mode] = float(np.median([h[i + 1] / h[i] for i in range(2, len(h) - 1)]))
+        assert res.relres <= 1e-10
+    assert rates["averaged"] < 0.8 * rates["nodal"], rates
+    assert rates["averaged"] < 0.35, rates
