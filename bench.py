@@ -224,6 +224,14 @@ def algorithmic_bytes(kind: int, n: int, N: int, s: int) -> float:
 KIND_NAMES = {1: "rbgs_half_kernel", 2: "residual_kernel", 4: "restrict_kernel", 8: "prolong_add_kernel"}
 
 
+def kernel_source_sha() -> str:
+    """Hash of the sources that define the node kernels (items + wrappers)."""
+    h = hashlib.sha256()
+    for name in ("cmg_items.cuh", "cmg_stencil.cu", "cmg_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2302_13680_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel: str, precision: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
@@ -234,8 +242,7 @@ def traffic_record(kernel: str, precision: str):
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2302_13680_gb300", "csrc", "cmg_stencil.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha()
     entry = rec.get(f"{kernel}:{precision}")
     if not entry or entry.get("source_sha") != sha:
         return None

@@ -84,6 +84,12 @@ typedef struct {
   int precision;    /* arithmetic of the cycle: CMG_FP64, or CMG_FP32 (single-precision
                        smoothing, residual and transfers; Schur scalar for u and the
                        coarsest solve in FP64) */
+  int tail_n;       /* grids with at most tail_n nodes per side (and the coarsest solve)
+                       run as ONE launch of a thread-block cluster whose phases are
+                       separated by cluster barriers; 0 = one launch per step on every
+                       grid.  Same arithmetic either way.  Ignored (one launch per step)
+                       when N needs more than 4 chunks per lane or the coarsest grid
+                       is 7 x 7. */
 } cmg_cycle;
 
 /* Solve statistics filled by cmg_solve. */
@@ -229,7 +235,8 @@ enum {
   CMG_KERNEL_RESIDUAL = 2,   /* residual / operator apply */
   CMG_KERNEL_RESTRICT = 4,
   CMG_KERNEL_PROLONG = 8,
-  CMG_KERNEL_COARSE = 16
+  CMG_KERNEL_COARSE = 16,
+  CMG_KERNEL_TAIL = 32       /* the cluster launch of the coarse-grid cycle (level = its first grid) */
 };
 
 /* Bracket every subsequent launch of the kernel kinds in `kinds` (a bit

@@ -39,7 +39,8 @@ class Problem(ctypes.Structure):
 
 class Cycle(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("theta", ctypes.c_double), ("n1", ctypes.c_int),
-                ("n2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("n2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tail_n", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -101,9 +102,10 @@ class CycleOptions:
     n2: int = 2
     gamma: int = 1
     precision: int = FP64
+    tail_n: int = 31          # grids with n <= tail_n run as one cluster launch; 0 = off
 
     def c(self) -> Cycle:
-        return Cycle(self.smoother, self.theta, self.n1, self.n2, self.gamma, self.precision)
+        return Cycle(self.smoother, self.theta, self.n1, self.n2, self.gamma, self.precision, self.tail_n)
 
 
 def _ptr(t):
@@ -278,7 +280,7 @@ class Hierarchy:
         return ms.value, cnt.value
 
 
-KERNEL_SMOOTH, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_COARSE = 1, 2, 4, 8, 16
+KERNEL_SMOOTH, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_COARSE, KERNEL_TAIL = 1, 2, 4, 8, 16, 32
 
 
 def kernel_launches() -> int:

@@ -24,7 +24,7 @@ struct Lev {
   int n = 0;
   double h = 0, c = 0, G = 0, d = 0, e = 0;
   size_t nodes = 0;                      // n*n
-  double *kx64 = nullptr, *ky64 = nullptr, *inva = nullptr, *sigma = nullptr;
+  double *kx64 = nullptr, *ky64 = nullptr, *inva = nullptr, *isigma = nullptr;
   float *kx32 = nullptr, *ky32 = nullptr;
   double* x64[3] = {nullptr, nullptr, nullptr};
   double* f64[3] = {nullptr, nullptr, nullptr};
@@ -123,12 +123,12 @@ LevelView<T> view(const cmg_handle* h, int l);
 template <>
 LevelView<double> view<double>(const cmg_handle* h, int l) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.sigma, v.c, v.G, v.d, v.e};
+  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.sigma, v.c, v.G, v.d, v.e};
+  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -142,11 +142,11 @@ cudaError_t setup_coefficients(cmg_handle* h) {
     Lev& v = h->lv[l];
     cudaError_t e;
     if (l == 0 || P.coarse_coeff == CMG_COARSE_NODAL) {
-      e = launch_level_setup(v.n, P.N, P.K, P.amp, h->xi, h->kap, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.sigma,
+      e = launch_level_setup(v.n, P.N, P.K, P.amp, h->xi, h->kap, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.isigma,
                              v.c, v.G, v.d, v.e, h->stream);
     } else {
       const Lev& f = h->lv[l - 1];
-      e = launch_coarse_level_setup(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.sigma, v.c,
+      e = launch_coarse_level_setup(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.isigma, v.c,
                                     v.G, v.d, v.e, h->stream);
     }
     if (e != cudaSuccess) return e;
@@ -195,10 +195,53 @@ cudaError_t zero_vec(cmg_handle* h, int l, Vec3<T> x) {
 // Algorithm 1 on grid l: smoothing, residual, restriction, gamma recursive
 // calls from a zero guess, prolongation, smoothing; direct solve on the
 // coarsest grid.
+// The coarse-grid part of the cycle from grid l down as one cluster launch
+// (cmg_tail.cuh).  Returns cudaErrorNotSupported when not applicable.
+template <typename T>
+cudaError_t tail_cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> f) {
+  const int nlev = h->L - l;
+  if (nlev > kTailMax || !tail_supported(h->prob.N, sizeof(T), h->coarse.m)) return cudaErrorNotSupported;
+  TailParams<T> P{};
+  P.nlev = nlev;
+  for (int k = 0; k < nlev; ++k) {
+    Lev& v = h->lv[l + k];
+    P.lev[k].L = view<T>(h, l + k);
+    P.lev[k].r = Work<T>::r(v);
+    if (k == 0) {
+      P.lev[k].x = x;
+      P.lev[k].f = Vec3<T>{const_cast<T*>(f.y), const_cast<T*>(f.u), const_cast<T*>(f.p)};
+    } else {
+      P.lev[k].x = Work<T>::x(v);
+      P.lev[k].f = Work<T>::f(v);
+    }
+  }
+  P.smoother = o.smoother;
+  P.n1 = o.n1;
+  P.n2 = o.n2;
+  P.gamma = o.gamma;
+  P.theta = o.theta;
+  P.lpn = choose_map(h->prob.N, sizeof(T), 0).lpn;
+  P.cm = h->coarse.m;
+  P.cN = h->coarse.N;
+  P.Ainv = h->coarse.Ainv;
+  P.Minv = h->coarse.Minv;
+  P.wz = h->coarse.wz;
+  const Lev& cl = h->lv[h->L - 1];
+  P.cc = cl.c;
+  P.cd = cl.d;
+  P.ce = cl.e;
+  ProfScope ps(h, CMG_KERNEL_TAIL, l);
+  return launch_tail_cycle<T>(P, h->stream);
+}
+
 template <typename T>
 cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> f) {
   Lev& v = h->lv[l];
   const int N = h->prob.N;
+  if (o.tail_n > 0 && v.n <= o.tail_n) {
+    const cudaError_t e = tail_cycle<T>(h, o, l, x, f);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (l == h->L - 1) {
     ProfScope ps(h, CMG_KERNEL_COARSE, l);
     return launch_coarse_solve<T>(h->coarse, v.c, v.d, v.e, f, x, h->stream);
@@ -234,6 +277,7 @@ cmg_status check_cycle(cmg_handle* h, const cmg_cycle* o) {
   if (o->n1 < 0 || o->n2 < 0 || o->n1 > 64 || o->n2 > 64) return fail(h, CMG_ERR_INVALID_ARG, "n1/n2 out of range");
   if (o->gamma < 1 || o->gamma > 2) return fail(h, CMG_ERR_INVALID_ARG, "gamma must be 1 or 2");
   if (o->precision != CMG_FP64 && o->precision != CMG_FP32) return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");
+  if (o->tail_n < 0) return fail(h, CMG_ERR_INVALID_ARG, "tail_n must be >= 0");
   if (o->smoother == CMG_SMOOTH_JACOBI && !(o->theta > 0.0 && o->theta <= 1.0))
     return fail(h, CMG_ERR_INVALID_ARG, "theta must be in (0, 1]");
   return CMG_OK;
@@ -275,7 +319,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   if (P.N < 1 || P.K < 0 || P.K > 64 || !(P.nu > 0.0) || !std::isfinite(P.amp)) return CMG_ERR_INVALID_ARG;
   if (P.coarse_coeff != CMG_COARSE_AVERAGED && P.coarse_coeff != CMG_COARSE_NODAL) return CMG_ERR_INVALID_ARG;
   if (P.K > 0 && !xi_host) return CMG_ERR_INVALID_ARG;
-  const SampleMap m64 = choose_map(P.N, 8), m32 = choose_map(P.N, 4);
+  const SampleMap m64 = choose_map(P.N, 8, 0), m32 = choose_map(P.N, 4, 0);   // most chunks per lane
   if (m64.spl > kMaxSPL || m32.spl > kMaxSPL) return CMG_ERR_UNSUPPORTED;
 
   cmg_handle* h = new (std::nothrow) cmg_handle();
@@ -307,7 +351,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     Lev& v = h->lv[l];
     const size_t faces = (size_t)v.n * (v.n + 1) * N;
     AL(v.kx64, faces); AL(v.ky64, faces); AL(v.kx32, faces); AL(v.ky32, faces);
-    AL(v.inva, v.nodes * N); AL(v.sigma, v.nodes);
+    AL(v.inva, v.nodes * N); AL(v.isigma, v.nodes);
     for (int b = 0; b < 3; ++b) {
       const size_t cnt = (b == 1) ? v.nodes : v.nodes * N;
       AL(v.r64[b], cnt); AL(v.x32[b], cnt); AL(v.f32[b], cnt); AL(v.r32[b], cnt); AL(v.f64[b], cnt);

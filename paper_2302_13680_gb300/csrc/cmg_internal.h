@@ -31,7 +31,7 @@ struct Vec3c {
   const T* p;
 };
 template <typename T>
-inline Vec3c<T> cview(const Vec3<T>& v) { return {v.y, v.u, v.p}; }
+__host__ __device__ inline Vec3c<T> cview(const Vec3<T>& v) { return {v.y, v.u, v.p}; }
 
 // Read-only view of one grid's operator for the kernels.  Face arrays:
 // kx[iy][f][j], f = 0..n (face f separates columns f-1 and f; f = 0 and n
@@ -44,7 +44,7 @@ struct LevelView {
   const T* kx;
   const T* ky;
   const double* inva;   // 1/diag(A_j) per node-sample (FP64 path only)
-  const double* sigma;  // Schur denominator of Eq. (13) per node
+  const double* isigma; // 1 / Schur denominator of Eq. (13) per node
   double c, G, d, e;    // scalar blocks of Eq. (12): C_j = c I, G, D_j = d I, E_j = e I
 };
 
@@ -55,7 +55,14 @@ struct SampleMap {
   int V;
   int spl;
 };
-SampleMap choose_map(int N, int elem_bytes);
+// Lanes per node for a launch over `items` nodes.  A lane takes up to 4
+// chunks so that one warp covers several nodes and the per-node FP64 work
+// (control-row sum, u) is shared by one warp instruction, as long as the
+// launch keeps at least kMinLanes lanes (two 256-thread CTAs per SM);
+// small grids are latency-bound and use more lanes per node.  items = 0
+// asks for the most lanes (one chunk per lane where N allows).
+constexpr long kMinLanes = 2L * 152 * 256;
+SampleMap choose_map(int N, int elem_bytes, long items);
 
 // Coarsest-grid factors (FP64).
 struct CoarseData {
@@ -82,6 +89,38 @@ cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s
 template <typename T>
 cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t s);
 
+// ---- cluster-resident coarse-grid cycle (cmg_tail.cuh, cmg_tail_f32/f64.cu) ----
+constexpr int kTailMax = 8;        // grids handled inside one cluster launch
+constexpr int kTailThreads = 512;  // threads per CTA of the cluster kernel
+
+template <typename T>
+struct TailLevel {
+  LevelView<T> L;
+  Vec3<T> x, f, r;   // iterate, right side, residual work vector of this grid
+};
+
+template <typename T>
+struct TailParams {
+  int nlev;                        // grids in the tail, the last is the coarsest
+  TailLevel<T> lev[kTailMax];
+  int smoother, n1, n2, gamma;
+  double theta;
+  int lpn;                         // lanes per node (SampleMap of N)
+  // coarsest grid (CoarseData) and its blocks c, d, e
+  int cm, cN;
+  const double* Ainv;
+  const double* Minv;
+  double* wz;
+  double cc, cd, ce;
+};
+
+// One launch of a thread-block cluster running Algorithm 1 from grid lev[0]
+// down to the coarsest.  Returns cudaErrorNotSupported (nothing launched)
+// when the sample count or the cluster configuration is not covered.
+template <typename T>
+cudaError_t launch_tail_cycle(const TailParams<T>& P, cudaStream_t s);
+bool tail_supported(int N, int elem_bytes, int coarse_m);
+
 // ---- coarsest grid (cmg_coarse.cu) ----
 template <typename T>
 cudaError_t launch_coarse_solve(const CoarseData& C, double c, double d, double e,
@@ -94,13 +133,13 @@ cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const dou
 // 1/diag and Schur denominators.  kap: scratch [(n+2)^2][N] doubles.
 cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi, double* kap,
                                double* kx64, double* ky64, float* kx32, float* ky32,
-                               double* inva, double* sigma, double c, double G, double d,
+                               double* inva, double* isigma, double c, double G, double d,
                                double e, cudaStream_t s);
 
 // Coarse grid (nf-1)/2 with faces averaged from the finer grid's faces, then
 // 1/diag and Schur denominators.
 cudaError_t launch_coarse_level_setup(int nf, int N, const double* kxf, const double* kyf, double* kx64,
-                                      double* ky64, float* kx32, float* ky32, double* inva, double* sigma,
+                                      double* ky64, float* kx32, float* ky32, double* inva, double* isigma,
                                       double c, double G, double d, double e, cudaStream_t s);
 
 // ---- vector kernels (cmg_blas.cu) ----

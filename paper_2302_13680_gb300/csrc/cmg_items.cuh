@@ -1,0 +1,387 @@
+// Per-node work items of the cycle, shared by the one-kernel-per-step path
+// (cmg_stencil.cu) and the cluster-resident coarse-grid cycle (cmg_tail.cu).
+//
+// An item is one mesh node: its lpn lanes (consecutive lanes of one warp)
+// cover the node's N samples in chunks of V contiguous elements.  Items may
+// be called with an out-of-range node index (valid == false); every lane of
+// the warp must reach the shuffle reductions, so no item returns early.
+//
+// CG selects loads that bypass L1 (ld.global.cg): required when the data was
+// written earlier in the same kernel by another CTA (the cluster kernel).
+#pragma once
+
+#include "cmg_common.cuh"
+
+namespace cmg {
+
+template <typename T, int V, bool CG>
+__device__ __forceinline__ vec<T, V> ldx(const T* p) {
+  if constexpr (!CG) {
+    return *reinterpret_cast<const vec<T, V>*>(p);
+  } else {
+    vec<T, V> r;
+    if constexpr (sizeof(T) == 4 && V == 4) {
+      const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+      r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+    } else if constexpr (sizeof(T) == 8 && V == 2) {
+      const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+      r.v[0] = t.x; r.v[1] = t.y;
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) r.v[k] = __ldcg(p + k);
+    }
+    return r;
+  }
+}
+template <typename T, int V, bool CG>
+__device__ __forceinline__ vec<T, V> ldx_if(bool ok, const T* p) {
+  return ok ? ldx<T, V, CG>(p) : vzero<T, V>();
+}
+template <typename T, bool CG>
+__device__ __forceinline__ T ld1(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void fma_faces(vec<T, V>& acc, const vec<T, V>& kW, const vec<T, V>& vW,
+                                          const vec<T, V>& kE, const vec<T, V>& vE, const vec<T, V>& kS,
+                                          const vec<T, V>& vS, const vec<T, V>& kN, const vec<T, V>& vN) {
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    T a = acc.v[k];
+    a = fma(kW.v[k], vW.v[k], a);
+    a = fma(kE.v[k], vE.v[k], a);
+    a = fma(kS.v[k], vS.v[k], a);
+    a = fma(kN.v[k], vN.v[k], a);
+    acc.v[k] = a;
+  }
+}
+
+// 1 / diag(A_j): stored (FP64 path) or from the four faces (FP32 path).
+template <typename T, int V, bool CG>
+__device__ __forceinline__ vec<T, V> inv_diag(const LevelView<T>& L, size_t off, const vec<T, V>& kW,
+                                              const vec<T, V>& kE, const vec<T, V>& kS, const vec<T, V>& kN) {
+  vec<T, V> ia;
+  if constexpr (sizeof(T) == 8) {
+    ia = ldx<T, V, CG>(reinterpret_cast<const T*>(L.inva) + off);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) ia.v[k] = __frcp_rn((kW.v[k] + kE.v[k]) + (kS.v[k] + kN.v[k]));
+  }
+  return ia;
+}
+
+// ---------------------------------------------------------------------------
+// r = f - S x (or r = S x when f.y == nullptr) at one node; y block times wy.
+// ---------------------------------------------------------------------------
+template <typename T, int V, int SPL, bool CG>
+__device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c<T>& x, const Vec3c<T>& f,
+                                              const Vec3<T>& r, long node, int lane, int lpn, T wy) {
+  const int n = L.n, N = L.N;
+  const size_t ld = (size_t)L.ld;
+  const bool valid = node < (long)n * n;
+  const T c = (T)L.c, e = (T)L.e;
+  const bool apply = f.y == nullptr;
+  T pacc = T(0);   // this lane's part of sum_j p_j (converted to FP64 once)
+  if (valid) {
+    const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
+    const size_t o = (size_t)node * ld;
+    const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
+    const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
+    const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
+    const T uu = ld1<T, CG>(x.u + node);
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+      const int j = (lane + s * lpn) * V;
+      if (j < N) {
+        const vec<T, V> kW = ldx<T, V, CG>(kWp + j), kE = ldx<T, V, CG>(kWp + ld + j);
+        const vec<T, V> kS = ldx<T, V, CG>(kSp + j), kN = ldx<T, V, CG>(kSp + (size_t)n * ld + j);
+        const vec<T, V> y = ldx<T, V, CG>(x.y + o + j), p = ldx<T, V, CG>(x.p + o + j);
+        vec<T, V> offy = vzero<T, V>(), offp = vzero<T, V>();
+        fma_faces<T, V>(offy, kW, ldx_if<T, V, CG>(hW, x.y + o - ld + j), kE, ldx_if<T, V, CG>(hE, x.y + o + ld + j),
+                        kS, ldx_if<T, V, CG>(hS, x.y + o - (size_t)n * ld + j), kN,
+                        ldx_if<T, V, CG>(hN, x.y + o + (size_t)n * ld + j));
+        fma_faces<T, V>(offp, kW, ldx_if<T, V, CG>(hW, x.p + o - ld + j), kE, ldx_if<T, V, CG>(hE, x.p + o + ld + j),
+                        kS, ldx_if<T, V, CG>(hS, x.p + o - (size_t)n * ld + j), kN,
+                        ldx_if<T, V, CG>(hN, x.p + o + (size_t)n * ld + j));
+        vec<T, V> ry, rp;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          const T a = (kW.v[k] + kE.v[k]) + (kS.v[k] + kN.v[k]);
+          // state rows: c y + A p ; adjoint rows: A y + e u
+          ry.v[k] = c * y.v[k] + (a * p.v[k] - offp.v[k]);
+          rp.v[k] = (a * y.v[k] - offy.v[k]) + e * uu;
+          pacc += p.v[k];
+        }
+        if (!apply) {
+          const vec<T, V> fy = ldx<T, V, CG>(f.y + o + j), fp = ldx<T, V, CG>(f.p + o + j);
+#pragma unroll
+          for (int k = 0; k < V; ++k) {
+            ry.v[k] = fy.v[k] - ry.v[k];
+            rp.v[k] = fp.v[k] - rp.v[k];
+          }
+        }
+        if (wy != T(1)) {
+#pragma unroll
+          for (int k = 0; k < V; ++k) ry.v[k] *= wy;
+        }
+        stv<T, V>(r.y + o + j, ry);
+        stv<T, V>(r.p + o + j, rp);
+      }
+    }
+  }
+  const double psum = group_sum((double)pacc, lpn);
+  if (valid && lane == 0) {
+    const double su = L.G * (double)ld1<T, CG>(x.u + node) + L.d * psum;   // control row: G u + d sum_j p_j
+    r.u[node] = (T)(apply ? su : (double)ld1<T, CG>(f.u + node) - su);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Red-black collective GS at the g-th node of `colour`: local right sides
+// from the current neighbours, then Eq. (13).  With b_p the rhs of the
+// first block row, b_y of the last, b_u of the control row:
+//   u = (b_u + d sum_j (c b_y,j / a_j^2 - b_p,j / a_j)) / sigma
+//   y_j = (b_y,j - e u) / a_j,   p_j = (b_p,j - c y_j) / a_j
+// with 1/sigma stored per node (FP64), so u costs one FP64 multiply: the
+// FP64 pipe of this GPU is narrow, and the per-node FP64 work is shared by
+// the lanes of one warp instruction.
+// ---------------------------------------------------------------------------
+template <typename T, int V, int SPL, bool CG>
+__device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& x, const Vec3c<T>& f, int colour,
+                                          long g, int lane, int lpn) {
+  const int n = L.n, N = L.N;
+  const size_t ld = (size_t)L.ld;
+  const bool valid = g < colour_count(n, colour);
+  const T c = (T)L.c;
+  int iy = 0, ix = 0;
+  if (valid) colour_node(g, n, colour, iy, ix);
+  const long node = (long)iy * n + ix;
+  const size_t o = (size_t)node * ld;
+  vec<T, V> bp[SPL], by[SPL], ia[SPL];
+  T tacc = T(0);   // this lane's part of the sum over samples (converted to FP64 once)
+  if (valid) {
+    const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
+    const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
+    const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+      const int j = (lane + s * lpn) * V;
+      if (j < N) {
+        const vec<T, V> kW = ldx<T, V, CG>(kWp + j), kE = ldx<T, V, CG>(kWp + ld + j);
+        const vec<T, V> kS = ldx<T, V, CG>(kSp + j), kN = ldx<T, V, CG>(kSp + (size_t)n * ld + j);
+        bp[s] = ldx<T, V, CG>(f.y + o + j);   // first block row: c y + A p = f_y
+        by[s] = ldx<T, V, CG>(f.p + o + j);   // last block row:  A y + e u = f_p
+        fma_faces<T, V>(bp[s], kW, ldx_if<T, V, CG>(hW, x.p + o - ld + j), kE,
+                        ldx_if<T, V, CG>(hE, x.p + o + ld + j), kS, ldx_if<T, V, CG>(hS, x.p + o - (size_t)n * ld + j),
+                        kN, ldx_if<T, V, CG>(hN, x.p + o + (size_t)n * ld + j));
+        fma_faces<T, V>(by[s], kW, ldx_if<T, V, CG>(hW, x.y + o - ld + j), kE,
+                        ldx_if<T, V, CG>(hE, x.y + o + ld + j), kS, ldx_if<T, V, CG>(hS, x.y + o - (size_t)n * ld + j),
+                        kN, ldx_if<T, V, CG>(hN, x.y + o + (size_t)n * ld + j));
+        ia[s] = inv_diag<T, V, CG>(L, o + j, kW, kE, kS, kN);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          const T iak = ia[s].v[k];
+          tacc += (c * iak) * (iak * by[s].v[k]) - iak * bp[s].v[k];
+        }
+      }
+    }
+  }
+  const double tsum = group_sum((double)tacc, lpn);
+  if (valid) {
+    const double uu = ((double)ld1<T, CG>(f.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
+    if (lane == 0) x.u[node] = (T)uu;
+    const T uT = (T)uu, e = (T)L.e;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+      const int j = (lane + s * lpn) * V;
+      if (j < N) {
+        vec<T, V> yn, pn;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          yn.v[k] = ia[s].v[k] * (by[s].v[k] - e * uT);
+          pn.v[k] = ia[s].v[k] * (bp[s].v[k] - c * yn.v[k]);
+        }
+        stv<T, V>(x.y + o + j, yn);
+        stv<T, V>(x.p + o + j, pn);
+      }
+    }
+  }
+}
+
+// Damped collective Jacobi, Eq. (11): x_i += theta S~_i^{-1} r_i.
+template <typename T, int V, int SPL, bool CG>
+__device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>& x, const Vec3c<T>& r,
+                                            double theta, long node, int lane, int lpn) {
+  const int n = L.n, N = L.N;
+  const size_t ld = (size_t)L.ld;
+  const bool valid = node < (long)n * n;
+  const T c = (T)L.c;
+  const size_t o = (size_t)(valid ? node : 0) * ld;
+  vec<T, V> bp[SPL], by[SPL], ia[SPL];
+  T tacc = T(0);
+  if (valid) {
+    const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
+    const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
+    const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+      const int j = (lane + s * lpn) * V;
+      if (j < N) {
+        bp[s] = ldx<T, V, CG>(r.y + o + j);
+        by[s] = ldx<T, V, CG>(r.p + o + j);
+        ia[s] = inv_diag<T, V, CG>(L, o + j, ldx<T, V, CG>(kWp + j), ldx<T, V, CG>(kWp + ld + j),
+                                   ldx<T, V, CG>(kSp + j), ldx<T, V, CG>(kSp + (size_t)n * ld + j));
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          const T iak = ia[s].v[k];
+          tacc += (c * iak) * (iak * by[s].v[k]) - iak * bp[s].v[k];
+        }
+      }
+    }
+  }
+  const double tsum = group_sum((double)tacc, lpn);
+  if (valid) {
+    const double du = ((double)ld1<T, CG>(r.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
+    if (lane == 0) x.u[node] = (T)((double)ld1<T, CG>(x.u + node) + theta * du);
+    const T duT = (T)du, e = (T)L.e, th = (T)theta;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+      const int j = (lane + s * lpn) * V;
+      if (j < N) {
+        vec<T, V> yv = ldx<T, V, CG>(x.y + o + j), pv = ldx<T, V, CG>(x.p + o + j);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          const T dy = ia[s].v[k] * (by[s].v[k] - e * duT);
+          const T dp = ia[s].v[k] * (bp[s].v[k] - c * dy);
+          yv.v[k] += th * dy;
+          pv.v[k] += th * dp;
+        }
+        stv<T, V>(x.y + o + j, yv);
+        stv<T, V>(x.p + o + j, pv);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transfers.  Coarse node (J, I) sits on fine node (2J+1, 2I+1).
+// ---------------------------------------------------------------------------
+
+// c = P^T r at one coarse node (weights 1, 1/2, 1/4); if zx.y is set, the
+// coarse iterate at that node is also cleared (zero initial guess).
+template <typename T, int V, int SPL, bool CG>
+__device__ __forceinline__ void restrict_item(int nf, int N, const Vec3c<T>& r, const Vec3<T>& cv,
+                                              const Vec3<T>& zx, long node, int lane, int lpn) {
+  const int nc = (nf - 1) / 2;
+  if (node >= (long)nc * nc) return;   // no shuffles below
+  const int J = (int)(node / nc), I = (int)(node - (long)J * nc);
+  const size_t ld = (size_t)N;
+  const long fc = (long)(2 * J + 1) * nf + (2 * I + 1);
+  const T w[3] = {T(0.5), T(1), T(0.5)};
+#pragma unroll
+  for (int s = 0; s < SPL; ++s) {
+    const int j = (lane + s * lpn) * V;
+    if (j < N) {
+      vec<T, V> ay = vzero<T, V>(), ap = vzero<T, V>();
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const T wt = w[dy + 1] * w[dx + 1];
+          const size_t o = (size_t)(fc + (long)dy * nf + dx) * ld + j;
+          const vec<T, V> vy = ldx<T, V, CG>(r.y + o), vp = ldx<T, V, CG>(r.p + o);
+#pragma unroll
+          for (int k = 0; k < V; ++k) {
+            ay.v[k] = fma(wt, vy.v[k], ay.v[k]);
+            ap.v[k] = fma(wt, vp.v[k], ap.v[k]);
+          }
+        }
+      stv<T, V>(cv.y + (size_t)node * ld + j, ay);
+      stv<T, V>(cv.p + (size_t)node * ld + j, ap);
+      if (zx.y) {
+        stv<T, V>(zx.y + (size_t)node * ld + j, vzero<T, V>());
+        stv<T, V>(zx.p + (size_t)node * ld + j, vzero<T, V>());
+      }
+    }
+  }
+  if (lane == 0) {
+    T au = T(0);
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) au = fma(w[dy + 1] * w[dx + 1], ld1<T, CG>(r.u + fc + (long)dy * nf + dx), au);
+    cv.u[node] = au;
+    if (zx.y) zx.u[node] = T(0);
+  }
+}
+
+// x += P e at one fine node: 1 x coinciding coarse node, 1/2 x each of two
+// edge neighbours, 1/4 x each of four cell corners (zero outside the grid).
+template <typename T, int V, int SPL, bool CG>
+__device__ __forceinline__ void prolong_item(int nf, int N, const Vec3c<T>& e, const Vec3<T>& x, long node,
+                                             int lane, int lpn) {
+  const int nc = (nf - 1) / 2;
+  if (node >= (long)nf * nf) return;   // no shuffles below
+  const int iy = (int)(node / nf), ix = (int)(node - (long)iy * nf);
+  int Jr[2] = {0, 0}, Ir[2] = {0, 0};
+  T wy[2] = {T(0), T(0)}, wx[2] = {T(0), T(0)};
+  int ny, nx;
+  if (iy & 1) { Jr[0] = (iy - 1) >> 1; wy[0] = T(1); ny = 1; }
+  else { Jr[0] = (iy >> 1) - 1; Jr[1] = iy >> 1; wy[0] = wy[1] = T(0.5); ny = 2; }
+  if (ix & 1) { Ir[0] = (ix - 1) >> 1; wx[0] = T(1); nx = 1; }
+  else { Ir[0] = (ix >> 1) - 1; Ir[1] = ix >> 1; wx[0] = wx[1] = T(0.5); nx = 2; }
+  const size_t ld = (size_t)N;
+#pragma unroll
+  for (int s = 0; s < SPL; ++s) {
+    const int j = (lane + s * lpn) * V;
+    if (j < N) {
+      vec<T, V> vy = ldx<T, V, CG>(x.y + (size_t)node * ld + j), vp = ldx<T, V, CG>(x.p + (size_t)node * ld + j);
+      for (int a = 0; a < ny; ++a) {
+        if (Jr[a] < 0 || Jr[a] >= nc) continue;
+        for (int b = 0; b < nx; ++b) {
+          if (Ir[b] < 0 || Ir[b] >= nc) continue;
+          const T wt = wy[a] * wx[b];
+          const size_t o = ((size_t)Jr[a] * nc + Ir[b]) * ld + j;
+          const vec<T, V> ey = ldx<T, V, CG>(e.y + o), ep = ldx<T, V, CG>(e.p + o);
+#pragma unroll
+          for (int k = 0; k < V; ++k) {
+            vy.v[k] = fma(wt, ey.v[k], vy.v[k]);
+            vp.v[k] = fma(wt, ep.v[k], vp.v[k]);
+          }
+        }
+      }
+      stv<T, V>(x.y + (size_t)node * ld + j, vy);
+      stv<T, V>(x.p + (size_t)node * ld + j, vp);
+    }
+  }
+  if (lane == 0) {
+    T vu = ld1<T, CG>(x.u + node);
+    for (int a = 0; a < ny; ++a) {
+      if (Jr[a] < 0 || Jr[a] >= nc) continue;
+      for (int b = 0; b < nx; ++b) {
+        if (Ir[b] < 0 || Ir[b] >= nc) continue;
+        vu = fma(wy[a] * wx[b], ld1<T, CG>(e.u + (size_t)Jr[a] * nc + Ir[b]), vu);
+      }
+    }
+    x.u[node] = vu;
+  }
+}
+
+// Dispatch on (V, SPL) chosen from N and the element size (see choose_map).
+#define CMG_SPL_SWITCH(SPLV, V_, ...)                                           \
+  switch (SPLV) {                                                              \
+    case 1: { constexpr int V = V_, SPL = 1; __VA_ARGS__; } break;             \
+    case 2: { constexpr int V = V_, SPL = 2; __VA_ARGS__; } break;             \
+    case 4: { constexpr int V = V_, SPL = 4; __VA_ARGS__; } break;             \
+    case 8: { constexpr int V = V_, SPL = 8; __VA_ARGS__; } break;             \
+    default: return cudaErrorInvalidValue;                                     \
+  }
+
+#define CMG_DISPATCH(T, MAP, ...)                                              \
+  do {                                                                         \
+    if ((MAP).V == 1) { CMG_SPL_SWITCH((MAP).spl, 1, __VA_ARGS__) }            \
+    else if constexpr (sizeof(T) == 8) { CMG_SPL_SWITCH((MAP).spl, 2, __VA_ARGS__) } \
+    else { CMG_SPL_SWITCH((MAP).spl, 4, __VA_ARGS__) }                         \
+  } while (0)
+
+}  // namespace cmg

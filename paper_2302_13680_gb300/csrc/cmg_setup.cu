@@ -64,10 +64,11 @@ __global__ void faces_kernel(int n, int N, const double* __restrict__ kap, doubl
   }
 }
 
-// inva[node][j] = 1 / (sum of the node's four faces); sigma[node] reduced
-// over samples by one warp per node in a fixed order.
+// inva[node][j] = 1 / (sum of the node's four faces); isigma[node] = 1 /
+// (Schur denominator), its sum over samples reduced by one warp per node in
+// a fixed order.
 __global__ void diag_kernel(int n, int N, const double* __restrict__ kx, const double* __restrict__ ky,
-                            double* __restrict__ inva, double* __restrict__ sigma, double dce, double G) {
+                            double* __restrict__ inva, double* __restrict__ isigma, double dce, double G) {
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (long)n * n) return;
@@ -82,7 +83,7 @@ __global__ void diag_kernel(int n, int N, const double* __restrict__ kx, const d
     s += ia * ia;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) sigma[warp] = G + dce * s;
+  if (lane == 0) isigma[warp] = 1.0 / (G + dce * s);
 }
 
 // Coarse faces averaged from the next finer grid (nf = 2 nc + 1): a coarse
@@ -126,25 +127,25 @@ inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + 
 }  // namespace
 
 cudaError_t launch_coarse_level_setup(int nf, int N, const double* kxf, const double* kyf, double* kx64,
-                                      double* ky64, float* kx32, float* ky32, double* inva, double* sigma, double c,
+                                      double* ky64, float* kx32, float* ky32, double* inva, double* isigma, double c,
                                       double G, double d, double e, cudaStream_t s) {
   const int nc = (nf - 1) / 2;
   coarse_faces_kernel<<<blocks_for(2L * nc * (nc + 1) * N, 256), 256, 0, s>>>(nf, N, kxf, kyf, kx64, ky64, kx32,
                                                                               ky32);
-  diag_kernel<<<blocks_for((long)nc * nc * 32, 256), 256, 0, s>>>(nc, N, kx64, ky64, inva, sigma, d * c * e, G);
+  diag_kernel<<<blocks_for((long)nc * nc * 32, 256), 256, 0, s>>>(nc, N, kx64, ky64, inva, isigma, d * c * e, G);
   count_launches(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi, double* kap, double* kx64,
-                               double* ky64, float* kx32, float* ky32, double* inva, double* sigma, double c,
+                               double* ky64, float* kx32, float* ky32, double* inva, double* isigma, double c,
                                double G, double d, double e, cudaStream_t s) {
   // gx lives in the tail of kap's scratch: (n+2)*N doubles after the field.
   double* gx = kap + (size_t)(n + 2) * (n + 2) * N;
   field_x_kernel<<<blocks_for((long)(n + 2) * N, 256), 256, 0, s>>>(n, N, K, xi, gx);
   field_kernel<<<blocks_for((long)(n + 2) * (n + 2) * N, 256), 256, 0, s>>>(n, N, amp, gx, kap);
   faces_kernel<<<blocks_for(2L * n * (n + 1) * N, 256), 256, 0, s>>>(n, N, kap, kx64, ky64, kx32, ky32);
-  diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, sigma, d * c * e, G);
+  diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, isigma, d * c * e, G);
   count_launches(4);
   return cudaGetLastError();
 }

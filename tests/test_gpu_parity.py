@@ -186,10 +186,13 @@ def test_coarse_solve(case, prec):
     assert_close(to_host(x, lv.n), O.coarse_solve(lv, f), tol, "coarse")
 
 
+@pytest.mark.parametrize("tail_n", [0, 31])
 @pytest.mark.parametrize("gamma", [1, 2])
 @pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
-def test_cycle_iterates(case, gamma, smoother):
-    """Cycle k of the GPU from the oracle's iterate k-1 matches the oracle's cycle k.
+def test_cycle_iterates(case, gamma, smoother, tail_n):
+    """Cycle k of the GPU from the oracle's iterate k-1 matches the oracle's cycle k,
+    with the coarse grids run one launch per step (tail_n = 0) or as one
+    cluster launch (tail_n = 31).
 
     Red-black iterates are held to 1e-12.  Damped Jacobi forms the explicit
     residual f - S x before each update; its rounding is relative to |f| +
@@ -202,7 +205,8 @@ def test_cycle_iterates(case, gamma, smoother):
     yd = inputs.target_modes(lv.n, 3)
     f = O.fine_rhs(lv, yd)
     oopts = O.CycleOptions(smoother=smoother, gamma=gamma)
-    gopts = P.CycleOptions(smoother=P.SMOOTH_RBGS if smoother == "rbgs" else P.SMOOTH_JACOBI, gamma=gamma)
+    gopts = P.CycleOptions(smoother=P.SMOOTH_RBGS if smoother == "rbgs" else P.SMOOTH_JACOBI, gamma=gamma,
+                           tail_n=tail_n)
     x = O.zeros_like_level(lv)
     fd = to_dev(f)
     for k in range(3):
