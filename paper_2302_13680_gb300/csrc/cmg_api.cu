@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
 #include <atomic>
 
 #include "cmg_common.cuh"
@@ -62,6 +63,15 @@ struct cmg_handle {
   double* red = nullptr;      // reduction partials
   double* dsc = nullptr;      // device scalars
   double* hsc = nullptr;      // pinned host scalars
+  double* part = nullptr;     // per-CTA partial sums of the fused refinement pass
+  int part_cap = 0;
+  // FP32 refinement loop as a CUDA graph with a device-side while node
+  cudaStream_t cap = nullptr;            // non-blocking stream used for capture
+  cudaGraph_t ir_graph = nullptr;
+  cudaGraphExec_t ir_exec = nullptr;
+  const void* ir_key[6] = {};
+  cmg_cycle ir_opts{};
+  double* ir_state = nullptr;            // device [sc, inv_sc, rho, it, maxit, tol_abs]
   // FGMRES workspace
   int gm_cap = 0;
   double* gm = nullptr;       // [2*cap + 2][nt_pad]
@@ -363,6 +373,9 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   AL(h->xi, (size_t)N * (P.K > 0 ? P.K : 1));
   AL(h->red, (size_t)kRedBlocks * 8 * 16);
   AL(h->dsc, 1024);
+  h->part_cap = (int)(((size_t)P.n * P.n * 32 + kBlock - 1) / kBlock + 16);
+  AL(h->part, (size_t)h->part_cap);
+  AL(h->ir_state, 8);
   const int cn = h->lv[L - 1].n;
   h->coarse.n = cn;
   h->coarse.m = cn * cn;
@@ -407,6 +420,9 @@ void cmg_destroy(cmg_handle* h) {
   if (!h) return;
   if (h->stream) (void)cudaStreamSynchronize(h->stream);
   else (void)cudaDeviceSynchronize();
+  if (h->ir_exec) (void)cudaGraphExecDestroy(h->ir_exec);
+  if (h->ir_graph) (void)cudaGraphDestroy(h->ir_graph);
+  if (h->cap) (void)cudaStreamDestroy(h->cap);
   for (void* p : h->allocs) (void)cudaFree(p);
   for (auto& ev : h->prof_ev) (void)cudaEventDestroy(ev);
   if (h->gm) (void)cudaFree(h->gm);
@@ -584,35 +600,168 @@ cmg_status precondition(cmg_handle* h, const cmg_cycle& o, Vec3c<double> v, Vec3
   return CMG_OK;
 }
 
+// End of one refinement iteration inside the graph: residual norm from the
+// partials (fixed-order sum), scales for the next iteration, iteration
+// count, and the loop condition of the enclosing while node.
+// state = [sc, inv_sc, rho, it, maxit, tol_abs].
+__global__ void ir_control_kernel(const double* __restrict__ partial, int count, double* __restrict__ state,
+                                  cudaGraphConditionalHandle cond) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) v += partial[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    const double sc = state[0];
+    const double rho = sqrt(t) / sc;
+    const double it = state[3] + 1.0;
+    state[1] = 1.0 / sc;     // the right side now holds r * sc
+    state[0] = 1.0 / rho;    // scale of the next right side
+    state[2] = rho;
+    state[3] = it;
+    const bool go = isfinite(rho) && rho > state[5] && it < state[4];
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+  }
+}
+
+bool same_cycle(const cmg_cycle& a, const cmg_cycle& b) {
+  return a.smoother == b.smoother && a.theta == b.theta && a.n1 == b.n1 && a.n2 == b.n2 && a.gamma == b.gamma &&
+         a.precision == b.precision && a.tail_n == b.tail_n;
+}
+
+// Capture (once per iterate / right-side pointers and cycle options) the
+// refinement loop: while (go) { e = cycle_FP32(0; r32); x += inv_sc e;
+// r32 = sc (f - S x); control }.
+cmg_status build_ir_graph(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<double> x) {
+  const void* key[6] = {f.y, f.u, f.p, x.y, x.u, x.p};
+  if (h->ir_exec && same_cycle(h->ir_opts, o) && std::equal(key, key + 6, h->ir_key)) return CMG_OK;
+  if (h->ir_exec) {
+    CK(cudaGraphExecDestroy(h->ir_exec));
+    h->ir_exec = nullptr;
+  }
+  if (h->ir_graph) {
+    CK(cudaGraphDestroy(h->ir_graph));
+    h->ir_graph = nullptr;
+  }
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  h->ir_graph = g;
+  cudaGraphConditionalHandle cond;
+  CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  Lev& l0 = h->lv[0];
+  const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes;
+  Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
+  const cudaStream_t user = h->stream;
+  const int prof = h->prof_kinds;
+  h->stream = h->cap;
+  h->prof_kinds = 0;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  int cnt = -1;
+  if (e == cudaSuccess) {
+    e = zero_vec<float>(h, 0, x32);
+    if (e == cudaSuccess) e = cycle<float>(h, o, 0, x32, cview(f32));
+    if (e == cudaSuccess) e = launch_axpy3(0.0, h->ir_state + 1, cview(x32), x, ny, nu, h->cap);
+    if (e == cudaSuccess) {
+      cnt = launch_residual_cast(view<double>(h, 0), cview(x), f, f32, 0.0, h->ir_state, paper_wy(h), h->part,
+                                 h->part_cap, h->cap);
+      if (cnt < 0) e = cudaErrorLaunchFailure;
+    }
+    if (e == cudaSuccess) {
+      ir_control_kernel<<<1, 256, 0, h->cap>>>(h->part, cnt, h->ir_state, cond);
+      count_launches(1);
+      e = cudaGetLastError();
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap, &captured);
+    if (e == cudaSuccess) e = e2;
+  }
+  h->stream = user;
+  h->prof_kinds = prof;
+  if (e != cudaSuccess) return cuda_fail(h, e, "capture of the refinement loop");
+  cudaGraphExec_t ex = nullptr;
+  CK(cudaGraphInstantiate(&ex, g, 0));
+  h->ir_exec = ex;
+  h->ir_opts = o;
+  std::copy(key, key + 6, h->ir_key);
+  return CMG_OK;
+}
+
 cmg_status solve_cycle(cmg_handle* h, const cmg_cycle& o, double tol, int maxit, Vec3c<double> f, Vec3<double> x,
                        double fnorm, cmg_stats* st) {
   Lev& l0 = h->lv[0];
   const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes;
   double rho = 0;
-  cmg_status s = true_residual(h, f, cview(x), &rho);
-  if (s != CMG_OK) return s;
-  st->relres0 = rho / fnorm;
+  cmg_status s = CMG_OK;
   int it = 0;
-  while (std::isfinite(rho) && rho > tol * fnorm && it < maxit) {
-    if (o.precision == CMG_FP64) {
-      CK(cycle<double>(h, o, 0, x, f));
-    } else {
-      // iterative refinement: e = cycle_FP32(0; r), x += e; r is in level-0 r64
-      Vec3<double> r = Work<double>::r(l0);
-      Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
-      const double sc = 1.0 / rho;
-      CK((launch_scale_cast<double, float>(sc, r.y, f32.y, ny, h->stream)));
-      CK((launch_scale_cast<double, float>(sc, r.u, f32.u, nu, h->stream)));
-      CK((launch_scale_cast<double, float>(sc, r.p, f32.p, ny, h->stream)));
-      CK(zero_vec<float>(h, 0, x32));
-      CK(cycle<float>(h, o, 0, x32, cview(f32)));
-      CK((launch_axpy<float, double>(rho, x32.y, x.y, ny, h->stream)));
-      CK((launch_axpy<float, double>(rho, x32.u, x.u, nu, h->stream)));
-      CK((launch_axpy<float, double>(rho, x32.p, x.p, ny, h->stream)));
-    }
-    ++it;
+  if (o.precision == CMG_FP64) {
     s = true_residual(h, f, cview(x), &rho);
     if (s != CMG_OK) return s;
+    st->relres0 = rho / fnorm;
+    while (std::isfinite(rho) && rho > tol * fnorm && it < maxit) {
+      CK(cycle<double>(h, o, 0, x, f));
+      ++it;
+      s = true_residual(h, f, cview(x), &rho);
+      if (s != CMG_OK) return s;
+    }
+  } else {
+    // FP64 iterative refinement around FP32 cycles.  One fused pass forms
+    // r = f - S x in FP64 and writes r * sc in FP32 (the next cycle's right
+    // side) with the norm partials; the cycle solves S e = r * sc from zero
+    // and x += e / sc.  sc = 1 / (previous residual norm) keeps the FP32
+    // right side O(1) whatever the residual level.
+    Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
+    auto outer = [&](double sc, double* out) -> cmg_status {
+      const int cnt = launch_residual_cast(view<double>(h, 0), cview(x), f, f32, sc, nullptr, paper_wy(h), h->part,
+                                           h->part_cap, h->stream);
+      if (cnt < 0) return fail(h, CMG_ERR_CUDA, "refinement pass launch failed");
+      CK(launch_finish_sum(h->part, cnt, h->dsc, h->stream));
+      CK(fetch(h, h->dsc, 1));
+      *out = std::sqrt(h->hsc[0]) / sc;
+      return CMG_OK;
+    };
+    double sc = 1.0 / fnorm;
+    s = outer(sc, &rho);
+    if (s != CMG_OK) return s;
+    st->relres0 = rho / fnorm;
+    const bool use_graph = h->prof_kinds == 0 && std::isfinite(rho) && rho > tol * fnorm && maxit > 0;
+    if (use_graph) {
+      // The loop runs on the device; the host reads the result once.
+      s = build_ir_graph(h, o, f, x);
+      if (s != CMG_OK) return s;
+      double* hs = h->hsc;
+      hs[0] = 1.0 / rho;
+      hs[1] = 1.0 / sc;
+      hs[2] = rho;
+      hs[3] = 0.0;
+      hs[4] = (double)maxit;
+      hs[5] = tol * fnorm;
+      CK(cudaMemcpyAsync(h->ir_state, hs, 6 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaGraphLaunch(h->ir_exec, h->stream));
+      CK(fetch(h, h->ir_state, 6));
+      rho = h->hsc[2];
+      it = (int)h->hsc[3];
+    }
+    while (!use_graph && std::isfinite(rho) && rho > tol * fnorm && it < maxit) {
+      CK(zero_vec<float>(h, 0, x32));
+      CK(cycle<float>(h, o, 0, x32, cview(f32)));
+      CK(launch_axpy3(1.0 / sc, nullptr, cview(x32), x, ny, nu, h->stream));
+      ++it;
+      sc = 1.0 / rho;
+      s = outer(sc, &rho);
+      if (s != CMG_OK) return s;
+    }
   }
   st->iters = it;
   st->cycles = it;

@@ -121,6 +121,17 @@ template <typename T>
 cudaError_t launch_tail_cycle(const TailParams<T>& P, cudaStream_t s);
 bool tail_supported(int N, int elem_bytes, int coarse_m);
 
+// FP64 refinement pass: r32 = s (f - S x) and per-CTA partial sums of
+// ||W r32||^2 (W scales the state block by wy).  Returns the number of
+// partials written, or -1 on error / if more than max_partials are needed.
+// The scale is *sdev when sdev is given (graph replays), else s.
+int launch_residual_cast(const LevelView<double>& L, Vec3c<double> x, Vec3c<double> f, Vec3<float> r, double s,
+                         const double* sdev, double wy, double* partial, int max_partials, cudaStream_t st);
+// x += a * e on the three blocks (ny elements in y and p, nu in u); a is
+// *adev when adev is given.
+cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<double> x, size_t ny, size_t nu,
+                         cudaStream_t st);
+
 // ---- coarsest grid (cmg_coarse.cu) ----
 template <typename T>
 cudaError_t launch_coarse_solve(const CoarseData& C, double c, double d, double e,

@@ -385,3 +385,71 @@ __device__ __forceinline__ void prolong_item(int nf, int N, const Vec3c<T>& e, c
   } while (0)
 
 }  // namespace cmg
+
+namespace cmg {
+
+// Outer-residual item of FP64 iterative refinement: r = f - S x in FP64 at
+// one node, written as FP32 scaled by s (the right side of the next FP32
+// cycle); returns this lane's part of ||W r s||^2 (state block weighted by
+// wy) accumulated in FP32 -- the stopping test needs the norm to ~1e-7
+// relative accuracy, not the residual itself.
+template <int V, int SPL>
+__device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, const Vec3c<double>& x,
+                                                    const Vec3c<double>& f, const Vec3<float>& r, long node,
+                                                    int lane, int lpn, double s, float wy2) {
+  using T = double;
+  const int n = L.n, N = L.N;
+  const size_t ld = (size_t)L.ld;
+  const bool valid = node < (long)n * n;
+  const T c = L.c, e = L.e;
+  T pacc = 0.0;
+  float sq = 0.f;
+  if (valid) {
+    const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
+    const size_t o = (size_t)node * ld;
+    const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
+    const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
+    const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
+    const T eu = e * x.u[node];
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      const int j = (lane + q * lpn) * V;
+      if (j < N) {
+        const vec<T, V> kW = ldv<T, V>(kWp + j), kE = ldv<T, V>(kWp + ld + j);
+        const vec<T, V> kS = ldv<T, V>(kSp + j), kN = ldv<T, V>(kSp + (size_t)n * ld + j);
+        const vec<T, V> y = ldv<T, V>(x.y + o + j), p = ldv<T, V>(x.p + o + j);
+        const vec<T, V> fy = ldv<T, V>(f.y + o + j), fp = ldv<T, V>(f.p + o + j);
+        vec<T, V> offy = vzero<T, V>(), offp = vzero<T, V>();
+        fma_faces<T, V>(offy, kW, ldv_if<T, V>(hW, x.y + o - ld + j), kE, ldv_if<T, V>(hE, x.y + o + ld + j), kS,
+                        ldv_if<T, V>(hS, x.y + o - (size_t)n * ld + j), kN,
+                        ldv_if<T, V>(hN, x.y + o + (size_t)n * ld + j));
+        fma_faces<T, V>(offp, kW, ldv_if<T, V>(hW, x.p + o - ld + j), kE, ldv_if<T, V>(hE, x.p + o + ld + j), kS,
+                        ldv_if<T, V>(hS, x.p + o - (size_t)n * ld + j), kN,
+                        ldv_if<T, V>(hN, x.p + o + (size_t)n * ld + j));
+        vec<float, V> ry, rp;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          const T a = (kW.v[k] + kE.v[k]) + (kS.v[k] + kN.v[k]);
+          const T ryk = fy.v[k] - fma(c, y.v[k], fma(a, p.v[k], -offp.v[k]));   // f_y - c y - A p
+          const T rpk = (fp.v[k] - eu) - fma(a, y.v[k], -offy.v[k]);             // f_p - e u - A y
+          ry.v[k] = (float)(ryk * s);
+          rp.v[k] = (float)(rpk * s);
+          sq = fmaf(wy2 * ry.v[k], ry.v[k], sq);
+          sq = fmaf(rp.v[k], rp.v[k], sq);
+          pacc += p.v[k];
+        }
+        stv<float, V>(r.y + o + j, ry);
+        stv<float, V>(r.p + o + j, rp);
+      }
+    }
+  }
+  const double psum = group_sum(pacc, lpn);
+  if (valid && lane == 0) {
+    const float ru = (float)((f.u[node] - (L.G * x.u[node] + L.d * psum)) * s);
+    r.u[node] = ru;
+    sq = fmaf(ru, ru, sq);
+  }
+  return sq;
+}
+
+}  // namespace cmg

@@ -51,6 +51,40 @@ __global__ void __launch_bounds__(kBlock) prolong_add_kernel(int nf, int N, Vec3
   prolong_item<T, V, SPL, false>(nf, N, e, x, node, threadIdx.x & (lpn - 1), lpn);
 }
 
+// One pass of FP64 refinement: r32 = s (f - S x) and per-CTA partial sums
+// of ||W r32||^2 (squares in FP32, CTA sum in FP64).
+template <int V, int SPL>
+__global__ void __launch_bounds__(kBlock) residual_cast_kernel(LevelView<double> L, Vec3c<double> x,
+                                                              Vec3c<double> f, Vec3<float> r, int lpn, double s,
+                                                              const double* __restrict__ sdev, float wy2,
+                                                              double* __restrict__ partial) {
+  __shared__ double sh[kBlock / 32];
+  const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
+  const double sc = sdev ? *sdev : s;
+  double v = (double)residual_cast_item<V, SPL>(L, x, f, r, node, threadIdx.x & (lpn - 1), lpn, sc, wy2);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += sh[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// x += a * e for the three blocks (FP64 iterate, FP32 correction); a read
+// from adev when given.
+__global__ void axpy3_kernel(double a0, const double* __restrict__ adev, Vec3c<float> e, Vec3<double> x, size_t ny,
+                             size_t nu) {
+  const double a = adev ? *adev : a0;
+  const size_t total = 2 * ny + nu;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    if (i < ny) x.y[i] = fma(a, (double)e.y[i], x.y[i]);
+    else if (i < ny + nu) x.u[i - ny] = fma(a, (double)e.u[i - ny], x.u[i - ny]);
+    else x.p[i - ny - nu] = fma(a, (double)e.p[i - ny - nu], x.p[i - ny - nu]);
+  }
+}
+
 inline unsigned grid_for(long groups, int lpn) {
   const long threads = groups * lpn;
   return (unsigned)((threads + kBlock - 1) / kBlock);
@@ -120,6 +154,33 @@ cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_
   const SampleMap m = choose_map(N, sizeof(T), (long)nf * nf);
   const unsigned grid = grid_for((long)nf * nf, m.lpn);
   CMG_DISPATCH(T, m, (prolong_add_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(nf, N, e, x, m.lpn)));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int launch_residual_cast(const LevelView<double>& L, Vec3c<double> x, Vec3c<double> f, Vec3<float> r, double s,
+                         const double* sdev, double wy, double* partial, int max_partials, cudaStream_t st) {
+  const SampleMap m = choose_map(L.N, 8, (long)L.n * L.n);
+  const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
+  if ((int)grid > max_partials) return -1;
+  const float wy2 = (float)(wy * wy);
+  using T = double;
+  auto go = [&]() -> cudaError_t {
+    CMG_DISPATCH(T, m, (residual_cast_kernel<V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, r, m.lpn, s, sdev, wy2,
+                                                                             partial)));
+    return cudaGetLastError();
+  };
+  if (go() != cudaSuccess) return -1;
+  count_launches(1);
+  return (int)grid;
+}
+
+cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<double> x, size_t ny, size_t nu,
+                         cudaStream_t st) {
+  const size_t total = 2 * ny + nu;
+  size_t blocks = (total + kBlock - 1) / kBlock;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  axpy3_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(a, adev, e, x, ny, nu);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -99,3 +99,35 @@ def test_set_samples_recomputes_coefficients(H):
         assert torch.equal(a, b)
     h.set_samples(torch.tensor(pr.xi, device="cuda"))
     h2.close()
+
+
+def test_graph_refinement_matches_eager_and_respects_maxit(H):
+    """The FP32 refinement loop runs as a captured graph with a device-side
+    while node; with a profiling window open it runs eagerly instead.  Both
+    enqueue the same kernels in the same order, so iterates and counts agree."""
+    h, P, pr = H
+    f = rhs(h, pr)
+    opts = P.CycleOptions(precision=P.FP32)
+    xg = h.zeros(0)
+    st_g, status = h.solve(opts, f, xg)
+    assert status == 0 and st_g.relres <= 1e-10
+    xe = h.zeros(0)
+    h.profile_begin(1, 0)
+    st_e, status = h.solve(opts, f, xe)
+    h.profile_end()
+    assert status == 0
+    assert st_e.iters == st_g.iters
+    for a, b in zip(xg, xe):
+        assert torch.equal(a, b)
+    # second graph solve from the same buffers reuses the captured graph
+    for t in xg:
+        t.zero_()
+    st_2, status = h.solve(opts, f, xg)
+    assert status == 0 and st_2.iters == st_g.iters
+    for a, b in zip(xg, xe):
+        assert torch.equal(a, b)
+    # the device loop stops at maxit
+    for t in xg:
+        t.zero_()
+    st_1, status = h.solve(opts, f, xg, maxit=2, raise_on_fail=False)
+    assert status == 4 and st_1.iters == 2
