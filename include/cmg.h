@@ -227,6 +227,36 @@ cmg_status cmg_norm(cmg_handle* h, int level, const double* y, const double* u,
 /* Wait for all work enqueued on the handle's stream. */
 cmg_status cmg_sync(cmg_handle* h);
 
+/* ---- batches of independent instances ---------------------------------- */
+
+typedef struct cmg_batch cmg_batch;
+
+/* Create `count` independent instances (own grid size, samples, field,
+ * nu), each as by cmg_create with prob[i] and xi_host[i] (host [N_i][K_i]),
+ * all enqueueing on `stream`.  Errors as cmg_create (nothing is kept). */
+cmg_status cmg_batch_create(const cmg_problem* probs, const double* const* xi_host, int count, void* stream,
+                            cmg_batch** out);
+void cmg_batch_destroy(cmg_batch* b);
+const char* cmg_batch_last_error(const cmg_batch* b);
+/* The i-th instance's handle (owned by the batch) for the level calls. */
+cmg_handle* cmg_batch_instance(cmg_batch* b, int i);
+
+/* Solve every instance to its own tolerance (as cmg_solve with
+ * CMG_METHOD_CYCLE).  Arguments are HOST arrays of `count` DEVICE pointers
+ * (instance i's vectors sized by its own n_i, N_i); stats: host array of
+ * `count`.  With opts->precision == CMG_FP32 all instances run in ONE graph
+ * launch: per instance an independent branch whose device-side while node
+ * runs FP64 refinement around FP32 cycles and stops that instance at its
+ * tolerance or maxit (convergence is decided on the device, instance by
+ * instance); the graph is captured on first use and reused while the
+ * pointers and options stay the same.  Three synchronisations per call.
+ * With CMG_FP64 the instances are solved one after another.
+ * Returns CMG_ERR_NOT_CONVERGED if any instance missed its tolerance
+ * (stats say which), CMG_ERR_NONFINITE if any norm is not finite. */
+cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, double tol, int maxit,
+                           const double* const* fy, const double* const* fu, const double* const* fp,
+                           double* const* y, double* const* u, double* const* p, cmg_stats* stats);
+
 /* ---- measurement ------------------------------------------------------- */
 
 /* Kernel kinds for cmg_profile_begin. */

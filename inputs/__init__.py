@@ -103,3 +103,20 @@ CONFIGS = {
     # large mixed-precision instance, n=1023, N=256, 32 modes, nu=1e-5
     "n1023_N256": dict(n=1023, N=256, K=32, nu=1e-5, amp=1.0, seed=3),
 }
+
+
+def batch_problems(seed: int = 4, count: int = 96, sizes=(63, 127, 255), n_range=(16, 128),
+                   nu_log10=(-6.0, -3.0), K: int = 16, amp: float = 1.0) -> list:
+    """Independent instances for batched solves: instance i uses seed + i for
+    its field draws and its 8-mode target; n uniform on `sizes`, N uniform on
+    [n_range], log10(nu) uniform on [nu_log10]."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        n = int(rng.choice(sizes))
+        N = int(rng.integers(n_range[0], n_range[1] + 1))
+        nu = float(10.0 ** rng.uniform(*nu_log10))
+        pr = make_problem(n=n, N=N, K=K, nu=nu, amp=amp, seed=seed + i, target="modes",
+                          target_seed=10_000 + seed + i)
+        out.append(pr)
+    return out

@@ -76,6 +76,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cmg_profile_begin": (_I, [H, _I, _I]),
         "cmg_profile_end": (_I, [H, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
         "cmg_kernel_launches": (ctypes.c_longlong, []),
+        "cmg_batch_create": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p), _I, _P,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+        "cmg_batch_destroy": (None, [_P]),
+        "cmg_batch_last_error": (ctypes.c_char_p, [_P]),
+        "cmg_batch_instance": (_P, [_P, _I]),
+        "cmg_batch_solve": (_I, [_P, ctypes.POINTER(Cycle), _D, _I] + [ctypes.POINTER(ctypes.c_void_p)] * 6
+                            + [ctypes.POINTER(Stats)]),
         "cmg_solve": (_I, [H, ctypes.POINTER(Cycle), _I, _D, _I, _I, _P, _P, _P, _P, _P, _P,
                            ctypes.POINTER(Stats)]),
     }
@@ -286,3 +293,72 @@ KERNEL_SMOOTH, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_COARSE, 
 def kernel_launches() -> int:
     """Kernels launched by libcmg in this process so far."""
     return int(load_library().cmg_kernel_launches())
+
+
+class Batch:
+    """Independent instances solved together (cmg_batch_*).
+
+    problems: sequence of objects with n, N, xi, nu, amp (e.g.
+    inputs.ProblemSpec).  Vectors are lists of (y, u, p) CUDA float64
+    tensors, one triple per instance, shaped by that instance's n and N.
+    """
+
+    def __init__(self, problems, coarsest_n: int = 3, coarse: str = "averaged", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libcmg needs a CUDA GPU; none is available")
+        self._lib = load_library()
+        self.count = len(problems)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        probs = (Problem * self.count)()
+        self._xi = []
+        for i, pr in enumerate(problems):
+            xi = np.ascontiguousarray(np.asarray(pr.xi, dtype=np.float64))
+            self._xi.append(xi)
+            probs[i] = Problem(pr.n, pr.N, xi.shape[1], pr.nu, pr.amp, coarsest_n, COARSE[coarse])
+        ptrs = (ctypes.c_void_p * self.count)(*[x.ctypes.data for x in self._xi])
+        b = ctypes.c_void_p()
+        st = self._lib.cmg_batch_create(probs, ptrs, self.count, ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(b))
+        if st != CMG_OK:
+            raise CMGError(st, "cmg_batch_create failed")
+        self._b = b
+        self.shapes = [(pr.n, pr.N) for pr in problems]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.cmg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros(self):
+        import torch
+
+        return [(torch.zeros(n * n, N, dtype=torch.float64, device="cuda"),
+                 torch.zeros(n * n, dtype=torch.float64, device="cuda"),
+                 torch.zeros(n * n, N, dtype=torch.float64, device="cuda")) for n, N in self.shapes]
+
+    def solve(self, opts: CycleOptions, fs, xs, tol=1e-10, maxit=100, raise_on_fail=True):
+        import torch
+
+        for (n, N), f, x in zip(self.shapes, fs, xs):
+            for v in (f, x):
+                for t, shape in zip(v, ((n * n, N), (n * n,), (n * n, N))):
+                    if t.dtype != torch.float64 or t.device.type != "cuda" or tuple(t.shape) != shape \
+                            or not t.is_contiguous():
+                        raise ValueError("batch vectors must be contiguous CUDA float64 of the instance's shape")
+        arr = lambda k, vs: (ctypes.c_void_p * self.count)(*[v[k].data_ptr() for v in vs])
+        stats = (Stats * self.count)()
+        c = opts.c()
+        status = self._lib.cmg_batch_solve(self._b, ctypes.byref(c), tol, maxit, arr(0, fs), arr(1, fs),
+                                           arr(2, fs), arr(0, xs), arr(1, xs), arr(2, xs), stats)
+        if raise_on_fail and status != CMG_OK:
+            msg = self._lib.cmg_batch_last_error(self._b)
+            raise CMGError(status, msg.decode() if msg else "")
+        return list(stats), status

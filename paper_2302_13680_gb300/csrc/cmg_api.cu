@@ -632,33 +632,42 @@ bool same_cycle(const cmg_cycle& a, const cmg_cycle& b) {
          a.precision == b.precision && a.tail_n == b.tail_n;
 }
 
-// Capture (once per iterate / right-side pointers and cycle options) the
-// refinement loop: while (go) { e = cycle_FP32(0; r32); x += inv_sc e;
-// r32 = sc (f - S x); control }.
-cmg_status build_ir_graph(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<double> x) {
-  const void* key[6] = {f.y, f.u, f.p, x.y, x.u, x.p};
-  if (h->ir_exec && same_cycle(h->ir_opts, o) && std::equal(key, key + 6, h->ir_key)) return CMG_OK;
-  if (h->ir_exec) {
-    CK(cudaGraphExecDestroy(h->ir_exec));
-    h->ir_exec = nullptr;
-  }
-  if (h->ir_graph) {
-    CK(cudaGraphDestroy(h->ir_graph));
-    h->ir_graph = nullptr;
-  }
+// Sets a loop condition from the state before the first iteration:
+// go = rho > tol_abs and maxit > 0 (state = [sc, inv_sc, rho, it, maxit, tol_abs]).
+__global__ void ir_start_kernel(const double* __restrict__ state, cudaGraphConditionalHandle cond) {
+  const double rho = state[2];
+  cudaGraphSetConditional(cond, (isfinite(rho) && rho > state[5] && state[3] < state[4]) ? 1u : 0u);
+}
+
+// Adds to graph g: [start kernel] -> [while(cond) { e = cycle_FP32(0; r32);
+// x += inv_sc e; r32 = sc (f - S x); control }] for one instance, after the
+// optional dependency dep.  Kernels are captured on the instance's capture
+// stream with all its launches redirected there.
+cmg_status add_ir_loop(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<double> x, cudaGraph_t g) {
   if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-  cudaGraph_t g = nullptr;
-  CK(cudaGraphCreate(&g, 0));
-  h->ir_graph = g;
   cudaGraphConditionalHandle cond;
-  CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+  // start kernel node
+  cudaGraphNode_t start;
+  {
+    cudaKernelNodeParams kp = {};
+    const double* st = h->ir_state;
+    void* args[2] = {(void*)&st, (void*)&cond};
+    kp.func = (void*)ir_start_kernel;
+    kp.gridDim = dim3(1, 1, 1);
+    kp.blockDim = dim3(1, 1, 1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CK(cudaGraphAddKernelNode(&start, g, nullptr, 0, &kp));
+  }
   cudaGraphNodeParams np = {};
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = cond;
   np.conditional.type = cudaGraphCondTypeWhile;
   np.conditional.size = 1;
   cudaGraphNode_t node;
-  CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  CK(cudaGraphAddNode(&node, g, &start, nullptr, 1, &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
   Lev& l0 = h->lv[0];
   const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes;
@@ -690,6 +699,27 @@ cmg_status build_ir_graph(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Ve
   h->stream = user;
   h->prof_kinds = prof;
   if (e != cudaSuccess) return cuda_fail(h, e, "capture of the refinement loop");
+  return CMG_OK;
+}
+
+// The single-instance refinement graph, rebuilt when the iterate / right-side
+// pointers or the cycle options change.
+cmg_status build_ir_graph(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<double> x) {
+  const void* key[6] = {f.y, f.u, f.p, x.y, x.u, x.p};
+  if (h->ir_exec && same_cycle(h->ir_opts, o) && std::equal(key, key + 6, h->ir_key)) return CMG_OK;
+  if (h->ir_exec) {
+    CK(cudaGraphExecDestroy(h->ir_exec));
+    h->ir_exec = nullptr;
+  }
+  if (h->ir_graph) {
+    CK(cudaGraphDestroy(h->ir_graph));
+    h->ir_graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  h->ir_graph = g;
+  const cmg_status s = add_ir_loop(h, o, f, x, g);
+  if (s != CMG_OK) return s;
   cudaGraphExec_t ex = nullptr;
   CK(cudaGraphInstantiate(&ex, g, 0));
   h->ir_exec = ex;
@@ -931,4 +961,178 @@ extern "C" cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method
   }
   if (method == CMG_METHOD_CYCLE) return solve_cycle(h, *opts, tol, maxit, f, x, fnorm, st);
   return solve_fgmres(h, *opts, tol, maxit, restart, f, x, fnorm, st);
+}
+
+// ============================================================================
+// Batched solves: many independent instances in one graph launch.
+struct cmg_batch {
+  std::vector<cmg_handle*> inst;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key;
+  cmg_cycle opts{};
+  std::string err;
+};
+
+namespace {
+
+cmg_status bfail(cmg_batch* b, cmg_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  return st;
+}
+
+#define BCK(call)                                                                                \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      (void)cudaGetLastError();                                                                  \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? CMG_ERR_OOM : CMG_ERR_CUDA,              \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+    }                                                                                            \
+  } while (0)
+
+}  // namespace
+
+extern "C" cmg_status cmg_batch_create(const cmg_problem* probs, const double* const* xi_host, int count,
+                                       void* stream, cmg_batch** out) {
+  if (!out) return CMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!probs || !xi_host || count < 1 || count > 4096) return CMG_ERR_INVALID_ARG;
+  cmg_batch* b = new (std::nothrow) cmg_batch();
+  if (!b) return CMG_ERR_OOM;
+  b->stream = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    cmg_handle* h = nullptr;
+    const cmg_status st = cmg_create(&probs[i], xi_host[i], stream, &h);
+    if (st != CMG_OK) {
+      cmg_batch_destroy(b);
+      return st;
+    }
+    b->inst.push_back(h);
+  }
+  *out = b;
+  return CMG_OK;
+}
+
+extern "C" void cmg_batch_destroy(cmg_batch* b) {
+  if (!b) return;
+  if (b->exec) (void)cudaGraphExecDestroy(b->exec);
+  if (b->graph) (void)cudaGraphDestroy(b->graph);
+  for (cmg_handle* h : b->inst) cmg_destroy(h);
+  delete b;
+}
+
+extern "C" const char* cmg_batch_last_error(const cmg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" cmg_handle* cmg_batch_instance(cmg_batch* b, int i) {
+  return (b && i >= 0 && i < (int)b->inst.size()) ? b->inst[i] : nullptr;
+}
+
+extern "C" cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, double tol, int maxit,
+                                      const double* const* fy, const double* const* fu, const double* const* fp,
+                                      double* const* y, double* const* u, double* const* p, cmg_stats* stats) {
+  if (!b) return CMG_ERR_INVALID_ARG;
+  if (!opts || !fy || !fu || !fp || !y || !u || !p || !stats) return bfail(b, CMG_ERR_INVALID_ARG, "null argument");
+  const int count = (int)b->inst.size();
+  for (int i = 0; i < count; ++i) {
+    if (check_cycle(b->inst[i], opts) != CMG_OK) return bfail(b, CMG_ERR_INVALID_ARG, b->inst[i]->err);
+    if (!vec_ok(fy[i], fu[i], fp[i]) || !vec_ok(y[i], u[i], p[i]))
+      return bfail(b, CMG_ERR_INVALID_ARG, "null vector pointer for instance " + std::to_string(i));
+  }
+  if (!(tol > 0.0) || maxit < 0) return bfail(b, CMG_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 0");
+  if (opts->precision != CMG_FP32) {
+    // FP64 cycles: instance by instance (the batched graph is the FP32 form)
+    cmg_status worst = CMG_OK;
+    for (int i = 0; i < count; ++i) {
+      const cmg_status st = cmg_solve(b->inst[i], opts, CMG_METHOD_CYCLE, tol, maxit, 1, fy[i], fu[i], fp[i], y[i],
+                                      u[i], p[i], &stats[i]);
+      if (st != CMG_OK && worst == CMG_OK) worst = st;
+    }
+    return worst;
+  }
+  // 1. ||W f|| of every instance, one synchronisation
+  for (int i = 0; i < count; ++i) {
+    cmg_handle* h = b->inst[i];
+    BCK(sumsq3(h, 0, fy[i], fu[i], fp[i], h->dsc, paper_wy(h) * paper_wy(h)));
+    BCK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  std::vector<double> fnorm(count);
+  for (int i = 0; i < count; ++i) {
+    fnorm[i] = std::sqrt(b->inst[i]->hsc[0]);
+    if (!std::isfinite(fnorm[i])) return bfail(b, CMG_ERR_NONFINITE, "right side " + std::to_string(i));
+  }
+  // 2. first refinement pass of every instance, one synchronisation
+  for (int i = 0; i < count; ++i) {
+    cmg_handle* h = b->inst[i];
+    stats[i] = cmg_stats{};
+    if (fnorm[i] == 0.0) {
+      BCK(zero_vec<double>(h, 0, Vec3<double>{y[i], u[i], p[i]}));
+      continue;
+    }
+    Vec3<float> f32 = Work<float>::f(h->lv[0]);
+    const int cnt = launch_residual_cast(view<double>(h, 0), Vec3c<double>{y[i], u[i], p[i]},
+                                         Vec3c<double>{fy[i], fu[i], fp[i]}, f32, 1.0 / fnorm[i], nullptr,
+                                         paper_wy(h), h->part, h->part_cap, b->stream);
+    if (cnt < 0) return bfail(b, CMG_ERR_CUDA, "refinement pass launch failed");
+    BCK(launch_finish_sum(h->part, cnt, h->dsc, b->stream));
+    BCK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < count; ++i) {
+    cmg_handle* h = b->inst[i];
+    double* hs = h->hsc;
+    const double rho = fnorm[i] > 0.0 ? std::sqrt(hs[0]) * fnorm[i] : 0.0;
+    stats[i].relres0 = fnorm[i] > 0.0 ? rho / fnorm[i] : 0.0;
+    hs[0] = rho > 0.0 ? 1.0 / rho : 0.0;
+    hs[1] = fnorm[i];
+    hs[2] = rho;
+    hs[3] = 0.0;
+    hs[4] = (double)maxit;
+    hs[5] = tol * fnorm[i];
+    BCK(cudaMemcpyAsync(h->ir_state, hs, 6 * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  }
+  // 3. the graph: one independent branch (start kernel + while loop) per instance
+  std::vector<const void*> key;
+  for (int i = 0; i < count; ++i) {
+    const void* k[6] = {fy[i], fu[i], fp[i], y[i], u[i], p[i]};
+    key.insert(key.end(), k, k + 6);
+  }
+  if (!b->exec || key != b->key || !same_cycle(b->opts, *opts)) {
+    if (b->exec) BCK(cudaGraphExecDestroy(b->exec));
+    if (b->graph) BCK(cudaGraphDestroy(b->graph));
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    BCK(cudaGraphCreate(&g, 0));
+    b->graph = g;
+    for (int i = 0; i < count; ++i) {
+      const cmg_status st = add_ir_loop(b->inst[i], *opts, Vec3c<double>{fy[i], fu[i], fp[i]},
+                                        Vec3<double>{y[i], u[i], p[i]}, g);
+      if (st != CMG_OK) return bfail(b, st, b->inst[i]->err);
+    }
+    cudaGraphExec_t ex = nullptr;
+    BCK(cudaGraphInstantiate(&ex, g, 0));
+    b->exec = ex;
+    b->key = key;
+    b->opts = *opts;
+  }
+  BCK(cudaGraphLaunch(b->exec, b->stream));
+  for (int i = 0; i < count; ++i) {
+    cmg_handle* h = b->inst[i];
+    BCK(cudaMemcpyAsync(h->hsc, h->ir_state, 6 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  cmg_status worst = CMG_OK;
+  for (int i = 0; i < count; ++i) {
+    const double* hs = b->inst[i]->hsc;
+    stats[i].iters = (int)hs[3];
+    stats[i].cycles = (int)hs[3];
+    stats[i].relres = fnorm[i] > 0.0 ? hs[2] / fnorm[i] : 0.0;
+    if (!std::isfinite(hs[2])) worst = CMG_ERR_NONFINITE;
+    else if (fnorm[i] > 0.0 && stats[i].relres > tol && worst == CMG_OK) worst = CMG_ERR_NOT_CONVERGED;
+  }
+  if (worst != CMG_OK) b->err = "some instances did not reach the tolerance";
+  return worst;
 }
