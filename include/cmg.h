@@ -257,6 +257,26 @@ cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, double tol, int 
                            const double* const* fy, const double* const* fu, const double* const* fp,
                            double* const* y, double* const* u, double* const* p, cmg_stats* stats);
 
+/* ---- launch-shape autotuning ------------------------------------------- */
+
+/* Choose, per grid, how many lanes share one node's samples for the node
+ * kernels of `precision` (CMG_FP64 or CMG_FP32): each candidate target of
+ * 1, 2 or 4 sample chunks per lane is timed with CUDA events on a few
+ * red+black half-sweep pairs on the handle's own work vectors, and the
+ * fastest is kept in the handle.  chosen (host, may be NULL) receives the
+ * target per grid (num_levels entries; the coarsest is not tuned: 0).
+ * Synchronises.  Numerical results do not depend on the choice except for
+ * the order of the sample sums (rounding). */
+cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
+/* Set the per-grid targets directly (e.g. from a cache of earlier
+ * cmg_autotune runs): num_levels entries of 0 (size heuristic), 1, 2 or 4;
+ * NULL resets all to 0. */
+cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets);
+
+/* cmg_autotune on every instance of a batch (the batch graph is re-captured
+ * on the next solve). */
+cmg_status cmg_batch_autotune(cmg_batch* b, int precision);
+
 /* ---- measurement ------------------------------------------------------- */
 
 /* Kernel kinds for cmg_profile_begin. */

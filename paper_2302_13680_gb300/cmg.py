@@ -76,6 +76,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cmg_profile_begin": (_I, [H, _I, _I]),
         "cmg_profile_end": (_I, [H, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
         "cmg_kernel_launches": (ctypes.c_longlong, []),
+        "cmg_autotune": (_I, [H, _I, ctypes.POINTER(ctypes.c_int)]),
+        "cmg_set_tuning": (_I, [H, _I, ctypes.POINTER(ctypes.c_int)]),
+        "cmg_batch_autotune": (_I, [_P, _I]),
         "cmg_batch_create": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p), _I, _P,
                                   ctypes.POINTER(ctypes.c_void_p)]),
         "cmg_batch_destroy": (None, [_P]),
@@ -278,6 +281,16 @@ class Hierarchy:
     def sync(self):
         self._check(self._lib.cmg_sync(self._h))
 
+    def autotune(self, precision: int = FP32):
+        """Time 1, 2 and 4 sample chunks per lane on every grid; keep the fastest."""
+        out = (ctypes.c_int * self.levels)()
+        self._check(self._lib.cmg_autotune(self._h, precision, out))
+        return list(out)
+
+    def set_tuning(self, precision: int, targets):
+        arr = None if targets is None else (ctypes.c_int * self.levels)(*targets)
+        self._check(self._lib.cmg_set_tuning(self._h, precision, arr))
+
     def profile_begin(self, kinds: int, level: int = 0):
         self._check(self._lib.cmg_profile_begin(self._h, kinds, level))
 
@@ -336,6 +349,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, precision: int = FP32):
+        st = self._lib.cmg_batch_autotune(self._b, precision)
+        if st != CMG_OK:
+            msg = self._lib.cmg_batch_last_error(self._b)
+            raise CMGError(st, msg.decode() if msg else "")
 
     def zeros(self):
         import torch

@@ -23,6 +23,7 @@ namespace {
 
 struct Lev {
   int n = 0;
+  int spl_target[2] = {0, 0};            // autotuned chunks per lane: [FP64, FP32]
   double h = 0, c = 0, G = 0, d = 0, e = 0;
   size_t nodes = 0;                      // n*n
   double *kx64 = nullptr, *ky64 = nullptr, *inva = nullptr, *isigma = nullptr;
@@ -72,6 +73,7 @@ struct cmg_handle {
   const void* ir_key[6] = {};
   cmg_cycle ir_opts{};
   double* ir_state = nullptr;            // device [sc, inv_sc, rho, it, maxit, tol_abs]
+  long long ir_body_kernels = 0;         // kernels in one iteration of the captured loop body
   // FGMRES workspace
   int gm_cap = 0;
   double* gm = nullptr;       // [2*cap + 2][nt_pad]
@@ -133,12 +135,12 @@ LevelView<T> view(const cmg_handle* h, int l);
 template <>
 LevelView<double> view<double>(const cmg_handle* h, int l) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e};
+  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0]};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e};
+  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1]};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -365,7 +367,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     for (int b = 0; b < 3; ++b) {
       const size_t cnt = (b == 1) ? v.nodes : v.nodes * N;
       AL(v.r64[b], cnt); AL(v.x32[b], cnt); AL(v.f32[b], cnt); AL(v.r32[b], cnt); AL(v.f64[b], cnt);
-      if (l > 0) AL(v.x64[b], cnt);
+      AL(v.x64[b], cnt);
     }
   }
   const size_t g = (size_t)P.n + 2;
@@ -552,6 +554,89 @@ long long cmg_kernel_launches(void) { return cmg::g_launches.load(); }
 
 }  // extern "C"
 
+namespace {
+
+// Time `reps` red+black half-sweep pairs on grid l with chunk target t.
+template <typename T>
+cmg_status time_sweeps(cmg_handle* h, int l, int t, int reps, float* ms) {
+  Lev& v = h->lv[l];
+  const int k = sizeof(T) == 8 ? 0 : 1;
+  const int saved = v.spl_target[k];
+  v.spl_target[k] = t;
+  const LevelView<T> L = view<T>(h, l);
+  Vec3<T> x = Work<T>::x(v), f = Work<T>::f(v);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaSuccess;
+  for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_rbgs_half<T>(L, x, cview(f), w & 1, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    e = launch_rbgs_half<T>(L, x, cview(f), 0, h->stream);
+    if (e == cudaSuccess) e = launch_rbgs_half<T>(L, x, cview(f), 1, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  (void)cudaEventDestroy(e0);
+  (void)cudaEventDestroy(e1);
+  v.spl_target[k] = saved;
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune timing");
+  return CMG_OK;
+}
+
+template <typename T>
+cmg_status autotune_levels(cmg_handle* h, int* chosen) {
+  const int k = sizeof(T) == 8 ? 0 : 1;
+  for (int l = 0; l + 1 < h->L; ++l) {
+    Lev& v = h->lv[l];
+    CK(zero_vec<T>(h, l, Work<T>::x(v)));
+    CK(zero_vec<T>(h, l, Work<T>::f(v)));
+    const int reps = v.n >= 255 ? 4 : 16;
+    float best = 1e30f;
+    int best_t = 0;
+    for (int t = 1; t <= 4; t <<= 1) {
+      float ms = 0.f;
+      const cmg_status s = time_sweeps<T>(h, l, t, reps, &ms);
+      if (s != CMG_OK) return s;
+      if (ms < best) {
+        best = ms;
+        best_t = t;
+      }
+    }
+    v.spl_target[k] = best_t;
+    if (chosen) chosen[l] = best_t;
+  }
+  return CMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  h->ir_opts.n1 = -1;   // captured graphs bake the launch shapes: force a re-capture
+  if (precision == CMG_FP64) return autotune_levels<double>(h, chosen);
+  if (precision == CMG_FP32) return autotune_levels<float>(h, chosen);
+  return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");
+}
+
+cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  if (precision != CMG_FP64 && precision != CMG_FP32) return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");
+  const int k = precision == CMG_FP64 ? 0 : 1;
+  for (int l = 0; l < h->L; ++l) {
+    const int t = spl_targets ? spl_targets[l] : 0;
+    if (t != 0 && t != 1 && t != 2 && t != 4) return fail(h, CMG_ERR_INVALID_ARG, "chunk target must be 0, 1, 2 or 4");
+  }
+  for (int l = 0; l < h->L; ++l) h->lv[l].spl_target[k] = spl_targets ? spl_targets[l] : 0;
+  h->ir_opts.n1 = -1;   // captured graphs bake the launch shapes: force a re-capture
+  return CMG_OK;
+}
+
+}  // extern "C"
+
 // ============================================================================
 // Outer solvers
 namespace {
@@ -678,6 +763,7 @@ cmg_status add_ir_loop(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<
   h->prof_kinds = 0;
   cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   int cnt = -1;
+  const long long k0 = cmg_kernel_launches();
   if (e == cudaSuccess) {
     e = zero_vec<float>(h, 0, x32);
     if (e == cudaSuccess) e = cycle<float>(h, o, 0, x32, cview(f32));
@@ -698,8 +784,18 @@ cmg_status add_ir_loop(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<
   }
   h->stream = user;
   h->prof_kinds = prof;
+  // kernels captured into the body run once per iteration; the launch
+  // counter is advanced by replays (see count_replay), not by the capture
+  h->ir_body_kernels = cmg_kernel_launches() - k0;
+  count_launches((int)-h->ir_body_kernels);
   if (e != cudaSuccess) return cuda_fail(h, e, "capture of the refinement loop");
   return CMG_OK;
+}
+
+// Kernels executed by one replay of an instance's loop: start kernel plus
+// the body per iteration.
+void count_replay(const cmg_handle* h, int iterations) {
+  count_launches((int)(1 + h->ir_body_kernels * iterations));
 }
 
 // The single-instance refinement graph, rebuilt when the iterate / right-side
@@ -782,6 +878,7 @@ cmg_status solve_cycle(cmg_handle* h, const cmg_cycle& o, double tol, int maxit,
       CK(fetch(h, h->ir_state, 6));
       rho = h->hsc[2];
       it = (int)h->hsc[3];
+      count_replay(h, it);
     }
     while (!use_graph && std::isfinite(rho) && rho > tol * fnorm && it < maxit) {
       CK(zero_vec<float>(h, 0, x32));
@@ -1127,6 +1224,7 @@ extern "C" cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, doubl
   cmg_status worst = CMG_OK;
   for (int i = 0; i < count; ++i) {
     const double* hs = b->inst[i]->hsc;
+    count_replay(b->inst[i], (int)hs[3]);
     stats[i].iters = (int)hs[3];
     stats[i].cycles = (int)hs[3];
     stats[i].relres = fnorm[i] > 0.0 ? hs[2] / fnorm[i] : 0.0;
@@ -1135,4 +1233,14 @@ extern "C" cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, doubl
   }
   if (worst != CMG_OK) b->err = "some instances did not reach the tolerance";
   return worst;
+}
+
+extern "C" cmg_status cmg_batch_autotune(cmg_batch* b, int precision) {
+  if (!b) return CMG_ERR_INVALID_ARG;
+  for (cmg_handle* h : b->inst) {
+    const cmg_status st = cmg_autotune(h, precision, nullptr);
+    if (st != CMG_OK) return bfail(b, st, h->err);
+  }
+  b->opts.n1 = -1;   // force a re-capture of the batch graph
+  return CMG_OK;
 }

@@ -46,6 +46,7 @@ struct LevelView {
   const double* inva;   // 1/diag(A_j) per node-sample (FP64 path only)
   const double* isigma; // 1 / Schur denominator of Eq. (13) per node
   double c, G, d, e;    // scalar blocks of Eq. (12): C_j = c I, G, D_j = d I, E_j = e I
+  int spl_target;       // chunks per lane chosen by the autotuner (0 = size heuristic)
 };
 
 // Sample mapping of a node's N samples: lanes-per-node (power of two <= 32),
@@ -62,7 +63,7 @@ struct SampleMap {
 // small grids are latency-bound and use more lanes per node.  items = 0
 // asks for the most lanes (one chunk per lane where N allows).
 constexpr long kMinLanes = 2L * 152 * 256;
-SampleMap choose_map(int N, int elem_bytes, long items);
+SampleMap choose_map(int N, int elem_bytes, long items, int spl_target = 0);
 
 // Coarsest-grid factors (FP64).
 struct CoarseData {

@@ -92,13 +92,14 @@ inline unsigned grid_for(long groups, int lpn) {
 
 }  // namespace
 
-SampleMap choose_map(int N, int elem_bytes, long items) {
+SampleMap choose_map(int N, int elem_bytes, long items, int spl_target) {
   SampleMap m;
   const int vmax = 16 / elem_bytes;     // 2 for double, 4 for float
   m.V = (N % vmax == 0) ? vmax : 1;
   const int chunks = (N + m.V - 1) / m.V;
   int target = 4;
   while (target > 1 && items * chunks / target < kMinLanes) target >>= 1;
+  if (spl_target > 0) target = spl_target;
   const int want = (chunks + target - 1) / target;   // lanes needed at `target` chunks each
   int lpn = 1;
   while (lpn < want && lpn < 32) lpn <<= 1;
@@ -114,7 +115,7 @@ SampleMap choose_map(int N, int elem_bytes, long items) {
 
 template <typename T>
 cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r, cudaStream_t st, double wy) {
-  const SampleMap m = choose_map(L.N, sizeof(T), (long)L.n * L.n);
+  const SampleMap m = choose_map(L.N, sizeof(T), (long)L.n * L.n, L.spl_target);
   const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
   CMG_DISPATCH(T, m, (residual_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, r, m.lpn, (T)wy)));
   count_launches(1);
@@ -123,7 +124,7 @@ cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<
 
 template <typename T>
 cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t st) {
-  const SampleMap m = choose_map(L.N, sizeof(T), colour_count(L.n, colour));
+  const SampleMap m = choose_map(L.N, sizeof(T), colour_count(L.n, colour), L.spl_target);
   const unsigned grid = grid_for(colour_count(L.n, colour), m.lpn);
   CMG_DISPATCH(T, m, (rbgs_half_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, colour, m.lpn)));
   count_launches(1);
@@ -132,7 +133,7 @@ cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int c
 
 template <typename T>
 cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, double theta, cudaStream_t st) {
-  const SampleMap m = choose_map(L.N, sizeof(T), (long)L.n * L.n);
+  const SampleMap m = choose_map(L.N, sizeof(T), (long)L.n * L.n, L.spl_target);
   const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
   CMG_DISPATCH(T, m, (jacobi_update_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(L, x, r, theta, m.lpn)));
   count_launches(1);

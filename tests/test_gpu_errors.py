@@ -131,3 +131,26 @@ def test_graph_refinement_matches_eager_and_respects_maxit(H):
         t.zero_()
     st_1, status = h.solve(opts, f, xg, maxit=2, raise_on_fail=False)
     assert status == 4 and st_1.iters == 2
+
+
+def test_autotune_keeps_results_and_validates(H, tmp_path):
+    h, P, pr = H
+    from paper_2302_13680_gb300 import tuning
+
+    f = rhs(h, pr)
+    opts = P.CycleOptions(precision=P.FP32)
+    x0 = h.zeros(0)
+    st0, _ = h.solve(opts, f, x0)
+    chosen = tuning.apply_or_tune(h, P.FP32, str(tmp_path / "tune.json"))
+    assert len(chosen) == h.levels and chosen[-1] == 0
+    assert all(t in (1, 2, 4) for t in chosen[:-1])
+    again = tuning.apply_or_tune(h, P.FP32, str(tmp_path / "tune.json"))   # from the cache
+    assert again == chosen
+    x1 = h.zeros(0)
+    st1, _ = h.solve(opts, f, x1)
+    assert st1.iters == st0.iters
+    for a, b in zip(x0, x1):
+        assert float((a - b).abs().max() / b.abs().max()) <= 1e-12
+    with pytest.raises(P.CMGError):
+        h.set_tuning(P.FP32, [3] * h.levels)
+    h.set_tuning(P.FP32, None)
