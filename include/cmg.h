@@ -277,6 +277,19 @@ cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets);
  * on the next solve). */
 cmg_status cmg_batch_autotune(cmg_batch* b, int precision);
 
+/* ---- learned warm start: network kernels --------------------------------- */
+
+/* C = A B^T (+ bias[N]) (then max(., 0) if relu) on the 5th-generation
+ * tensor cores: A [M][K] and B [N][K] BF16 row-major (K contiguous), FP32
+ * accumulation in tensor memory; C32 [M][ldc] FP32 and/or C16 [M][ldc]
+ * BF16 outputs (either may be NULL).  K must be a positive multiple of 64;
+ * A, B 16-byte aligned.  status (DEVICE int) is set to 1 if a tensor-core
+ * completion wait exceeded its limit (the output is then incomplete); it is
+ * never cleared by the call.  Enqueued on `stream`.  Used for the
+ * convolution layers of the warm-start network (not part of the paper). */
+cmg_status cmg_nn_gemm_bf16(const void* A, const void* B, int M, int N, int K, const float* bias, int relu,
+                            float* C32, void* C16, int ldc, int* status, void* stream);
+
 /* ---- measurement ------------------------------------------------------- */
 
 /* Kernel kinds for cmg_profile_begin. */

@@ -177,4 +177,9 @@ cudaError_t launch_scale_cast(double a, const Tx* x, Ty* y, size_t n, cudaStream
 cudaError_t launch_rhs(int n, int N, double h, const double* yd, const double* fsrc, double* fy,
                        double* fu, double* fp, cudaStream_t s);
 
+// ---- warm-start network kernels (cmg_nn_*.cu) ----
+// C[M][N] = A[M][K] * B[N][K]^T (+ bias, ReLU) on tcgen05; K % 64 == 0.
+cudaError_t launch_gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const float* bias, int relu,
+                                float* C32, void* C16, int ldc, int* status, cudaStream_t s);
+
 }  // namespace cmg

@@ -1,0 +1,241 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05) for the warm-start
+// network:  C[M][N] = A[M][K] * B[N][K]^T  (+ bias[N], optional ReLU),
+// A and B K-major BF16, FP32 accumulation in tensor memory (TMEM).
+//
+// One CTA of 128 threads computes a 128 x 64 tile of C.  Per K step of 64:
+//   * all threads copy the A (128 x 64) and B (64 x 64) tiles from global
+//     memory into shared memory in the no-swizzle K-major layout of 8-row x
+//     16-byte core matrices (core (r8, k8) at byte (r8 * 8 + k8) * 128),
+//     then make the writes visible to the tensor-core (async) proxy;
+//   * one thread issues four tcgen05.mma (K = 16 each) into the TMEM
+//     accumulator and commits them to an mbarrier;
+//   * all threads wait on the mbarrier (bounded) before the tiles are
+//     overwritten (two shared-memory stages let the next copy overlap).
+// The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+// lanes 32w..32w+31 = rows of the tile), applies bias / ReLU and stores
+// FP32 and/or BF16.
+//
+// Every wait has an iteration limit; on expiry the kernel records an error
+// code, stops issuing work, frees its TMEM columns and returns.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "cmg_internal.h"
+
+namespace cmg {
+namespace nn {
+
+constexpr int kBM = 128, kBN = 64, kBK = 64;
+constexpr int kThreads = 128;
+constexpr int kStages = 2;
+constexpr uint32_t kTmemCols = 64;                 // FP32 accumulator columns (= kBN)
+constexpr long kSpinLimit = 1L << 22;              // mbarrier polls before giving up
+constexpr int kSmemBytes = kStages * (kBM + kBN) * kBK * 2;   // 48 KiB of operand tiles
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading (K
+// direction) and stride (M/N direction) byte offsets, descriptor version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A and B BF16, both
+// K-major, N and M of the MMA.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Wait for phase `parity` of the mbarrier; false if the poll limit expires.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Copy a rows x 64 BF16 tile (row stride ld elements) into the core-matrix
+// layout; rows beyond `valid` read as zero.
+__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, const __nv_bfloat16* src, int rows, int ld,
+                                          int valid, int k0) {
+  // each 16-byte chunk: (row, k8) with k8 in 0..7
+  for (int c = threadIdx.x; c < rows * 8; c += kThreads) {
+    const int row = c >> 3, k8 = c & 7;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (row < valid) v = *reinterpret_cast<const uint4*>(src + (size_t)row * ld + k0 + k8 * 8);
+    const int core = (row >> 3) * 8 + k8;            // core matrices: 8 per 8-row group along K
+    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst) + core * 128 + (row & 7) * 16) = v;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloat16* __restrict__ A,
+                                                                const __nv_bfloat16* __restrict__ B, int M, int N,
+                                                                int K, const float* __restrict__ bias, int relu,
+                                                                float* __restrict__ C32, __nv_bfloat16* __restrict__ C16,
+                                                                int ldc, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char dyn_smem[];   // kSmemBytes: A and B tiles of both stages
+  __nv_bfloat16* sA[kStages];
+  __nv_bfloat16* sB[kStages];
+  for (int s = 0; s < kStages; ++s) {
+    sA[s] = reinterpret_cast<__nv_bfloat16*>(dyn_smem + s * (kBM + kBN) * kBK * 2);
+    sB[s] = sA[s] + kBM * kBK;
+  }
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = instr_desc(kBM, kBN);
+  const int ksteps = K / kBK;
+  uint32_t phase[kStages] = {0, 0};
+
+  for (int ks = 0; ks < ksteps; ++ks) {
+    const int s = ks % kStages;
+    if (ks >= kStages) {
+      // the MMAs that last read this stage must have finished
+      if (!mbar_wait(&bar[s], phase[s])) {
+        if (threadIdx.x == 0) failed = 1;
+      }
+      phase[s] ^= 1;
+    }
+    __syncthreads();
+    if (failed) break;
+    load_tile(sA[s], A + (size_t)m0 * K, kBM, K, M - m0, ks * kBK);
+    load_tile(sB[s], B + (size_t)n0 * K, kBN, K, N - n0, ks * kBK);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        // K = 16 covers two core matrices along K: advance 2 * 128 bytes per step
+        const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
+        const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
+        mma_bf16(tmem, ad, bd, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&bar[s]);
+    }
+  }
+  // Each stage has exactly one commit not yet waited for (its last one); the
+  // i-th commit on a barrier completes phase i, so the last of `uses`
+  // commits has parity (uses - 1) & 1.
+  if (!failed) {
+    for (int s = 0; s < kStages; ++s) {
+      const int uses = (ksteps - s + kStages - 1) / kStages;   // commits made on stage s
+      if (uses > 0 && !mbar_wait(&bar[s], (uint32_t)((uses - 1) & 1))) failed = 1;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+
+  if (!failed) {
+    // epilogue: warp w reads rows 32w + lane, 64 columns in two loads of 32
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + half * 32 + j;
+          if (col < N) {
+            float v = __uint_as_float(r[j]);
+            if (bias) v += bias[col];
+            if (relu) v = fmaxf(v, 0.f);
+            if (C32) C32[(size_t)row * ldc + col] = v;
+            if (C16) C16[(size_t)row * ldc + col] = __float2bfloat16_rn(v);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+  if (failed && threadIdx.x == 0) atomicExch(status, 1);
+}
+
+}  // namespace nn
+
+cudaError_t launch_gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const float* bias, int relu,
+                                float* C32, void* C16, int ldc, int* status, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(nn::gemm_bf16_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               nn::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((M + nn::kBM - 1) / nn::kBM, (N + nn::kBN - 1) / nn::kBN);
+  nn::gemm_bf16_tn_kernel<<<grid, nn::kThreads, nn::kSmemBytes, s>>>(
+      static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), M, N, K, bias, relu, C32,
+      static_cast<__nv_bfloat16*>(C16), ldc, status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace cmg
