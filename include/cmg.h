@@ -90,6 +90,12 @@ typedef struct {
                        grid.  Same arithmetic either way.  Ignored (one launch per step)
                        when N needs more than 4 chunks per lane or the coarsest grid
                        is 7 x 7. */
+  int freeze_u;     /* 1: keep the control fixed: each node solves only its state and
+                       adjoint rows for the current u_i (Eq. (14) with u_i given instead
+                       of zero) and the coarse corrections of u are zero.  Cycles then
+                       solve the 2N PDEs for a given control (used to complete a
+                       predicted control into a consistent initial iterate); 0 = the
+                       collective smoother of Eq. (13). */
 } cmg_cycle;
 
 /* Solve statistics filled by cmg_solve. */
@@ -123,6 +129,10 @@ void cmg_destroy(cmg_handle* h);
 const char* cmg_last_error(const cmg_handle* h);
 int cmg_num_levels(const cmg_handle* h);
 int cmg_level_n(const cmg_handle* h, int level);   /* -1 if out of range */
+
+/* Mean over samples of log kappa_j at the finest grid's n*n interior nodes
+ * (DEVICE out[n*n], FP64); an input of the warm-start network. */
+cmg_status cmg_mean_log_kappa(cmg_handle* h, double* out);
 
 /* ---- right-hand side -------------------------------------------------- */
 
@@ -287,8 +297,57 @@ cmg_status cmg_batch_autotune(cmg_batch* b, int precision);
  * completion wait exceeded its limit (the output is then incomplete); it is
  * never cleared by the call.  Enqueued on `stream`.  Used for the
  * convolution layers of the warm-start network (not part of the paper). */
-cmg_status cmg_nn_gemm_bf16(const void* A, const void* B, int M, int N, int K, const float* bias, int relu,
-                            float* C32, void* C16, int ldc, int* status, void* stream);
+cmg_status cmg_nn_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int M, int N, int K,
+                            const float* bias, int relu, float* C32, void* C16, int ldc, int* status,
+                            void* stream);
+
+/* Layer kernels (activations NHWC BF16 [B][H][W][C]; weights [Cout][9 Cin]
+ * BF16, column t*Cin + c for tap t = 3 dy + dx; all DEVICE pointers,
+ * enqueued on `stream`; CMG_ERR_INVALID_ARG on null pointers or sizes out
+ * of range, nothing enqueued):
+ *   im2col      3x3 patches [B*H*W][9C] (transposed = 1: [9C][B*H*W]), zero
+ *               outside the image; C a multiple of 8;
+ *   col2im      data gradient dX from patch gradients dcol [B*H*W][9C] FP32;
+ *   transpose   BF16 [R][Cc] -> [Cc][R];
+ *   relu_bwd    dz = dy where y > 0 else 0;
+ *   avgpool     2x2 mean (backward = 1: spread dY/4 over [B][H][W][C]);
+ *   upsample_add  Y = nearest 2x upsampling of X [B][H/2][W/2][C] plus S;
+ *   upsample_bwd  dX [B][H][W][C] = sum over each 2x2 block of dY;
+ *   add, to_bf16, sum_slices (fixed-order sum of split-K partials), colsum
+ *               (per-channel sums, bias gradients);
+ *   mse         masked mean squared error on the interior m x m of [B][S][S]
+ *               FP32 images: BF16 gradient and per-CTA partial sums;
+ *   adamw       AdamW step on FP32 master weights, BF16 copy refreshed;
+ *   pack_input / pack_target / unpack_output  between solver grids
+ *               ([B][n*n] FP64) and S x S network images. */
+/* Split-K form of cmg_nn_gemm_bf16 for long reductions (weight gradients):
+ * slice z of ksplit reads columns [z Kslice, (z+1) Kslice) of A and B and
+ * writes the FP32 partial product to partials + z*M*ldc (sum the slices
+ * with cmg_nn_sum_slices). */
+cmg_status cmg_nn_gemm_bf16_splitk(const void* A, long long lda, const void* B, long long ldb, int M, int N,
+                                   int Kslice, int ksplit, float* partials, int ldc, int* status, void* stream);
+/*   outer       out[p][c] = a[p] w[c] (data gradient of a 1x1 convolution to one channel). */
+cmg_status cmg_nn_outer(const void* a, const float* w, void* out, long long P, int C, void* stream);
+cmg_status cmg_nn_im2col(const void* X, void* col, int B, int H, int W, int C, int transposed, void* stream);
+cmg_status cmg_nn_col2im(const float* dcol, void* dX, int B, int H, int W, int C, void* stream);
+cmg_status cmg_nn_transpose(const void* in, void* out, long long R, long long Cc, void* stream);
+cmg_status cmg_nn_relu_bwd(const void* y, const void* dy, void* dz, long long n, void* stream);
+cmg_status cmg_nn_avgpool(const void* X, void* Y, int B, int H, int W, int C, int backward, void* stream);
+cmg_status cmg_nn_upsample_add(const void* X, const void* S, void* Y, int B, int H, int W, int C, void* stream);
+cmg_status cmg_nn_upsample_bwd(const void* dY, void* dX, int B, int H, int W, int C, void* stream);
+cmg_status cmg_nn_add(const void* a, const void* b, void* out, long long n, void* stream);
+cmg_status cmg_nn_to_bf16(const float* in, void* out, long long n, void* stream);
+cmg_status cmg_nn_sum_slices(const float* part, int slices, float* out, long long n, void* stream);
+cmg_status cmg_nn_colsum(const void* in, long long P, int C, float* out, void* stream);
+cmg_status cmg_nn_mse(const float* pred, const float* tgt, int B, int S, int m, void* grad, float* partial,
+                      int max_partials, int* used_partials, void* stream);
+cmg_status cmg_nn_adamw(float* w, const float* g, float* m1, float* m2, void* w16, long long n, float lr,
+                        float b1, float b2, float eps, float wd, int step, void* stream);
+cmg_status cmg_nn_pack_input(const double* f0, const double* f1, int B, int n, int S, int Cp, float s0,
+                             float s1, void* X, void* stream);
+cmg_status cmg_nn_unpack_output(const float* img, int B, int n, int S, double scale, double* out,
+                                void* stream);
+cmg_status cmg_nn_pack_target(const double* u, int B, int n, int S, double scale, float* img, void* stream);
 
 /* ---- measurement ------------------------------------------------------- */
 

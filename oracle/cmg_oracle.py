@@ -269,7 +269,16 @@ def colour_mask(n: int, colour: int) -> np.ndarray:
     return (ix + iy) % 2 == colour
 
 
-def rbgs_half_sweep(level: Level, x, f, colour: int):
+def local_solve_fixed_u(b_p, u, b_y, a, c, e):
+    """Eq. (14) with a given control u_i (the paper sets u_i = 0 at nodes
+    without a control dof): y~ = diag(a)^-1 (b_y - e u), p~ = diag(a)^-1 (b_p - c y~)."""
+    ainv = 1.0 / a
+    y = ainv * (b_y - e * u[..., None])
+    p = ainv * (b_p - c * y)
+    return y, p
+
+
+def rbgs_half_sweep(level: Level, x, f, colour: int, freeze_u: bool = False):
     """Collective GS on all nodes of one colour.
 
     Nodes of one colour couple only to nodes of the other colour, so each
@@ -282,15 +291,19 @@ def rbgs_half_sweep(level: Level, x, f, colour: int):
     b_p = (fy + offdiag_sum(level, p))[m]      # first block row: c y + A p = f_y
     b_y = (fp + offdiag_sum(level, y))[m]      # last block row:  A y + e u = f_p
     b_u = fu[m]                                # control row has no neighbour coupling
+    if freeze_u:
+        yn, pn = local_solve_fixed_u(b_p, u[m], b_y, level.a[m], level.c, level.e)
+        y[m], p[m] = yn, pn
+        return y, u, p
     yn, un, pn = local_solve(b_p, b_u, b_y, level.a[m], level.c, level.G, level.d, level.e)
     y[m], u[m], p[m] = yn, un, pn
     return y, u, p
 
 
-def rbgs_sweep(level: Level, x, f):
+def rbgs_sweep(level: Level, x, f, freeze_u: bool = False):
     """One red-black collective GS sweep: red (ix+iy even) first, then black."""
-    x = rbgs_half_sweep(level, x, f, 0)
-    return rbgs_half_sweep(level, x, f, 1)
+    x = rbgs_half_sweep(level, x, f, 0, freeze_u)
+    return rbgs_half_sweep(level, x, f, 1, freeze_u)
 
 
 def lexgs_sweep(level: Level, x, f):
@@ -324,9 +337,12 @@ def lexgs_sweep(level: Level, x, f):
     return y, u, p
 
 
-def jacobi_sweep(level: Level, x, f, theta: float):
+def jacobi_sweep(level: Level, x, f, theta: float, freeze_u: bool = False):
     """Damped collective Jacobi, Eq. (11): x <- x + theta sum_i P_i S~_i^{-1} R_i (f - S x)."""
     ry, ru, rp = residual(level, x, f)
+    if freeze_u:
+        dy, dp = local_solve_fixed_u(ry, np.zeros_like(ru), rp, level.a, level.c, level.e)
+        return x[0] + theta * dy, x[1], x[2] + theta * dp
     dy, du, dp = local_solve(ry, ru, rp, level.a, level.c, level.G, level.d, level.e)
     return x[0] + theta * dy, x[1] + theta * du, x[2] + theta * dp
 
@@ -338,16 +354,19 @@ class CycleOptions:
     n1: int = 2                   # pre-smoothing steps
     n2: int = 2                   # post-smoothing steps
     gamma: int = 1                # 1 = V-cycle, 2 = W-cycle
+    freeze_u: bool = False        # keep u fixed: solve the state and adjoint rows only
 
 
 def smooth(level: Level, x, f, steps: int, opts: CycleOptions):
     for _ in range(steps):
         if opts.smoother == "rbgs":
-            x = rbgs_sweep(level, x, f)
+            x = rbgs_sweep(level, x, f, opts.freeze_u)
         elif opts.smoother == "lexgs":
+            if opts.freeze_u:
+                raise ValueError("frozen control is defined for the red-black and Jacobi smoothers")
             x = lexgs_sweep(level, x, f)
         elif opts.smoother == "jacobi":
-            x = jacobi_sweep(level, x, f, opts.theta)
+            x = jacobi_sweep(level, x, f, opts.theta, opts.freeze_u)
         else:
             raise ValueError(opts.smoother)
     return x
@@ -413,6 +432,19 @@ def dense_A(level: Level, j: int) -> np.ndarray:
         v.reshape(m, level.N)[col, j] = 1.0
         A[:, col] = apply_A(level, v)[:, :, j].reshape(m)
     return A
+
+
+def coarse_solve_fixed_u(level: Level, f):
+    """Coarsest solve of the correction equation with a zero control
+    correction: y_j = A_j^{-1} f_p,j, p_j = A_j^{-1} (f_y,j - c y_j), u = 0."""
+    n, N = level.n, level.N
+    y = np.zeros((n, n, N))
+    p = np.zeros((n, n, N))
+    for j in range(N):
+        A = dense_A(level, j)
+        y[:, :, j] = np.linalg.solve(A, f[2][:, :, j].ravel()).reshape(n, n)
+        p[:, :, j] = np.linalg.solve(A, (f[0][:, :, j] - level.c * y[:, :, j]).ravel()).reshape(n, n)
+    return y, np.zeros((n, n)), p
 
 
 def coarse_solve(level: Level, f):
@@ -483,6 +515,10 @@ def cycle(levels, l: int, x, f, opts: CycleOptions):
     """Algorithm 1 (V-cycle; gamma = 2 recursive calls gives the W-cycle)."""
     level = levels[l]
     if l == len(levels) - 1:
+        if opts.freeze_u:
+            # the correction keeps u: x + (y, 0, p) with the coarsest PDEs solved for it
+            ey, _, ep = coarse_solve_fixed_u(level, residual(level, x, f))
+            return x[0] + ey, x[1], x[2] + ep
         return coarse_solve(level, f)
     x = smooth(level, x, f, opts.n1, opts)
     r = residual(level, x, f)

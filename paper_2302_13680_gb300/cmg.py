@@ -40,7 +40,7 @@ class Problem(ctypes.Structure):
 class Cycle(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("theta", ctypes.c_double), ("n1", ctypes.c_int),
                 ("n2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
-                ("tail_n", ctypes.c_int)]
+                ("tail_n", ctypes.c_int), ("freeze_u", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cmg_rhs": (_I, [H, _P, _P, _P, _P, _P]),
         "cmg_norm": (_I, [H, _I, _P, _P, _P, ctypes.POINTER(_D)]),
         "cmg_sync": (_I, [H]),
+        "cmg_mean_log_kappa": (_I, [H, _P]),
         "cmg_profile_begin": (_I, [H, _I, _I]),
         "cmg_profile_end": (_I, [H, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
         "cmg_kernel_launches": (ctypes.c_longlong, []),
@@ -113,9 +114,11 @@ class CycleOptions:
     gamma: int = 1
     precision: int = FP64
     tail_n: int = 31          # grids with n <= tail_n run as one cluster launch; 0 = off
+    freeze_u: int = 0         # 1: keep u fixed, solve the state and adjoint rows only
 
     def c(self) -> Cycle:
-        return Cycle(self.smoother, self.theta, self.n1, self.n2, self.gamma, self.precision, self.tail_n)
+        return Cycle(self.smoother, self.theta, self.n1, self.n2, self.gamma, self.precision, self.tail_n,
+                     self.freeze_u)
 
 
 def _ptr(t):
@@ -280,6 +283,13 @@ class Hierarchy:
 
     def sync(self):
         self._check(self._lib.cmg_sync(self._h))
+
+    def mean_log_kappa(self, out=None):
+        import torch
+
+        out = torch.empty(self.n * self.n, dtype=torch.float64, device=self.device) if out is None else out
+        self._check(self._lib.cmg_mean_log_kappa(self._h, _ptr(out)))
+        return out
 
     def autotune(self, precision: int = FP32):
         """Time 1, 2 and 4 sample chunks per lane on every grid; keep the fastest."""

@@ -131,16 +131,16 @@ struct ProfScope {
 };
 
 template <typename T>
-LevelView<T> view(const cmg_handle* h, int l);
+LevelView<T> view(const cmg_handle* h, int l, int freeze_u = 0);
 template <>
-LevelView<double> view<double>(const cmg_handle* h, int l) {
+LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0]};
+  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0], freeze_u};
 }
 template <>
-LevelView<float> view<float>(const cmg_handle* h, int l) {
+LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1]};
+  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1], freeze_u};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -171,7 +171,7 @@ cudaError_t setup_coefficients(cmg_handle* h) {
 
 template <typename T>
 cudaError_t smooth(cmg_handle* h, const cmg_cycle& o, int l, int sweeps, Vec3<T> x, Vec3c<T> f) {
-  const LevelView<T> L = view<T>(h, l);
+  const LevelView<T> L = view<T>(h, l, o.freeze_u);
   for (int s = 0; s < sweeps; ++s) {
     if (o.smoother == CMG_SMOOTH_RBGS) {
       for (int colour = 0; colour < 2; ++colour) {
@@ -217,7 +217,7 @@ cudaError_t tail_cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3
   P.nlev = nlev;
   for (int k = 0; k < nlev; ++k) {
     Lev& v = h->lv[l + k];
-    P.lev[k].L = view<T>(h, l + k);
+    P.lev[k].L = view<T>(h, l + k, o.freeze_u);
     P.lev[k].r = Work<T>::r(v);
     if (k == 0) {
       P.lev[k].x = x;
@@ -232,6 +232,7 @@ cudaError_t tail_cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3
   P.n2 = o.n2;
   P.gamma = o.gamma;
   P.theta = o.theta;
+  P.freeze_u = o.freeze_u;
   P.lpn = choose_map(h->prob.N, sizeof(T), 0).lpn;
   P.cm = h->coarse.m;
   P.cN = h->coarse.N;
@@ -256,7 +257,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   }
   if (l == h->L - 1) {
     ProfScope ps(h, CMG_KERNEL_COARSE, l);
-    return launch_coarse_solve<T>(h->coarse, v.c, v.d, v.e, f, x, h->stream);
+    return launch_coarse_solve<T>(h->coarse, v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
   }
   cudaError_t e = smooth<T>(h, o, l, o.n1, x, f);
   if (e != cudaSuccess) return e;
@@ -290,6 +291,8 @@ cmg_status check_cycle(cmg_handle* h, const cmg_cycle* o) {
   if (o->gamma < 1 || o->gamma > 2) return fail(h, CMG_ERR_INVALID_ARG, "gamma must be 1 or 2");
   if (o->precision != CMG_FP64 && o->precision != CMG_FP32) return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");
   if (o->tail_n < 0) return fail(h, CMG_ERR_INVALID_ARG, "tail_n must be >= 0");
+  if (o->freeze_u != 0 && o->freeze_u != 1) return fail(h, CMG_ERR_INVALID_ARG, "freeze_u must be 0 or 1");
+  if (o->freeze_u && h && h->L < 2) return fail(h, CMG_ERR_INVALID_ARG, "freeze_u needs at least two grids");
   if (o->smoother == CMG_SMOOTH_JACOBI && !(o->theta > 0.0 && o->theta <= 1.0))
     return fail(h, CMG_ERR_INVALID_ARG, "theta must be in (0, 1]");
   return CMG_OK;
@@ -515,6 +518,13 @@ cmg_status cmg_norm(cmg_handle* h, int level, const double* y, const double* u, 
   return CMG_OK;
 }
 
+cmg_status cmg_mean_log_kappa(cmg_handle* h, double* out) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  if (!out) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");
+  CK(launch_mean_log_kappa(h->prob.n, h->prob.N, h->prob.K, h->prob.amp, h->xi, out, h->stream));
+  return CMG_OK;
+}
+
 cmg_status cmg_sync(cmg_handle* h) {
   if (!h) return CMG_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize(h->stream));
@@ -714,7 +724,7 @@ __global__ void ir_control_kernel(const double* __restrict__ partial, int count,
 
 bool same_cycle(const cmg_cycle& a, const cmg_cycle& b) {
   return a.smoother == b.smoother && a.theta == b.theta && a.n1 == b.n1 && a.n2 == b.n2 && a.gamma == b.gamma &&
-         a.precision == b.precision && a.tail_n == b.tail_n;
+         a.precision == b.precision && a.tail_n == b.tail_n && a.freeze_u == b.freeze_u;
 }
 
 // Sets a loop condition from the state before the first iteration:

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_b(int m, int N, i
                                                                 double e, const T* __restrict__ fu,
                                                                 const double* __restrict__ wz,
                                                                 const double* __restrict__ partial, T* __restrict__ y,
-                                                                T* __restrict__ u, T* __restrict__ p) {
+                                                                T* __restrict__ u, T* __restrict__ p, int freeze_u) {
   __shared__ double rhs[MM], us[MM];
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     double s = 0.0;
@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_b(int m, int N, i
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     double s = 0.0;
-    for (int k = 0; k < m; ++k) s += Minv[r * m + k] * rhs[k];
+    if (!freeze_u)   // frozen control: zero correction of u, state and adjoint solved for it
+      for (int k = 0; k < m; ++k) s += Minv[r * m + k] * rhs[k];
     us[r] = s;
     if (blockIdx.x == 0) u[r] = (T)s;
   }
@@ -215,11 +216,11 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_b(int m, int N, i
 
 template <typename T, int MM>
 cudaError_t coarse_solve_mm(const CoarseData& C, double c, double d, double e, Vec3c<T> f, Vec3<T> x,
-                            cudaStream_t s) {
+                            cudaStream_t s, int freeze_u) {
   const int nblk = (C.N + kCoarseThreads - 1) / kCoarseThreads;
   coarse_solve_a<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, C.Ainv, c, f.y, f.p, C.wz, C.partial);
   coarse_solve_b<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, nblk, C.Ainv, C.Minv, c, d, e, f.u, C.wz,
-                                                         C.partial, x.y, x.u, x.p);
+                                                         C.partial, x.y, x.u, x.p, freeze_u);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -228,10 +229,10 @@ cudaError_t coarse_solve_mm(const CoarseData& C, double c, double d, double e, V
 
 template <typename T>
 cudaError_t launch_coarse_solve(const CoarseData& C, double c, double d, double e, Vec3c<T> f, Vec3<T> x,
-                                cudaStream_t s) {
-  if (C.m == 1) return coarse_solve_mm<T, 1>(C, c, d, e, f, x, s);
-  if (C.m == 9) return coarse_solve_mm<T, 9>(C, c, d, e, f, x, s);
-  if (C.m == 49) return coarse_solve_mm<T, 49>(C, c, d, e, f, x, s);
+                                cudaStream_t s, int freeze_u) {
+  if (C.m == 1) return coarse_solve_mm<T, 1>(C, c, d, e, f, x, s, freeze_u);
+  if (C.m == 9) return coarse_solve_mm<T, 9>(C, c, d, e, f, x, s, freeze_u);
+  if (C.m == 49) return coarse_solve_mm<T, 49>(C, c, d, e, f, x, s, freeze_u);
   return cudaErrorInvalidValue;
 }
 
@@ -247,8 +248,8 @@ cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const dou
 }
 
 template cudaError_t launch_coarse_solve<double>(const CoarseData&, double, double, double, Vec3c<double>,
-                                                 Vec3<double>, cudaStream_t);
+                                                 Vec3<double>, cudaStream_t, int);
 template cudaError_t launch_coarse_solve<float>(const CoarseData&, double, double, double, Vec3c<float>,
-                                                Vec3<float>, cudaStream_t);
+                                                Vec3<float>, cudaStream_t, int);
 
 }  // namespace cmg

@@ -47,6 +47,7 @@ struct LevelView {
   const double* isigma; // 1 / Schur denominator of Eq. (13) per node
   double c, G, d, e;    // scalar blocks of Eq. (12): C_j = c I, G, D_j = d I, E_j = e I
   int spl_target;       // chunks per lane chosen by the autotuner (0 = size heuristic)
+  int freeze_u;         // 1: keep u fixed (local solves of the state and adjoint rows only)
 };
 
 // Sample mapping of a node's N samples: lanes-per-node (power of two <= 32),
@@ -106,6 +107,7 @@ struct TailParams {
   TailLevel<T> lev[kTailMax];
   int smoother, n1, n2, gamma;
   double theta;
+  int freeze_u;                    // coarsest solve with a zero control correction
   int lpn;                         // lanes per node (SampleMap of N)
   // coarsest grid (CoarseData) and its blocks c, d, e
   int cm, cN;
@@ -136,7 +138,7 @@ cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<doub
 // ---- coarsest grid (cmg_coarse.cu) ----
 template <typename T>
 cudaError_t launch_coarse_solve(const CoarseData& C, double c, double d, double e,
-                                Vec3c<T> f, Vec3<T> x, cudaStream_t s);
+                                Vec3c<T> f, Vec3<T> x, cudaStream_t s, int freeze_u = 0);
 cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const double* ky,
                                 double c, double G, double d, double e, cudaStream_t s);
 
@@ -178,8 +180,15 @@ cudaError_t launch_rhs(int n, int N, double h, const double* yd, const double* f
                        double* fu, double* fp, cudaStream_t s);
 
 // ---- warm-start network kernels (cmg_nn_*.cu) ----
-// C[M][N] = A[M][K] * B[N][K]^T (+ bias, ReLU) on tcgen05; K % 64 == 0.
-cudaError_t launch_gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const float* bias, int relu,
-                                float* C32, void* C16, int ldc, int* status, cudaStream_t s);
+// mean over samples of log kappa_j at the n x n interior nodes of the finest grid.
+cudaError_t launch_mean_log_kappa(int n, int N, int K, double amp, const double* xi, double* out, cudaStream_t s);
+
+// C[M][N] = A[M][K] * B[N][K]^T (+ bias, ReLU) on tcgen05; row strides lda,
+// ldb; K % 8 == 0.
+// ksplit > 1: K is the slice length, slice z reads columns z*K.. and writes
+// C32 + z*M*ldc (FP32 partials, no bias / ReLU / C16).
+cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb, int M, int N, int K,
+                                const float* bias, int relu, float* C32, void* C16, int ldc, int* status,
+                                cudaStream_t s, int ksplit = 1);
 
 }  // namespace cmg

@@ -190,8 +190,11 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
   }
   const double tsum = group_sum((double)tacc, lpn);
   if (valid) {
-    const double uu = ((double)ld1<T, CG>(f.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
-    if (lane == 0) x.u[node] = (T)uu;
+    // frozen control: u_i keeps its value and only the state and adjoint
+    // rows are solved (Eq. (14) with u_i given instead of zero)
+    const double uu = L.freeze_u ? (double)ld1<T, CG>(x.u + node)
+                                 : ((double)ld1<T, CG>(f.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
+    if (lane == 0 && !L.freeze_u) x.u[node] = (T)uu;
     const T uT = (T)uu, e = (T)L.e;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {
@@ -243,7 +246,8 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   }
   const double tsum = group_sum((double)tacc, lpn);
   if (valid) {
-    const double du = ((double)ld1<T, CG>(r.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
+    const double du =
+        L.freeze_u ? 0.0 : ((double)ld1<T, CG>(r.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
     if (lane == 0) x.u[node] = (T)((double)ld1<T, CG>(x.u + node) + theta * du);
     const T duT = (T)du, e = (T)L.e, th = (T)theta;
 #pragma unroll

@@ -10,13 +10,32 @@ namespace {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 }  // namespace
 
-extern "C" cmg_status cmg_nn_gemm_bf16(const void* A, const void* B, int M, int N, int K, const float* bias,
-                                       int relu, float* C32, void* C16, int ldc, int* status, void* stream) {
+extern "C" cmg_status cmg_nn_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int M, int N, int K,
+                                       const float* bias, int relu, float* C32, void* C16, int ldc, int* status,
+                                       void* stream) {
   if (!A || !B || !status || (!C32 && !C16)) return CMG_ERR_INVALID_ARG;
-  if (M < 1 || N < 1 || K < 64 || K % 64 != 0 || ldc < N) return CMG_ERR_INVALID_ARG;
+  if (M < 1 || N < 1 || K < 8 || K % 8 != 0 || ldc < N || lda < K || ldb < K || lda % 8 || ldb % 8)
+    return CMG_ERR_INVALID_ARG;
   if (!aligned16(A) || !aligned16(B)) return CMG_ERR_INVALID_ARG;
-  const cudaError_t e = launch_gemm_bf16_tn(A, B, M, N, K, bias, relu, C32, C16, ldc, status,
+  const cudaError_t e = launch_gemm_bf16_tn(A, lda, B, ldb, M, N, K, bias, relu, C32, C16, ldc, status,
                                             static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return CMG_ERR_CUDA;
+  }
+  return CMG_OK;
+}
+
+extern "C" cmg_status cmg_nn_gemm_bf16_splitk(const void* A, long long lda, const void* B, long long ldb, int M,
+                                              int N, int Kslice, int ksplit, float* partials, int ldc, int* status,
+                                              void* stream) {
+  if (!A || !B || !status || !partials) return CMG_ERR_INVALID_ARG;
+  if (M < 1 || N < 1 || Kslice < 8 || Kslice % 8 || ksplit < 1 || ksplit > 65535 || ldc < N || lda % 8 || ldb % 8 ||
+      lda < (long long)Kslice * ksplit || ldb < (long long)Kslice * ksplit)
+    return CMG_ERR_INVALID_ARG;
+  if (!aligned16(A) || !aligned16(B)) return CMG_ERR_INVALID_ARG;
+  const cudaError_t e = launch_gemm_bf16_tn(A, lda, B, ldb, M, N, Kslice, nullptr, 0, partials, nullptr, ldc, status,
+                                            static_cast<cudaStream_t>(stream), ksplit);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return CMG_ERR_CUDA;

@@ -2,6 +2,8 @@
 // network:  C[M][N] = A[M][K] * B[N][K]^T  (+ bias[N], optional ReLU),
 // A and B K-major BF16, FP32 accumulation in tensor memory (TMEM).
 //
+// A and B have row strides lda, ldb (elements, multiples of 8); K % 8 == 0
+// (the last K step is zero-filled).
 // One CTA of 128 threads computes a 128 x 64 tile of C.  Per K step of 64:
 //   * all threads copy the A (128 x 64) and B (64 x 64) tiles from global
 //     memory into shared memory in the no-swizzle K-major layout of 8-row x
@@ -88,22 +90,22 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 // Copy a rows x 64 BF16 tile (row stride ld elements) into the core-matrix
-// layout; rows beyond `valid` read as zero.
-__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, const __nv_bfloat16* src, int rows, int ld,
-                                          int valid, int k0) {
+// layout; rows beyond `valid` and columns beyond K read as zero (K % 8 == 0).
+__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, const __nv_bfloat16* src, int rows, long ld,
+                                          int valid, int k0, int K) {
   // each 16-byte chunk: (row, k8) with k8 in 0..7
   for (int c = threadIdx.x; c < rows * 8; c += kThreads) {
     const int row = c >> 3, k8 = c & 7;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (row < valid) v = *reinterpret_cast<const uint4*>(src + (size_t)row * ld + k0 + k8 * 8);
+    if (row < valid && k0 + k8 * 8 < K) v = *reinterpret_cast<const uint4*>(src + (size_t)row * ld + k0 + k8 * 8);
     const int core = (row >> 3) * 8 + k8;            // core matrices: 8 per 8-row group along K
     *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst) + core * 128 + (row & 7) * 16) = v;
   }
 }
 
-__global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloat16* __restrict__ A,
-                                                                const __nv_bfloat16* __restrict__ B, int M, int N,
-                                                                int K, const float* __restrict__ bias, int relu,
+__global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloat16* __restrict__ A, long lda,
+                                                                const __nv_bfloat16* __restrict__ B, long ldb, int M,
+                                                                int N, int K, const float* __restrict__ bias, int relu,
                                                                 float* __restrict__ C32, __nv_bfloat16* __restrict__ C16,
                                                                 int ldc, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dyn_smem[];   // kSmemBytes: A and B tiles of both stages
@@ -119,6 +121,11 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  // split-K: slice z covers K columns [z*K, (z+1)*K) of the full operands and
+  // writes its own FP32 partial matrix
+  A += (size_t)blockIdx.z * K;
+  B += (size_t)blockIdx.z * K;
+  if (C32) C32 += (size_t)blockIdx.z * M * ldc;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = instr_desc(kBM, kBN);
-  const int ksteps = K / kBK;
+  const int ksteps = (K + kBK - 1) / kBK;
   uint32_t phase[kStages] = {0, 0};
 
   for (int ks = 0; ks < ksteps; ++ks) {
@@ -150,8 +157,8 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
     }
     __syncthreads();
     if (failed) break;
-    load_tile(sA[s], A + (size_t)m0 * K, kBM, K, M - m0, ks * kBK);
-    load_tile(sB[s], B + (size_t)n0 * K, kBN, K, N - n0, ks * kBK);
+    load_tile(sA[s], A + (size_t)m0 * lda, kBM, lda, M - m0, ks * kBK, K);
+    load_tile(sB[s], B + (size_t)n0 * ldb, kBN, ldb, N - n0, ks * kBK, K);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -221,8 +228,9 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
 
 }  // namespace nn
 
-cudaError_t launch_gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const float* bias, int relu,
-                                float* C32, void* C16, int ldc, int* status, cudaStream_t s) {
+cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb, int M, int N, int K,
+                                const float* bias, int relu, float* C32, void* C16, int ldc, int* status,
+                                cudaStream_t s, int ksplit) {
   static bool attr = false;
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(nn::gemm_bf16_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -230,9 +238,9 @@ cudaError_t launch_gemm_bf16_tn(const void* A, const void* B, int M, int N, int 
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid((M + nn::kBM - 1) / nn::kBM, (N + nn::kBN - 1) / nn::kBN);
+  dim3 grid((M + nn::kBM - 1) / nn::kBM, (N + nn::kBN - 1) / nn::kBN, ksplit);
   nn::gemm_bf16_tn_kernel<<<grid, nn::kThreads, nn::kSmemBytes, s>>>(
-      static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), M, N, K, bias, relu, C32,
+      static_cast<const __nv_bfloat16*>(A), lda, static_cast<const __nv_bfloat16*>(B), ldb, M, N, K, bias, relu, C32,
       static_cast<__nv_bfloat16*>(C16), ldc, status);
   count_launches(1);
   return cudaGetLastError();

@@ -124,7 +124,30 @@ __global__ void coarse_faces_kernel(int nf, int N, const double* __restrict__ kx
 
 inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
+// (1/N) sum_j log kappa_j = amp sin(pi y) sum_k xbar_k sin(k pi x) / k with
+// xbar_k the sample mean of xi_{jk}, at the interior nodes.
+__global__ void mean_log_kappa_kernel(int n, int N, int K, double amp, const double* __restrict__ xi,
+                                      double* __restrict__ out) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)n * n) return;
+  const int iy = (int)(t / n), ix = (int)(t - (long)iy * n);
+  const double x = (double)(ix + 1) / (double)(n + 1), y = (double)(iy + 1) / (double)(n + 1);
+  double g = 0.0;
+  for (int k = 1; k <= K; ++k) {
+    double m = 0.0;
+    for (int j = 0; j < N; ++j) m += xi[(size_t)j * K + (k - 1)];
+    g += (m / N) * sinpi((double)k * x) / (double)k;
+  }
+  out[t] = amp * sinpi(y) * g;
+}
+
 }  // namespace
+
+cudaError_t launch_mean_log_kappa(int n, int N, int K, double amp, const double* xi, double* out, cudaStream_t s) {
+  mean_log_kappa_kernel<<<blocks_for((long)n * n, 256), 256, 0, s>>>(n, N, K, amp, xi, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_coarse_level_setup(int nf, int N, const double* kxf, const double* kyf, double* kx64,
                                       double* ky64, float* kx32, float* ky32, double* inva, double* isigma, double c,

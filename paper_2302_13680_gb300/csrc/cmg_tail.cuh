@@ -93,7 +93,8 @@ __device__ void coarse_cta(const TailParams<T>& P, const Vec3<T>& x, const Vec3<
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     double s = 0.0;
-    for (int k = 0; k < m; ++k) s += P.Minv[r * m + k] * rhs[k];
+    if (!P.freeze_u)
+      for (int k = 0; k < m; ++k) s += P.Minv[r * m + k] * rhs[k];
     us[r] = s;
     x.u[r] = (T)s;
   }

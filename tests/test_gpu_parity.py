@@ -259,3 +259,22 @@ def test_mixed_precision_solve(case, method):
     got = to_host(xd, lv.n)
     for name, g, r in zip("yup", got, ref.x):
         assert relerr(g, r) <= 1e-6, name
+
+
+@pytest.mark.parametrize("tail_n", [0, 31])
+def test_frozen_control_cycle_iterates(case, tail_n):
+    """Cycles with the control held fixed (Eq. (14) local solves with u_i
+    given, zero control correction on coarse grids) against the oracle."""
+    H, levels = case
+    import paper_2302_13680_gb300 as P
+
+    lv = levels[0]
+    f = O.fine_rhs(lv, inputs.target_modes(lv.n, 4))
+    rng = np.random.default_rng(12)
+    x = (np.zeros((lv.n, lv.n, lv.N)), rng.standard_normal((lv.n, lv.n)), np.zeros((lv.n, lv.n, lv.N)))
+    fd = to_dev(f)
+    for k in range(2):
+        xd = to_dev(x)
+        H.cycle(P.CycleOptions(freeze_u=1, tail_n=tail_n), xd, fd)
+        x = O.cycle(levels, 0, x, f, O.CycleOptions(freeze_u=True))
+        assert_close(to_host(xd, lv.n), x, TOL64, f"frozen cycle {k}")

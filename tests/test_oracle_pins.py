@@ -575,3 +575,27 @@ def test_averaged_coarsening_improves_contraction_on_rough_fields():
         assert res.relres <= 1e-10
     assert rates["averaged"] < 0.8 * rates["nodal"], rates
     assert rates["averaged"] < 0.35, rates
+
+
+def test_frozen_control_cycles_solve_the_pdes_for_that_control():
+    """With u fixed the system decouples into, per sample, A_j y_j = f_p,j - e u
+    (state) and A_j p_j = f_y,j - c y_j (adjoint); frozen-control cycles
+    (Eq. (14) smoothing with u_i given) converge to those dense solutions and
+    leave u untouched."""
+    n, N = 15, 3
+    xi = inputs.draw_xi(70, N, 3)
+    levels = O.make_hierarchy(n, N, 1e-4, O.sine_mode_field(xi, 0.9))
+    lv = levels[0]
+    f = O.fine_rhs(lv, inputs.target_modes(n, 8))
+    u0 = np.sin(np.pi * inputs.grid_nodes(n)[0]) * 3.0
+    x = (np.zeros((n, n, N)), u0.copy(), np.zeros((n, n, N)))
+    opts = O.CycleOptions(freeze_u=True)
+    for _ in range(25):
+        x = O.cycle(levels, 0, x, f, opts)
+    assert np.array_equal(x[1], u0)
+    for j in range(N):
+        A = assemble_A_by_faces(lv, j)
+        yj = np.linalg.solve(A, (f[2][:, :, j] - lv.e * u0).ravel())
+        pj = np.linalg.solve(A, (f[0][:, :, j] - lv.c * yj.reshape(n, n)).ravel())
+        assert np.allclose(x[0][:, :, j].ravel(), yj, rtol=1e-9, atol=1e-12)
+        assert np.allclose(x[2][:, :, j].ravel(), pj, rtol=1e-9, atol=1e-14)
