@@ -370,7 +370,9 @@ def run_cmg(args, world, rank, local):
     launches0 = C.kernel_launches()
     barrier()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed_region")     # lets ncu --nvtx-include "timed_region/" select it
     times, cycles, _, st = timed_steps(chosen, args.steps)
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     launches = C.kernel_launches() - launches0

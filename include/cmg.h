@@ -221,7 +221,13 @@ cmg_status cmg_cycle_apply_f32(cmg_handle* h, const cmg_cycle* opts,
  *   on W S x = W f with one cycle (FP64 or FP32) applied to W^{-1} v as
  *   preconditioner; Arnoldi by classical Gram-Schmidt applied twice, all
  *   Krylov vectors FP64.
- * Synchronises once per outer iteration to test convergence.  Returns
+ * With CMG_FP32 and CMG_METHOD_CYCLE the refinement loop runs on the device
+ * as one CUDA graph with a conditional while node (the host synchronises
+ * once per solve); it runs eagerly, one synchronisation per outer
+ * iteration, while a profiling window is open or when the environment held
+ * CMG_GRAPHS=0 at cmg_create (the same kernels; for tools that replay
+ * kernels one by one).  The other forms synchronise once per outer
+ * iteration to test convergence.  Returns
  * CMG_ERR_NOT_CONVERGED if maxit is reached (x holds the last iterate),
  * CMG_ERR_NONFINITE if a residual norm is not finite. */
 cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method, double tol,

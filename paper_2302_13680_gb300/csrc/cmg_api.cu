@@ -2,6 +2,7 @@
 // outer solvers.  All device work is enqueued on the handle's stream.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -74,6 +75,7 @@ struct cmg_handle {
   cmg_cycle ir_opts{};
   double* ir_state = nullptr;            // device [sc, inv_sc, rho, it, maxit, tol_abs]
   long long ir_body_kernels = 0;         // kernels in one iteration of the captured loop body
+  bool graphs = true;                    // false: CMG_GRAPHS=0 in the environment at creation
   // FGMRES workspace
   int gm_cap = 0;
   double* gm = nullptr;       // [2*cap + 2][nt_pad]
@@ -341,6 +343,8 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   if (!h) return CMG_ERR_OOM;
   h->prob = P;
   h->stream = static_cast<cudaStream_t>(stream);
+  const char* graphs_env = std::getenv("CMG_GRAPHS");
+  h->graphs = !(graphs_env && std::strcmp(graphs_env, "0") == 0);
   int n = P.n, L = 0;
   while (true) {
     Lev& v = h->lv[L];
@@ -871,7 +875,7 @@ cmg_status solve_cycle(cmg_handle* h, const cmg_cycle& o, double tol, int maxit,
     s = outer(sc, &rho);
     if (s != CMG_OK) return s;
     st->relres0 = rho / fnorm;
-    const bool use_graph = h->prof_kinds == 0 && std::isfinite(rho) && rho > tol * fnorm && maxit > 0;
+    const bool use_graph = h->graphs && h->prof_kinds == 0 && std::isfinite(rho) && rho > tol * fnorm && maxit > 0;
     if (use_graph) {
       // The loop runs on the device; the host reads the result once.
       s = build_ir_graph(h, o, f, x);

@@ -133,6 +133,29 @@ def test_graph_refinement_matches_eager_and_respects_maxit(H):
     assert status == 4 and st_1.iters == 2
 
 
+def test_graphs_disabled_by_environment(H, monkeypatch):
+    """CMG_GRAPHS=0 at creation runs the same refinement loop eagerly:
+    same iterate, same cycle count, one host round trip per cycle."""
+    h, P, pr = H
+    f = rhs(h, pr)
+    opts = P.CycleOptions(precision=P.FP32)
+    xg = h.zeros(0)
+    st_g, _ = h.solve(opts, f, xg)
+    monkeypatch.setenv("CMG_GRAPHS", "0")
+    h2 = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp)
+    try:
+        xe = h2.zeros(0)
+        from paper_2302_13680_gb300.cmg import kernel_launches
+        k0 = kernel_launches()
+        st_e, status = h2.solve(opts, h2.rhs(torch.tensor(pr.yd.reshape(-1), dtype=torch.float64, device="cuda")), xe)
+        assert status == 0 and st_e.iters == st_g.iters
+        assert kernel_launches() > k0
+        for a, b in zip(xg, xe):
+            assert torch.equal(a, b)
+    finally:
+        h2.close()
+
+
 def test_autotune_keeps_results_and_validates(H, tmp_path):
     h, P, pr = H
     from paper_2302_13680_gb300 import tuning

@@ -1,0 +1,103 @@
+"""Parity at the benchmark's full size (n = 255, N = 64, 16 modes, nu = 1e-6)
+in the launch configuration bench.py times (autotuned lanes per node, FP32
+refinement loop as a CUDA graph): single kernels and one cycle against the
+oracle element by element, and the converged solution through the oracle's
+own residual."""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+import oracle.cmg_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full():
+    from paper_2302_13680_gb300 import build, tuning
+
+    build.build()
+    import paper_2302_13680_gb300 as P
+
+    pr = inputs.make_problem(**inputs.CONFIGS["n255_N64"])
+    H = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp)
+    tuning.apply_or_tune(H, P.FP32)
+    tuning.apply_or_tune(H, P.FP64)
+    levels = O.make_hierarchy(pr.n, pr.N, pr.nu, O.sine_mode_field(pr.xi, pr.amp))
+    yield H, levels, pr, P
+    H.close()
+
+
+def dev(v, dtype=torch.float64):
+    y, u, p = v
+    n = u.shape[0]
+    return (torch.tensor(y.reshape(n * n, -1), dtype=dtype, device="cuda"),
+            torch.tensor(u.reshape(-1), dtype=dtype, device="cuda"),
+            torch.tensor(p.reshape(n * n, -1), dtype=dtype, device="cuda"))
+
+
+def host(v, n):
+    y, u, p = (t.double().cpu().numpy() for t in v)
+    return y.reshape(n, n, -1), u.reshape(n, n), p.reshape(n, n, -1)
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_fullsize_sweep_and_residual(full):
+    H, levels, pr, P = full
+    lv = levels[0]
+    rng = np.random.default_rng(0)
+    x = tuple(rng.standard_normal(s) for s in ((lv.n, lv.n, lv.N), (lv.n, lv.n), (lv.n, lv.n, lv.N)))
+    f = O.fine_rhs(lv, pr.yd)
+    for prec, dt, tol in ((P.FP64, torch.float64, 1e-12), (P.FP32, torch.float32, 2e-5)):
+        xq = tuple(np.asarray(b, dtype=np.float32).astype(np.float64) for b in x) if prec == P.FP32 else x
+        fq = tuple(np.asarray(b, dtype=np.float32).astype(np.float64) for b in f) if prec == P.FP32 else f
+        r = H.zeros(0, dt)
+        H.residual(0, dev(xq, dt), dev(fq, dt), r)
+        ref = O.residual(lv, xq, fq)
+        for g, rr in zip(host(r, lv.n), ref):
+            assert rel(g, rr) <= tol
+        xd = dev(xq, dt)
+        H.smooth(0, P.CycleOptions(), 1, xd, dev(fq, dt))
+        ref = O.rbgs_sweep(lv, xq, fq)
+        for g, rr in zip(host(xd, lv.n), ref):
+            assert rel(g, rr) <= tol
+
+
+def test_fullsize_cycle_iterate(full):
+    H, levels, pr, P = full
+    lv = levels[0]
+    f = O.fine_rhs(lv, pr.yd)
+    xd = H.zeros(0)
+    H.cycle(P.CycleOptions(), xd, dev(f))
+    ref = O.cycle(levels, 0, O.zeros_like_level(lv), f, O.CycleOptions())
+    for g, rr in zip(host(xd, lv.n), ref):
+        assert rel(g, rr) <= 1e-12
+
+
+def test_fullsize_converged_solution_checked_by_oracle_residual(full):
+    """The benchmark's chosen form (FP32 cycles in FP64 refinement, graph)
+    and plain FP64 FGMRES both reach 1e-10 as measured by the ORACLE's
+    operator, and agree with each other to the accuracy the tolerance
+    implies."""
+    H, levels, pr, P = full
+    lv = levels[0]
+    f = O.fine_rhs(lv, pr.yd)
+    fd = dev(f)
+    xm = H.zeros(0)
+    st, status = H.solve(P.CycleOptions(precision=P.FP32), fd, xm, tol=1e-10, maxit=100)
+    assert status == 0
+    xm_h = host(xm, lv.n)
+    rr = O.residual(lv, xm_h, f)
+    assert O.paper_norm(rr, lv.N) / O.paper_norm(f, lv.N) <= 1.05e-10
+    xp = H.zeros(0)
+    st, status = H.solve(P.CycleOptions(), fd, xp, method=P.METHOD_FGMRES, tol=1e-10, maxit=100, restart=30)
+    assert status == 0
+    xp_h = host(xp, lv.n)
+    rr = O.residual(lv, xp_h, f)
+    assert O.paper_norm(rr, lv.N) / O.paper_norm(f, lv.N) <= 1.05e-10
+    for a, b in zip(xm_h, xp_h):
+        assert rel(a, b) <= 1e-7
