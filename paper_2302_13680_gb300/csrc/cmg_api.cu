@@ -28,6 +28,7 @@ struct Lev {
   double h = 0, c = 0, G = 0, d = 0, e = 0;
   size_t nodes = 0;                      // n*n
   double *kx64 = nullptr, *ky64 = nullptr, *inva = nullptr, *isigma = nullptr;
+  float* isigma32 = nullptr;             // 1/sigma in FP32 for the FP32 cycle
   float *kx32 = nullptr, *ky32 = nullptr;
   double* x64[3] = {nullptr, nullptr, nullptr};
   double* f64[3] = {nullptr, nullptr, nullptr};
@@ -137,12 +138,14 @@ LevelView<T> view(const cmg_handle* h, int l, int freeze_u = 0);
 template <>
 LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0], freeze_u};
+  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0], freeze_u,
+          nullptr};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1], freeze_u};
+  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1], freeze_u,
+          v.isigma32};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -163,6 +166,7 @@ cudaError_t setup_coefficients(cmg_handle* h) {
       e = launch_coarse_level_setup(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.isigma, v.c,
                                     v.G, v.d, v.e, h->stream);
     }
+    if (e == cudaSuccess) e = launch_scale_cast<double, float>(1.0, v.isigma, v.isigma32, v.nodes, h->stream);
     if (e != cudaSuccess) return e;
   }
   const Lev& cl = h->lv[h->L - 1];
@@ -370,7 +374,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     Lev& v = h->lv[l];
     const size_t faces = (size_t)v.n * (v.n + 1) * N;
     AL(v.kx64, faces); AL(v.ky64, faces); AL(v.kx32, faces); AL(v.ky32, faces);
-    AL(v.inva, v.nodes * N); AL(v.isigma, v.nodes);
+    AL(v.inva, v.nodes * N); AL(v.isigma, v.nodes); AL(v.isigma32, v.nodes);
     for (int b = 0; b < 3; ++b) {
       const size_t cnt = (b == 1) ? v.nodes : v.nodes * N;
       AL(v.r64[b], cnt); AL(v.x32[b], cnt); AL(v.f32[b], cnt); AL(v.r32[b], cnt); AL(v.f64[b], cnt);

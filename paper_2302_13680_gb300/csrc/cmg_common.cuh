@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cmg_internal.h"
 
 namespace cmg {
@@ -36,9 +38,23 @@ __device__ __forceinline__ vec<T, V> ldv_if(bool ok, const T* p) {
 
 // Sum over the lpn lanes that share a node (aligned groups inside a warp).
 // Every lane of the warp must call this.
-__device__ __forceinline__ double group_sum(double v, int lpn) {
+template <typename A>
+__device__ __forceinline__ A group_sum(A v, int lpn) {
   for (int o = lpn >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Arithmetic of the per-node control-row work (sums over samples, u): FP32
+// in the FP32 cycle, FP64 in the FP64 one.  On this GPU an FP64 warp
+// instruction holds the narrow FP64 pipe for tens of cycles, and this work
+// sits on every node group's critical path.
+template <typename T>
+using acc_t = typename std::conditional<sizeof(T) == 4, float, double>::type;
+
+template <typename T>
+__device__ __forceinline__ acc_t<T> isigma_of(const LevelView<T>& L, long node) {
+  if constexpr (sizeof(T) == 4) return L.isigma32[node];
+  else return L.isigma[node];
 }
 
 // Red-black ordering: map the g-th node of colour `colour` (red = (ix+iy)

@@ -48,6 +48,7 @@ struct LevelView {
   double c, G, d, e;    // scalar blocks of Eq. (12): C_j = c I, G, D_j = d I, E_j = e I
   int spl_target;       // chunks per lane chosen by the autotuner (0 = size heuristic)
   int freeze_u;         // 1: keep u fixed (local solves of the state and adjoint rows only)
+  const float* isigma32;  // 1/sigma rounded to FP32 (FP32 path: the control update runs in FP32)
 };
 
 // Sample mapping of a node's N samples: lanes-per-node (power of two <= 32),

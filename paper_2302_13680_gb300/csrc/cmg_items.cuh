@@ -83,7 +83,8 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
   const bool valid = node < (long)n * n;
   const T c = (T)L.c, e = (T)L.e;
   const bool apply = f.y == nullptr;
-  T pacc = T(0);   // this lane's part of sum_j p_j (converted to FP64 once)
+  using A = acc_t<T>;
+  T pacc = T(0);   // this lane's part of sum_j p_j
   if (valid) {
     const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
     const size_t o = (size_t)node * ld;
@@ -131,10 +132,10 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
       }
     }
   }
-  const double psum = group_sum((double)pacc, lpn);
+  const A psum = group_sum((A)pacc, lpn);
   if (valid && lane == 0) {
-    const double su = L.G * (double)ld1<T, CG>(x.u + node) + L.d * psum;   // control row: G u + d sum_j p_j
-    r.u[node] = (T)(apply ? su : (double)ld1<T, CG>(f.u + node) - su);
+    const A su = (A)L.G * (A)ld1<T, CG>(x.u + node) + (A)L.d * psum;   // control row: G u + d sum_j p_j
+    r.u[node] = (T)(apply ? su : (A)ld1<T, CG>(f.u + node) - su);
   }
 }
 
@@ -144,9 +145,9 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
 // first block row, b_y of the last, b_u of the control row:
 //   u = (b_u + d sum_j (c b_y,j / a_j^2 - b_p,j / a_j)) / sigma
 //   y_j = (b_y,j - e u) / a_j,   p_j = (b_p,j - c y_j) / a_j
-// with 1/sigma stored per node (FP64), so u costs one FP64 multiply: the
-// FP64 pipe of this GPU is narrow, and the per-node FP64 work is shared by
-// the lanes of one warp instruction.
+// with 1/sigma stored per node, so u costs one multiply; the control-row
+// work runs in the cycle's own precision (acc_t) and its loads are issued
+// together with the node's other loads, ahead of the group sum.
 // ---------------------------------------------------------------------------
 template <typename T, int V, int SPL, bool CG>
 __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& x, const Vec3c<T>& f, int colour,
@@ -160,8 +161,12 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
   const long node = (long)iy * n + ix;
   const size_t o = (size_t)node * ld;
   vec<T, V> bp[SPL], by[SPL], ia[SPL];
-  T tacc = T(0);   // this lane's part of the sum over samples (converted to FP64 once)
+  using A = acc_t<T>;
+  T tacc = T(0);   // this lane's part of the sum over samples
+  A bu = A(0), isg = A(0);   // control-row right side (or the frozen u) and 1/sigma, loaded with the rest
   if (valid) {
+    bu = L.freeze_u ? (A)ld1<T, CG>(x.u + node) : (A)ld1<T, CG>(f.u + node);
+    isg = isigma_of<T>(L, node);
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
     const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
@@ -188,12 +193,11 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
       }
     }
   }
-  const double tsum = group_sum((double)tacc, lpn);
+  const A tsum = group_sum((A)tacc, lpn);
   if (valid) {
     // frozen control: u_i keeps its value and only the state and adjoint
     // rows are solved (Eq. (14) with u_i given instead of zero)
-    const double uu = L.freeze_u ? (double)ld1<T, CG>(x.u + node)
-                                 : ((double)ld1<T, CG>(f.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
+    const A uu = L.freeze_u ? bu : (bu + (A)L.d * tsum) * isg;
     if (lane == 0 && !L.freeze_u) x.u[node] = (T)uu;
     const T uT = (T)uu, e = (T)L.e;
 #pragma unroll
@@ -223,8 +227,13 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   const T c = (T)L.c;
   const size_t o = (size_t)(valid ? node : 0) * ld;
   vec<T, V> bp[SPL], by[SPL], ia[SPL];
+  using A = acc_t<T>;
   T tacc = T(0);
+  A ru = A(0), xu = A(0), isg = A(0);   // loaded with the rest, ahead of the group sum
   if (valid) {
+    ru = (A)ld1<T, CG>(r.u + node);
+    xu = (A)ld1<T, CG>(x.u + node);
+    isg = isigma_of<T>(L, node);
     const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
@@ -244,11 +253,10 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
       }
     }
   }
-  const double tsum = group_sum((double)tacc, lpn);
+  const A tsum = group_sum((A)tacc, lpn);
   if (valid) {
-    const double du =
-        L.freeze_u ? 0.0 : ((double)ld1<T, CG>(r.u + node) + L.d * tsum) * ld1<double, CG>(L.isigma + node);
-    if (lane == 0) x.u[node] = (T)((double)ld1<T, CG>(x.u + node) + theta * du);
+    const A du = L.freeze_u ? A(0) : (ru + (A)L.d * tsum) * isg;
+    if (lane == 0) x.u[node] = (T)(xu + (A)theta * du);
     const T duT = (T)du, e = (T)L.e, th = (T)theta;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {

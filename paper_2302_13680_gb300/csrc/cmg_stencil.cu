@@ -10,7 +10,7 @@
 // vectors (coalesced 128-bit loads); neighbour rows are re-read from L2 by
 // the CTAs of adjacent rows, which run close together in launch order.
 // The sum over samples in the control row (u) is a shuffle reduction over
-// the node group, carried in FP64 in both precisions.
+// the node group, carried in the cycle's precision (FP32 or FP64).
 #include "cmg_items.cuh"
 
 namespace cmg {
