@@ -60,9 +60,11 @@ __device__ __forceinline__ acc_t<T> isigma_of(const LevelView<T>& L, long node) 
 // Red-black ordering: map the g-th node of colour `colour` (red = (ix+iy)
 // even = 0) to (iy, ix).  Rows are paired: row 2P holds the first count0
 // nodes of pair P, row 2P+1 the remaining n - count0.
+// 32-bit arithmetic: grids have n <= 4095, so g < n^2 < 2^31.
 __device__ __forceinline__ void colour_node(long g, int n, int colour, int& iy, int& ix) {
-  const long P = g / n;
-  const int q = (int)(g - P * n);
+  const int gi = (int)g;
+  const int P = gi / n;
+  const int q = gi - P * n;
   const int s0 = colour & 1;
   const int count0 = (n - s0 + 1) >> 1;
   if (q < count0) {
