@@ -275,18 +275,22 @@ cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, double tol, int 
 
 /* ---- launch-shape autotuning ------------------------------------------- */
 
-/* Choose, per grid, how many lanes share one node's samples for the node
- * kernels of `precision` (CMG_FP64 or CMG_FP32): each candidate target of
- * 1, 2 or 4 sample chunks per lane is timed with CUDA events on a few
- * red+black half-sweep pairs on the handle's own work vectors, and the
- * fastest is kept in the handle.  chosen (host, may be NULL) receives the
- * target per grid (num_levels entries; the coarsest is not tuned: 0).
- * Synchronises.  Numerical results do not depend on the choice except for
- * the order of the sample sums (rounding). */
+/* Choose, per grid, the launch shape of the node kernels of `precision`
+ * (CMG_FP64 or CMG_FP32): how many sample chunks one lane takes (1, 2 or 4,
+ * which fixes how many lanes share a node) and, for CMG_FP32 with N a
+ * multiple of 4, whether the red-black half-sweep stages its loads through
+ * shared memory (CMG_TUNE_STAGED | 1 or 2 chunks).  Each candidate is timed
+ * with CUDA events on a few red+black half-sweep pairs on the handle's own
+ * work vectors, and the fastest is kept in the handle.  chosen (host, may
+ * be NULL) receives the target per grid (num_levels entries; the coarsest
+ * is not tuned: 0).  Synchronises.  Numerical results do not depend on the
+ * choice except for the order of the sample sums (rounding). */
 cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
 /* Set the per-grid targets directly (e.g. from a cache of earlier
- * cmg_autotune runs): num_levels entries of 0 (size heuristic), 1, 2 or 4;
- * NULL resets all to 0. */
+ * cmg_autotune runs): num_levels entries of 0 (size heuristic), 1, 2 or 4,
+ * and for CMG_FP32 also CMG_TUNE_STAGED | 1 or CMG_TUNE_STAGED | 2; NULL
+ * resets all to 0.  Other values return CMG_ERR_INVALID_ARG. */
+#define CMG_TUNE_STAGED 16
 cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets);
 
 /* cmg_autotune on every instance of a batch (the batch graph is re-captured

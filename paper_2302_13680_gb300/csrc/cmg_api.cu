@@ -1,6 +1,7 @@
 // C ABI of libcmg (include/cmg.h): handle, grid hierarchy, cycles and
 // outer solvers.  All device work is enqueued on the handle's stream.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -151,7 +152,12 @@ LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
 
 template <typename T>
-bool vec_ok(const T* y, const T* u, const T* p) { return y && u && p; }
+bool vec_ok(const T* y, const T* u, const T* p) {
+  // the node kernels move 16-byte vectors: a misaligned pointer is refused
+  // here instead of faulting on the device
+  const auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  return y && u && p && a16(y) && a16(u) && a16(p);
+}
 
 cudaError_t setup_coefficients(cmg_handle* h) {
   const cmg_problem& P = h->prob;
@@ -613,7 +619,15 @@ cmg_status autotune_levels(cmg_handle* h, int* chosen) {
     const int reps = v.n >= 255 ? 4 : 16;
     float best = 1e30f;
     int best_t = 0;
-    for (int t = 1; t <= 4; t <<= 1) {
+    // direct-load sweeps with 1, 2, 4 chunks per lane; FP32 also the staged
+    // sweep with 1 or 2 (kTuneStaged)
+    int cand[5] = {1, 2, 4, 0, 0}, nc = 3;
+    if (sizeof(T) == 4 && staged_supported(h->prob.N, 1)) {
+      cand[nc++] = kTuneStaged | 1;
+      cand[nc++] = kTuneStaged | 2;
+    }
+    for (int ci = 0; ci < nc; ++ci) {
+      const int t = cand[ci];
       float ms = 0.f;
       const cmg_status s = time_sweeps<T>(h, l, t, reps, &ms);
       if (s != CMG_OK) return s;
@@ -646,7 +660,9 @@ cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets) 
   const int k = precision == CMG_FP64 ? 0 : 1;
   for (int l = 0; l < h->L; ++l) {
     const int t = spl_targets ? spl_targets[l] : 0;
-    if (t != 0 && t != 1 && t != 2 && t != 4) return fail(h, CMG_ERR_INVALID_ARG, "chunk target must be 0, 1, 2 or 4");
+    const int c = t & ~kTuneStaged;
+    if ((c != 0 && c != 1 && c != 2 && c != 4) || ((t & kTuneStaged) && (k == 0 || (c != 1 && c != 2))))
+      return fail(h, CMG_ERR_INVALID_ARG, "target must be 0, 1, 2 or 4 (FP32: or CMG_TUNE_STAGED | 1 or 2)");
   }
   for (int l = 0; l < h->L; ++l) h->lv[l].spl_target[k] = spl_targets ? spl_targets[l] : 0;
   h->ir_opts.n1 = -1;   // captured graphs bake the launch shapes: force a re-capture

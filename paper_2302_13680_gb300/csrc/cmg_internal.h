@@ -83,6 +83,12 @@ struct CoarseData {
 template <typename T>
 cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r, cudaStream_t s,
                             double wy = 1.0);
+// Tuning target flag (FP32): the half-sweep stages its loads through
+// shared memory (cmg_staged.cu); the low bits are the chunks per lane.
+constexpr int kTuneStaged = 16;
+bool staged_supported(int N, int spl);
+cudaError_t launch_rbgs_half_staged(const LevelView<float>& L, Vec3<float> x, Vec3c<float> f, int colour,
+                                    const SampleMap& m, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t s);
 template <typename T>

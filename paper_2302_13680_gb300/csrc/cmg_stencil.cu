@@ -99,7 +99,7 @@ SampleMap choose_map(int N, int elem_bytes, long items, int spl_target) {
   const int chunks = (N + m.V - 1) / m.V;
   int target = 4;
   while (target > 1 && items * chunks / target < kMinLanes) target >>= 1;
-  if (spl_target > 0) target = spl_target;
+  if ((spl_target & 15) > 0) target = spl_target & 15;   // the staged flag is not part of the map
   const int want = (chunks + target - 1) / target;   // lanes needed at `target` chunks each
   int lpn = 1;
   while (lpn < want && lpn < 32) lpn <<= 1;
@@ -125,6 +125,12 @@ cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<
 template <typename T>
 cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t st) {
   const SampleMap m = choose_map(L.N, sizeof(T), colour_count(L.n, colour), L.spl_target);
+  if constexpr (sizeof(T) == 4) {
+    if (L.spl_target & kTuneStaged) {
+      const cudaError_t e = launch_rbgs_half_staged(L, x, f, colour, m, st);
+      if (e != cudaErrorNotSupported) return e;
+    }
+  }
   const unsigned grid = grid_for(colour_count(L.n, colour), m.lpn);
   CMG_DISPATCH(T, m, (rbgs_half_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, colour, m.lpn)));
   count_launches(1);

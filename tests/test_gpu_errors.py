@@ -177,3 +177,36 @@ def test_autotune_keeps_results_and_validates(H, tmp_path):
     with pytest.raises(P.CMGError):
         h.set_tuning(P.FP32, [3] * h.levels)
     h.set_tuning(P.FP32, None)
+
+
+def test_set_tuning_validates_targets(H):
+    h, P, pr = H
+    L = h.levels
+    with pytest.raises(P.CMGError):
+        h.set_tuning(P.FP32, [16 | 4] + [0] * (L - 1))      # staged sweep takes 1 or 2 chunks per lane
+    with pytest.raises(P.CMGError):
+        h.set_tuning(P.FP64, [16 | 1] + [0] * (L - 1))      # FP32 only
+    with pytest.raises(P.CMGError):
+        h.set_tuning(P.FP32, [3] + [0] * (L - 1))
+    h.set_tuning(P.FP32, [16 | 2] + [0] * (L - 1))
+    h.set_tuning(P.FP32, None)
+
+
+def test_misaligned_vector_is_refused(H):
+    """Node kernels move 16-byte vectors; a pointer off a 16-byte boundary
+    is refused with an argument error instead of reaching the device."""
+    h, P, pr = H
+    import ctypes
+    from paper_2302_13680_gb300.cmg import load_library
+
+    lib = load_library()
+    m = h.level_n[0] ** 2
+    buf = torch.zeros(m * h.N + 4, dtype=torch.float64, device="cuda")
+    u = torch.zeros(m, dtype=torch.float64, device="cuda")
+    p = torch.zeros(m * h.N, dtype=torch.float64, device="cuda")
+    out = ctypes.c_double()
+    ptr = lambda t, off=0: ctypes.c_void_p(t.data_ptr() + off)
+    st = lib.cmg_norm(h._h, 0, ptr(buf, 8), ptr(u), ptr(p), ctypes.byref(out))
+    assert st == 1
+    st = lib.cmg_norm(h._h, 0, ptr(buf), ptr(u), ptr(p), ctypes.byref(out))
+    assert st == 0

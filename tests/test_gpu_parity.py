@@ -278,3 +278,32 @@ def test_frozen_control_cycle_iterates(case, tail_n):
         H.cycle(P.CycleOptions(freeze_u=1, tail_n=tail_n), xd, fd)
         x = O.cycle(levels, 0, x, f, O.CycleOptions(freeze_u=True))
         assert_close(to_host(xd, lv.n), x, TOL64, f"frozen cycle {k}")
+
+
+@pytest.mark.parametrize("spl", [1, 2])
+@pytest.mark.parametrize("freeze", [0, 1])
+def test_staged_half_sweep_matches_direct(case, spl, freeze):
+    """The FP32 half-sweep that stages its loads through shared memory
+    (CMG_TUNE_STAGED) performs the same operations in the same order as the
+    direct-load sweep: two sweeps on every grid agree bit for bit (grids
+    whose sample count is not a multiple of 4 fall back to the direct
+    sweep)."""
+    H, levels = case
+    import paper_2302_13680_gb300 as P
+
+    staged = 16
+    out = []
+    for t in (spl, staged | spl):
+        H.set_tuning(P.FP32, [t] * (H.levels - 1) + [0])
+        res = []
+        for lv in range(H.levels - 1):
+            n = H.level_n[lv]
+            x = to_dev(rand_level_vec(n, levels[lv].N, 900 + lv, np.float32), torch.float32)
+            f = to_dev(rand_level_vec(n, levels[lv].N, 950 + lv, np.float32), torch.float32)
+            H.smooth(lv, P.CycleOptions(precision=P.FP32, freeze_u=freeze), 2, x, f)
+            res.append(x)
+        out.append(res)
+    H.set_tuning(P.FP32, None)
+    for a, b in zip(*out):
+        for ta, tb in zip(a, b):
+            assert torch.equal(ta, tb)
