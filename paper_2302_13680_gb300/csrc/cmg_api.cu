@@ -30,6 +30,7 @@ struct Lev {
   size_t nodes = 0;                      // n*n
   double *kx64 = nullptr, *ky64 = nullptr, *inva = nullptr, *isigma = nullptr;
   float* isigma32 = nullptr;             // 1/sigma in FP32 for the FP32 cycle
+  double* a64 = nullptr;                 // finest grid: diag(A_j) for the FP64 refinement residual
   float *kx32 = nullptr, *ky32 = nullptr;
   double* x64[3] = {nullptr, nullptr, nullptr};
   double* f64[3] = {nullptr, nullptr, nullptr};
@@ -140,13 +141,13 @@ template <>
 LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0], freeze_u,
-          nullptr};
+          nullptr, v.a64};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1], freeze_u,
-          v.isigma32};
+          v.isigma32, nullptr};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -173,6 +174,7 @@ cudaError_t setup_coefficients(cmg_handle* h) {
                                     v.G, v.d, v.e, h->stream);
     }
     if (e == cudaSuccess) e = launch_scale_cast<double, float>(1.0, v.isigma, v.isigma32, v.nodes, h->stream);
+    if (e == cudaSuccess && v.a64) e = launch_diag_sum(v.n, P.N, v.kx64, v.ky64, v.a64, h->stream);
     if (e != cudaSuccess) return e;
   }
   const Lev& cl = h->lv[h->L - 1];
@@ -387,6 +389,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
       AL(v.x64[b], cnt);
     }
   }
+  AL(h->lv[0].a64, h->lv[0].nodes * N);
   const size_t g = (size_t)P.n + 2;
   AL(h->kap, g * g * N + g * N);
   AL(h->xi, (size_t)N * (P.K > 0 ? P.K : 1));

@@ -49,6 +49,7 @@ struct LevelView {
   int spl_target;       // chunks per lane chosen by the autotuner (0 = size heuristic)
   int freeze_u;         // 1: keep u fixed (local solves of the state and adjoint rows only)
   const float* isigma32;  // 1/sigma rounded to FP32 (FP32 path: the control update runs in FP32)
+  const double* a64;      // diag(A_j) = sum of the four faces per node-sample (FP64, finest grid only, else null)
 };
 
 // Sample mapping of a node's N samples: lanes-per-node (power of two <= 32),
@@ -152,6 +153,8 @@ cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const dou
 // ---- coefficients (cmg_setup.cu) ----
 // Nodal field on the (n+2)^2 grid including boundary points, then faces,
 // 1/diag and Schur denominators.  kap: scratch [(n+2)^2][N] doubles.
+// a[node][j] = sum of the node's four faces (FP64).
+cudaError_t launch_diag_sum(int n, int N, const double* kx, const double* ky, double* a, cudaStream_t s);
 cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi, double* kap,
                                double* kx64, double* ky64, float* kx32, float* ky32,
                                double* inva, double* isigma, double c, double G, double d,

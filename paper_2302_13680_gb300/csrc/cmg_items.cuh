@@ -416,6 +416,7 @@ __device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, 
   const T c = L.c, e = L.e;
   T pacc = 0.0;
   float sq = 0.f;
+  const float sf = (float)s;
   if (valid) {
     const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
     const size_t o = (size_t)node * ld;
@@ -431,6 +432,15 @@ __device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, 
         const vec<T, V> kS = ldv<T, V>(kSp + j), kN = ldv<T, V>(kSp + (size_t)n * ld + j);
         const vec<T, V> y = ldv<T, V>(x.y + o + j), p = ldv<T, V>(x.p + o + j);
         const vec<T, V> fy = ldv<T, V>(f.y + o + j), fp = ldv<T, V>(f.p + o + j);
+        // diag(A_j) read (finest grid) instead of three FP64 adds: this pass is
+        // bound by the FP64 pipe, not by memory
+        vec<T, V> av;
+        if (L.a64) {
+          av = ldv<T, V>(L.a64 + o + j);
+        } else {
+#pragma unroll
+          for (int k = 0; k < V; ++k) av.v[k] = (kW.v[k] + kE.v[k]) + (kS.v[k] + kN.v[k]);
+        }
         vec<T, V> offy = vzero<T, V>(), offp = vzero<T, V>();
         fma_faces<T, V>(offy, kW, ldv_if<T, V>(hW, x.y + o - ld + j), kE, ldv_if<T, V>(hE, x.y + o + ld + j), kS,
                         ldv_if<T, V>(hS, x.y + o - (size_t)n * ld + j), kN,
@@ -441,11 +451,11 @@ __device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, 
         vec<float, V> ry, rp;
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-          const T a = (kW.v[k] + kE.v[k]) + (kS.v[k] + kN.v[k]);
+          const T a = av.v[k];
           const T ryk = fy.v[k] - fma(c, y.v[k], fma(a, p.v[k], -offp.v[k]));   // f_y - c y - A p
           const T rpk = (fp.v[k] - eu) - fma(a, y.v[k], -offy.v[k]);             // f_p - e u - A y
-          ry.v[k] = (float)(ryk * s);
-          rp.v[k] = (float)(rpk * s);
+          ry.v[k] = (float)ryk * sf;   // scaled after rounding: FP32 multiplies instead of FP64
+          rp.v[k] = (float)rpk * sf;
           sq = fmaf(wy2 * ry.v[k], ry.v[k], sq);
           sq = fmaf(rp.v[k], rp.v[k], sq);
           pacc += p.v[k];

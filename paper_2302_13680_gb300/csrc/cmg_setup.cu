@@ -124,6 +124,20 @@ __global__ void coarse_faces_kernel(int nf, int N, const double* __restrict__ kx
 
 inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
+// a[node][j] = (kW + kE) + (kS + kN), the same expression as in the kernels
+// that form it on the fly.
+__global__ void diag_sum_kernel(int n, int N, const double* __restrict__ kx, const double* __restrict__ ky,
+                                double* __restrict__ a) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)n * n * N) return;
+  const long node = t / N;
+  const int j = (int)(t - node * N);
+  const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
+  const double* kW = kx + ((size_t)iy * (n + 1) + ix) * N;
+  const double* kS = ky + ((size_t)iy * n + ix) * N;
+  a[t] = (kW[j] + kW[N + j]) + (kS[j] + kS[(size_t)n * N + j]);
+}
+
 // (1/N) sum_j log kappa_j = amp sin(pi y) sum_k xbar_k sin(k pi x) / k with
 // xbar_k the sample mean of xi_{jk}, at the interior nodes.
 __global__ void mean_log_kappa_kernel(int n, int N, int K, double amp, const double* __restrict__ xi,
@@ -170,6 +184,12 @@ cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi
   faces_kernel<<<blocks_for(2L * n * (n + 1) * N, 256), 256, 0, s>>>(n, N, kap, kx64, ky64, kx32, ky32);
   diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, isigma, d * c * e, G);
   count_launches(4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_sum(int n, int N, const double* kx, const double* ky, double* a, cudaStream_t s) {
+  diag_sum_kernel<<<blocks_for((long)n * n * N, 256), 256, 0, s>>>(n, N, kx, ky, a);
+  count_launches(1);
   return cudaGetLastError();
 }
 
