@@ -36,6 +36,7 @@ struct Lev {
   double* f64[3] = {nullptr, nullptr, nullptr};
   double* r64[3] = {nullptr, nullptr, nullptr};
   float* x32[3] = {nullptr, nullptr, nullptr};
+  float* d32[3] = {nullptr, nullptr, nullptr};   // finest grid: FP32 correction since the last refinement anchor
   float* f32[3] = {nullptr, nullptr, nullptr};
   float* r32[3] = {nullptr, nullptr, nullptr};
 };
@@ -76,7 +77,7 @@ struct cmg_handle {
   cudaGraphExec_t ir_exec = nullptr;
   const void* ir_key[6] = {};
   cmg_cycle ir_opts{};
-  double* ir_state = nullptr;            // device [sc, inv_sc, rho, it, maxit, tol_abs]
+  double* ir_state = nullptr;            // device refinement state, see IrState
   long long ir_body_kernels = 0;         // kernels in one iteration of the captured loop body
   bool graphs = true;                    // false: CMG_GRAPHS=0 in the environment at creation
   // FGMRES workspace
@@ -397,7 +398,11 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   AL(h->dsc, 1024);
   h->part_cap = (int)(((size_t)P.n * P.n * 32 + kBlock - 1) / kBlock + 16);
   AL(h->part, (size_t)h->part_cap);
-  AL(h->ir_state, 8);
+  AL(h->ir_state, 16);
+  {
+    Lev& l0 = h->lv[0];
+    AL(l0.d32[0], l0.nodes * N); AL(l0.d32[1], l0.nodes); AL(l0.d32[2], l0.nodes * N);
+  }
   const int cn = h->lv[L - 1].n;
   h->coarse.n = cn;
   h->coarse.m = cn * cn;
@@ -726,27 +731,132 @@ cmg_status precondition(cmg_handle* h, const cmg_cycle& o, Vec3c<double> v, Vec3
 // partials (fixed-order sum), scales for the next iteration, iteration
 // count, and the loop condition of the enclosing while node.
 // state = [sc, inv_sc, rho, it, maxit, tol_abs].
-__global__ void ir_control_kernel(const double* __restrict__ partial, int count, double* __restrict__ state,
-                                  cudaGraphConditionalHandle cond) {
+// FP32 refinement with residual replacement.  Between anchors the cycle's
+// right side r^ = sc r is updated recursively in FP32 (r^ <- r^ - S e) and
+// the corrections are summed in FP32 (d += e); an anchor folds x += d / sc,
+// recomputes the true residual in FP64 and rescales r^ to norm 1.  The FP32
+// recursion drifts from the true residual by about eps32 * (cancellation of
+// S) per step relative to the residual it started from, so an anchor is
+// taken once the recursive norm has dropped kAnchorDrop below the last true
+// one, after kAnchorMax cycles, at maxit, or when the recursive norm reaches
+// the tolerance (the stopping test is always made on a true residual).
+// State (device doubles):
+enum IrState {
+  kSc = 0,       // scale for the next FP64 pass (1 / latest norm)
+  kInvSc = 1,    // 1 / scale of the current right side r^ (also of d)
+  kRho = 2,      // latest residual norm (recursive between anchors, true at one)
+  kIt = 3,       // cycles done
+  kMaxit = 4,
+  kTolAbs = 5,
+  kRhoAnchor = 6,   // true norm at the last anchor
+  kSince = 7,       // cycles since the last anchor
+  kAnchor = 8,      // 1: the anchor kernels of this iteration run
+  kGo = 9,          // 1: another iteration follows
+  kIrStateSize = 10
+};
+constexpr double kAnchorDrop = 1e-2;
+constexpr int kAnchorMax = 5;
+
+__device__ double block_total(const double* __restrict__ partial, int count) {
   __shared__ double sh[32];
   double v = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) v += partial[i];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
+  double t = 0.0;
+  if (threadIdx.x == 0)
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    const double sc = state[0];
-    const double rho = sqrt(t) / sc;
-    const double it = state[3] + 1.0;
-    state[1] = 1.0 / sc;     // the right side now holds r * sc
-    state[0] = 1.0 / rho;    // scale of the next right side
-    state[2] = rho;
-    state[3] = it;
-    const bool go = isfinite(rho) && rho > state[5] && it < state[4];
-    cudaGraphSetConditional(cond, go ? 1u : 0u);
-  }
+  return t;   // valid in thread 0
+}
+
+// After the cycle and the recursive update: the recursive norm, whether the
+// anchor runs this iteration, whether the loop continues (if it does not
+// anchor).  cond is set only when `graph` (a conditional node exists).
+__global__ void ir_recur_control_kernel(const double* __restrict__ partial, int count, double* __restrict__ s,
+                                        cudaGraphConditionalHandle cond, int graph) {
+  const double t = block_total(partial, count);
+  if (threadIdx.x != 0) return;
+  const double rho = sqrt(t) * s[kInvSc];
+  const double it = s[kIt] + 1.0, since = s[kSince] + 1.0;
+  s[kRho] = rho;
+  s[kIt] = it;
+  s[kSince] = since;
+  const bool anchor = !isfinite(rho) || rho <= s[kTolAbs] || rho <= kAnchorDrop * s[kRhoAnchor] ||
+                      it >= s[kMaxit] || since >= (double)kAnchorMax;
+  s[kSc] = (isfinite(rho) && rho > 0.0) ? 1.0 / rho : 1.0 / s[kRhoAnchor];
+  s[kAnchor] = anchor ? 1.0 : 0.0;
+  s[kGo] = anchor ? 0.0 : 1.0;
+  if (graph) cudaGraphSetConditional(cond, anchor ? 0u : 1u);
+}
+
+// After the anchor's FP64 pass (scale s[kSc]): the true norm, the new scale,
+// the stopping test.  Does nothing when no anchor ran.
+__global__ void ir_anchor_control_kernel(const double* __restrict__ partial, int count, double* __restrict__ s,
+                                         cudaGraphConditionalHandle cond, int graph) {
+  if (s[kAnchor] == 0.0) return;
+  const double t = block_total(partial, count);
+  if (threadIdx.x != 0) return;
+  const double sc = s[kSc];
+  const double rho = sqrt(t) / sc;
+  s[kInvSc] = 1.0 / sc;   // the right side now holds r * sc
+  s[kSc] = 1.0 / rho;
+  s[kRho] = rho;
+  s[kRhoAnchor] = rho;
+  s[kSince] = 0.0;
+  const bool go = isfinite(rho) && rho > s[kTolAbs] && s[kIt] < s[kMaxit];
+  s[kGo] = go ? 1.0 : 0.0;
+  if (graph) cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+// Host image of the state before the first iteration: right side r^ = sc r
+// with true norm rho.
+void ir_state_init(double* hs, double rho, double sc, int maxit, double tol_abs) {
+  for (int i = 0; i < kIrStateSize; ++i) hs[i] = 0.0;
+  hs[kSc] = rho > 0.0 ? 1.0 / rho : 0.0;
+  hs[kInvSc] = 1.0 / sc;
+  hs[kRho] = rho;
+  hs[kMaxit] = (double)maxit;
+  hs[kTolAbs] = tol_abs;
+  hs[kRhoAnchor] = rho;
+  hs[kGo] = 1.0;
+}
+
+// The anchor kernels (each does nothing unless the anchor flag is set).
+cmg_status ir_iteration_anchor(cmg_handle* h, Vec3c<double> f, Vec3<double> x, cudaGraphConditionalHandle cond,
+                               int graph) {
+  Lev& l0 = h->lv[0];
+  const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes;
+  Vec3<float> f32 = Work<float>::f(l0);
+  Vec3<float> d32{l0.d32[0], l0.d32[1], l0.d32[2]};
+  double* st = h->ir_state;
+  CK(launch_fold(st + kInvSc, st + kAnchor, d32, x, ny, nu, h->stream));
+  const int cnt = launch_residual_cast(view<double>(h, 0), cview(x), f, f32, 0.0, st + kSc, paper_wy(h), h->part,
+                                       h->part_cap, h->stream, st + kAnchor);
+  if (cnt < 0) return fail(h, CMG_ERR_CUDA, "refinement pass launch failed");
+  ir_anchor_control_kernel<<<1, 256, 0, h->stream>>>(h->part, cnt, st, cond, graph);
+  count_launches(1);
+  CK(cudaGetLastError());
+  return CMG_OK;
+}
+
+// One refinement iteration on the handle's stream (eager) or into a capture:
+// cycle, recursive update, control, then the gated anchor.
+cmg_status ir_iteration(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<double> x,
+                        cudaGraphConditionalHandle cond, int graph, bool anchor_kernels) {
+  Lev& l0 = h->lv[0];
+  Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
+  Vec3<float> d32{l0.d32[0], l0.d32[1], l0.d32[2]};
+  double* st = h->ir_state;
+  CK(zero_vec<float>(h, 0, x32));
+  CK(cycle<float>(h, o, 0, x32, cview(f32)));
+  int cnt = launch_recur(view<float>(h, 0), cview(x32), f32, d32, paper_wy(h), h->part, h->part_cap, h->stream);
+  if (cnt < 0) return fail(h, CMG_ERR_CUDA, "recursive residual launch failed");
+  ir_recur_control_kernel<<<1, 256, 0, h->stream>>>(h->part, cnt, st, cond, graph);
+  count_launches(1);
+  CK(cudaGetLastError());
+  if (!anchor_kernels) return CMG_OK;
+  return ir_iteration_anchor(h, f, x, cond, graph);
 }
 
 bool same_cycle(const cmg_cycle& a, const cmg_cycle& b) {
@@ -761,10 +871,9 @@ __global__ void ir_start_kernel(const double* __restrict__ state, cudaGraphCondi
   cudaGraphSetConditional(cond, (isfinite(rho) && rho > state[5] && state[3] < state[4]) ? 1u : 0u);
 }
 
-// Adds to graph g: [start kernel] -> [while(cond) { e = cycle_FP32(0; r32);
-// x += inv_sc e; r32 = sc (f - S x); control }] for one instance, after the
-// optional dependency dep.  Kernels are captured on the instance's capture
-// stream with all its launches redirected there.
+// Adds to graph g: [start kernel] -> [while(cond) { one refinement iteration
+// (ir_iteration) }] for one instance.  Kernels are captured on the
+// instance's capture stream with all its launches redirected there.
 cmg_status add_ir_loop(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<double> x, cudaGraph_t g) {
   if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   cudaGraphConditionalHandle cond;
@@ -791,36 +900,26 @@ cmg_status add_ir_loop(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<
   cudaGraphNode_t node;
   CK(cudaGraphAddNode(&node, g, &start, nullptr, 1, &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
-  Lev& l0 = h->lv[0];
-  const size_t ny = l0.nodes * h->prob.N, nu = l0.nodes;
-  Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
   const cudaStream_t user = h->stream;
   const int prof = h->prof_kinds;
   h->stream = h->cap;
   h->prof_kinds = 0;
   cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-  int cnt = -1;
+  cmg_status ist = CMG_OK;
   const long long k0 = cmg_kernel_launches();
   if (e == cudaSuccess) {
-    e = zero_vec<float>(h, 0, x32);
-    if (e == cudaSuccess) e = cycle<float>(h, o, 0, x32, cview(f32));
-    if (e == cudaSuccess) e = launch_axpy3(0.0, h->ir_state + 1, cview(x32), x, ny, nu, h->cap);
-    if (e == cudaSuccess) {
-      cnt = launch_residual_cast(view<double>(h, 0), cview(x), f, f32, 0.0, h->ir_state, paper_wy(h), h->part,
-                                 h->part_cap, h->cap);
-      if (cnt < 0) e = cudaErrorLaunchFailure;
-    }
-    if (e == cudaSuccess) {
-      ir_control_kernel<<<1, 256, 0, h->cap>>>(h->part, cnt, h->ir_state, cond);
-      count_launches(1);
-      e = cudaGetLastError();
-    }
+    ist = ir_iteration(h, o, f, x, cond, 1, true);
     cudaGraph_t captured = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->cap, &captured);
     if (e == cudaSuccess) e = e2;
   }
   h->stream = user;
   h->prof_kinds = prof;
+  if (ist != CMG_OK) {
+    h->ir_body_kernels = cmg_kernel_launches() - k0;
+    count_launches((int)-h->ir_body_kernels);
+    return ist;
+  }
   // kernels captured into the body run once per iteration; the launch
   // counter is advanced by replays (see count_replay), not by the capture
   h->ir_body_kernels = cmg_kernel_launches() - k0;
@@ -899,32 +998,38 @@ cmg_status solve_cycle(cmg_handle* h, const cmg_cycle& o, double tol, int maxit,
     if (s != CMG_OK) return s;
     st->relres0 = rho / fnorm;
     const bool use_graph = h->graphs && h->prof_kinds == 0 && std::isfinite(rho) && rho > tol * fnorm && maxit > 0;
+    if (std::isfinite(rho) && rho > tol * fnorm && maxit > 0) {
+      Vec3<float> d32{l0.d32[0], l0.d32[1], l0.d32[2]};
+      CK(zero_vec<float>(h, 0, d32));
+      ir_state_init(h->hsc, rho, sc, maxit, tol * fnorm);
+      CK(cudaMemcpyAsync(h->ir_state, h->hsc, kIrStateSize * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
     if (use_graph) {
       // The loop runs on the device; the host reads the result once.
       s = build_ir_graph(h, o, f, x);
       if (s != CMG_OK) return s;
-      double* hs = h->hsc;
-      hs[0] = 1.0 / rho;
-      hs[1] = 1.0 / sc;
-      hs[2] = rho;
-      hs[3] = 0.0;
-      hs[4] = (double)maxit;
-      hs[5] = tol * fnorm;
-      CK(cudaMemcpyAsync(h->ir_state, hs, 6 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
       CK(cudaGraphLaunch(h->ir_exec, h->stream));
-      CK(fetch(h, h->ir_state, 6));
-      rho = h->hsc[2];
-      it = (int)h->hsc[3];
+      CK(fetch(h, h->ir_state, kIrStateSize));
+      rho = h->hsc[kRho];
+      it = (int)h->hsc[kIt];
       count_replay(h, it);
-    }
-    while (!use_graph && std::isfinite(rho) && rho > tol * fnorm && it < maxit) {
-      CK(zero_vec<float>(h, 0, x32));
-      CK(cycle<float>(h, o, 0, x32, cview(f32)));
-      CK(launch_axpy3(1.0 / sc, nullptr, cview(x32), x, ny, nu, h->stream));
-      ++it;
-      sc = 1.0 / rho;
-      s = outer(sc, &rho);
-      if (s != CMG_OK) return s;
+    } else if (std::isfinite(rho) && rho > tol * fnorm && maxit > 0) {
+      // the same kernels launched one by one; the host reads the device's
+      // decisions after each step and skips the anchor kernels when none is due
+      cudaGraphConditionalHandle none = 0;
+      while (true) {
+        s = ir_iteration(h, o, f, x, none, 0, false);
+        if (s != CMG_OK) return s;
+        CK(fetch(h, h->ir_state, kIrStateSize));
+        if (h->hsc[kAnchor] != 0.0) {
+          s = ir_iteration_anchor(h, f, x, none, 0);
+          if (s != CMG_OK) return s;
+          CK(fetch(h, h->ir_state, kIrStateSize));
+        }
+        if (h->hsc[kGo] == 0.0) break;
+      }
+      rho = h->hsc[kRho];
+      it = (int)h->hsc[kIt];
     }
   }
   st->iters = it;
@@ -1219,13 +1324,13 @@ extern "C" cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, doubl
     double* hs = h->hsc;
     const double rho = fnorm[i] > 0.0 ? std::sqrt(hs[0]) * fnorm[i] : 0.0;
     stats[i].relres0 = fnorm[i] > 0.0 ? rho / fnorm[i] : 0.0;
-    hs[0] = rho > 0.0 ? 1.0 / rho : 0.0;
-    hs[1] = fnorm[i];
-    hs[2] = rho;
-    hs[3] = 0.0;
-    hs[4] = (double)maxit;
-    hs[5] = tol * fnorm[i];
-    BCK(cudaMemcpyAsync(h->ir_state, hs, 6 * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    ir_state_init(hs, rho, fnorm[i] > 0.0 ? 1.0 / fnorm[i] : 1.0, maxit, tol * fnorm[i]);
+    BCK(cudaMemcpyAsync(h->ir_state, hs, kIrStateSize * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    Lev& l0 = h->lv[0];
+    const size_t ny = l0.nodes * h->prob.N;
+    BCK(cudaMemsetAsync(l0.d32[0], 0, ny * sizeof(float), b->stream));
+    BCK(cudaMemsetAsync(l0.d32[1], 0, l0.nodes * sizeof(float), b->stream));
+    BCK(cudaMemsetAsync(l0.d32[2], 0, ny * sizeof(float), b->stream));
   }
   // 3. the graph: one independent branch (start kernel + while loop) per instance
   std::vector<const void*> key;
@@ -1255,17 +1360,17 @@ extern "C" cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, doubl
   BCK(cudaGraphLaunch(b->exec, b->stream));
   for (int i = 0; i < count; ++i) {
     cmg_handle* h = b->inst[i];
-    BCK(cudaMemcpyAsync(h->hsc, h->ir_state, 6 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaMemcpyAsync(h->hsc, h->ir_state, kIrStateSize * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
   }
   BCK(cudaStreamSynchronize(b->stream));
   cmg_status worst = CMG_OK;
   for (int i = 0; i < count; ++i) {
     const double* hs = b->inst[i]->hsc;
-    count_replay(b->inst[i], (int)hs[3]);
-    stats[i].iters = (int)hs[3];
-    stats[i].cycles = (int)hs[3];
-    stats[i].relres = fnorm[i] > 0.0 ? hs[2] / fnorm[i] : 0.0;
-    if (!std::isfinite(hs[2])) worst = CMG_ERR_NONFINITE;
+    count_replay(b->inst[i], (int)hs[kIt]);
+    stats[i].iters = (int)hs[kIt];
+    stats[i].cycles = (int)hs[kIt];
+    stats[i].relres = fnorm[i] > 0.0 ? hs[kRho] / fnorm[i] : 0.0;
+    if (!std::isfinite(hs[kRho])) worst = CMG_ERR_NONFINITE;
     else if (fnorm[i] > 0.0 && stats[i].relres > tol && worst == CMG_OK) worst = CMG_ERR_NOT_CONVERGED;
   }
   if (worst != CMG_OK) b->err = "some instances did not reach the tolerance";

@@ -137,9 +137,17 @@ bool tail_supported(int N, int elem_bytes, int coarse_m);
 // partials written, or -1 on error / if more than max_partials are needed.
 // The scale is *sdev when sdev is given (graph replays), else s.
 int launch_residual_cast(const LevelView<double>& L, Vec3c<double> x, Vec3c<double> f, Vec3<float> r, double s,
-                         const double* sdev, double wy, double* partial, int max_partials, cudaStream_t st);
+                         const double* sdev, double wy, double* partial, int max_partials, cudaStream_t st,
+                         const double* gate = nullptr);
 // x += a * e on the three blocks (ny elements in y and p, nu in u); a is
 // *adev when adev is given.
+// Residual replacement in FP32 refinement (cmg_stencil.cu): r <- r - S e in
+// place, d += e, partials of ||W r||^2 (returns their count or -1); and the
+// gated anchor fold x += (*adev) d, d = 0 (nothing when *gate == 0).
+int launch_recur(const LevelView<float>& L, Vec3c<float> e, Vec3<float> r, Vec3<float> d, double wy, double* partial,
+                 int max_partials, cudaStream_t s);
+cudaError_t launch_fold(const double* adev, const double* gate, Vec3<float> d, Vec3<double> x, size_t ny, size_t nu,
+                        cudaStream_t s);
 cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<double> x, size_t ny, size_t nu,
                          cudaStream_t st);
 

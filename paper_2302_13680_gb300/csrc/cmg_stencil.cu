@@ -57,8 +57,10 @@ template <int V, int SPL>
 __global__ void __launch_bounds__(kBlock) residual_cast_kernel(LevelView<double> L, Vec3c<double> x,
                                                               Vec3c<double> f, Vec3<float> r, int lpn, double s,
                                                               const double* __restrict__ sdev, float wy2,
-                                                              double* __restrict__ partial) {
+                                                              double* __restrict__ partial,
+                                                              const double* __restrict__ gate) {
   __shared__ double sh[kBlock / 32];
+  if (gate && *gate == 0.0) return;   // refinement anchor not due (residual replacement)
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   const double sc = sdev ? *sdev : s;
   double v = (double)residual_cast_item<V, SPL>(L, x, f, r, node, threadIdx.x & (lpn - 1), lpn, sc, wy2);
@@ -69,6 +71,80 @@ __global__ void __launch_bounds__(kBlock) residual_cast_kernel(LevelView<double>
     double t = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) t += sh[w];
     partial[blockIdx.x] = t;
+  }
+}
+
+// FP32 refinement between FP64 anchors (residual replacement): the scaled
+// residual r (the cycle's right side) is updated in place, r <- r - S e, the
+// running correction d += e, and per-CTA partial sums of ||W r||^2 are
+// written (squares in FP32, CTA sum in FP64).  Each lane reads its own f
+// entries before writing r at the same place, so the update in place is safe.
+template <int V, int SPL>
+__global__ void __launch_bounds__(kBlock) recur_kernel(LevelView<float> L, Vec3c<float> e, Vec3<float> r,
+                                                       Vec3<float> d, int lpn, float wy2,
+                                                       double* __restrict__ partial) {
+  __shared__ double sh[kBlock / 32];
+  const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
+  const int lane = threadIdx.x & (lpn - 1);
+  residual_item<float, V, SPL, false>(L, e, cview(r), r, node, lane, lpn, 1.0f);
+  const int N = L.N;
+  const size_t ld = (size_t)L.ld;
+  float sq = 0.f;
+  if (node < (long)L.n * L.n) {
+    const size_t o = (size_t)node * ld;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+      const int j = (lane + s * lpn) * V;
+      if (j < N) {
+        const vec<float, V> ry = ldv<float, V>(r.y + o + j), rp = ldv<float, V>(r.p + o + j);
+        const vec<float, V> ey = ldv<float, V>(e.y + o + j), ep = ldv<float, V>(e.p + o + j);
+        vec<float, V> dy = ldv<float, V>(d.y + o + j), dp = ldv<float, V>(d.p + o + j);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          sq = fmaf(wy2 * ry.v[k], ry.v[k], sq);
+          sq = fmaf(rp.v[k], rp.v[k], sq);
+          dy.v[k] += ey.v[k];
+          dp.v[k] += ep.v[k];
+        }
+        stv<float, V>(d.y + o + j, dy);
+        stv<float, V>(d.p + o + j, dp);
+      }
+    }
+    if (lane == 0) {
+      const float ru = r.u[node];
+      sq = fmaf(ru, ru, sq);
+      d.u[node] += e.u[node];
+    }
+  }
+  double v = (double)sq;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += sh[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// Anchor of residual replacement: x += a d (a = *adev) and d = 0, when
+// *gate is nonzero.
+__global__ void fold_kernel(const double* __restrict__ adev, const double* __restrict__ gate, Vec3<float> d,
+                            Vec3<double> x, size_t ny, size_t nu) {
+  if (*gate == 0.0) return;
+  const double a = *adev;
+  const size_t total = 2 * ny + nu;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    if (i < ny) {
+      x.y[i] = fma(a, (double)d.y[i], x.y[i]);
+      d.y[i] = 0.f;
+    } else if (i < ny + nu) {
+      x.u[i - ny] = fma(a, (double)d.u[i - ny], x.u[i - ny]);
+      d.u[i - ny] = 0.f;
+    } else {
+      x.p[i - ny - nu] = fma(a, (double)d.p[i - ny - nu], x.p[i - ny - nu]);
+      d.p[i - ny - nu] = 0.f;
+    }
   }
 }
 
@@ -166,7 +242,8 @@ cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_
 }
 
 int launch_residual_cast(const LevelView<double>& L, Vec3c<double> x, Vec3c<double> f, Vec3<float> r, double s,
-                         const double* sdev, double wy, double* partial, int max_partials, cudaStream_t st) {
+                         const double* sdev, double wy, double* partial, int max_partials, cudaStream_t st,
+                         const double* gate) {
   const SampleMap m = choose_map(L.N, 8, (long)L.n * L.n);
   const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
   if ((int)grid > max_partials) return -1;
@@ -174,12 +251,38 @@ int launch_residual_cast(const LevelView<double>& L, Vec3c<double> x, Vec3c<doub
   using T = double;
   auto go = [&]() -> cudaError_t {
     CMG_DISPATCH(T, m, (residual_cast_kernel<V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, r, m.lpn, s, sdev, wy2,
-                                                                             partial)));
+                                                                             partial, gate)));
     return cudaGetLastError();
   };
   if (go() != cudaSuccess) return -1;
   count_launches(1);
   return (int)grid;
+}
+
+int launch_recur(const LevelView<float>& L, Vec3c<float> e, Vec3<float> r, Vec3<float> d, double wy, double* partial,
+                 int max_partials, cudaStream_t st) {
+  const SampleMap m = choose_map(L.N, 4, (long)L.n * L.n, L.spl_target);
+  const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
+  if ((int)grid > max_partials) return -1;
+  const float wy2 = (float)(wy * wy);
+  using T = float;
+  auto go = [&]() -> cudaError_t {
+    CMG_DISPATCH(T, m, (recur_kernel<V, SPL><<<grid, kBlock, 0, st>>>(L, e, r, d, m.lpn, wy2, partial)));
+    return cudaGetLastError();
+  };
+  if (go() != cudaSuccess) return -1;
+  count_launches(1);
+  return (int)grid;
+}
+
+cudaError_t launch_fold(const double* adev, const double* gate, Vec3<float> d, Vec3<double> x, size_t ny, size_t nu,
+                        cudaStream_t st) {
+  const size_t total = 2 * ny + nu;
+  size_t blocks = (total + kBlock - 1) / kBlock;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  fold_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(adev, gate, d, x, ny, nu);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<double> x, size_t ny, size_t nu,
