@@ -210,3 +210,30 @@ def test_misaligned_vector_is_refused(H):
     assert st == 1
     st = lib.cmg_norm(h._h, 0, ptr(buf), ptr(u), ptr(p), ctypes.byref(out))
     assert st == 0
+
+
+def test_refinement_reports_a_true_residual(H):
+    """FP32 refinement updates its residual recursively in FP32 between FP64
+    anchors; the solve must still stop on, and report, a true FP64 residual
+    of the returned iterate in the paper's row scaling (state rows times N)."""
+    h, P, pr = H
+    f = rhs(h, pr)
+    for graphs in ("1", "0"):
+        import os
+        os.environ["CMG_GRAPHS"] = graphs
+        h2 = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp)
+        try:
+            x = h2.zeros(0)
+            st, status = h2.solve(P.CycleOptions(precision=P.FP32), f, x, tol=1e-10)
+            assert status == 0
+            r = h2.zeros(0)
+            h2.residual(0, x, f, r)
+            w = float(pr.N)
+            num = torch.sqrt((w * r[0]).square().sum() + r[1].square().sum() + r[2].square().sum())
+            den = torch.sqrt((w * f[0]).square().sum() + f[1].square().sum() + f[2].square().sum())
+            true_rel = float(num / den)
+            assert true_rel <= 1e-10
+            assert abs(true_rel - st.relres) <= 1e-3 * st.relres
+        finally:
+            os.environ.pop("CMG_GRAPHS", None)
+            h2.close()
