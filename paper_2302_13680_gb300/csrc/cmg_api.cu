@@ -286,9 +286,8 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   Vec3<T> fc = Work<T>::f(cl), xc = Work<T>::x(cl);
   {
     ProfScope ps(h, CMG_KERNEL_RESTRICT, l);
-    e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream);
+    e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream, xc);   // also sets the coarse iterate to zero
   }
-  if (e == cudaSuccess) e = zero_vec<T>(h, l + 1, xc);
   for (int g = 0; g < o.gamma && e == cudaSuccess; ++g) e = cycle<T>(h, o, l + 1, xc, cview(fc));
   if (e == cudaSuccess) {
     ProfScope ps(h, CMG_KERNEL_PROLONG, l);
@@ -775,6 +774,7 @@ __device__ double block_total(const double* __restrict__ partial, int count) {
 // anchor).  cond is set only when `graph` (a conditional node exists).
 __global__ void ir_recur_control_kernel(const double* __restrict__ partial, int count, double* __restrict__ s,
                                         cudaGraphConditionalHandle cond, int graph) {
+  pdl_enter();
   const double t = block_total(partial, count);
   if (threadIdx.x != 0) return;
   const double rho = sqrt(t) * s[kInvSc];
@@ -794,6 +794,7 @@ __global__ void ir_recur_control_kernel(const double* __restrict__ partial, int 
 // the stopping test.  Does nothing when no anchor ran.
 __global__ void ir_anchor_control_kernel(const double* __restrict__ partial, int count, double* __restrict__ s,
                                          cudaGraphConditionalHandle cond, int graph) {
+  pdl_enter();
   if (s[kAnchor] == 0.0) return;
   const double t = block_total(partial, count);
   if (threadIdx.x != 0) return;
@@ -834,9 +835,9 @@ cmg_status ir_iteration_anchor(cmg_handle* h, Vec3c<double> f, Vec3<double> x, c
   const int cnt = launch_residual_cast(view<double>(h, 0), cview(x), f, f32, 0.0, st + kSc, paper_wy(h), h->part,
                                        h->part_cap, h->stream, st + kAnchor);
   if (cnt < 0) return fail(h, CMG_ERR_CUDA, "refinement pass launch failed");
-  ir_anchor_control_kernel<<<1, 256, 0, h->stream>>>(h->part, cnt, st, cond, graph);
+  CK(launch_k(ir_anchor_control_kernel, dim3(1), dim3(256), 0, h->stream, (const double*)h->part, cnt, st, cond,
+              graph));
   count_launches(1);
-  CK(cudaGetLastError());
   return CMG_OK;
 }
 
@@ -848,13 +849,13 @@ cmg_status ir_iteration(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3
   Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
   Vec3<float> d32{l0.d32[0], l0.d32[1], l0.d32[2]};
   double* st = h->ir_state;
-  CK(zero_vec<float>(h, 0, x32));
+  CK(launch_zero3(x32, l0.nodes * h->prob.N, l0.nodes, h->stream));
   CK(cycle<float>(h, o, 0, x32, cview(f32)));
   int cnt = launch_recur(view<float>(h, 0), cview(x32), f32, d32, paper_wy(h), h->part, h->part_cap, h->stream);
   if (cnt < 0) return fail(h, CMG_ERR_CUDA, "recursive residual launch failed");
-  ir_recur_control_kernel<<<1, 256, 0, h->stream>>>(h->part, cnt, st, cond, graph);
+  CK(launch_k(ir_recur_control_kernel, dim3(1), dim3(256), 0, h->stream, (const double*)h->part, cnt, st, cond,
+              graph));
   count_launches(1);
-  CK(cudaGetLastError());
   if (!anchor_kernels) return CMG_OK;
   return ir_iteration_anchor(h, f, x, cond, graph);
 }

@@ -36,6 +36,16 @@ __device__ __forceinline__ vec<T, V> ldv_if(bool ok, const T* p) {
   return ok ? ldv<T, V>(p) : vzero<T, V>();
 }
 
+// Programmatic dependent launch: a kernel launched with launch_k may start
+// while its predecessor in the stream drains; it waits here, before touching
+// any memory, until the predecessor has completed and its writes are
+// visible, and at once allows its own successor to be scheduled (which in
+// turn waits).  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Sum over the lpn lanes that share a node (aligned groups inside a warp).
 // Every lane of the warp must call this.
 template <typename A>

@@ -2,6 +2,8 @@
 // Nothing here is part of the C ABI (include/cmg.h).
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -78,6 +80,26 @@ struct CoarseData {
   int blocks;
 };
 
+// ---- launches ----
+// Programmatic dependent launch for the kernels of the cycle and the
+// refinement loop (every kernel launched this way starts with pdl_enter);
+// CMG_PDL=0 in the environment turns the attribute off.
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // ---- stencil kernels (cmg_stencil.cu) ----
 // r = f - S x (or r = S x when f.y == nullptr); the y block of r is then
 // multiplied by wy (wy = N gives the paper's row scaling).
@@ -95,7 +117,8 @@ cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int c
 template <typename T>
 cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, double theta, cudaStream_t s);
 template <typename T>
-cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s);
+cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s,
+                            Vec3<T> zx = Vec3<T>{nullptr, nullptr, nullptr});
 template <typename T>
 cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t s);
 
@@ -148,6 +171,7 @@ int launch_recur(const LevelView<float>& L, Vec3c<float> e, Vec3<float> r, Vec3<
                  int max_partials, cudaStream_t s);
 cudaError_t launch_fold(const double* adev, const double* gate, Vec3<float> d, Vec3<double> x, size_t ny, size_t nu,
                         cudaStream_t s);
+cudaError_t launch_zero3(Vec3<float> v, size_t ny, size_t nu, cudaStream_t s);
 cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<double> x, size_t ny, size_t nu,
                          cudaStream_t st);
 

@@ -44,6 +44,7 @@ template <int SPL>
 __global__ void __launch_bounds__(kStageWarps * 32) rbgs_staged_kernel(LevelView<float> L, Vec3<float> x,
                                                                        Vec3c<float> f, int colour, int lpn,
                                                                        long groups) {
+  pdl_enter();
   extern __shared__ __align__(16) float4 sbuf[];
   constexpr int VEC = SPL * kStageVecs;   // vectors per lane per buffer
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -200,12 +201,16 @@ cudaError_t launch_rbgs_half_staged(const LevelView<float>& L, Vec3<float> x, Ve
     const int cap = staged_grid_cap<1>();
     if (cap <= 0) return cudaErrorNotSupported;
     const unsigned grid = (unsigned)(need < cap ? need : cap);
-    rbgs_staged_kernel<1><<<grid, kStageWarps * 32, staged_smem_bytes<1>(), st>>>(L, x, f, colour, m.lpn, groups);
+    const cudaError_t e = launch_k(rbgs_staged_kernel<1>, dim3(grid), dim3(kStageWarps * 32), staged_smem_bytes<1>(),
+                                   st, L, x, f, colour, m.lpn, groups);
+    if (e != cudaSuccess) return e;
   } else {
     const int cap = staged_grid_cap<2>();
     if (cap <= 0) return cudaErrorNotSupported;
     const unsigned grid = (unsigned)(need < cap ? need : cap);
-    rbgs_staged_kernel<2><<<grid, kStageWarps * 32, staged_smem_bytes<2>(), st>>>(L, x, f, colour, m.lpn, groups);
+    const cudaError_t e = launch_k(rbgs_staged_kernel<2>, dim3(grid), dim3(kStageWarps * 32), staged_smem_bytes<2>(),
+                                   st, L, x, f, colour, m.lpn, groups);
+    if (e != cudaSuccess) return e;
   }
   const cudaError_t e = cudaGetLastError();
   count_launches(1);

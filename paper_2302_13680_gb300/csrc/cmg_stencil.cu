@@ -11,6 +11,8 @@
 // the CTAs of adjacent rows, which run close together in launch order.
 // The sum over samples in the control row (u) is a shuffle reduction over
 // the node group, carried in the cycle's precision (FP32 or FP64).
+#include <cstdlib>
+
 #include "cmg_items.cuh"
 
 namespace cmg {
@@ -20,6 +22,7 @@ namespace {
 template <typename T, int V, int SPL>
 __global__ void __launch_bounds__(kBlock) residual_kernel(LevelView<T> L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r,
                                                           int lpn, T wy) {
+  pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   residual_item<T, V, SPL, false>(L, x, f, r, node, threadIdx.x & (lpn - 1), lpn, wy);
 }
@@ -27,6 +30,7 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(LevelView<T> L, Vec3c<
 template <typename T, int V, int SPL>
 __global__ void __launch_bounds__(kBlock) rbgs_half_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, int colour,
                                                            int lpn) {
+  pdl_enter();
   const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   rbgs_item<T, V, SPL, false>(L, x, f, colour, g, threadIdx.x & (lpn - 1), lpn);
 }
@@ -34,19 +38,22 @@ __global__ void __launch_bounds__(kBlock) rbgs_half_kernel(LevelView<T> L, Vec3<
 template <typename T, int V, int SPL>
 __global__ void __launch_bounds__(kBlock) jacobi_update_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> r,
                                                                double theta, int lpn) {
+  pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   jacobi_item<T, V, SPL, false>(L, x, r, theta, node, threadIdx.x & (lpn - 1), lpn);
 }
 
 template <typename T, int V, int SPL>
-__global__ void __launch_bounds__(kBlock) restrict_kernel(int nf, int N, Vec3c<T> r, Vec3<T> cv, int lpn) {
+__global__ void __launch_bounds__(kBlock) restrict_kernel(int nf, int N, Vec3c<T> r, Vec3<T> cv, Vec3<T> zx,
+                                                          int lpn) {
+  pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
-  restrict_item<T, V, SPL, false>(nf, N, r, cv, Vec3<T>{nullptr, nullptr, nullptr}, node, threadIdx.x & (lpn - 1),
-                                  lpn);
+  restrict_item<T, V, SPL, false>(nf, N, r, cv, zx, node, threadIdx.x & (lpn - 1), lpn);
 }
 
 template <typename T, int V, int SPL>
 __global__ void __launch_bounds__(kBlock) prolong_add_kernel(int nf, int N, Vec3c<T> e, Vec3<T> x, int lpn) {
+  pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   prolong_item<T, V, SPL, false>(nf, N, e, x, node, threadIdx.x & (lpn - 1), lpn);
 }
@@ -59,6 +66,7 @@ __global__ void __launch_bounds__(kBlock) residual_cast_kernel(LevelView<double>
                                                               const double* __restrict__ sdev, float wy2,
                                                               double* __restrict__ partial,
                                                               const double* __restrict__ gate) {
+  pdl_enter();
   __shared__ double sh[kBlock / 32];
   if (gate && *gate == 0.0) return;   // refinement anchor not due (residual replacement)
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
@@ -83,6 +91,7 @@ template <int V, int SPL>
 __global__ void __launch_bounds__(kBlock) recur_kernel(LevelView<float> L, Vec3c<float> e, Vec3<float> r,
                                                        Vec3<float> d, int lpn, float wy2,
                                                        double* __restrict__ partial) {
+  pdl_enter();
   __shared__ double sh[kBlock / 32];
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   const int lane = threadIdx.x & (lpn - 1);
@@ -131,6 +140,7 @@ __global__ void __launch_bounds__(kBlock) recur_kernel(LevelView<float> L, Vec3c
 // *gate is nonzero.
 __global__ void fold_kernel(const double* __restrict__ adev, const double* __restrict__ gate, Vec3<float> d,
                             Vec3<double> x, size_t ny, size_t nu) {
+  pdl_enter();
   if (*gate == 0.0) return;
   const double a = *adev;
   const size_t total = 2 * ny + nu;
@@ -148,10 +158,23 @@ __global__ void fold_kernel(const double* __restrict__ adev, const double* __res
   }
 }
 
+// (y, u, p) = 0 for an FP32 level vector (a kernel, so that it can be a
+// programmatic dependent of the kernels around it).
+__global__ void zero3_kernel(Vec3<float> v, size_t ny, size_t nu) {
+  pdl_enter();
+  const size_t total = 2 * ny + nu;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    if (i < ny) v.y[i] = 0.f;
+    else if (i < ny + nu) v.u[i - ny] = 0.f;
+    else v.p[i - ny - nu] = 0.f;
+  }
+}
+
 // x += a * e for the three blocks (FP64 iterate, FP32 correction); a read
 // from adev when given.
 __global__ void axpy3_kernel(double a0, const double* __restrict__ adev, Vec3c<float> e, Vec3<double> x, size_t ny,
                              size_t nu) {
+  pdl_enter();
   const double a = adev ? *adev : a0;
   const size_t total = 2 * ny + nu;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -167,6 +190,14 @@ inline unsigned grid_for(long groups, int lpn) {
 }
 
 }  // namespace
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("CMG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 
 SampleMap choose_map(int N, int elem_bytes, long items, int spl_target) {
   SampleMap m;
@@ -193,9 +224,10 @@ template <typename T>
 cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r, cudaStream_t st, double wy) {
   const SampleMap m = choose_map(L.N, sizeof(T), (long)L.n * L.n, L.spl_target);
   const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
-  CMG_DISPATCH(T, m, (residual_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, r, m.lpn, (T)wy)));
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(residual_kernel<T, V, SPL>, grid, kBlock, 0, st, L, x, f, r, m.lpn, (T)wy)));
   count_launches(1);
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 template <typename T>
@@ -208,37 +240,41 @@ cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int c
     }
   }
   const unsigned grid = grid_for(colour_count(L.n, colour), m.lpn);
-  CMG_DISPATCH(T, m, (rbgs_half_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, colour, m.lpn)));
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(rbgs_half_kernel<T, V, SPL>, grid, kBlock, 0, st, L, x, f, colour, m.lpn)));
   count_launches(1);
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, double theta, cudaStream_t st) {
   const SampleMap m = choose_map(L.N, sizeof(T), (long)L.n * L.n, L.spl_target);
   const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
-  CMG_DISPATCH(T, m, (jacobi_update_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(L, x, r, theta, m.lpn)));
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(jacobi_update_kernel<T, V, SPL>, grid, kBlock, 0, st, L, x, r, theta, m.lpn)));
   count_launches(1);
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t st) {
+cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t st, Vec3<T> zx) {
   const int nc = (nf - 1) / 2;
   const SampleMap m = choose_map(N, sizeof(T), (long)nc * nc);
   const unsigned grid = grid_for((long)nc * nc, m.lpn);
-  CMG_DISPATCH(T, m, (restrict_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(nf, N, r, c, m.lpn)));
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(restrict_kernel<T, V, SPL>, grid, kBlock, 0, st, nf, N, r, c, zx, m.lpn)));
   count_launches(1);
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t st) {
   const SampleMap m = choose_map(N, sizeof(T), (long)nf * nf);
   const unsigned grid = grid_for((long)nf * nf, m.lpn);
-  CMG_DISPATCH(T, m, (prolong_add_kernel<T, V, SPL><<<grid, kBlock, 0, st>>>(nf, N, e, x, m.lpn)));
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(prolong_add_kernel<T, V, SPL>, grid, kBlock, 0, st, nf, N, e, x, m.lpn)));
   count_launches(1);
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 int launch_residual_cast(const LevelView<double>& L, Vec3c<double> x, Vec3c<double> f, Vec3<float> r, double s,
@@ -250,9 +286,10 @@ int launch_residual_cast(const LevelView<double>& L, Vec3c<double> x, Vec3c<doub
   const float wy2 = (float)(wy * wy);
   using T = double;
   auto go = [&]() -> cudaError_t {
-    CMG_DISPATCH(T, m, (residual_cast_kernel<V, SPL><<<grid, kBlock, 0, st>>>(L, x, f, r, m.lpn, s, sdev, wy2,
-                                                                             partial, gate)));
-    return cudaGetLastError();
+    cudaError_t e_ = cudaSuccess;
+    CMG_DISPATCH(T, m, (e_ = launch_k(residual_cast_kernel<V, SPL>, grid, kBlock, 0, st, L, x, f, r, m.lpn, s, sdev,
+                                                   wy2, partial, gate)));
+    return e_ != cudaSuccess ? e_ : cudaGetLastError();
   };
   if (go() != cudaSuccess) return -1;
   count_launches(1);
@@ -267,8 +304,9 @@ int launch_recur(const LevelView<float>& L, Vec3c<float> e, Vec3<float> r, Vec3<
   const float wy2 = (float)(wy * wy);
   using T = float;
   auto go = [&]() -> cudaError_t {
-    CMG_DISPATCH(T, m, (recur_kernel<V, SPL><<<grid, kBlock, 0, st>>>(L, e, r, d, m.lpn, wy2, partial)));
-    return cudaGetLastError();
+    cudaError_t e_ = cudaSuccess;
+    CMG_DISPATCH(T, m, (e_ = launch_k(recur_kernel<V, SPL>, grid, kBlock, 0, st, L, e, r, d, m.lpn, wy2, partial)));
+    return e_ != cudaSuccess ? e_ : cudaGetLastError();
   };
   if (go() != cudaSuccess) return -1;
   count_launches(1);
@@ -280,9 +318,19 @@ cudaError_t launch_fold(const double* adev, const double* gate, Vec3<float> d, V
   const size_t total = 2 * ny + nu;
   size_t blocks = (total + kBlock - 1) / kBlock;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  fold_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(adev, gate, d, x, ny, nu);
+  const cudaError_t e_ = launch_k(fold_kernel, dim3((unsigned)blocks), dim3(kBlock), 0, st, adev, gate, d, x, ny, nu);
+  if (e_ != cudaSuccess) return e_;
   count_launches(1);
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
+}
+
+cudaError_t launch_zero3(Vec3<float> v, size_t ny, size_t nu, cudaStream_t st) {
+  const size_t total = 2 * ny + nu;
+  size_t blocks = (total + kBlock - 1) / kBlock;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const cudaError_t e_ = launch_k(zero3_kernel, dim3((unsigned)blocks), dim3(kBlock), 0, st, v, ny, nu);
+  count_launches(1);
+  return e_;
 }
 
 cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<double> x, size_t ny, size_t nu,
@@ -290,16 +338,17 @@ cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<doub
   const size_t total = 2 * ny + nu;
   size_t blocks = (total + kBlock - 1) / kBlock;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  axpy3_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(a, adev, e, x, ny, nu);
+  const cudaError_t e_ = launch_k(axpy3_kernel, dim3((unsigned)blocks), dim3(kBlock), 0, st, a, adev, e, x, ny, nu);
+  if (e_ != cudaSuccess) return e_;
   count_launches(1);
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 #define CMG_INST(T)                                                                                   \
   template cudaError_t launch_residual<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t, double); \
   template cudaError_t launch_rbgs_half<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, int, cudaStream_t);    \
   template cudaError_t launch_jacobi_update<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, double, cudaStream_t); \
-  template cudaError_t launch_restrict<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t);                     \
+  template cudaError_t launch_restrict<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t, Vec3<T>);                     \
   template cudaError_t launch_prolong_add<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t);
 
 CMG_INST(double)

@@ -137,6 +137,7 @@ __device__ void coarse_cta(const TailParams<T>& P, const Vec3<T>& x, const Vec3<
 
 template <typename T, int V, int SPL, int MM>
 __global__ void __launch_bounds__(kTailThreads) tail_cycle_kernel(const __grid_constant__ TailParams<T> P) {
+  pdl_enter();
   const cg::cluster_group cl = cg::this_cluster();
   const int lpn = P.lpn;
   const long ctid = (long)cl.block_rank() * blockDim.x + threadIdx.x;
