@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--impl", default="cmg", choices=["cmg", "reference"])
     ap.add_argument("--config", default="n255_N64", choices=sorted(inputs.CONFIGS) + ["batch96"])
     ap.add_argument("--form", default="auto", choices=["auto", "fp64-fgmres", "fp64-cycle", "fp32-ir",
-                                                        "fp32-fgmres"])
+                                                        "fp32-ir-launches", "fp32-fgmres"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -210,6 +210,9 @@ FORMS = {
     "fp64-fgmres": dict(precision=0, method=1),
     "fp64-cycle": dict(precision=0, method=0),
     "fp32-ir": dict(precision=1, method=0),
+    # the same with every coarse grid run one launch per step (tail_n = 0)
+    # instead of the cluster kernel for n <= 31
+    "fp32-ir-launches": dict(precision=1, method=0, tail_n=0),
     "fp32-fgmres": dict(precision=1, method=1),
 }
 
@@ -313,7 +316,8 @@ def run_cmg(args, world, rank, local):
             a.copy_(b)
         for t in x:
             t.zero_()
-        st, status = H.solve(P.CycleOptions(precision=spec["precision"]), f, x, method=spec["method"],
+        st, status = H.solve(P.CycleOptions(precision=spec["precision"], tail_n=spec.get("tail_n", 31)), f, x,
+                             method=spec["method"],
                              tol=tol, maxit=200, restart=restart, raise_on_fail=False)
         if status != 0:
             raise RuntimeError(f"form {form} did not reach {tol}: status {status}, relres {st.relres:.3e}")
@@ -341,7 +345,7 @@ def run_cmg(args, world, rank, local):
     # --- compare forms (untimed for the result line, reported as context)
     forms = list(FORMS) if args.form == "auto" else [args.form]
     if args.form == "auto" and n * n * N > 50_000_000:
-        forms = ["fp64-cycle", "fp32-ir"]     # the Krylov forms would hold 2 x restart 4 GB vectors
+        forms = ["fp64-cycle", "fp32-ir", "fp32-ir-launches"]   # the Krylov forms would hold 2 x restart 4 GB vectors
     survey = {}
     for form in forms:
         for _ in range(2):
