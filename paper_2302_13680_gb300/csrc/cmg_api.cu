@@ -63,7 +63,11 @@ struct cmg_handle {
   cudaStream_t stream = nullptr;
   int L = 0;
   Lev lv[kMaxLevels];
-  CoarseData coarse{};
+  CoarseData coarse{};     // coarsest-grid inverses from the FP64 operators (FP64 cycles)
+  CoarseData coarse32{};   // from the FP32 operators (FP32 cycles; averaged coarse grids only)
+  double* cface64 = nullptr;   // coarsest FP32 faces promoted to FP64 for coarse32's set-up
+  bool fp64_ready = false;     // FP64 operators below the finest faces are current
+  CoarseData& c32() { return prob.coarse_coeff == CMG_COARSE_NODAL ? coarse : coarse32; }
   double* xi = nullptr;       // [N][K] device
   double* kap = nullptr;      // setup scratch
   double* red = nullptr;      // reduction partials
@@ -161,25 +165,69 @@ bool vec_ok(const T* y, const T* u, const T* p) {
   return y && u && p && a16(y) && a16(u) && a16(p);
 }
 
+// Operators for a new sample set.  Averaged coarse grids (default): the
+// finest FP64 + FP32 faces and diag(A) (the FP64 refinement residual needs
+// them), then the FP32 cycle's operators on every grid, built in FP32; the
+// FP64 operators below the finest faces wait for ensure_fp64.  Nodal coarse
+// grids: everything at once, as each grid samples the field itself.
 cudaError_t setup_coefficients(cmg_handle* h) {
   const cmg_problem& P = h->prob;
-  for (int l = 0; l < h->L; ++l) {
-    Lev& v = h->lv[l];
-    cudaError_t e;
-    if (l == 0 || P.coarse_coeff == CMG_COARSE_NODAL) {
-      e = launch_level_setup(v.n, P.N, P.K, P.amp, h->xi, h->kap, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.isigma,
-                             v.c, v.G, v.d, v.e, h->stream);
-    } else {
-      const Lev& f = h->lv[l - 1];
-      e = launch_coarse_level_setup(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, v.kx32, v.ky32, v.inva, v.isigma, v.c,
-                                    v.G, v.d, v.e, h->stream);
+  if (P.coarse_coeff == CMG_COARSE_NODAL) {
+    for (int l = 0; l < h->L; ++l) {
+      Lev& v = h->lv[l];
+      cudaError_t e = launch_level_setup(v.n, P.N, P.K, P.amp, h->xi, h->kap, v.kx64, v.ky64, v.kx32, v.ky32, v.inva,
+                                         v.isigma, v.c, v.G, v.d, v.e, h->stream);
+      if (e == cudaSuccess) e = launch_scale_cast<double, float>(1.0, v.isigma, v.isigma32, v.nodes, h->stream);
+      if (e == cudaSuccess && v.a64) e = launch_diag_sum(v.n, P.N, v.kx64, v.ky64, v.a64, h->stream);
+      if (e != cudaSuccess) return e;
     }
-    if (e == cudaSuccess) e = launch_scale_cast<double, float>(1.0, v.isigma, v.isigma32, v.nodes, h->stream);
-    if (e == cudaSuccess && v.a64) e = launch_diag_sum(v.n, P.N, v.kx64, v.ky64, v.a64, h->stream);
-    if (e != cudaSuccess) return e;
+    const Lev& cl = h->lv[h->L - 1];
+    h->fp64_ready = true;
+    return launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
   }
+  h->fp64_ready = false;
+  Lev& v0 = h->lv[0];
+  cudaError_t e = launch_field_faces(v0.n, P.N, P.K, P.amp, h->xi, h->kap, v0.kx64, v0.ky64, v0.kx32, v0.ky32,
+                                     h->stream);
+  if (e == cudaSuccess) e = launch_diag_sum(v0.n, P.N, v0.kx64, v0.ky64, v0.a64, h->stream);
+  for (int l = 0; l < h->L && e == cudaSuccess; ++l) {
+    Lev& v = h->lv[l];
+    if (l > 0) {
+      const Lev& f = h->lv[l - 1];
+      e = launch_coarse_faces32(f.n, P.N, f.kx32, f.ky32, v.kx32, v.ky32, h->stream);
+    }
+    if (e == cudaSuccess) e = launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G, h->stream);
+  }
+  if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
-  return launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
+  const size_t cf = (size_t)cl.n * (cl.n + 1) * P.N;
+  e = launch_scale_cast<float, double>(1.0, cl.kx32, h->cface64, cf, h->stream);
+  if (e == cudaSuccess) e = launch_scale_cast<float, double>(1.0, cl.ky32, h->cface64 + cf, cf, h->stream);
+  if (e != cudaSuccess) return e;
+  return launch_coarse_setup(h->coarse32, h->cface64, h->cface64 + cf, cl.c, cl.G, cl.d, cl.e, h->stream);
+}
+
+// The FP64 operators below the finest faces (1/diag, 1/sigma on every grid,
+// the averaged coarse faces, the coarsest inverses), built on the handle's
+// stream the first time an FP64 cycle, smoother or coarse solve needs them
+// after a new sample set.
+cudaError_t ensure_fp64(cmg_handle* h) {
+  if (h->fp64_ready) return cudaSuccess;
+  const cmg_problem& P = h->prob;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < h->L && e == cudaSuccess; ++l) {
+    Lev& v = h->lv[l];
+    if (l > 0) {
+      const Lev& f = h->lv[l - 1];
+      e = launch_coarse_faces64(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, h->stream);
+    }
+    if (e == cudaSuccess) e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, v.G, h->stream);
+  }
+  if (e != cudaSuccess) return e;
+  const Lev& cl = h->lv[h->L - 1];
+  e = launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
+  if (e == cudaSuccess) h->fp64_ready = true;
+  return e;
 }
 
 // ---- smoothing and cycles --------------------------------------------------
@@ -249,11 +297,12 @@ cudaError_t tail_cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3
   P.theta = o.theta;
   P.freeze_u = o.freeze_u;
   P.lpn = choose_map(h->prob.N, sizeof(T), 0).lpn;
-  P.cm = h->coarse.m;
-  P.cN = h->coarse.N;
-  P.Ainv = h->coarse.Ainv;
-  P.Minv = h->coarse.Minv;
-  P.wz = h->coarse.wz;
+  const CoarseData& cd = sizeof(T) == 4 ? h->c32() : h->coarse;
+  P.cm = cd.m;
+  P.cN = cd.N;
+  P.Ainv = cd.Ainv;
+  P.Minv = cd.Minv;
+  P.wz = cd.wz;
   const Lev& cl = h->lv[h->L - 1];
   P.cc = cl.c;
   P.cd = cl.d;
@@ -272,7 +321,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   }
   if (l == h->L - 1) {
     ProfScope ps(h, CMG_KERNEL_COARSE, l);
-    return launch_coarse_solve<T>(h->coarse, v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
+    return launch_coarse_solve<T>(sizeof(T) == 4 ? h->c32() : h->coarse, v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
   }
   cudaError_t e = smooth<T>(h, o, l, o.n1, x, f);
   if (e != cudaSuccess) return e;
@@ -411,6 +460,17 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   AL(h->coarse.Minv, (size_t)h->coarse.m * h->coarse.m);
   AL(h->coarse.wz, std::max(2 * N * h->coarse.m, (size_t)h->coarse.m * h->coarse.m));
   AL(h->coarse.partial, (size_t)h->coarse.blocks * h->coarse.m);
+  if (P.coarse_coeff != CMG_COARSE_NODAL) {
+    h->coarse32.n = h->coarse.n;
+    h->coarse32.m = h->coarse.m;
+    h->coarse32.N = h->coarse.N;
+    h->coarse32.blocks = h->coarse.blocks;
+    AL(h->coarse32.Ainv, N * h->coarse.m * h->coarse.m);
+    AL(h->coarse32.Minv, (size_t)h->coarse.m * h->coarse.m);
+    AL(h->coarse32.wz, std::max(2 * N * h->coarse.m, (size_t)h->coarse.m * h->coarse.m));
+    AL(h->coarse32.partial, (size_t)h->coarse.blocks * h->coarse.m);
+    AL(h->cface64, 2 * (size_t)cn * (cn + 1) * N);
+  }
 #undef AL
   if (e == cudaSuccess) {
     void* hp = nullptr;
@@ -474,6 +534,7 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!level_ok(h, level)) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");                        \
     if (!vec_ok(y, u, p) || !vec_ok(ry, ru, rp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
     if ((fy || fu || fp) && !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "partial rhs");           \
+    if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
     CK(launch_residual<T>(view<T>(h, level), Vec3c<T>{y, u, p}, Vec3c<T>{fy, fu, fp}, Vec3<T>{ry, ru, rp},     \
                           h->stream));                                                                          \
     return CMG_OK;                                                                                              \
@@ -488,6 +549,7 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     o.n1 = o.n2 = 0; o.gamma = 1; o.precision = sizeof(T) == 8 ? CMG_FP64 : CMG_FP32;                           \
     const cmg_status st = check_cycle(h, &o);                                                                   \
     if (st != CMG_OK) return st;                                                                                \
+    if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
     CK(smooth<T>(h, o, level, sweeps, Vec3<T>{y, u, p}, Vec3c<T>{fy, fu, fp}));                                \
     return CMG_OK;                                                                                              \
   }                                                                                                             \
@@ -511,7 +573,9 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
     if (!vec_ok(fy, fu, fp) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
     const Lev& v = h->lv[h->L - 1];                                                                             \
-    CK(launch_coarse_solve<T>(h->coarse, v.c, v.d, v.e, Vec3c<T>{fy, fu, fp}, Vec3<T>{y, u, p}, h->stream));   \
+    if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
+    CK(launch_coarse_solve<T>(sizeof(T) == 4 ? h->c32() : h->coarse, v.c, v.d, v.e, Vec3c<T>{fy, fu, fp},      \
+                              Vec3<T>{y, u, p}, h->stream));                                                    \
     return CMG_OK;                                                                                              \
   }                                                                                                             \
   cmg_status cmg_cycle_apply##SUF(cmg_handle* h, const cmg_cycle* opts, T* y, T* u, T* p, const T* fy,          \
@@ -522,6 +586,7 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (opts->precision != (sizeof(T) == 8 ? CMG_FP64 : CMG_FP32))                                              \
       return fail(h, CMG_ERR_INVALID_ARG, "precision does not match the vector type");                         \
     if (!vec_ok(y, u, p) || !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
+    if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
     CK(cycle<T>(h, *opts, 0, Vec3<T>{y, u, p}, Vec3c<T>{fy, fu, fp}));                                          \
     return CMG_OK;                                                                                              \
   }
@@ -656,7 +721,10 @@ extern "C" {
 cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen) {
   if (!h) return CMG_ERR_INVALID_ARG;
   h->ir_opts.n1 = -1;   // captured graphs bake the launch shapes: force a re-capture
-  if (precision == CMG_FP64) return autotune_levels<double>(h, chosen);
+  if (precision == CMG_FP64) {
+    CK(ensure_fp64(h));
+    return autotune_levels<double>(h, chosen);
+  }
   if (precision == CMG_FP32) return autotune_levels<float>(h, chosen);
   return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");
 }
@@ -1199,6 +1267,7 @@ extern "C" cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method
     CK(cudaStreamSynchronize(h->stream));
     return CMG_OK;
   }
+  if (opts->precision == CMG_FP64) CK(ensure_fp64(h));
   if (method == CMG_METHOD_CYCLE) return solve_cycle(h, *opts, tol, maxit, f, x, fnorm, st);
   return solve_fgmres(h, *opts, tol, maxit, restart, f, x, fnorm, st);
 }

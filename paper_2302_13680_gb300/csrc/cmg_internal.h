@@ -198,6 +198,21 @@ cudaError_t launch_coarse_level_setup(int nf, int N, const double* kxf, const do
                                       double* ky64, float* kx32, float* ky32, double* inva, double* isigma,
                                       double c, double G, double d, double e, cudaStream_t s);
 
+// Split set-up used for the averaged coarse grids: the FP32 cycle's
+// operators (finest FP32 faces rounded from FP64, coarse FP32 faces averaged
+// in FP32, 1/sigma from those) are built with every new sample set; the FP64
+// coarse operators only when an FP64 cycle needs them.
+cudaError_t launch_field_faces(int n, int N, int K, double amp, const double* xi, double* kap, double* kx64,
+                               double* ky64, float* kx32, float* ky32, cudaStream_t s);
+cudaError_t launch_diag64(int n, int N, const double* kx64, const double* ky64, double* inva, double* isigma,
+                          double dce, double G, cudaStream_t s);
+cudaError_t launch_coarse_faces64(int nf, int N, const double* kxf, const double* kyf, double* kx64, double* ky64,
+                                  cudaStream_t s);
+cudaError_t launch_coarse_faces32(int nf, int N, const float* kxf, const float* kyf, float* kx32, float* ky32,
+                                  cudaStream_t s);
+cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double dce, double G,
+                          cudaStream_t s);
+
 // ---- vector kernels (cmg_blas.cu) ----
 constexpr int kRedBlocks = 304;    // fixed partial count: deterministic reductions
 // partial[0..kRedBlocks) (+)= w2 * per-block sums of squares; call finish to combine.

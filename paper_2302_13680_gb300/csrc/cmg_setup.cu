@@ -25,15 +25,22 @@ __global__ void field_x_kernel(int n, int N, int K, const double* __restrict__ x
 }
 
 // kap[iy][ix][j] = exp(amp * sin(pi y_iy) * gx[ix][j]) on the (n+2)^2 grid.
+// sin(pi y) is symmetric about y = 1/2 (rows iy and n+1-iy), so each
+// exponential is evaluated once for both rows (the FP64 exponential is the
+// cost of this kernel on a GPU with a narrow FP64 pipe); the boundary rows
+// have sin(pi y) = 0, kappa = 1.
 __global__ void field_kernel(int n, int N, double amp, const double* __restrict__ gx, double* __restrict__ kap) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long total = (long)(n + 2) * (n + 2) * N;
+  const int half = (n + 1) / 2;   // rows 0 .. half; n + 1 is even
+  const long total = (long)(half + 1) * (n + 2) * N;
   if (t >= total) return;
   const long node = t / N;
   const int j = (int)(t - node * N);
   const int iy = (int)(node / (n + 2)), ix = (int)(node - (long)iy * (n + 2));
-  const double sy = sinpi((double)iy / (double)(n + 1));
-  kap[t] = exp(amp * sy * gx[(size_t)ix * N + j]);
+  const double v = iy == 0 ? 1.0 : exp(amp * sinpi((double)iy / (double)(n + 1)) * gx[(size_t)ix * N + j]);
+  kap[((size_t)iy * (n + 2) + ix) * N + j] = v;
+  const int mirror = n + 1 - iy;
+  if (mirror != iy) kap[((size_t)mirror * (n + 2) + ix) * N + j] = v;
 }
 
 __device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
@@ -107,7 +114,7 @@ __global__ void coarse_faces_kernel(int nf, int N, const double* __restrict__ kx
       v += w[k] * harmonic(kxf[(row + 2 * I) * N + j], kxf[(row + 2 * I + 1) * N + j]);
     }
     kx64[t] = v;
-    kx32[t] = (float)v;
+    if (kx32) kx32[t] = (float)v;
   } else {
     const long tt = t - per;
     const long face = tt / N;
@@ -118,8 +125,60 @@ __global__ void coarse_faces_kernel(int nf, int N, const double* __restrict__ kx
       v += w[k] * harmonic(kyf[((size_t)(2 * J) * nf + col) * N + j], kyf[((size_t)(2 * J + 1) * nf + col) * N + j]);
     }
     ky64[tt] = v;
-    ky32[tt] = (float)v;
+    if (ky32) ky32[tt] = (float)v;
   }
+}
+
+// The same averaging in FP32 from the finer grid's FP32 faces: the FP32
+// cycle's coarse operators, built without the FP64 pipe.
+__global__ void coarse_faces32_kernel(int nf, int N, const float* __restrict__ kxf, const float* __restrict__ kyf,
+                                      float* __restrict__ kx32, float* __restrict__ ky32) {
+  const int nc = (nf - 1) / 2;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per = (long)nc * (nc + 1) * N;
+  if (t >= 2 * per) return;
+  const float w[3] = {0.25f, 0.5f, 0.25f};
+  const auto hm = [](float a, float b) { return 2.0f * a * b / (a + b); };
+  float v = 0.f;
+  if (t < per) {
+    const long face = t / N;
+    const int j = (int)(t - face * N);
+    const int J = (int)(face / (nc + 1)), I = (int)(face - (long)J * (nc + 1));
+    for (int k = 0; k < 3; ++k) {
+      const size_t row = (size_t)(2 * J + k) * (nf + 1);
+      v += w[k] * hm(kxf[(row + 2 * I) * N + j], kxf[(row + 2 * I + 1) * N + j]);
+    }
+    kx32[t] = v;
+  } else {
+    const long tt = t - per;
+    const long face = tt / N;
+    const int j = (int)(tt - face * N);
+    const int J = (int)(face / nc), I = (int)(face - (long)J * nc);
+    for (int k = 0; k < 3; ++k) {
+      const size_t col = (size_t)(2 * I + k);
+      v += w[k] * hm(kyf[((size_t)(2 * J) * nf + col) * N + j], kyf[((size_t)(2 * J + 1) * nf + col) * N + j]);
+    }
+    ky32[tt] = v;
+  }
+}
+
+// isigma32[node] = 1 / (G + dce sum_j 1/a_j^2) from the FP32 faces (sum in
+// FP32 over a warp per node, the quotient in FP64).
+__global__ void diag32_kernel(int n, int N, const float* __restrict__ kx, const float* __restrict__ ky,
+                              float* __restrict__ isigma32, double dce, double G) {
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (long)n * n) return;
+  const int iy = (int)(warp / n), ix = (int)(warp - (long)iy * n);
+  const float* kW = kx + ((size_t)iy * (n + 1) + ix) * N;
+  const float* kS = ky + ((size_t)iy * n + ix) * N;
+  float s = 0.f;
+  for (int j = lane; j < N; j += 32) {
+    const float ia = __frcp_rn((kW[j] + kW[N + j]) + (kS[j] + kS[(size_t)n * N + j]));
+    s += ia * ia;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) isigma32[warp] = (float)(1.0 / (G + dce * (double)s));
 }
 
 inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
@@ -180,7 +239,7 @@ cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi
   // gx lives in the tail of kap's scratch: (n+2)*N doubles after the field.
   double* gx = kap + (size_t)(n + 2) * (n + 2) * N;
   field_x_kernel<<<blocks_for((long)(n + 2) * N, 256), 256, 0, s>>>(n, N, K, xi, gx);
-  field_kernel<<<blocks_for((long)(n + 2) * (n + 2) * N, 256), 256, 0, s>>>(n, N, amp, gx, kap);
+  field_kernel<<<blocks_for((long)((n + 1) / 2 + 1) * (n + 2) * N, 256), 256, 0, s>>>(n, N, amp, gx, kap);
   faces_kernel<<<blocks_for(2L * n * (n + 1) * N, 256), 256, 0, s>>>(n, N, kap, kx64, ky64, kx32, ky32);
   diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, isigma, d * c * e, G);
   count_launches(4);
@@ -189,6 +248,48 @@ cudaError_t launch_level_setup(int n, int N, int K, double amp, const double* xi
 
 cudaError_t launch_diag_sum(int n, int N, const double* kx, const double* ky, double* a, cudaStream_t s) {
   diag_sum_kernel<<<blocks_for((long)n * n * N, 256), 256, 0, s>>>(n, N, kx, ky, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Finest grid (or a nodal grid): field and FP64 + FP32 faces only.
+cudaError_t launch_field_faces(int n, int N, int K, double amp, const double* xi, double* kap, double* kx64,
+                               double* ky64, float* kx32, float* ky32, cudaStream_t s) {
+  double* gx = kap + (size_t)(n + 2) * (n + 2) * N;
+  field_x_kernel<<<blocks_for((long)(n + 2) * N, 256), 256, 0, s>>>(n, N, K, xi, gx);
+  field_kernel<<<blocks_for((long)((n + 1) / 2 + 1) * (n + 2) * N, 256), 256, 0, s>>>(n, N, amp, gx, kap);
+  faces_kernel<<<blocks_for(2L * n * (n + 1) * N, 256), 256, 0, s>>>(n, N, kap, kx64, ky64, kx32, ky32);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag64(int n, int N, const double* kx64, const double* ky64, double* inva, double* isigma,
+                          double dce, double G, cudaStream_t s) {
+  diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, isigma, dce, G);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_faces64(int nf, int N, const double* kxf, const double* kyf, double* kx64, double* ky64,
+                                  cudaStream_t s) {
+  const int nc = (nf - 1) / 2;
+  coarse_faces_kernel<<<blocks_for(2L * nc * (nc + 1) * N, 256), 256, 0, s>>>(nf, N, kxf, kyf, kx64, ky64, nullptr,
+                                                                              nullptr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_faces32(int nf, int N, const float* kxf, const float* kyf, float* kx32, float* ky32,
+                                  cudaStream_t s) {
+  const int nc = (nf - 1) / 2;
+  coarse_faces32_kernel<<<blocks_for(2L * nc * (nc + 1) * N, 256), 256, 0, s>>>(nf, N, kxf, kyf, kx32, ky32);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double dce, double G,
+                          cudaStream_t s) {
+  diag32_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx32, ky32, isigma32, dce, G);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -237,3 +237,35 @@ def test_refinement_reports_a_true_residual(H):
         finally:
             os.environ.pop("CMG_GRAPHS", None)
             h2.close()
+
+
+def test_new_samples_rebuild_fp64_and_fp32_operators(H):
+    """After cmg_set_samples the FP32 operators are rebuilt at once and the
+    FP64 coarse operators on first FP64 use: both precisions then agree bit
+    for bit with a handle created with the new samples."""
+    h, P, pr = H
+    spec = dict(inputs.CONFIGS["n31_N8"])
+    spec["seed"] = 11
+    pr2 = inputs.make_problem(**spec)
+    fresh = P.Hierarchy(pr2.n, pr2.N, pr2.xi, pr2.nu, pr2.amp)
+    try:
+        h.set_samples(torch.tensor(pr2.xi, device="cuda"))
+        yd = torch.tensor(pr2.yd.reshape(-1), dtype=torch.float64, device="cuda")
+        for hh in (h, fresh):
+            hh.f = hh.rhs(yd)
+        outs = []
+        for hh in (h, fresh):
+            x32 = hh.zeros(0, torch.float32)
+            hh.cycle(P.CycleOptions(precision=P.FP32), x32, tuple(t.float() for t in hh.f))
+            x64 = hh.zeros(0)
+            hh.cycle(P.CycleOptions(), x64, hh.f)
+            xs = hh.zeros(0)
+            st, status = hh.solve(P.CycleOptions(precision=P.FP32), hh.f, xs)
+            assert status == 0
+            outs.append((x32, x64, xs))
+        for a, b in zip(*outs):
+            for ta, tb in zip(a, b):
+                assert torch.equal(ta, tb)
+    finally:
+        h.set_samples(torch.tensor(pr.xi, device="cuda"))
+        fresh.close()
