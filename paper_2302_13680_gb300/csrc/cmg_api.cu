@@ -326,16 +326,20 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   cudaError_t e = smooth<T>(h, o, l, o.n1, x, f);
   if (e != cudaSuccess) return e;
   Vec3<T> r = Work<T>::r(v);
+  // after red-black pre-smoothing (last half-sweep: colour 1) with the control
+  // updated, the residual vanishes at colour 1: compute and restrict colour 0
+  const int c0 = (o.smoother == CMG_SMOOTH_RBGS && o.n1 >= 1 && !o.freeze_u) ? 1 : 0;
   {
     ProfScope ps(h, CMG_KERNEL_RESIDUAL, l);
-    e = launch_residual<T>(view<T>(h, l), cview(x), f, r, h->stream);
+    e = c0 ? launch_residual_c0<T>(view<T>(h, l), cview(x), f, r, h->stream)
+           : launch_residual<T>(view<T>(h, l), cview(x), f, r, h->stream);
   }
   if (e != cudaSuccess) return e;
   Lev& cl = h->lv[l + 1];
   Vec3<T> fc = Work<T>::f(cl), xc = Work<T>::x(cl);
   {
     ProfScope ps(h, CMG_KERNEL_RESTRICT, l);
-    e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream, xc);   // also sets the coarse iterate to zero
+    e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream, xc, c0);   // also sets the coarse iterate to zero
   }
   for (int g = 0; g < o.gamma && e == cudaSuccess; ++g) e = cycle<T>(h, o, l + 1, xc, cview(fc));
   if (e == cudaSuccess) {

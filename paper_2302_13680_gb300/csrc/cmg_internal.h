@@ -116,9 +116,16 @@ template <typename T>
 cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t s);
 template <typename T>
 cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, double theta, cudaStream_t s);
+// r = f - S x at the colour-0 nodes only: after a red-black sweep whose
+// last half-sweep updated colour 1, the residual at the colour-1 nodes
+// vanishes (each local solve satisfied that node's equations given
+// neighbours that did not change since), so the restriction reads only
+// colour-0 points (launch_restrict with colour0 = 1).
+template <typename T>
+cudaError_t launch_residual_c0(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s,
-                            Vec3<T> zx = Vec3<T>{nullptr, nullptr, nullptr});
+                            Vec3<T> zx = Vec3<T>{nullptr, nullptr, nullptr}, int colour0 = 0);
 template <typename T>
 cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t s);
 

@@ -282,10 +282,12 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
 // ---------------------------------------------------------------------------
 
 // c = P^T r at one coarse node (weights 1, 1/2, 1/4); if zx.y is set, the
-// coarse iterate at that node is also cleared (zero initial guess).
+// coarse iterate at that node is also cleared (zero initial guess).  With
+// colour0, r is known to vanish at the colour-1 fine points (the four edge
+// neighbours of the coinciding point), which are then not read.
 template <typename T, int V, int SPL, bool CG>
 __device__ __forceinline__ void restrict_item(int nf, int N, const Vec3c<T>& r, const Vec3<T>& cv,
-                                              const Vec3<T>& zx, long node, int lane, int lpn) {
+                                              const Vec3<T>& zx, long node, int lane, int lpn, bool colour0 = false) {
   const int nc = (nf - 1) / 2;
   if (node >= (long)nc * nc) return;   // no shuffles below
   const int J = (int)(node / nc), I = (int)(node - (long)J * nc);
@@ -301,6 +303,7 @@ __device__ __forceinline__ void restrict_item(int nf, int N, const Vec3c<T>& r, 
       for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
+          if (colour0 && ((dx + dy) & 1)) continue;   // edge points are colour 1: residual zero
           const T wt = w[dy + 1] * w[dx + 1];
           const size_t o = (size_t)(fc + (long)dy * nf + dx) * ld + j;
           const vec<T, V> vy = ldx<T, V, CG>(r.y + o), vp = ldx<T, V, CG>(r.p + o);
@@ -321,7 +324,10 @@ __device__ __forceinline__ void restrict_item(int nf, int N, const Vec3c<T>& r, 
   if (lane == 0) {
     T au = T(0);
     for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) au = fma(w[dy + 1] * w[dx + 1], ld1<T, CG>(r.u + fc + (long)dy * nf + dx), au);
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (colour0 && ((dx + dy) & 1)) continue;
+        au = fma(w[dy + 1] * w[dx + 1], ld1<T, CG>(r.u + fc + (long)dy * nf + dx), au);
+      }
     cv.u[node] = au;
     if (zx.y) zx.u[node] = T(0);
   }

@@ -27,6 +27,21 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(LevelView<T> L, Vec3c<
   residual_item<T, V, SPL, false>(L, x, f, r, node, threadIdx.x & (lpn - 1), lpn, wy);
 }
 
+// r = f - S x at the colour-0 nodes only (the g-th node of colour 0).
+template <typename T, int V, int SPL>
+__global__ void __launch_bounds__(kBlock) residual_c0_kernel(LevelView<T> L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r,
+                                                             int lpn) {
+  pdl_enter();
+  const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
+  long node = (long)L.n * L.n;   // out of range: the item does nothing but its shuffles
+  if (g < colour_count(L.n, 0)) {
+    int iy, ix;
+    colour_node(g, L.n, 0, iy, ix);
+    node = (long)iy * L.n + ix;
+  }
+  residual_item<T, V, SPL, false>(L, x, f, r, node, threadIdx.x & (lpn - 1), lpn, T(1));
+}
+
 template <typename T, int V, int SPL>
 __global__ void __launch_bounds__(kBlock) rbgs_half_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, int colour,
                                                            int lpn) {
@@ -45,10 +60,10 @@ __global__ void __launch_bounds__(kBlock) jacobi_update_kernel(LevelView<T> L, V
 
 template <typename T, int V, int SPL>
 __global__ void __launch_bounds__(kBlock) restrict_kernel(int nf, int N, Vec3c<T> r, Vec3<T> cv, Vec3<T> zx,
-                                                          int lpn) {
+                                                          int lpn, int colour0) {
   pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
-  restrict_item<T, V, SPL, false>(nf, N, r, cv, zx, node, threadIdx.x & (lpn - 1), lpn);
+  restrict_item<T, V, SPL, false>(nf, N, r, cv, zx, node, threadIdx.x & (lpn - 1), lpn, colour0 != 0);
 }
 
 template <typename T, int V, int SPL>
@@ -231,6 +246,17 @@ cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<
 }
 
 template <typename T>
+cudaError_t launch_residual_c0(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r, cudaStream_t st) {
+  const long groups = colour_count(L.n, 0);
+  const SampleMap m = choose_map(L.N, sizeof(T), groups, L.spl_target);
+  const unsigned grid = grid_for(groups, m.lpn);
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(residual_c0_kernel<T, V, SPL>, grid, kBlock, 0, st, L, x, f, r, m.lpn)));
+  count_launches(1);
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t st) {
   const SampleMap m = choose_map(L.N, sizeof(T), colour_count(L.n, colour), L.spl_target);
   if constexpr (sizeof(T) == 4) {
@@ -257,12 +283,12 @@ cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, d
 }
 
 template <typename T>
-cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t st, Vec3<T> zx) {
+cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t st, Vec3<T> zx, int colour0) {
   const int nc = (nf - 1) / 2;
   const SampleMap m = choose_map(N, sizeof(T), (long)nc * nc);
   const unsigned grid = grid_for((long)nc * nc, m.lpn);
   cudaError_t e_ = cudaSuccess;
-  CMG_DISPATCH(T, m, (e_ = launch_k(restrict_kernel<T, V, SPL>, grid, kBlock, 0, st, nf, N, r, c, zx, m.lpn)));
+  CMG_DISPATCH(T, m, (e_ = launch_k(restrict_kernel<T, V, SPL>, grid, kBlock, 0, st, nf, N, r, c, zx, m.lpn, colour0)));
   count_launches(1);
   return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
@@ -348,7 +374,8 @@ cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<doub
   template cudaError_t launch_residual<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t, double); \
   template cudaError_t launch_rbgs_half<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, int, cudaStream_t);    \
   template cudaError_t launch_jacobi_update<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, double, cudaStream_t); \
-  template cudaError_t launch_restrict<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t, Vec3<T>);                     \
+  template cudaError_t launch_restrict<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t, Vec3<T>, int);         \
+  template cudaError_t launch_residual_c0<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t);                     \
   template cudaError_t launch_prolong_add<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t);
 
 CMG_INST(double)

@@ -599,3 +599,29 @@ def test_frozen_control_cycles_solve_the_pdes_for_that_control():
         pj = np.linalg.solve(A, (f[0][:, :, j] - lv.c * yj.reshape(n, n)).ravel())
         assert np.allclose(x[0][:, :, j].ravel(), yj, rtol=1e-9, atol=1e-12)
         assert np.allclose(x[2][:, :, j].ravel(), pj, rtol=1e-9, atol=1e-14)
+
+
+def test_residual_vanishes_on_the_last_swept_colour():
+    """After a collective red-black sweep (colour 0, then colour 1) every
+    colour-1 node satisfies its own 2N+1 equations given neighbours that did
+    not change afterwards, so f - S x is zero there in all three blocks (up
+    to rounding) and not at colour 0; the GPU cycle computes and restricts
+    only the colour-0 residual on this basis.  With the control frozen the
+    control row is not solved and keeps its residual."""
+    lv = small_level(n=7, N=3)
+    rng = np.random.default_rng(5)
+    n, N = lv.n, lv.N
+    f = (rng.standard_normal((n, n, N)), rng.standard_normal((n, n)), rng.standard_normal((n, n, N)))
+    x = (rng.standard_normal((n, n, N)), rng.standard_normal((n, n)), rng.standard_normal((n, n, N)))
+    x = O.rbgs_sweep(lv, x, f)
+    r = O.residual(lv, x, f)
+    c1 = O.colour_mask(n, 1)
+    c0 = O.colour_mask(n, 0)
+    scale = max(np.abs(b).max() for b in f)
+    for blk in r:
+        assert np.abs(blk[c1]).max() <= 1e-12 * scale
+    assert max(np.abs(blk[c0]).max() for blk in r) > 1e-3 * scale
+    xf = O.rbgs_sweep(lv, x, f, freeze_u=True)
+    rf = O.residual(lv, xf, f)
+    assert np.abs(rf[0][c1]).max() <= 1e-12 * scale and np.abs(rf[2][c1]).max() <= 1e-12 * scale
+    assert np.abs(rf[1][c1]).max() > 1e-6 * scale
