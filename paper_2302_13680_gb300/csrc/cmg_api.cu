@@ -342,7 +342,23 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
     e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream, xc, c0);   // also sets the coarse iterate to zero
   }
   for (int g = 0; g < o.gamma && e == cudaSuccess; ++g) e = cycle<T>(h, o, l + 1, xc, cview(fc));
-  if (e == cudaSuccess) {
+  if (e != cudaSuccess) return e;
+  if (o.smoother == CMG_SMOOTH_RBGS && o.n2 >= 1 && !o.freeze_u) {
+    // prolongation fused into the first post-smoothing half-sweep (colour 0);
+    // identical results, one pass over x fewer
+    const LevelView<T> L = view<T>(h, l, o.freeze_u);
+    {
+      ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+      e = launch_rbgs_prolong<T>(L, x, f, cview(xc), cl.n, h->stream);
+    }
+    if (e == cudaSuccess) {
+      ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+      e = launch_rbgs_half<T>(L, x, f, 1, h->stream);
+    }
+    if (e == cudaSuccess) e = smooth<T>(h, o, l, o.n2 - 1, x, f);
+    return e;
+  }
+  {
     ProfScope ps(h, CMG_KERNEL_PROLONG, l);
     e = launch_prolong_add<T>(v.n, N, cview(xc), x, h->stream);
   }

@@ -123,6 +123,13 @@ cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, d
 // colour-0 points (launch_restrict with colour0 = 1).
 template <typename T>
 cudaError_t launch_residual_c0(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<T> r, cudaStream_t s);
+// Colour-0 half-sweep with the prolongation of the coarse correction e
+// fused in: the neighbours (colour 1) are read as x + P e.  The colour-0
+// values of x + P e are never needed (this sweep overwrites them from the
+// neighbours) and the colour-1 values are needed only here (the next
+// half-sweep overwrites them), so the prolongation pass is not run.
+template <typename T>
+cudaError_t launch_rbgs_prolong(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, Vec3c<T> e, int nc, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s,
                             Vec3<T> zx = Vec3<T>{nullptr, nullptr, nullptr}, int colour0 = 0);

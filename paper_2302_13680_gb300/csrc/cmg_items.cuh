@@ -139,6 +139,33 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
   }
 }
 
+// x + (P e) at fine node (fy, fx), samples j .. j+V-1: the value the
+// prolongation kernel would leave there (same operations in the same
+// order), formed where a half-sweep reads it as a neighbour.
+template <typename T, int V, bool CG>
+__device__ __forceinline__ vec<T, V> prolonged(const T* xv, const T* ev, int nf, int nc, size_t ld, int fy, int fx,
+                                               int j) {
+  vec<T, V> v = ldx<T, V, CG>(xv + ((size_t)fy * nf + fx) * ld + j);
+  int Jr[2] = {0, 0}, Ir[2] = {0, 0};
+  T wy[2] = {T(0), T(0)}, wx[2] = {T(0), T(0)};
+  int ny, nx;
+  if (fy & 1) { Jr[0] = (fy - 1) >> 1; wy[0] = T(1); ny = 1; }
+  else { Jr[0] = (fy >> 1) - 1; Jr[1] = fy >> 1; wy[0] = wy[1] = T(0.5); ny = 2; }
+  if (fx & 1) { Ir[0] = (fx - 1) >> 1; wx[0] = T(1); nx = 1; }
+  else { Ir[0] = (fx >> 1) - 1; Ir[1] = fx >> 1; wx[0] = wx[1] = T(0.5); nx = 2; }
+  for (int a = 0; a < ny; ++a) {
+    if (Jr[a] < 0 || Jr[a] >= nc) continue;
+    for (int b = 0; b < nx; ++b) {
+      if (Ir[b] < 0 || Ir[b] >= nc) continue;
+      const T wt = wy[a] * wx[b];
+      const vec<T, V> ec = ldx<T, V, CG>(ev + ((size_t)Jr[a] * nc + Ir[b]) * ld + j);
+#pragma unroll
+      for (int k = 0; k < V; ++k) v.v[k] = fma(wt, ec.v[k], v.v[k]);
+    }
+  }
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Red-black collective GS at the g-th node of `colour`: local right sides
 // from the current neighbours, then Eq. (13).  With b_p the rhs of the
@@ -149,9 +176,13 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
 // work runs in the cycle's own precision (acc_t) and its loads are issued
 // together with the node's other loads, ahead of the group sum.
 // ---------------------------------------------------------------------------
-template <typename T, int V, int SPL, bool CG>
+// PRO: the neighbours are read as x + P e (coarse correction e on the grid
+// of nc nodes per side), i.e. the prolongation is fused into this half-sweep.
+template <typename T, int V, int SPL, bool CG, bool PRO = false>
 __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& x, const Vec3c<T>& f, int colour,
-                                          long g, int lane, int lpn) {
+                                          long g, int lane, int lpn, const Vec3c<T> e = Vec3c<T>{nullptr, nullptr,
+                                                                                                   nullptr},
+                                          int nc = 0) {
   const int n = L.n, N = L.N;
   const size_t ld = (size_t)L.ld;
   const bool valid = g < colour_count(n, colour);
@@ -178,12 +209,24 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
         const vec<T, V> kS = ldx<T, V, CG>(kSp + j), kN = ldx<T, V, CG>(kSp + (size_t)n * ld + j);
         bp[s] = ldx<T, V, CG>(f.y + o + j);   // first block row: c y + A p = f_y
         by[s] = ldx<T, V, CG>(f.p + o + j);   // last block row:  A y + e u = f_p
-        fma_faces<T, V>(bp[s], kW, ldx_if<T, V, CG>(hW, x.p + o - ld + j), kE,
-                        ldx_if<T, V, CG>(hE, x.p + o + ld + j), kS, ldx_if<T, V, CG>(hS, x.p + o - (size_t)n * ld + j),
-                        kN, ldx_if<T, V, CG>(hN, x.p + o + (size_t)n * ld + j));
-        fma_faces<T, V>(by[s], kW, ldx_if<T, V, CG>(hW, x.y + o - ld + j), kE,
-                        ldx_if<T, V, CG>(hE, x.y + o + ld + j), kS, ldx_if<T, V, CG>(hS, x.y + o - (size_t)n * ld + j),
-                        kN, ldx_if<T, V, CG>(hN, x.y + o + (size_t)n * ld + j));
+        if constexpr (PRO) {
+          const auto nb = [&](bool h, const T* xv, const T* ev, int fy, int fx) {
+            return h ? prolonged<T, V, CG>(xv, ev, n, nc, ld, fy, fx, j) : vzero<T, V>();
+          };
+          fma_faces<T, V>(bp[s], kW, nb(hW, x.p, e.p, iy, ix - 1), kE, nb(hE, x.p, e.p, iy, ix + 1), kS,
+                          nb(hS, x.p, e.p, iy - 1, ix), kN, nb(hN, x.p, e.p, iy + 1, ix));
+          fma_faces<T, V>(by[s], kW, nb(hW, x.y, e.y, iy, ix - 1), kE, nb(hE, x.y, e.y, iy, ix + 1), kS,
+                          nb(hS, x.y, e.y, iy - 1, ix), kN, nb(hN, x.y, e.y, iy + 1, ix));
+        } else {
+          fma_faces<T, V>(bp[s], kW, ldx_if<T, V, CG>(hW, x.p + o - ld + j), kE,
+                          ldx_if<T, V, CG>(hE, x.p + o + ld + j), kS,
+                          ldx_if<T, V, CG>(hS, x.p + o - (size_t)n * ld + j), kN,
+                          ldx_if<T, V, CG>(hN, x.p + o + (size_t)n * ld + j));
+          fma_faces<T, V>(by[s], kW, ldx_if<T, V, CG>(hW, x.y + o - ld + j), kE,
+                          ldx_if<T, V, CG>(hE, x.y + o + ld + j), kS,
+                          ldx_if<T, V, CG>(hS, x.y + o - (size_t)n * ld + j), kN,
+                          ldx_if<T, V, CG>(hN, x.y + o + (size_t)n * ld + j));
+        }
         ia[s] = inv_diag<T, V, CG>(L, o + j, kW, kE, kS, kN);
 #pragma unroll
         for (int k = 0; k < V; ++k) {

@@ -50,6 +50,16 @@ __global__ void __launch_bounds__(kBlock) rbgs_half_kernel(LevelView<T> L, Vec3<
   rbgs_item<T, V, SPL, false>(L, x, f, colour, g, threadIdx.x & (lpn - 1), lpn);
 }
 
+// Colour-0 half-sweep that reads its neighbours as x + P e (prolongation of
+// the coarse correction e fused in; see rbgs_item).
+template <typename T, int V, int SPL>
+__global__ void __launch_bounds__(kBlock) rbgs_prolong_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, Vec3c<T> e,
+                                                              int nc, int lpn) {
+  pdl_enter();
+  const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
+  rbgs_item<T, V, SPL, false, true>(L, x, f, 0, g, threadIdx.x & (lpn - 1), lpn, e, nc);
+}
+
 template <typename T, int V, int SPL>
 __global__ void __launch_bounds__(kBlock) jacobi_update_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> r,
                                                                double theta, int lpn) {
@@ -273,6 +283,17 @@ cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int c
 }
 
 template <typename T>
+cudaError_t launch_rbgs_prolong(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, Vec3c<T> e, int nc, cudaStream_t st) {
+  const long groups = colour_count(L.n, 0);
+  const SampleMap m = choose_map(L.N, sizeof(T), groups, L.spl_target);
+  const unsigned grid = grid_for(groups, m.lpn);
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(rbgs_prolong_kernel<T, V, SPL>, grid, kBlock, 0, st, L, x, f, e, nc, m.lpn)));
+  count_launches(1);
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, double theta, cudaStream_t st) {
   const SampleMap m = choose_map(L.N, sizeof(T), (long)L.n * L.n, L.spl_target);
   const unsigned grid = grid_for((long)L.n * L.n, m.lpn);
@@ -375,7 +396,8 @@ cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<doub
   template cudaError_t launch_rbgs_half<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, int, cudaStream_t);    \
   template cudaError_t launch_jacobi_update<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, double, cudaStream_t); \
   template cudaError_t launch_restrict<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t, Vec3<T>, int);         \
-  template cudaError_t launch_residual_c0<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t);                     \
+  template cudaError_t launch_residual_c0<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t);       \
+  template cudaError_t launch_rbgs_prolong<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, Vec3c<T>, int, cudaStream_t);                     \
   template cudaError_t launch_prolong_add<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t);
 
 CMG_INST(double)
