@@ -343,12 +343,13 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   }
   for (int g = 0; g < o.gamma && e == cudaSuccess; ++g) e = cycle<T>(h, o, l + 1, xc, cview(fc));
   if (e != cudaSuccess) return e;
-  if (o.smoother == CMG_SMOOTH_RBGS && o.n2 >= 1 && !o.freeze_u) {
-    // prolongation fused into the first post-smoothing half-sweep (colour 0);
-    // identical results, one pass over x fewer
+  if (sizeof(T) == 4 && o.smoother == CMG_SMOOTH_RBGS && o.n2 >= 1 && !o.freeze_u) {
+    // FP32: prolongation fused into the first post-smoothing half-sweep
+    // (colour 0); identical results, one pass over x fewer.  (In FP64 the
+    // fused sweep is bound by the FP64 pipe and costs more than the pass.)
     const LevelView<T> L = view<T>(h, l, o.freeze_u);
     {
-      ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+      ProfScope ps(h, CMG_KERNEL_PROLONG, l);
       e = launch_rbgs_prolong<T>(L, x, f, cview(xc), cl.n, h->stream);
     }
     if (e == cudaSuccess) {
