@@ -366,7 +366,7 @@ enum {
   CMG_KERNEL_SMOOTH = 1,     /* red-black half-sweep or Jacobi update */
   CMG_KERNEL_RESIDUAL = 2,   /* residual / operator apply */
   CMG_KERNEL_RESTRICT = 4,
-  CMG_KERNEL_PROLONG = 8,
+  CMG_KERNEL_PROLONG = 8,    /* prolongation; in the FP32 red-black cycle the colour-0 half-sweep with it fused in */
   CMG_KERNEL_COARSE = 16,
   CMG_KERNEL_TAIL = 32       /* the cluster launch of the coarse-grid cycle (level = its first grid) */
 };

@@ -4,15 +4,18 @@
 //
 // A and B have row strides lda, ldb (elements, multiples of 8); K % 8 == 0
 // (the last K step is zero-filled).
-// One CTA of 128 threads computes a 128 x 64 tile of C.  Per K step of 64:
-//   * all threads copy the A (128 x 64) and B (64 x 64) tiles from global
-//     memory into shared memory in the no-swizzle K-major layout of 8-row x
-//     16-byte core matrices (core (r8, k8) at byte (r8 * 8 + k8) * 128),
-//     then make the writes visible to the tensor-core (async) proxy;
-//   * one thread issues four tcgen05.mma (K = 16 each) into the TMEM
-//     accumulator and commits them to an mbarrier;
-//   * all threads wait on the mbarrier (bounded) before the tiles are
-//     overwritten (two shared-memory stages let the next copy overlap).
+// One CTA of 128 threads computes a 128 x 64 tile of C through a pipeline of
+// kStages shared-memory stages, each holding one K step of 64:
+//   * all threads copy the A (128 x 64) and B (64 x 64) tiles of a K step
+//     from global memory with asynchronous 16-byte copies (cp.async, zero
+//     fill outside M, N, K) straight into the no-swizzle K-major layout of
+//     8-row x 16-byte core matrices (core (r8, k8) at byte (r8 * 8 + k8) *
+//     128); kStages - 1 K steps are in flight while the tensor cores work;
+//   * when a step has landed (copy-group wait, proxy fence, CTA barrier) one
+//     thread issues four tcgen05.mma (K = 16 each) into the TMEM
+//     accumulator and commits them to the stage's mbarrier;
+//   * a stage is refilled only after the mbarrier reports that the MMAs
+//     reading it have completed (bounded wait).
 // The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 // lanes 32w..32w+31 = rows of the tile), applies bias / ReLU and stores
 // FP32 and/or BF16.
@@ -29,10 +32,10 @@ namespace nn {
 
 constexpr int kBM = 128, kBN = 64, kBK = 64;
 constexpr int kThreads = 128;
-constexpr int kStages = 2;
+constexpr int kStages = 4;
 constexpr uint32_t kTmemCols = 64;                 // FP32 accumulator columns (= kBN)
 constexpr long kSpinLimit = 1L << 22;              // mbarrier polls before giving up
-constexpr int kSmemBytes = kStages * (kBM + kBN) * kBK * 2;   // 48 KiB of operand tiles
+constexpr int kSmemBytes = kStages * (kBM + kBN) * kBK * 2;   // 96 KiB of operand tiles
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -89,25 +92,30 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// Copy a rows x 64 BF16 tile (row stride ld elements) into the core-matrix
-// layout; rows beyond `valid` and columns beyond K read as zero (K % 8 == 0).
-__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, const __nv_bfloat16* src, int rows, long ld,
-                                          int valid, int k0, int K) {
-  // each 16-byte chunk: (row, k8) with k8 in 0..7
+// Asynchronous copy of a rows x 64 BF16 tile (row stride ld elements) into
+// the core-matrix layout; rows beyond `valid` and columns beyond K are
+// zero-filled (K % 8 == 0).  The source of a zero-filled chunk is the
+// (valid) tile base, read with size 0.
+__device__ __forceinline__ void load_tile_async(__nv_bfloat16* dst, const __nv_bfloat16* src, int rows, long ld,
+                                                int valid, int k0, int K) {
   for (int c = threadIdx.x; c < rows * 8; c += kThreads) {
     const int row = c >> 3, k8 = c & 7;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (row < valid && k0 + k8 * 8 < K) v = *reinterpret_cast<const uint4*>(src + (size_t)row * ld + k0 + k8 * 8);
+    const bool ok = row < valid && k0 + k8 * 8 < K;
+    const __nv_bfloat16* g = ok ? src + (size_t)row * ld + k0 + k8 * 8 : src;
     const int core = (row >> 3) * 8 + k8;            // core matrices: 8 per 8-row group along K
-    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst) + core * 128 + (row & 7) * 16) = v;
+    const uint32_t d = smem_u32(reinterpret_cast<char*>(dst) + core * 128 + (row & 7) * 16);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(ok ? 16 : 0) : "memory");
   }
 }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloat16* __restrict__ A, long lda,
                                                                 const __nv_bfloat16* __restrict__ B, long ldb, int M,
                                                                 int N, int K, const float* __restrict__ bias, int relu,
                                                                 float* __restrict__ C32, __nv_bfloat16* __restrict__ C16,
-                                                                int ldc, int* __restrict__ status) {
+                                                                int ldc, int* __restrict__ status, int vec16, int vec32) {
   extern __shared__ __align__(1024) unsigned char dyn_smem[];   // kSmemBytes: A and B tiles of both stages
   __nv_bfloat16* sA[kStages];
   __nv_bfloat16* sB[kStages];
@@ -144,23 +152,25 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = instr_desc(kBM, kBN);
   const int ksteps = (K + kBK - 1) / kBK;
-  uint32_t phase[kStages] = {0, 0};
+  const __nv_bfloat16* Ablk = A + (size_t)m0 * lda;
+  const __nv_bfloat16* Bblk = B + (size_t)n0 * ldb;
+  uint32_t phase[kStages] = {0, 0, 0, 0};
+  int commits[kStages] = {0, 0, 0, 0};   // MMA commits made on each stage's barrier
 
+  // prologue: K steps 0 .. kStages-2 in flight (one copy group each, empty past the end)
+  for (int p = 0; p < kStages - 1; ++p) {
+    if (p < ksteps) {
+      load_tile_async(sA[p], Ablk, kBM, lda, M - m0, p * kBK, K);
+      load_tile_async(sB[p], Bblk, kBN, ldb, N - n0, p * kBK, K);
+    }
+    cp_commit();
+  }
   for (int ks = 0; ks < ksteps; ++ks) {
     const int s = ks % kStages;
-    if (ks >= kStages) {
-      // the MMAs that last read this stage must have finished
-      if (!mbar_wait(&bar[s], phase[s])) {
-        if (threadIdx.x == 0) failed = 1;
-      }
-      phase[s] ^= 1;
-    }
-    __syncthreads();
+    cp_wait<kStages - 2>();                              // this thread's copies of step ks have landed
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
+    __syncthreads();                                     // ... everyone's
     if (failed) break;
-    load_tile(sA[s], A + (size_t)m0 * lda, kBM, lda, M - m0, ks * kBK, K);
-    load_tile(sB[s], B + (size_t)n0 * ldb, kBN, ldb, N - n0, ks * kBK, K);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
@@ -173,7 +183,23 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
       }
       mma_commit(&bar[s]);
     }
+    ++commits[s];
+    // refill the stage read by step ks-1 with step ks+kStages-1, once those MMAs are done
+    const int nxt = ks + kStages - 1;
+    if (nxt < ksteps) {
+      const int sn = nxt % kStages;
+      if (commits[sn] > 0) {
+        if (!mbar_wait(&bar[sn], phase[sn])) {
+          if (threadIdx.x == 0) failed = 1;
+        }
+        phase[sn] ^= 1;
+      }
+      load_tile_async(sA[sn], Ablk, kBM, lda, M - m0, nxt * kBK, K);
+      load_tile_async(sB[sn], Bblk, kBN, ldb, N - n0, nxt * kBK, K);
+    }
+    cp_commit();
   }
+  cp_wait<0>();
   // Each stage has exactly one commit not yet waited for (its last one); the
   // i-th commit on a barrier completes phase i, so the last of `uses`
   // commits has parity (uses - 1) & 1.
@@ -183,6 +209,7 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
       if (uses > 0 && !mbar_wait(&bar[s], (uint32_t)((uses - 1) & 1))) failed = 1;
     }
   }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
 
@@ -204,15 +231,47 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < M) {
+        const int c0 = n0 + half * 32;
+        float v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int col = n0 + half * 32 + j;
-          if (col < N) {
-            float v = __uint_as_float(r[j]);
-            if (bias) v += bias[col];
-            if (relu) v = fmaxf(v, 0.f);
-            if (C32) C32[(size_t)row * ldc + col] = v;
-            if (C16) C16[(size_t)row * ldc + col] = __float2bfloat16_rn(v);
+          v[j] = __uint_as_float(r[j]);
+          if (bias && c0 + j < N) v[j] += bias[c0 + j];
+          if (relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        // 16-byte stores of consecutive columns of this thread's row (a
+        // scalar store per element only at a ragged right edge or when the
+        // row stride does not keep 16-byte alignment)
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) {
+          const int col = c0 + q;
+          if (C16) {
+            __nv_bfloat16* dst = C16 + (size_t)row * ldc + col;
+            if (vec16 && col + 8 <= N) {
+              uint4 pk;
+              uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[q + 2 * t], v[q + 2 * t + 1]);
+                w[t] = *reinterpret_cast<const uint32_t*>(&b2);
+              }
+              *reinterpret_cast<uint4*>(dst) = pk;
+            } else {
+              for (int t = 0; t < 8; ++t)
+                if (col + t < N) dst[t] = __float2bfloat16_rn(v[q + t]);
+            }
+          }
+          if (C32) {
+            float* dst = C32 + (size_t)row * ldc + col;
+#pragma unroll
+            for (int t = 0; t < 8; t += 4) {
+              if (vec32 && col + t + 4 <= N) {
+                *reinterpret_cast<float4*>(dst + t) = make_float4(v[q + t], v[q + t + 1], v[q + t + 2], v[q + t + 3]);
+              } else {
+                for (int u = 0; u < 4; ++u)
+                  if (col + t + u < N) dst[t + u] = v[q + t + u];
+              }
+            }
           }
         }
       }
@@ -239,9 +298,13 @@ cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb
     attr = true;
   }
   dim3 grid((M + nn::kBM - 1) / nn::kBM, (N + nn::kBN - 1) / nn::kBN, ksplit);
+  // 16-byte epilogue stores need every row start 16-byte aligned
+  const int vec16 = C16 && (ldc % 8 == 0) && ((reinterpret_cast<uintptr_t>(C16) & 15) == 0);
+  const int vec32 = C32 && (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C32) & 15) == 0) &&
+                    (ksplit == 1 || ((size_t)M * ldc) % 4 == 0);
   nn::gemm_bf16_tn_kernel<<<grid, nn::kThreads, nn::kSmemBytes, s>>>(
       static_cast<const __nv_bfloat16*>(A), lda, static_cast<const __nv_bfloat16*>(B), ldb, M, N, K, bias, relu, C32,
-      static_cast<__nv_bfloat16*>(C16), ldc, status);
+      static_cast<__nv_bfloat16*>(C16), ldc, status, vec16, vec32);
   count_launches(1);
   return cudaGetLastError();
 }
