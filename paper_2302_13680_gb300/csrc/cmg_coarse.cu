@@ -214,9 +214,109 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_b(int m, int N, i
   }
 }
 
+// The whole coarsest solve in one CTA, with every A_j^{-1} and the right
+// sides staged in shared memory by coalesced loads and one thread per
+// (sample j, row r) for the products.  The two-kernel form above gives each
+// thread a whole sample (81 strided loads of A_j^{-1} per product) and is
+// latency-bound.  Same block elimination; the control right side is summed
+// over the samples in sample order.
+constexpr int kCoarseCtaThreads = 512;
+
+inline size_t coarse_cta_smem(int N, int m) { return ((size_t)N * m * m + 4 * (size_t)N * m + 2 * 64) * 8; }
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int N, const double* __restrict__ Ainv,
+                                                                     const double* __restrict__ Minv, double c,
+                                                                     double d, double e, Vec3c<T> f, Vec3<T> x,
+                                                                     int freeze_u) {
+  pdl_enter();
+  extern __shared__ __align__(16) double sm[];
+  const int mm = m * m, nm = N * m;
+  double* A = sm;                    // [N][m][m]
+  double* by = A + (size_t)N * mm;   // [N][m] f_y, later y
+  double* bp = by + nm;              // [N][m] f_p, later w - c A^{-1} z
+  double* w = bp + nm;               // [N][m] A^{-1} f_y
+  double* z = w + nm;                // [N][m] A^{-1} f_p
+  double* rhs = z + nm;              // [m] control right side
+  double* us = rhs + 64;             // [m] control
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < N * mm; i += nt) A[i] = Ainv[i];
+  for (int i = tid; i < nm; i += nt) {   // f.y, f.p are [node r][sample j]
+    const int r = i / N, j = i - r * N;
+    by[j * m + r] = (double)f.y[i];
+    bp[j * m + r] = (double)f.p[i];
+  }
+  __syncthreads();
+  for (int i = tid; i < nm; i += nt) {
+    const int j = i / m, r = i - j * m;
+    const double* Ar = A + (size_t)j * mm + r * m;
+    double sw = 0.0, sz = 0.0;
+    for (int k = 0; k < m; ++k) {
+      sw += Ar[k] * by[j * m + k];
+      sz += Ar[k] * bp[j * m + k];
+    }
+    w[i] = sw;
+    z[i] = sz;
+  }
+  __syncthreads();
+  for (int i = tid; i < nm; i += nt) {   // w - c A^{-1} z, into bp (f_p no longer needed)
+    const int j = i / m, r = i - j * m;
+    const double* Ar = A + (size_t)j * mm + r * m;
+    double v = 0.0;
+    for (int k = 0; k < m; ++k) v += Ar[k] * z[j * m + k];
+    bp[i] = w[i] - c * v;
+  }
+  __syncthreads();
+  for (int r = tid; r < m; r += nt) {
+    double q = 0.0;
+    for (int j = 0; j < N; ++j) q += bp[j * m + r];
+    rhs[r] = (double)f.u[r] - d * q;
+  }
+  __syncthreads();
+  for (int r = tid; r < m; r += nt) {
+    double u = 0.0;
+    if (!freeze_u)   // frozen control: zero correction of u, state and adjoint solved for it
+      for (int k = 0; k < m; ++k) u += Minv[r * m + k] * rhs[k];
+    us[r] = u;
+    x.u[r] = (T)u;
+  }
+  __syncthreads();
+  for (int i = tid; i < nm; i += nt) {   // y = z - e A^{-1} u, into by
+    const int j = i / m, r = i - j * m;
+    const double* Ar = A + (size_t)j * mm + r * m;
+    double t = 0.0;
+    for (int k = 0; k < m; ++k) t += Ar[k] * us[k];
+    const double yv = z[i] - e * t;
+    by[i] = yv;
+    x.y[(size_t)r * N + j] = (T)yv;
+  }
+  __syncthreads();
+  for (int i = tid; i < nm; i += nt) {   // p = w - c A^{-1} y
+    const int j = i / m, r = i - j * m;
+    const double* Ar = A + (size_t)j * mm + r * m;
+    double t = 0.0;
+    for (int k = 0; k < m; ++k) t += Ar[k] * by[j * m + k];
+    x.p[(size_t)r * N + j] = (T)(w[i] - c * t);
+  }
+}
+
 template <typename T, int MM>
 cudaError_t coarse_solve_mm(const CoarseData& C, double c, double d, double e, Vec3c<T> f, Vec3<T> x,
                             cudaStream_t s, int freeze_u) {
+  if (MM <= 9 && coarse_cta_smem(C.N, C.m) <= 200 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      const cudaError_t ea = cudaFuncSetAttribute(coarse_solve_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  200 * 1024);
+      if (ea != cudaSuccess) return ea;
+      attr = true;
+    }
+    const cudaError_t ek = launch_k(coarse_solve_cta<T>, dim3(1), dim3(kCoarseCtaThreads), coarse_cta_smem(C.N, C.m),
+                                    s, C.m, C.N, (const double*)C.Ainv, (const double*)C.Minv, c, d, e, f, x,
+                                    freeze_u);
+    count_launches(1);
+    return ek != cudaSuccess ? ek : cudaGetLastError();
+  }
   const int nblk = (C.N + kCoarseThreads - 1) / kCoarseThreads;
   coarse_solve_a<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, C.Ainv, c, f.y, f.p, C.wz, C.partial);
   coarse_solve_b<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, nblk, C.Ainv, C.Minv, c, d, e, f.u, C.wz,
