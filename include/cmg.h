@@ -82,14 +82,17 @@ typedef struct {
   int n1, n2;       /* pre- and post-smoothing sweeps */
   int gamma;        /* recursive calls per level: 1 = V-cycle, 2 = W-cycle */
   int precision;    /* arithmetic of the cycle: CMG_FP64, or CMG_FP32 (single-precision
-                       smoothing, residual and transfers; Schur scalar for u and the
-                       coarsest solve in FP64) */
+                       smoothing, control update, residual and transfers; the coarsest
+                       solve in FP64 on FP32-built operators) */
   int tail_n;       /* grids with at most tail_n nodes per side (and the coarsest solve)
                        run as ONE launch of a thread-block cluster whose phases are
                        separated by cluster barriers; 0 = one launch per step on every
-                       grid.  Same arithmetic either way.  Ignored (one launch per step)
-                       when N needs more than 4 chunks per lane or the coarsest grid
-                       is 7 x 7. */
+                       grid (faster inside the refinement graph on GB300).  The same
+                       algorithm either way, results equal up to rounding (the
+                       per-launch path computes the residual after red-black
+                       pre-smoothing at colour 0 only and fuses the prolongation into
+                       the next half-sweep).  Ignored (one launch per step) when N
+                       needs more than 4 chunks per lane or the coarsest grid is 7 x 7. */
   int freeze_u;     /* 1: keep the control fixed: each node solves only its state and
                        adjoint rows for the current u_i (Eq. (14) with u_i given instead
                        of zero) and the coarse corrections of u are zero.  Cycles then

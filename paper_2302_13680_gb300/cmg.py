@@ -113,7 +113,8 @@ class CycleOptions:
     n2: int = 2
     gamma: int = 1
     precision: int = FP64
-    tail_n: int = 31          # grids with n <= tail_n run as one cluster launch; 0 = off
+    tail_n: int = 0           # grids with n <= tail_n run as one cluster launch; 0 = one launch per step
+                              # (the faster choice inside the refinement graph on GB300)
     freeze_u: int = 0         # 1: keep u fixed, solve the state and adjoint rows only
 
     def c(self) -> Cycle:
