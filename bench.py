@@ -249,9 +249,9 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel: str, precision: str):
+def traffic_record(kernel: str, precision: str, n: int, N: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current kernel source and on this workload (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -260,7 +260,7 @@ def traffic_record(kernel: str, precision: str):
     except (OSError, ValueError):
         return None
     sha = kernel_source_sha()
-    entry = rec.get(f"{kernel}:{precision}")
+    entry = rec.get(f"{kernel}:{precision}:n{n}_N{N}")
     if not entry or entry.get("source_sha") != sha:
         return None
     return entry.get("dram_bytes_per_launch")
@@ -433,7 +433,7 @@ def run_cmg(args, world, rank, local):
     roofline = {"bound": "hbm", "kernel": f"{kname} ({prec}, finest grid)", "achieved": achieved,
                 "measured": "CUDA events around each launch, instrumented pass of the timed steps",
                 "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_record(kname, prec), "algorithmic_bytes_per_launch": alg,
+                "traffic": traffic_record(kname, prec, n, N), "algorithmic_bytes_per_launch": alg,
                 "avg_launch_ms": avg_ms, "launches_timed": dom_cnt}
 
     cpu = None
