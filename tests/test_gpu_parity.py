@@ -307,3 +307,26 @@ def test_staged_half_sweep_matches_direct(case, spl, freeze):
     for a, b in zip(*out):
         for ta, tb in zip(a, b):
             assert torch.equal(ta, tb)
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+@pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
+def test_fp32_cycle_cluster_matches_per_launch(case, gamma, smoother):
+    """FP32 cycles with every grid n <= 31 in one cluster launch against the
+    one-launch-per-step path (which computes the post-smoothing residual at
+    colour 0 only and fuses the prolongation into the next half-sweep): the
+    same algorithm, FP32 rounding in different orders."""
+    H, levels = case
+    import paper_2302_13680_gb300 as P
+
+    lv = levels[0]
+    f = tuple(np.asarray(b, dtype=np.float32).astype(np.float64) for b in O.fine_rhs(lv, inputs.target_modes(lv.n, 5)))
+    sm = P.SMOOTH_RBGS if smoother == "rbgs" else P.SMOOTH_JACOBI
+    fd = to_dev(f, torch.float32)
+    out = []
+    for tail_n in (0, 31):
+        xd = H.zeros(0, torch.float32)
+        for _ in range(2):
+            H.cycle(P.CycleOptions(precision=P.FP32, smoother=sm, gamma=gamma, tail_n=tail_n), xd, fd)
+        out.append(to_host(xd, lv.n))
+    assert_close(out[1], out[0], TOL32, "fp32 cluster vs per-launch")
