@@ -303,10 +303,13 @@ cmg_status cmg_batch_autotune(cmg_batch* b, int precision);
 /* ---- learned warm start: network kernels --------------------------------- */
 
 /* C = A B^T (+ bias[N]) (then max(., 0) if relu) on the 5th-generation
- * tensor cores: A [M][K] and B [N][K] BF16 row-major (K contiguous), FP32
- * accumulation in tensor memory; C32 [M][ldc] FP32 and/or C16 [M][ldc]
- * BF16 outputs (either may be NULL).  K must be a positive multiple of 64;
- * A, B 16-byte aligned.  status (DEVICE int) is set to 1 if a tensor-core
+ * tensor cores: A [M][K] and B [N][K] BF16 row-major (K contiguous, row
+ * strides lda, ldb >= K), FP32 accumulation in tensor memory; C32 [M][ldc]
+ * FP32 and/or C16 [M][ldc] BF16 outputs (either may be NULL).  K, lda and
+ * ldb must be multiples of 8; A, B 16-byte aligned.  Operands are loaded
+ * by TMA (tensor maps made per call); with the environment variable
+ * CMG_GEMM_TMA=0, or if no tensor map can be made, by cp.async instead
+ * (same results).  status (DEVICE int) is set to 1 if a tensor-core
  * completion wait exceeded its limit (the output is then incomplete); it is
  * never cleared by the call.  Enqueued on `stream`.  Used for the
  * convolution layers of the warm-start network (not part of the paper). */

@@ -2,28 +2,44 @@
 // network:  C[M][N] = A[M][K] * B[N][K]^T  (+ bias[N], optional ReLU),
 // A and B K-major BF16, FP32 accumulation in tensor memory (TMEM).
 //
-// A and B have row strides lda, ldb (elements, multiples of 8); K % 8 == 0
-// (the last K step is zero-filled).
-// One CTA of 128 threads computes a 128 x 64 tile of C through a pipeline of
-// kStages shared-memory stages, each holding one K step of 64:
-//   * all threads copy the A (128 x 64) and B (64 x 64) tiles of a K step
-//     from global memory with asynchronous 16-byte copies (cp.async, zero
-//     fill outside M, N, K) straight into the no-swizzle K-major layout of
-//     8-row x 16-byte core matrices (core (r8, k8) at byte (r8 * 8 + k8) *
-//     128); kStages - 1 K steps are in flight while the tensor cores work;
-//   * when a step has landed (copy-group wait, proxy fence, CTA barrier) one
-//     thread issues four tcgen05.mma (K = 16 each) into the TMEM
-//     accumulator and commits them to the stage's mbarrier;
-//   * a stage is refilled only after the mbarrier reports that the MMAs
-//     reading it have completed (bounded wait).
-// The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
-// lanes 32w..32w+31 = rows of the tile), applies bias / ReLU and stores
-// FP32 and/or BF16.
+// Two kernels share the tensor-core step and the epilogue:
+//
+// gemm_bf16_tn_tma_kernel (default): one CTA of 128 threads computes a
+// 128 x BN tile of C (BN = 64, 128 or 256, chosen per shape) with the roles
+// split by warp:
+//   * one thread of warp 0 is the producer: for each K step of 64 it arms
+//     the stage's "full" mbarrier with the byte count and issues two TMA
+//     tile loads (cp.async.bulk.tensor, 128-byte swizzle, zero fill outside
+//     M, N, K) of the A (128 x 64) and B (BN x 64) tiles into a ring of
+//     stages; it refills a stage once its "empty" mbarrier reports that the
+//     MMAs reading it have completed;
+//   * one thread of warp 1 issues the MMAs: it waits for a stage's "full"
+//     barrier, issues four tcgen05.mma (K = 16 each, 128-byte-swizzle
+//     K-major descriptors) into the TMEM accumulator and commits them to the
+//     stage's "empty" barrier; after the last K step it commits to "done";
+//   * all four warps wait for "done" and run the epilogue.
+// The operands are viewed as 3-D tensors {K slice, slice, rows} so the
+// split-K form (slice z covers K columns [z Kslice, (z+1) Kslice)) reads
+// zeros past the end of its own slice.
+//
+// gemm_bf16_tn_kernel (fallback when no tensor map can be made, or
+// CMG_GEMM_TMA=0): a 128 x 64 tile, every thread copying with cp.async into
+// the no-swizzle core-matrix layout, kStages - 1 K steps in flight, one
+// thread issuing the MMAs after a CTA barrier.
+//
+// Epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of the tile) with
+// tcgen05.ld, 32 columns at a time, adds bias, applies ReLU, and stores FP32
+// and/or BF16 with 16-byte stores where alignment allows.
 //
 // Every wait has an iteration limit; on expiry the kernel records an error
-// code, stops issuing work, frees its TMEM columns and returns.
+// code, stops issuing work, waits (again bounded) for the copies it has in
+// flight, frees its TMEM columns and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <cstdlib>
+#include <mutex>
 
 #include "cmg_internal.h"
 
@@ -53,6 +69,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
+// The same descriptor for a K-major tile written by TMA with the 128-byte
+// swizzle: rows of 128 bytes (64 BF16 of K), 8-row groups 1024 bytes apart
+// (stride byte offset), layout type 2 (128-byte swizzle) in bits 61-63; the
+// leading byte offset is unused for this layout.  The tile base is 1024-byte
+// aligned, so a K step of 16 inside the 128-byte row advances the start
+// address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulate, A and B BF16, both
 // K-major, N and M of the MMA.
 __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
@@ -63,8 +95,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Wait for phase `parity` of the mbarrier; false if the poll limit expires.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of the mbarrier; false if the poll limit expires
+// or, when `abort` is given, once another thread has set it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort = nullptr) {
   const uint32_t a = smem_u32(bar);
   for (long i = 0; i < kSpinLimit; ++i) {
     uint32_t done;
@@ -74,8 +107,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if (abort && *abort) return false;
   }
   return false;
+}
+
+// Arrive on the barrier and add `bytes` to the transaction count its phase
+// waits for (the TMA loads of one stage).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// TMA load of one box of a 3-D tensor map at coordinates (c0, c1, c2),
+// completing on `bar` with the box's byte count.  c0 (the K coordinate) is
+// always a multiple of 64 elements, which keeps the copy 16-byte aligned.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -110,6 +162,76 @@ __device__ __forceinline__ void load_tile_async(__nv_bfloat16* dst, const __nv_b
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Epilogue of one warp: rows m0 + 32 warp + lane of C, `chunks` blocks of
+// 32 accumulator columns (TMEM columns 32c.., C columns n0 + 32c..), bias,
+// ReLU, FP32 and/or BF16 stores.  Called by all 32 lanes together.
+__device__ __forceinline__ void store_tile(uint32_t tmem, int chunks, int warp, int lane, int m0, int n0, int M, int N,
+                                           const float* __restrict__ bias, int relu, float* __restrict__ C32,
+                                           __nv_bfloat16* __restrict__ C16, int ldc, int vec16, int vec32) {
+  const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+  for (int ch = 0; ch < chunks; ++ch) {
+    if (n0 + ch * 32 >= N) break;   // uniform over the warp
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (row < M) {
+      const int c0 = n0 + ch * 32;
+      float v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        v[j] = __uint_as_float(r[j]);
+        if (bias && c0 + j < N) v[j] += bias[c0 + j];
+        if (relu) v[j] = fmaxf(v[j], 0.f);
+      }
+      // 16-byte stores of consecutive columns of this thread's row (a
+      // scalar store per element only at a ragged right edge or when the
+      // row stride does not keep 16-byte alignment)
+#pragma unroll
+      for (int q = 0; q < 32; q += 8) {
+        const int col = c0 + q;
+        if (C16) {
+          __nv_bfloat16* dst = C16 + (size_t)row * ldc + col;
+          if (vec16 && col + 8 <= N) {
+            uint4 pk;
+            uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[q + 2 * t], v[q + 2 * t + 1]);
+              w[t] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            *reinterpret_cast<uint4*>(dst) = pk;
+          } else {
+            for (int t = 0; t < 8; ++t)
+              if (col + t < N) dst[t] = __float2bfloat16_rn(v[q + t]);
+          }
+        }
+        if (C32) {
+          float* dst = C32 + (size_t)row * ldc + col;
+#pragma unroll
+          for (int t = 0; t < 8; t += 4) {
+            if (vec32 && col + t + 4 <= N) {
+              *reinterpret_cast<float4*>(dst + t) = make_float4(v[q + t], v[q + t + 1], v[q + t + 2], v[q + t + 3]);
+            } else {
+              for (int u = 0; u < 4; ++u)
+                if (col + t + u < N) dst[t + u] = v[q + t + u];
+            }
+          }
+        }
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloat16* __restrict__ A, long lda,
                                                                 const __nv_bfloat16* __restrict__ B, long ldb, int M,
@@ -213,70 +335,7 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
 
-  if (!failed) {
-    // epilogue: warp w reads rows 32w + lane, 64 columns in two loads of 32
-    const int row = m0 + warp * 32 + lane;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 32);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        const int c0 = n0 + half * 32;
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          v[j] = __uint_as_float(r[j]);
-          if (bias && c0 + j < N) v[j] += bias[c0 + j];
-          if (relu) v[j] = fmaxf(v[j], 0.f);
-        }
-        // 16-byte stores of consecutive columns of this thread's row (a
-        // scalar store per element only at a ragged right edge or when the
-        // row stride does not keep 16-byte alignment)
-#pragma unroll
-        for (int q = 0; q < 32; q += 8) {
-          const int col = c0 + q;
-          if (C16) {
-            __nv_bfloat16* dst = C16 + (size_t)row * ldc + col;
-            if (vec16 && col + 8 <= N) {
-              uint4 pk;
-              uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-              for (int t = 0; t < 4; ++t) {
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[q + 2 * t], v[q + 2 * t + 1]);
-                w[t] = *reinterpret_cast<const uint32_t*>(&b2);
-              }
-              *reinterpret_cast<uint4*>(dst) = pk;
-            } else {
-              for (int t = 0; t < 8; ++t)
-                if (col + t < N) dst[t] = __float2bfloat16_rn(v[q + t]);
-            }
-          }
-          if (C32) {
-            float* dst = C32 + (size_t)row * ldc + col;
-#pragma unroll
-            for (int t = 0; t < 8; t += 4) {
-              if (vec32 && col + t + 4 <= N) {
-                *reinterpret_cast<float4*>(dst + t) = make_float4(v[q + t], v[q + t + 1], v[q + t + 2], v[q + t + 3]);
-              } else {
-                for (int u = 0; u < 4; ++u)
-                  if (col + t + u < N) dst[t + u] = v[q + t + u];
-              }
-            }
-          }
-        }
-      }
-    }
-  }
+  if (!failed) store_tile(tmem, kBN / 32, warp, lane, m0, n0, M, N, bias, relu, C32, C16, ldc, vec16, vec32);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -285,11 +344,219 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
   if (failed && threadIdx.x == 0) atomicExch(status, 1);
 }
 
+
+// ---- TMA-fed, warp-specialised kernel ---------------------------------------
+
+template <int BN, int S>
+struct TmaTile {
+  static constexpr uint32_t kABytes = kBM * kBK * 2;              // 16 KiB
+  static constexpr uint32_t kBBytes = BN * kBK * 2;
+  static constexpr uint32_t kStageBytes = kABytes + kBBytes;      // multiple of 1024
+  static constexpr int kSmem = S * kStageBytes + 1024;            // + slack to align the ring to 1024 bytes
+  static_assert(BN == 64 || BN == 128 || BN == 256, "MMA N and TMEM allocation");
+  static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
+};
+
+template <int BN, int S>
+__global__ void __launch_bounds__(kThreads) gemm_bf16_tn_tma_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                                    const __grid_constant__ CUtensorMap mapB, int M,
+                                                                    int N, int K, const float* __restrict__ bias,
+                                                                    int relu, float* __restrict__ C32,
+                                                                    __nv_bfloat16* __restrict__ C16, int ldc,
+                                                                    int* __restrict__ status, int vec16, int vec32) {
+  using T = TmaTile<BN, S>;
+  extern __shared__ __align__(1024) unsigned char dyn_smem[];
+  __shared__ __align__(8) uint64_t full[S], empty[S], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int failed;
+  __shared__ int issued, consumed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, z = blockIdx.z;
+  if (C32) C32 += (size_t)z * M * ldc;
+  // the 128-byte swizzle pattern repeats every 1024 bytes: align the ring
+  const uint32_t raw = smem_u32(dyn_smem);
+  unsigned char* ring = dyn_smem + ((1024u - (raw & 1023u)) & 1023u);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    failed = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int ksteps = (K + kBK - 1) / kBK;
+
+  if (warp == 0 && lane == 0) {
+    // producer: K step kt goes to stage kt % S; its (kt / S)-th use waits for
+    // the MMAs of the previous use (completion kt / S - 1 of "empty")
+    int kt = 0;
+    for (; kt < ksteps; ++kt) {
+      const int s = kt % S;
+      if (kt >= S && !mbar_wait(&empty[s], (uint32_t)((kt / S - 1) & 1), &failed)) {
+        failed = 1;
+        break;
+      }
+      unsigned char* sa = ring + s * T::kStageBytes;
+      mbar_expect_tx(&full[s], T::kStageBytes);
+      tma_load_3d(sa, &mapA, kt * kBK, z, m0, &full[s]);
+      tma_load_3d(sa + T::kABytes, &mapB, kt * kBK, z, n0, &full[s]);
+    }
+    issued = kt;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = instr_desc(kBM, BN);
+    int kt = 0;
+    for (; kt < ksteps; ++kt) {
+      const int s = kt % S;
+      if (!mbar_wait(&full[s], (uint32_t)((kt / S) & 1), &failed)) {
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(ring + s * T::kStageBytes), b0 = a0 + T::kABytes;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)
+        mma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                 (kt > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    consumed = kt;
+    mma_commit(&done);   // completes once every MMA issued above has completed
+  }
+  __syncwarp();
+  if (!mbar_wait(&done, 0)) failed = 1;
+  __syncthreads();
+  if (failed && threadIdx.x == 0) {
+    // loads issued but never consumed are still landing in the ring
+    for (int kt = consumed; kt < issued; ++kt) (void)mbar_wait(&full[kt % S], (uint32_t)((kt / S) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!failed) store_tile(tmem, BN / 32, warp, lane, m0, n0, M, N, bias, relu, C32, C16, ldc, vec16, vec32);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+  }
+  if (failed && threadIdx.x == 0) atomicExch(status, 1);
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of a K-major BF16 operand [rows][ld] read as `ksplit` slices of
+// `kslice` columns: dimensions {kslice, ksplit, rows}, strides {kslice, ld}
+// elements (both multiples of 8, i.e. of 16 bytes), box {64, 1, box_rows},
+// 128-byte swizzle, zero fill outside.
+bool operand_map(CUtensorMap* map, const void* base, long ld, int rows, int kslice, int ksplit, int box_rows) {
+  const EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)kslice, (cuuint64_t)ksplit, (cuuint64_t)rows};
+  const cuuint64_t strides[2] = {(cuuint64_t)kslice * 2, (cuuint64_t)ld * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)kBK, 1, (cuuint32_t)box_rows};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  static std::once_flag once;
+  static int sms = 0;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 0;
+    (void)cudaGetLastError();
+  });
+  return sms;
+}
+
+// Tile width: the widest of 256, 128 that pads N no more than 64 does and
+// still gives every SM a tile; else 64.
+int pick_bn(int M, int N) {
+  const long mt = (M + kBM - 1) / kBM;
+  const long pad64 = (N + 63L) / 64 * 64;
+  for (int bn : {256, 128}) {
+    const long nt = (N + bn - 1) / bn;
+    if (nt * bn == pad64 && mt * nt >= sm_count()) return bn;
+  }
+  return 64;
+}
+
+template <int BN, int S>
+cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int N, int K, const float* bias, int relu,
+                       float* C32, __nv_bfloat16* C16, int ldc, int* status, cudaStream_t s, int ksplit, int vec16,
+                       int vec32) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(gemm_bf16_tn_tma_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaTile<BN, S>::kSmem);
+  });
+  if (attr != cudaSuccess) return attr;
+  const dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, ksplit);
+  gemm_bf16_tn_tma_kernel<BN, S><<<grid, kThreads, TmaTile<BN, S>::kSmem, s>>>(mA, mB, M, N, K, bias, relu, C32, C16,
+                                                                               ldc, status, vec16, vec32);
+  return cudaGetLastError();
+}
+
 }  // namespace nn
 
 cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb, int M, int N, int K,
                                 const float* bias, int relu, float* C32, void* C16, int ldc, int* status,
                                 cudaStream_t s, int ksplit) {
+  // 16-byte epilogue stores need every row start 16-byte aligned
+  const int vec16 = C16 && (ldc % 8 == 0) && ((reinterpret_cast<uintptr_t>(C16) & 15) == 0);
+  const int vec32 = C32 && (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C32) & 15) == 0) &&
+                    (ksplit == 1 || ((size_t)M * ldc) % 4 == 0);
+  __nv_bfloat16* c16 = static_cast<__nv_bfloat16*>(C16);
+  const char* env = std::getenv("CMG_GEMM_TMA");
+  if (!(env && env[0] == '0')) {
+    const int bn = nn::pick_bn(M, N);
+    CUtensorMap mA, mB;
+    if (nn::operand_map(&mA, A, lda, M, K, ksplit, nn::kBM) && nn::operand_map(&mB, B, ldb, N, K, ksplit, bn)) {
+      cudaError_t e;
+      if (bn == 256)
+        e = nn::launch_tma<256, 4>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
+      else if (bn == 128)
+        e = nn::launch_tma<128, 3>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
+      else
+        e = nn::launch_tma<64, 4>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
+      count_launches(1);
+      return e;
+    }
+  }
   static bool attr = false;
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(nn::gemm_bf16_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -298,13 +565,9 @@ cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb
     attr = true;
   }
   dim3 grid((M + nn::kBM - 1) / nn::kBM, (N + nn::kBN - 1) / nn::kBN, ksplit);
-  // 16-byte epilogue stores need every row start 16-byte aligned
-  const int vec16 = C16 && (ldc % 8 == 0) && ((reinterpret_cast<uintptr_t>(C16) & 15) == 0);
-  const int vec32 = C32 && (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C32) & 15) == 0) &&
-                    (ksplit == 1 || ((size_t)M * ldc) % 4 == 0);
   nn::gemm_bf16_tn_kernel<<<grid, nn::kThreads, nn::kSmemBytes, s>>>(
       static_cast<const __nv_bfloat16*>(A), lda, static_cast<const __nv_bfloat16*>(B), ldb, M, N, K, bias, relu, C32,
-      static_cast<__nv_bfloat16*>(C16), ldc, status, vec16, vec32);
+      c16, ldc, status, vec16, vec32);
   count_launches(1);
   return cudaGetLastError();
 }

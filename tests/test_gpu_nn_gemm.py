@@ -1,4 +1,7 @@
-"""tcgen05 BF16 GEMM of the warm-start network against an FP32 CPU matmul."""
+"""tcgen05 BF16 GEMM of the warm-start network against an FP32 CPU matmul.
+
+Every case runs through both kernels: the TMA-fed warp-specialised one (the
+default) and the cp.async one (CMG_GEMM_TMA=0)."""
 import ctypes
 
 import pytest
@@ -23,14 +26,23 @@ def gemm():
     return fn
 
 
+@pytest.fixture(params=["tma", "cp_async"])
+def path(request, monkeypatch):
+    monkeypatch.setenv("CMG_GEMM_TMA", "1" if request.param == "tma" else "0")
+    return request.param
+
+
 def ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+# the last two shapes select the 256- and 128-column tiles of the TMA kernel
+# (N a multiple of the tile, at least one tile per SM); the last has a
+# ragged M and a K of two full steps plus 8
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 128, 192), (200, 50, 128), (1024, 64, 640), (131, 96, 64),
-                                   (300, 1, 32), (128, 288, 72)])
+                                   (300, 1, 32), (128, 288, 72), (2560, 2048, 320), (6600, 384, 136)])
 @pytest.mark.parametrize("epilogue", ["plain", "bias_relu"])
-def test_gemm_matches_cpu(gemm, M, N, K, epilogue):
+def test_gemm_matches_cpu(gemm, path, M, N, K, epilogue):
     g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, generator=g).to(torch.bfloat16)
@@ -55,14 +67,17 @@ def test_gemm_matches_cpu(gemm, M, N, K, epilogue):
     assert (C16.float().cpu() - ref).abs().max().item() <= 8e-3 * scale
 
 
-def test_gemm_rejects_bad_shapes(gemm):
+def test_gemm_rejects_bad_shapes(gemm, path):
     A = torch.zeros(128, 96, dtype=torch.bfloat16, device="cuda")
     C = torch.zeros(128, 64, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     assert gemm(ptr(A), 96, ptr(A), 96, 128, 64, 12, None, 0, ptr(C), None, 64, ptr(status), None) == 1   # K % 8
 
 
-def test_gemm_splitk_matches_cpu(gemm):
+# Kslice = 200 is not a multiple of the K step of 64: each slice's last step
+# must read zeros, not the next slice's columns
+@pytest.mark.parametrize("M,N,S,Z", [(64, 288, 1024, 6), (96, 40, 200, 5)])
+def test_gemm_splitk_matches_cpu(gemm, path, M, N, S, Z):
     import paper_2302_13680_gb300 as P
 
     lib = P.load_library()
@@ -71,8 +86,7 @@ def test_gemm_splitk_matches_cpu(gemm):
     fn.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                    ctypes.c_void_p]
-    M, N, S, Z = 64, 288, 1024, 6
-    g = torch.Generator().manual_seed(9)
+    g = torch.Generator().manual_seed(9 + S)
     A = torch.randn(M, S * Z, generator=g).to(torch.bfloat16)
     B = torch.randn(N, S * Z, generator=g).to(torch.bfloat16)
     part = torch.zeros(Z, M, N, device="cuda")
@@ -83,3 +97,20 @@ def test_gemm_splitk_matches_cpu(gemm):
     for z in range(Z):
         ref = A[:, z * S:(z + 1) * S].float() @ B[:, z * S:(z + 1) * S].float().T
         assert (part[z].cpu() - ref).abs().max().item() <= 1e-5 * S ** 0.5 * ref.abs().max().item()
+
+
+def test_gemm_row_stride_wider_than_k(gemm, path):
+    # A and B are column windows of wider matrices (lda, ldb > K); C has ldc > N
+    M, N, K, lda, ldb, ldc = 520, 200, 136, 200, 152, 208
+    g = torch.Generator().manual_seed(31)
+    Aw = torch.randn(M, lda, generator=g).to(torch.bfloat16)
+    Bw = torch.randn(N, ldb, generator=g).to(torch.bfloat16)
+    ref = Aw[:, :K].float() @ Bw[:, :K].float().T
+    C = torch.full((M, ldc), 7.0, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert gemm(ptr(Aw.cuda()), lda, ptr(Bw.cuda()), ldb, M, N, K, None, 0, ptr(C), None, ldc, ptr(status), None) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    got = C.cpu()
+    assert (got[:, :N] - ref).abs().max().item() <= 1e-5 * K ** 0.5 * ref.abs().max().item() + 1e-6
+    assert bool((got[:, N:] == 7.0).all())   # columns past N untouched
