@@ -2,22 +2,28 @@
 // network:  C[M][N] = A[M][K] * B[N][K]^T  (+ bias[N], optional ReLU),
 // A and B K-major BF16, FP32 accumulation in tensor memory (TMEM).
 //
-// Two kernels share the tensor-core step and the epilogue:
+// Two kernels share the tensor-core step:
 //
-// gemm_bf16_tn_tma_kernel (default): one CTA of 128 threads computes a
-// 128 x BN tile of C (BN = 64, 128 or 256, chosen per shape) with the roles
-// split by warp:
+// gemm_bf16_tn_tma_kernel (default): persistent, one CTA of 192 threads per
+// SM walking 128 x BN tiles of C (BN = 64, 128 or 256, chosen per shape),
+// roles split by warp:
 //   * one thread of warp 0 is the producer: for each K step of 64 it arms
-//     the stage's "full" mbarrier with the byte count and issues two TMA
-//     tile loads (cp.async.bulk.tensor, 128-byte swizzle, zero fill outside
-//     M, N, K) of the A (128 x 64) and B (BN x 64) tiles into a ring of
-//     stages; it refills a stage once its "empty" mbarrier reports that the
-//     MMAs reading it have completed;
-//   * one thread of warp 1 issues the MMAs: it waits for a stage's "full"
-//     barrier, issues four tcgen05.mma (K = 16 each, 128-byte-swizzle
-//     K-major descriptors) into the TMEM accumulator and commits them to the
-//     stage's "empty" barrier; after the last K step it commits to "done";
-//   * all four warps wait for "done" and run the epilogue.
+//     a stage's "full" mbarrier with the byte count and issues two TMA tile
+//     loads (cp.async.bulk.tensor, 128-byte swizzle, zero fill outside M, N,
+//     K) of the A (128 x 64) and B (BN x 64) tiles into a ring of stages
+//     that runs on across tiles; it refills a stage once its "empty"
+//     mbarrier reports that the MMAs reading it have completed;
+//   * one thread of warp 1 issues the MMAs: per K step it waits for the
+//     stage's "full" barrier, issues four tcgen05.mma (K = 16 each,
+//     128-byte-swizzle K-major descriptors) and commits them to the stage's
+//     "empty" barrier.  Tiles alternate between two TMEM accumulators
+//     (2 BN columns), so the MMAs of tile i + 1 run while tile i is being
+//     stored; a tile's last commit goes to its accumulator's "full" barrier;
+//   * warps 2-5 are the epilogue: warp w reads TMEM lanes 32 (w % 4)..+31
+//     (rows of the tile), 32 columns at a time, transposes each 32 x 32 block
+//     through shared memory so that every store instruction writes
+//     consecutive columns of one row (coalesced), adds bias, applies ReLU,
+//     stores FP32 and/or BF16, then releases the accumulator.
 // The operands are viewed as 3-D tensors {K slice, slice, rows} so the
 // split-K form (slice z covers K columns [z Kslice, (z+1) Kslice)) reads
 // zeros past the end of its own slice.
@@ -27,9 +33,9 @@
 // the no-swizzle core-matrix layout, kStages - 1 K steps in flight, one
 // thread issuing the MMAs after a CTA barrier.
 //
-// Epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of the tile) with
-// tcgen05.ld, 32 columns at a time, adds bias, applies ReLU, and stores FP32
-// and/or BF16 with 16-byte stores where alignment allows.
+// Its epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of the tile)
+// with tcgen05.ld, adds bias, applies ReLU, and stores FP32 and/or BF16 with
+// 16-byte stores where alignment allows.
 //
 // Every wait has an iteration limit; on expiry the kernel records an error
 // code, stops issuing work, waits (again bounded) for the copies it has in
@@ -345,42 +351,58 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
 }
 
 
-// ---- TMA-fed, warp-specialised kernel ---------------------------------------
+// ---- TMA-fed, warp-specialised, persistent kernel ---------------------------
+
+constexpr int kTmaThreads = 192;   // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int kEpiWarps = 4;
+constexpr int kStageRow = 33;      // padded row of the epilogue transpose buffer (floats)
 
 template <int BN, int S>
 struct TmaTile {
   static constexpr uint32_t kABytes = kBM * kBK * 2;              // 16 KiB
   static constexpr uint32_t kBBytes = BN * kBK * 2;
   static constexpr uint32_t kStageBytes = kABytes + kBBytes;      // multiple of 1024
-  static constexpr int kSmem = S * kStageBytes + 1024;            // + slack to align the ring to 1024 bytes
+  static constexpr uint32_t kEpiBytes = kEpiWarps * 32 * kStageRow * 4;
+  static constexpr int kSmem = S * kStageBytes + kEpiBytes + 1024;   // + slack to align the ring to 1024 bytes
+  static constexpr uint32_t kTmemCols = 2 * BN;                   // two accumulators
   static_assert(BN == 64 || BN == 128 || BN == 256, "MMA N and TMEM allocation");
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
+// Tile t of the persistent walk: N tile fastest, then M tile, then split-K
+// slice.  CTAs running at the same time then share the A block of their
+// rows (read once from memory) and together write whole rows of C.
+struct TileIdx {
+  int m0, n0, z;
+};
+__device__ __forceinline__ TileIdx tile_of(int t, int mtiles, int ntiles, int bn) {
+  const int per = mtiles * ntiles;
+  const int z = t / per, r = t - z * per;
+  return {(r / ntiles) * kBM, (r % ntiles) * bn, z};
+}
+
 template <int BN, int S>
-__global__ void __launch_bounds__(kThreads) gemm_bf16_tn_tma_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                                    const __grid_constant__ CUtensorMap mapB, int M,
-                                                                    int N, int K, const float* __restrict__ bias,
-                                                                    int relu, float* __restrict__ C32,
-                                                                    __nv_bfloat16* __restrict__ C16, int ldc,
-                                                                    int* __restrict__ status, int vec16, int vec32) {
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    gemm_bf16_tn_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
+                            int N, int K, const float* __restrict__ bias, int relu, float* __restrict__ C32,
+                            __nv_bfloat16* __restrict__ C16, int ldc, int* __restrict__ status, int vec16,
+                            int mtiles, int ntiles, int tiles) {
   using T = TmaTile<BN, S>;
   extern __shared__ __align__(1024) unsigned char dyn_smem[];
-  __shared__ __align__(8) uint64_t full[S], empty[S], done;
+  __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int failed;
   __shared__ int issued, consumed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, z = blockIdx.z;
-  if (C32) C32 += (size_t)z * M * ldc;
   // the 128-byte swizzle pattern repeats every 1024 bytes: align the ring
   const uint32_t raw = smem_u32(dyn_smem);
   unsigned char* ring = dyn_smem + ((1024u - (raw & 1023u)) & 1023u);
+  float* epi = reinterpret_cast<float*>(ring + S * T::kStageBytes);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"((uint32_t)BN)
+                 "r"(T::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -389,7 +411,11 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_tma_kernel(const __grid
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps);
+    }
+    mbar_init(&drain, 1);
     failed = 0;
     issued = 0;
     consumed = 0;
@@ -401,56 +427,164 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_tma_kernel(const __grid
   const uint32_t tmem = tmem_base;
   const int ksteps = (K + kBK - 1) / kBK;
 
-  if (warp == 0 && lane == 0) {
-    // producer: K step kt goes to stage kt % S; its (kt / S)-th use waits for
-    // the MMAs of the previous use (completion kt / S - 1 of "empty")
-    int kt = 0;
-    for (; kt < ksteps; ++kt) {
-      const int s = kt % S;
-      if (kt >= S && !mbar_wait(&empty[s], (uint32_t)((kt / S - 1) & 1), &failed)) {
-        failed = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: the it-th K step overall (across this CTA's tiles) goes to
+      // stage it % S; its (it / S)-th use of the stage waits for completion
+      // it / S - 1 of the stage's "empty" barrier
+      int it = 0;
+      for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+        const TileIdx ti = tile_of(t, mtiles, ntiles, BN);
+        for (int kt = 0; kt < ksteps; ++kt, ++it) {
+          const int s = it % S;
+          if (it >= S && !mbar_wait(&empty[s], (uint32_t)((it / S - 1) & 1), &failed)) {
+            failed = 1;
+            break;
+          }
+          unsigned char* sa = ring + s * T::kStageBytes;
+          mbar_expect_tx(&full[s], T::kStageBytes);
+          tma_load_3d(sa, &mapA, kt * kBK, ti.z, ti.m0, &full[s]);
+          tma_load_3d(sa + T::kABytes, &mapB, kt * kBK, ti.z, ti.n0, &full[s]);
+        }
       }
-      unsigned char* sa = ring + s * T::kStageBytes;
-      mbar_expect_tx(&full[s], T::kStageBytes);
-      tma_load_3d(sa, &mapA, kt * kBK, z, m0, &full[s]);
-      tma_load_3d(sa + T::kABytes, &mapB, kt * kBK, z, n0, &full[s]);
+      issued = it;
     }
-    issued = kt;
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    const uint32_t idesc = instr_desc(kBM, BN);
-    int kt = 0;
-    for (; kt < ksteps; ++kt) {
-      const int s = kt % S;
-      if (!mbar_wait(&full[s], (uint32_t)((kt / S) & 1), &failed)) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: tile number tc of this CTA accumulates into TMEM columns
+      // (tc % 2) * BN, after the epilogue has drained that buffer's previous
+      // tile (completion tc / 2 - 1 of acc_empty)
+      const uint32_t idesc = instr_desc(kBM, BN);
+      int it = 0, tc = 0;
+      for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x, ++tc) {
+        const int b = tc & 1;
+        if (tc >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((tc / 2 - 1) & 1), &failed)) {
+          failed = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        bool ok = true;
+        for (int kt = 0; kt < ksteps; ++kt, ++it) {
+          const int s = it % S;
+          if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), &failed)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(ring + s * T::kStageBytes), b0 = a0 + T::kABytes;
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            mma_bf16(acc, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                     (kt > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (!ok) {
+          failed = 1;
+          break;
+        }
+        mma_commit(&acc_full[b]);
+      }
+      consumed = it;
+      mma_commit(&drain);   // completes once every MMA issued above has completed
+      if (!mbar_wait(&drain, 0)) failed = 1;
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. rows
+    // 32 (w % 4) .. of the tile; each 32 x 32 block goes through this warp's
+    // transpose buffer so that a store instruction writes one row segment
+    // (consecutive lanes, consecutive columns)
+    const int q = warp & 3;
+    float* st = epi + (warp - 2) * 32 * kStageRow;
+    int tc = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
+      const int b = tc & 1;
+      // every lane waits; the outcome is made uniform over the warp before the
+      // warp-collective TMEM loads
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((tc / 2) & 1), &failed))) {
         failed = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(ring + s * T::kStageBytes), b0 = a0 + T::kABytes;
+      const TileIdx ti = tile_of(t, mtiles, ntiles, BN);
+      float* c32 = C32 ? C32 + (size_t)ti.z * M * ldc : nullptr;
+      const int rbase = ti.m0 + q * 32;
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        const int c0 = ti.n0 + ch * 32;
+        if (c0 >= N) break;   // uniform over the warp
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + ch * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        __syncwarp();   // the previous block's reads of the buffer are done
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk)
-        mma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
-                 (kt > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
+        for (int j = 0; j < 32; ++j) st[lane * kStageRow + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        // lane l now owns column c0 + l of the 32 rows
+        const int col = c0 + lane;
+        const float bj = (bias && col < N) ? bias[col] : 0.f;
+        if (c32) {
+          if (col < N) {
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+              const int row = rbase + i;
+              if (row >= M) break;
+              float v = st[i * kStageRow + lane] + bj;
+              if (relu) v = fmaxf(v, 0.f);
+              c32[(size_t)row * ldc + col] = v;
+            }
+          }
+        }
+        if (C16) {
+          // two rows per instruction: lanes 0-15 row i, lanes 16-31 row i + 1,
+          // two consecutive columns per lane
+          const int hl = lane & 15, cc = c0 + 2 * hl;
+          const float b0 = (bias && cc < N) ? bias[cc] : 0.f, b1 = (bias && cc + 1 < N) ? bias[cc + 1] : 0.f;
+#pragma unroll 4
+          for (int i = 0; i < 32; i += 2) {
+            const int rr = i + (lane >> 4), row = rbase + rr;
+            if (row < M && cc < N) {
+              float v0 = st[rr * kStageRow + 2 * hl] + b0, v1 = st[rr * kStageRow + 2 * hl + 1] + b1;
+              if (relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+              }
+              __nv_bfloat16* dst = C16 + (size_t)row * ldc + cc;
+              if (vec16 && cc + 1 < N) {
+                *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(v0, v1);
+              } else {
+                dst[0] = __float2bfloat16_rn(v0);
+                if (cc + 1 < N) dst[1] = __float2bfloat16_rn(v1);
+              }
+            }
+          }
+        }
+      }
+      // this warp's reads of accumulator b are complete
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
     }
-    consumed = kt;
-    mma_commit(&done);   // completes once every MMA issued above has completed
   }
   __syncwarp();
-  if (!mbar_wait(&done, 0)) failed = 1;
   __syncthreads();
   if (failed && threadIdx.x == 0) {
     // loads issued but never consumed are still landing in the ring
-    for (int kt = consumed; kt < issued; ++kt) (void)mbar_wait(&full[kt % S], (uint32_t)((kt / S) & 1));
+    for (int it = consumed; it < issued; ++it) (void)mbar_wait(&full[it % S], (uint32_t)((it / S) & 1));
   }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!failed) store_tile(tmem, BN / 32, warp, lane, m0, n0, M, N, bias, relu, C32, C16, ldc, vec16, vec32);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T::kTmemCols) : "memory");
   }
   if (failed && threadIdx.x == 0) atomicExch(status, 1);
 }
@@ -516,8 +650,7 @@ int pick_bn(int M, int N) {
 
 template <int BN, int S>
 cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int N, int K, const float* bias, int relu,
-                       float* C32, __nv_bfloat16* C16, int ldc, int* status, cudaStream_t s, int ksplit, int vec16,
-                       int vec32) {
+                       float* C32, __nv_bfloat16* C16, int ldc, int* status, cudaStream_t s, int ksplit, int vec16) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
@@ -525,9 +658,13 @@ cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int 
                                 TmaTile<BN, S>::kSmem);
   });
   if (attr != cudaSuccess) return attr;
-  const dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, ksplit);
-  gemm_bf16_tn_tma_kernel<BN, S><<<grid, kThreads, TmaTile<BN, S>::kSmem, s>>>(mA, mB, M, N, K, bias, relu, C32, C16,
-                                                                               ldc, status, vec16, vec32);
+  const int mtiles = (M + kBM - 1) / kBM, ntiles = (N + BN - 1) / BN;
+  const long tiles = (long)mtiles * ntiles * ksplit;
+  if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
+  const int sms = sm_count();
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));   // persistent: one CTA per SM
+  gemm_bf16_tn_tma_kernel<BN, S><<<grid, kTmaThreads, TmaTile<BN, S>::kSmem, s>>>(
+      mA, mB, M, N, K, bias, relu, C32, C16, ldc, status, vec16, mtiles, ntiles, (int)tiles);
   return cudaGetLastError();
 }
 
@@ -547,12 +684,13 @@ cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb
     CUtensorMap mA, mB;
     if (nn::operand_map(&mA, A, lda, M, K, ksplit, nn::kBM) && nn::operand_map(&mB, B, ldb, N, K, ksplit, bn)) {
       cudaError_t e;
+      // persistent, one CTA per SM: as many stages as fit beside the epilogue buffers
       if (bn == 256)
-        e = nn::launch_tma<256, 4>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
+        e = nn::launch_tma<256, 4>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16);
       else if (bn == 128)
-        e = nn::launch_tma<128, 3>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
+        e = nn::launch_tma<128, 6>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16);
       else
-        e = nn::launch_tma<64, 4>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
+        e = nn::launch_tma<64, 8>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16);
       count_launches(1);
       return e;
     }

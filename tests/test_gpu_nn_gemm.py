@@ -36,11 +36,14 @@ def ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-# the last two shapes select the 256- and 128-column tiles of the TMA kernel
-# (N a multiple of the tile, at least one tile per SM); the last has a
-# ragged M and a K of two full steps plus 8
+# (2560, 2048, 320) and (6600, 384, 136) select the 256- and 128-column
+# tiles of the TMA kernel (N a multiple of the tile, at least one tile per
+# SM; the latter with a ragged M and a K of two full steps plus 8); the last
+# two give each persistent CTA three or four tiles, so both TMEM
+# accumulators are reused
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 128, 192), (200, 50, 128), (1024, 64, 640), (131, 96, 64),
-                                   (300, 1, 32), (128, 288, 72), (2560, 2048, 320), (6600, 384, 136)])
+                                   (300, 1, 32), (128, 288, 72), (2560, 2048, 320), (6600, 384, 136),
+                                   (40000, 96, 72), (70000, 40, 64)])
 @pytest.mark.parametrize("epilogue", ["plain", "bias_relu"])
 def test_gemm_matches_cpu(gemm, path, M, N, K, epilogue):
     g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
