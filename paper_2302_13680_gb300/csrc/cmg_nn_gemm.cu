@@ -4,7 +4,7 @@
 //
 // Two kernels share the tensor-core step:
 //
-// gemm_bf16_tn_tma_kernel (default): persistent, one CTA of 192 threads per
+// gemm_bf16_tn_tma_kernel (default): persistent, one CTA of 320 threads per
 // SM walking 128 x BN tiles of C (BN = 64, 128 or 256, chosen per shape),
 // roles split by warp:
 //   * one thread of warp 0 is the producer: for each K step of 64 it arms
@@ -19,11 +19,12 @@
 //     "empty" barrier.  Tiles alternate between two TMEM accumulators
 //     (2 BN columns), so the MMAs of tile i + 1 run while tile i is being
 //     stored; a tile's last commit goes to its accumulator's "full" barrier;
-//   * warps 2-5 are the epilogue: warp w reads TMEM lanes 32 (w % 4)..+31
-//     (rows of the tile), 32 columns at a time, transposes each 32 x 32 block
-//     through shared memory so that every store instruction writes
-//     consecutive columns of one row (coalesced), adds bias, applies ReLU,
-//     stores FP32 and/or BF16, then releases the accumulator.
+//   * warps 2-9 are the epilogue: warp w reads TMEM lanes 32 (w % 4)..+31
+//     (rows of the tile), the two warps of a lane quadrant taking alternate
+//     32-column blocks; each 32 x 32 block is transposed through a swizzled
+//     shared-memory buffer so that every 16-byte store writes consecutive
+//     columns of a row (whole row segments per instruction), with bias,
+//     ReLU, FP32 and/or BF16 output; then the accumulator is released.
 // The operands are viewed as 3-D tensors {K slice, slice, rows} so the
 // split-K form (slice z covers K columns [z Kslice, (z+1) Kslice)) reads
 // zeros past the end of its own slice.
@@ -353,16 +354,15 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(const __nv_bfloa
 
 // ---- TMA-fed, warp-specialised, persistent kernel ---------------------------
 
-constexpr int kTmaThreads = 192;   // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
-constexpr int kEpiWarps = 4;
-constexpr int kStageRow = 33;      // padded row of the epilogue transpose buffer (floats)
+constexpr int kEpiWarps = 8;                            // two per TMEM lane quadrant
+constexpr int kTmaThreads = 64 + 32 * kEpiWarps;        // warp 0 producer, warp 1 MMA, warps 2-9 epilogue
 
 template <int BN, int S>
 struct TmaTile {
   static constexpr uint32_t kABytes = kBM * kBK * 2;              // 16 KiB
   static constexpr uint32_t kBBytes = BN * kBK * 2;
   static constexpr uint32_t kStageBytes = kABytes + kBBytes;      // multiple of 1024
-  static constexpr uint32_t kEpiBytes = kEpiWarps * 32 * kStageRow * 4;
+  static constexpr uint32_t kEpiBytes = kEpiWarps * 32 * 32 * 4;   // one 32 x 32 FP32 block per warp
   static constexpr int kSmem = S * kStageBytes + kEpiBytes + 1024;   // + slack to align the ring to 1024 bytes
   static constexpr uint32_t kTmemCols = 2 * BN;                   // two accumulators
   static_assert(BN == 64 || BN == 128 || BN == 256, "MMA N and TMEM allocation");
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     gemm_bf16_tn_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                             int N, int K, const float* __restrict__ bias, int relu, float* __restrict__ C32,
                             __nv_bfloat16* __restrict__ C16, int ldc, int* __restrict__ status, int vec16,
-                            int mtiles, int ntiles, int tiles) {
+                            int vec32, int mtiles, int ntiles, int tiles) {
   using T = TmaTile<BN, S>;
   extern __shared__ __align__(1024) unsigned char dyn_smem[];
   __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], drain;
@@ -491,11 +491,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. rows
-    // 32 (w % 4) .. of the tile; each 32 x 32 block goes through this warp's
-    // transpose buffer so that a store instruction writes one row segment
-    // (consecutive lanes, consecutive columns)
-    const int q = warp & 3;
-    float* st = epi + (warp - 2) * 32 * kStageRow;
+    // 32 (w % 4) .. of the tile; the two warps of a quadrant take alternate
+    // 32-column blocks.  A block goes through this warp's transpose buffer
+    // (rows of 128 bytes, 16-byte slot j of row r stored at slot j ^ (r % 8),
+    // so that both the row-per-lane writes and the row-segment reads are
+    // free of bank conflicts); each store instruction then writes whole row
+    // segments of C.
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    float* st = epi + (warp - 2) * 32 * 32;
     int tc = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
       const int b = tc & 1;
@@ -509,7 +512,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       const TileIdx ti = tile_of(t, mtiles, ntiles, BN);
       float* c32 = C32 ? C32 + (size_t)ti.z * M * ldc : nullptr;
       const int rbase = ti.m0 + q * 32;
-      for (int ch = 0; ch < BN / 32; ++ch) {
+      for (int ch = half; ch < BN / 32; ch += 2) {
         const int c0 = ti.n0 + ch * 32;
         if (c0 >= N) break;   // uniform over the warp
         uint32_t r[32];
@@ -526,45 +529,72 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         __syncwarp();   // the previous block's reads of the buffer are done
+        {
+          float4* row = reinterpret_cast<float4*>(st + lane * 32);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) st[lane * kStageRow + j] = __uint_as_float(r[j]);
+          for (int j = 0; j < 8; ++j)
+            row[j ^ (lane & 7)] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                              __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+        }
         __syncwarp();
-        // lane l now owns column c0 + l of the 32 rows
-        const int col = c0 + lane;
-        const float bj = (bias && col < N) ? bias[col] : 0.f;
+        const bool full_rows = rbase + 32 <= M, full_cols = c0 + 32 <= N;
         if (c32) {
-          if (col < N) {
-#pragma unroll 4
-            for (int i = 0; i < 32; ++i) {
-              const int row = rbase + i;
-              if (row >= M) break;
-              float v = st[i * kStageRow + lane] + bj;
-              if (relu) v = fmaxf(v, 0.f);
-              c32[(size_t)row * ldc + col] = v;
+          // lane l: columns c0 + 4 (l % 8) .. + 3 of rows 4 i + l / 8
+          const int j = lane & 7, cc = c0 + 4 * j;
+          float bv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) bv[u] = (bias && cc + u < N) ? bias[cc + u] : 0.f;
+          const bool fast = full_rows && full_cols && vec32;
+#pragma unroll 2
+          for (int i = 0; i < 8; ++i) {
+            const int rr = 4 * i + (lane >> 3), row = rbase + rr;
+            float4 v = reinterpret_cast<const float4*>(st + rr * 32)[j ^ (rr & 7)];
+            float* e = &v.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              e[u] += bv[u];
+              if (relu) e[u] = fmaxf(e[u], 0.f);
+            }
+            float* dst = c32 + (size_t)row * ldc + cc;
+            if (fast) {
+              *reinterpret_cast<float4*>(dst) = v;
+            } else if (row < M) {
+              for (int u = 0; u < 4; ++u)
+                if (cc + u < N) dst[u] = e[u];
             }
           }
         }
         if (C16) {
-          // two rows per instruction: lanes 0-15 row i, lanes 16-31 row i + 1,
-          // two consecutive columns per lane
-          const int hl = lane & 15, cc = c0 + 2 * hl;
-          const float b0 = (bias && cc < N) ? bias[cc] : 0.f, b1 = (bias && cc + 1 < N) ? bias[cc + 1] : 0.f;
-#pragma unroll 4
-          for (int i = 0; i < 32; i += 2) {
-            const int rr = i + (lane >> 4), row = rbase + rr;
-            if (row < M && cc < N) {
-              float v0 = st[rr * kStageRow + 2 * hl] + b0, v1 = st[rr * kStageRow + 2 * hl + 1] + b1;
-              if (relu) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
+          // lane l: columns c0 + 8 (l % 4) .. + 7 of rows 8 i + l / 4
+          const int p = lane & 3, cc = c0 + 8 * p;
+          float bv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) bv[u] = (bias && cc + u < N) ? bias[cc + u] : 0.f;
+          const bool fast = full_rows && full_cols && vec16;
+#pragma unroll 2
+          for (int i = 0; i < 4; ++i) {
+            const int rr = 8 * i + (lane >> 2), row = rbase + rr;
+            const float4* srow = reinterpret_cast<const float4*>(st + rr * 32);
+            const float4 v0 = srow[(2 * p) ^ (rr & 7)], v1 = srow[(2 * p + 1) ^ (rr & 7)];
+            float e[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              e[u] += bv[u];
+              if (relu) e[u] = fmaxf(e[u], 0.f);
+            }
+            __nv_bfloat16* dst = C16 + (size_t)row * ldc + cc;
+            if (fast) {
+              uint4 pk;
+              uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(e[2 * u], e[2 * u + 1]);
+                w[u] = *reinterpret_cast<const uint32_t*>(&b2);
               }
-              __nv_bfloat16* dst = C16 + (size_t)row * ldc + cc;
-              if (vec16 && cc + 1 < N) {
-                *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(v0, v1);
-              } else {
-                dst[0] = __float2bfloat16_rn(v0);
-                if (cc + 1 < N) dst[1] = __float2bfloat16_rn(v1);
-              }
+              *reinterpret_cast<uint4*>(dst) = pk;
+            } else if (row < M) {
+              for (int u = 0; u < 8; ++u)
+                if (cc + u < N) dst[u] = __float2bfloat16_rn(e[u]);
             }
           }
         }
@@ -650,7 +680,8 @@ int pick_bn(int M, int N) {
 
 template <int BN, int S>
 cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int N, int K, const float* bias, int relu,
-                       float* C32, __nv_bfloat16* C16, int ldc, int* status, cudaStream_t s, int ksplit, int vec16) {
+                       float* C32, __nv_bfloat16* C16, int ldc, int* status, cudaStream_t s, int ksplit, int vec16,
+                       int vec32) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
@@ -664,7 +695,7 @@ cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int 
   const int sms = sm_count();
   const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));   // persistent: one CTA per SM
   gemm_bf16_tn_tma_kernel<BN, S><<<grid, kTmaThreads, TmaTile<BN, S>::kSmem, s>>>(
-      mA, mB, M, N, K, bias, relu, C32, C16, ldc, status, vec16, mtiles, ntiles, (int)tiles);
+      mA, mB, M, N, K, bias, relu, C32, C16, ldc, status, vec16, vec32, mtiles, ntiles, (int)tiles);
   return cudaGetLastError();
 }
 
@@ -686,11 +717,11 @@ cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb
       cudaError_t e;
       // persistent, one CTA per SM: as many stages as fit beside the epilogue buffers
       if (bn == 256)
-        e = nn::launch_tma<256, 4>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16);
+        e = nn::launch_tma<256, 3>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
       else if (bn == 128)
-        e = nn::launch_tma<128, 6>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16);
+        e = nn::launch_tma<128, 5>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
       else
-        e = nn::launch_tma<64, 8>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16);
+        e = nn::launch_tma<64, 7>(mA, mB, M, N, K, bias, relu, C32, c16, ldc, status, s, ksplit, vec16, vec32);
       count_launches(1);
       return e;
     }
