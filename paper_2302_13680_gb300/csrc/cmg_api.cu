@@ -311,8 +311,22 @@ cudaError_t tail_cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3
   return launch_tail_cycle<T>(P, h->stream);
 }
 
+// True when a cycle on grid l from a zero iterate never reads that iterate,
+// so it need not be cleared first: the coarsest direct solve forms x from f
+// alone, and red-black pre-smoothing starts with the zero-guess colour-0
+// half-sweep (launch_rbgs_zero).  Not with a frozen control (the sweeps and
+// the direct solve read u) nor for grids handed to the cluster tail.
+bool zero_guess_ok(const cmg_handle* h, const cmg_cycle& o, int l) {
+  if (o.freeze_u) return false;
+  if (o.tail_n > 0 && h->lv[l].n <= o.tail_n) return false;
+  if (l == h->L - 1) return true;
+  return o.smoother == CMG_SMOOTH_RBGS && o.n1 >= 1;
+}
+
+// zg: x is logically zero on entry but its memory has not been cleared
+// (callers pass it only where zero_guess_ok holds).
 template <typename T>
-cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> f) {
+cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> f, bool zg = false) {
   Lev& v = h->lv[l];
   const int N = h->prob.N;
   if (o.tail_n > 0 && v.n <= o.tail_n) {
@@ -323,7 +337,22 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
     ProfScope ps(h, CMG_KERNEL_COARSE, l);
     return launch_coarse_solve<T>(sizeof(T) == 4 ? h->c32() : h->coarse, v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
   }
-  cudaError_t e = smooth<T>(h, o, l, o.n1, x, f);
+  cudaError_t e = cudaSuccess;
+  if (zg) {
+    // first pre-smoothing sweep from the zero iterate
+    const LevelView<T> L = view<T>(h, l, o.freeze_u);
+    {
+      ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+      e = launch_rbgs_zero<T>(L, x, f, h->stream);
+    }
+    if (e == cudaSuccess) {
+      ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+      e = launch_rbgs_half<T>(L, x, f, 1, h->stream);
+    }
+    if (e == cudaSuccess) e = smooth<T>(h, o, l, o.n1 - 1, x, f);
+  } else {
+    e = smooth<T>(h, o, l, o.n1, x, f);
+  }
   if (e != cudaSuccess) return e;
   Vec3<T> r = Work<T>::r(v);
   // after red-black pre-smoothing (last half-sweep: colour 1) with the control
@@ -337,11 +366,14 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   if (e != cudaSuccess) return e;
   Lev& cl = h->lv[l + 1];
   Vec3<T> fc = Work<T>::f(cl), xc = Work<T>::x(cl);
+  // the coarse iterate starts at zero: cleared by the restriction unless the
+  // coarse cycle's first visit does not read it
+  const bool czg = zero_guess_ok(h, o, l + 1);
   {
     ProfScope ps(h, CMG_KERNEL_RESTRICT, l);
-    e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream, xc, c0);   // also sets the coarse iterate to zero
+    e = launch_restrict<T>(v.n, N, cview(r), fc, h->stream, czg ? Vec3<T>{nullptr, nullptr, nullptr} : xc, c0);
   }
-  for (int g = 0; g < o.gamma && e == cudaSuccess; ++g) e = cycle<T>(h, o, l + 1, xc, cview(fc));
+  for (int g = 0; g < o.gamma && e == cudaSuccess; ++g) e = cycle<T>(h, o, l + 1, xc, cview(fc), czg && g == 0);
   if (e != cudaSuccess) return e;
   if (sizeof(T) == 4 && o.smoother == CMG_SMOOTH_RBGS && o.n2 >= 1 && !o.freeze_u) {
     // FP32: prolongation fused into the first post-smoothing half-sweep
@@ -796,8 +828,9 @@ cmg_status precondition(cmg_handle* h, const cmg_cycle& o, Vec3c<double> v, Vec3
   if (o.precision == CMG_FP64) {
     double* fy = l0.f64[0];
     CK((launch_scale_cast<double, double>(1.0 / wy, v.y, fy, ny, h->stream)));
-    CK(zero_vec<double>(h, 0, z));
-    CK(cycle<double>(h, o, 0, z, Vec3c<double>{fy, v.u, v.p}));
+    const bool zg = zero_guess_ok(h, o, 0);
+    if (!zg) CK(zero_vec<double>(h, 0, z));
+    CK(cycle<double>(h, o, 0, z, Vec3c<double>{fy, v.u, v.p}, zg));
     return CMG_OK;
   }
   // FP32 cycle on the right side (Krylov vectors have unit norm, no scaling
@@ -807,8 +840,9 @@ cmg_status precondition(cmg_handle* h, const cmg_cycle& o, Vec3c<double> v, Vec3
   CK((launch_scale_cast<double, float>(vscale / wy, v.y, f32.y, ny, h->stream)));
   CK((launch_scale_cast<double, float>(vscale, v.u, f32.u, nu, h->stream)));
   CK((launch_scale_cast<double, float>(vscale, v.p, f32.p, ny, h->stream)));
-  CK(zero_vec<float>(h, 0, x32));
-  CK(cycle<float>(h, o, 0, x32, cview(f32)));
+  const bool zg = zero_guess_ok(h, o, 0);
+  if (!zg) CK(zero_vec<float>(h, 0, x32));
+  CK(cycle<float>(h, o, 0, x32, cview(f32), zg));
   CK((launch_scale_cast<float, double>(1.0 / vscale, x32.y, z.y, ny, h->stream)));
   CK((launch_scale_cast<float, double>(1.0 / vscale, x32.u, z.u, nu, h->stream)));
   CK((launch_scale_cast<float, double>(1.0 / vscale, x32.p, z.p, ny, h->stream)));
@@ -938,8 +972,10 @@ cmg_status ir_iteration(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3
   Vec3<float> f32 = Work<float>::f(l0), x32 = Work<float>::x(l0);
   Vec3<float> d32{l0.d32[0], l0.d32[1], l0.d32[2]};
   double* st = h->ir_state;
-  CK(launch_zero3(x32, l0.nodes * h->prob.N, l0.nodes, h->stream));
-  CK(cycle<float>(h, o, 0, x32, cview(f32)));
+  // the correction equation starts from zero
+  const bool zg = zero_guess_ok(h, o, 0);
+  if (!zg) CK(launch_zero3(x32, l0.nodes * h->prob.N, l0.nodes, h->stream));
+  CK(cycle<float>(h, o, 0, x32, cview(f32), zg));
   int cnt = launch_recur(view<float>(h, 0), cview(x32), f32, d32, paper_wy(h), h->part, h->part_cap, h->stream);
   if (cnt < 0) return fail(h, CMG_ERR_CUDA, "recursive residual launch failed");
   CK(launch_k(ir_recur_control_kernel, dim3(1), dim3(256), 0, h->stream, (const double*)h->part, cnt, st, cond,

@@ -114,6 +114,10 @@ cudaError_t launch_rbgs_half_staged(const LevelView<float>& L, Vec3<float> x, Ve
                                     const SampleMap& m, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t s);
+// Colour-0 half-sweep of a cycle that starts from a zero iterate: x is not
+// read (its neighbour terms are zero) and need not have been cleared.
+template <typename T>
+cudaError_t launch_rbgs_zero(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_jacobi_update(const LevelView<T>& L, Vec3<T> x, Vec3c<T> r, double theta, cudaStream_t s);
 // r = f - S x at the colour-0 nodes only: after a red-black sweep whose

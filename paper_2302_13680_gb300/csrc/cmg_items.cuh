@@ -178,7 +178,13 @@ __device__ __forceinline__ vec<T, V> prolonged(const T* xv, const T* ev, int nf,
 // ---------------------------------------------------------------------------
 // PRO: the neighbours are read as x + P e (coarse correction e on the grid
 // of nc nodes per side), i.e. the prolongation is fused into this half-sweep.
-template <typename T, int V, int SPL, bool CG, bool PRO = false>
+// ZG: x is zero on entry (the first half-sweep of a cycle from a zero
+// guess): the neighbour terms vanish and are neither loaded nor added, so
+// x need not be cleared beforehand (a colour-0 sweep writes every colour-0
+// value and the colour-1 sweep after it every colour-1 value, reading only
+// colour-0 neighbours).  Same values as the plain sweep on a cleared x:
+// adding k * 0 leaves a sum unchanged, up to the sign of a zero.
+template <typename T, int V, int SPL, bool CG, bool PRO = false, bool ZG = false>
 __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& x, const Vec3c<T>& f, int colour,
                                           long g, int lane, int lpn, const Vec3c<T> e = Vec3c<T>{nullptr, nullptr,
                                                                                                    nullptr},
@@ -217,7 +223,7 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
                           nb(hS, x.p, e.p, iy - 1, ix), kN, nb(hN, x.p, e.p, iy + 1, ix));
           fma_faces<T, V>(by[s], kW, nb(hW, x.y, e.y, iy, ix - 1), kE, nb(hE, x.y, e.y, iy, ix + 1), kS,
                           nb(hS, x.y, e.y, iy - 1, ix), kN, nb(hN, x.y, e.y, iy + 1, ix));
-        } else {
+        } else if constexpr (!ZG) {
           fma_faces<T, V>(bp[s], kW, ldx_if<T, V, CG>(hW, x.p + o - ld + j), kE,
                           ldx_if<T, V, CG>(hE, x.p + o + ld + j), kS,
                           ldx_if<T, V, CG>(hS, x.p + o - (size_t)n * ld + j), kN,

@@ -50,6 +50,14 @@ __global__ void __launch_bounds__(kBlock) rbgs_half_kernel(LevelView<T> L, Vec3<
   rbgs_item<T, V, SPL, false>(L, x, f, colour, g, threadIdx.x & (lpn - 1), lpn);
 }
 
+// Colour-0 half-sweep from a zero iterate (see rbgs_item, ZG).
+template <typename T, int V, int SPL>
+__global__ void __launch_bounds__(kBlock) rbgs_zero_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, int lpn) {
+  pdl_enter();
+  const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
+  rbgs_item<T, V, SPL, false, false, true>(L, x, f, 0, g, threadIdx.x & (lpn - 1), lpn);
+}
+
 // Colour-0 half-sweep that reads its neighbours as x + P e (prolongation of
 // the coarse correction e fused in; see rbgs_item).
 template <typename T, int V, int SPL>
@@ -283,6 +291,17 @@ cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int c
 }
 
 template <typename T>
+cudaError_t launch_rbgs_zero(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, cudaStream_t st) {
+  const long groups = colour_count(L.n, 0);
+  const SampleMap m = choose_map(L.N, sizeof(T), groups, L.spl_target);
+  const unsigned grid = grid_for(groups, m.lpn);
+  cudaError_t e_ = cudaSuccess;
+  CMG_DISPATCH(T, m, (e_ = launch_k(rbgs_zero_kernel<T, V, SPL>, grid, kBlock, 0, st, L, x, f, m.lpn)));
+  count_launches(1);
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_rbgs_prolong(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, Vec3c<T> e, int nc, cudaStream_t st) {
   const long groups = colour_count(L.n, 0);
   const SampleMap m = choose_map(L.N, sizeof(T), groups, L.spl_target);
@@ -394,6 +413,7 @@ cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<doub
 #define CMG_INST(T)                                                                                   \
   template cudaError_t launch_residual<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t, double); \
   template cudaError_t launch_rbgs_half<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, int, cudaStream_t);    \
+  template cudaError_t launch_rbgs_zero<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, cudaStream_t);         \
   template cudaError_t launch_jacobi_update<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, double, cudaStream_t); \
   template cudaError_t launch_restrict<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t, Vec3<T>, int);         \
   template cudaError_t launch_residual_c0<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t);       \

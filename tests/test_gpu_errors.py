@@ -269,3 +269,33 @@ def test_new_samples_rebuild_fp64_and_fp32_operators(H):
     finally:
         h.set_samples(torch.tensor(pr.xi, device="cuda"))
         fresh.close()
+
+
+@pytest.mark.parametrize("precision,method,gamma", [("FP32", "METHOD_CYCLE", 1), ("FP32", "METHOD_CYCLE", 2),
+                                                    ("FP32", "METHOD_FGMRES", 1), ("FP64", "METHOD_FGMRES", 1),
+                                                    ("FP64", "METHOD_CYCLE", 2)])
+def test_solve_does_not_read_stale_work_buffers(H, precision, method, gamma):
+    """Corrections and coarse iterates start from zero without their memory
+    being cleared (the first colour-0 half-sweep does not read them): a solve
+    on a handle whose work buffers hold another solve's values must return
+    bit for bit what a fresh handle returns."""
+    h, P, pr = H
+    f = rhs(h, pr)
+    g = tuple(t.clone() for t in f)
+    g[0].mul_(-3.0).add_(1e-3)
+    opts = P.CycleOptions(precision=getattr(P, precision), gamma=gamma)
+    m = getattr(P, method)
+    h1 = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp)
+    h2 = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp)
+    try:
+        x0 = h1.zeros(0)
+        h1.solve(opts, g, x0, method=m, tol=1e-10)   # leaves its corrections in the work buffers
+        x1, x2 = h1.zeros(0), h2.zeros(0)
+        s1, _ = h1.solve(opts, f, x1, method=m, tol=1e-10)
+        s2, _ = h2.solve(opts, f, x2, method=m, tol=1e-10)
+        assert s1.iters == s2.iters
+        for a, b in zip(x1, x2):
+            assert torch.equal(a, b)
+    finally:
+        h1.close()
+        h2.close()
