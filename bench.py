@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--form", default="auto", choices=["auto", "fp64-fgmres", "fp64-cycle", "fp32-ir",
                                                         "fp32-ir-launches", "fp32-fgmres"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="JSON file of autotuned targets: used if it holds this hierarchy, else written "
+                         "(repeat runs, e.g. a profiler pass, then launch the same kernels)")
     return ap.parse_args()
 
 
@@ -306,7 +309,8 @@ def run_cmg(args, world, rank, local):
     restart = 30 if n * n * N < 50_000_000 else 8     # FP64 Krylov basis: 2 x restart full vectors
     from paper_2302_13680_gb300 import tuning as T
 
-    tuned = {"f32": T.apply_or_tune(H, P.FP32), "f64": T.apply_or_tune(H, P.FP64)}
+    tuned = {"f32": T.apply_or_tune(H, P.FP32, args.tuning_cache),
+             "f64": T.apply_or_tune(H, P.FP64, args.tuning_cache)}
 
     def step(form):
         spec = FORMS[form]
