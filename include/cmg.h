@@ -218,8 +218,14 @@ cmg_status cmg_cycle_apply_f32(cmg_handle* h, const cmg_cycle* opts,
  * (In the symmetric scaling the FP64 rounding floor of ||f - S x|| / ||f||
  * grows like N (n+1)^2 eps and lies above 1e-10 for n = 255, N = 64.)
  * method CMG_METHOD_CYCLE: repeated cycles (stationary iteration, Algorithm 1
- *   repeated); with opts->precision == CMG_FP32 each step is FP64 iterative
- *   refinement: r = f - S x in FP64, e = cycle_FP32(0; r), x += e.
+ *   repeated); with opts->precision == CMG_FP32 it is iterative refinement
+ *   with residual replacement: each step runs e = cycle_FP32(0; r), updates
+ *   the FP32 residual recursively (r -= S e) and sums the corrections in
+ *   FP32; an anchor adds the sum to x and recomputes r = f - S x in FP64
+ *   once the recursive norm has dropped by 1e-3 since the last anchor, after
+ *   8 steps, or at the tolerance, and the stopping test is made on that
+ *   FP64 residual.  The environment variables CMG_ANCHOR_DROP (in (0, 1))
+ *   and CMG_ANCHOR_MAX (1..1000), read at cmg_create, change the two limits.
  * method CMG_METHOD_FGMRES: right-preconditioned flexible GMRES(restart)
  *   on W S x = W f with one cycle (FP64 or FP32) applied to W^{-1} v as
  *   preconditioner; Arnoldi by classical Gram-Schmidt applied twice, all

@@ -82,6 +82,8 @@ struct cmg_handle {
   const void* ir_key[6] = {};
   cmg_cycle ir_opts{};
   double* ir_state = nullptr;            // device refinement state, see IrState
+  double anchor_drop = 1e-3;             // anchor policy of FP32 refinement (see IrState)
+  int anchor_max = 8;
   long long ir_body_kernels = 0;         // kernels in one iteration of the captured loop body
   bool graphs = true;                    // false: CMG_GRAPHS=0 in the environment at creation
   // FGMRES workspace
@@ -459,6 +461,14 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   h->stream = static_cast<cudaStream_t>(stream);
   const char* graphs_env = std::getenv("CMG_GRAPHS");
   h->graphs = !(graphs_env && std::strcmp(graphs_env, "0") == 0);
+  if (const char* v = std::getenv("CMG_ANCHOR_DROP")) {
+    const double d = std::atof(v);
+    if (d > 0.0 && d < 1.0) h->anchor_drop = d;
+  }
+  if (const char* v = std::getenv("CMG_ANCHOR_MAX")) {
+    const int m = std::atoi(v);
+    if (m >= 1 && m <= 1000) h->anchor_max = m;
+  }
   int n = P.n, L = 0;
   while (true) {
     Lev& v = h->lv[L];
@@ -857,11 +867,15 @@ cmg_status precondition(cmg_handle* h, const cmg_cycle& o, Vec3c<double> v, Vec3
 // right side r^ = sc r is updated recursively in FP32 (r^ <- r^ - S e) and
 // the corrections are summed in FP32 (d += e); an anchor folds x += d / sc,
 // recomputes the true residual in FP64 and rescales r^ to norm 1.  The FP32
-// recursion drifts from the true residual by about eps32 * (cancellation of
-// S) per step relative to the residual it started from, so an anchor is
-// taken once the recursive norm has dropped kAnchorDrop below the last true
-// one, after kAnchorMax cycles, at maxit, or when the recursive norm reaches
-// the tolerance (the stopping test is always made on a true residual).
+// recursion drifts from the true residual by about eps32 times the size of
+// the terms of S e per step, relative to the residual it started from; it
+// forms A e from neighbour differences (launch_recur), which keeps those
+// terms small for the smooth corrections a cycle returns.  An anchor is taken
+// once the recursive norm has dropped below drop = 1e-3 times the last true
+// one, after 8 cycles, at maxit, or when the recursive norm reaches the
+// tolerance (the stopping test is always made on a true residual).  The
+// environment variables CMG_ANCHOR_DROP and CMG_ANCHOR_MAX, read when a
+// handle is created, override the two limits.
 // State (device doubles):
 enum IrState {
   kSc = 0,       // scale for the next FP64 pass (1 / latest norm)
@@ -874,10 +888,10 @@ enum IrState {
   kSince = 7,       // cycles since the last anchor
   kAnchor = 8,      // 1: the anchor kernels of this iteration run
   kGo = 9,          // 1: another iteration follows
-  kIrStateSize = 10
+  kDrop = 10,       // anchor once the recursive norm is below kDrop times the last true one
+  kAmax = 11,       // ... or after kAmax cycles since the last anchor
+  kIrStateSize = 12
 };
-constexpr double kAnchorDrop = 1e-2;
-constexpr int kAnchorMax = 5;
 
 __device__ double block_total(const double* __restrict__ partial, int count) {
   __shared__ double sh[32];
@@ -905,8 +919,8 @@ __global__ void ir_recur_control_kernel(const double* __restrict__ partial, int 
   s[kRho] = rho;
   s[kIt] = it;
   s[kSince] = since;
-  const bool anchor = !isfinite(rho) || rho <= s[kTolAbs] || rho <= kAnchorDrop * s[kRhoAnchor] ||
-                      it >= s[kMaxit] || since >= (double)kAnchorMax;
+  const bool anchor = !isfinite(rho) || rho <= s[kTolAbs] || rho <= s[kDrop] * s[kRhoAnchor] ||
+                      it >= s[kMaxit] || since >= s[kAmax];
   s[kSc] = (isfinite(rho) && rho > 0.0) ? 1.0 / rho : 1.0 / s[kRhoAnchor];
   s[kAnchor] = anchor ? 1.0 : 0.0;
   s[kGo] = anchor ? 0.0 : 1.0;
@@ -935,8 +949,10 @@ __global__ void ir_anchor_control_kernel(const double* __restrict__ partial, int
 
 // Host image of the state before the first iteration: right side r^ = sc r
 // with true norm rho.
-void ir_state_init(double* hs, double rho, double sc, int maxit, double tol_abs) {
+void ir_state_init(const cmg_handle* h, double* hs, double rho, double sc, int maxit, double tol_abs) {
   for (int i = 0; i < kIrStateSize; ++i) hs[i] = 0.0;
+  hs[kDrop] = h->anchor_drop;
+  hs[kAmax] = (double)h->anchor_max;
   hs[kSc] = rho > 0.0 ? 1.0 / rho : 0.0;
   hs[kInvSc] = 1.0 / sc;
   hs[kRho] = rho;
@@ -1127,7 +1143,7 @@ cmg_status solve_cycle(cmg_handle* h, const cmg_cycle& o, double tol, int maxit,
     if (std::isfinite(rho) && rho > tol * fnorm && maxit > 0) {
       Vec3<float> d32{l0.d32[0], l0.d32[1], l0.d32[2]};
       CK(zero_vec<float>(h, 0, d32));
-      ir_state_init(h->hsc, rho, sc, maxit, tol * fnorm);
+      ir_state_init(h, h->hsc, rho, sc, maxit, tol * fnorm);
       CK(cudaMemcpyAsync(h->ir_state, h->hsc, kIrStateSize * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     }
     if (use_graph) {
@@ -1451,7 +1467,7 @@ extern "C" cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, doubl
     double* hs = h->hsc;
     const double rho = fnorm[i] > 0.0 ? std::sqrt(hs[0]) * fnorm[i] : 0.0;
     stats[i].relres0 = fnorm[i] > 0.0 ? rho / fnorm[i] : 0.0;
-    ir_state_init(hs, rho, fnorm[i] > 0.0 ? 1.0 / fnorm[i] : 1.0, maxit, tol * fnorm[i]);
+    ir_state_init(h, hs, rho, fnorm[i] > 0.0 ? 1.0 / fnorm[i] : 1.0, maxit, tol * fnorm[i]);
     BCK(cudaMemcpyAsync(h->ir_state, hs, kIrStateSize * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     Lev& l0 = h->lv[0];
     const size_t ny = l0.nodes * h->prob.N;

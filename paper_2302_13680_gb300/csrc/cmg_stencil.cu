@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kBlock) residual_cast_kernel(LevelView<double>
 }
 
 // FP32 refinement between FP64 anchors (residual replacement): the scaled
-// residual r (the cycle's right side) is updated in place, r <- r - S e, the
+// residual r (the cycle's right side) is updated in place, r <- r - S e (A e
+// from neighbour differences, see residual_item), the
 // running correction d += e, and per-CTA partial sums of ||W r||^2 are
 // written (squares in FP32, CTA sum in FP64).  Each lane reads its own f
 // entries before writing r at the same place, so the update in place is safe.
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kBlock) recur_kernel(LevelView<float> L, Vec3c
   __shared__ double sh[kBlock / 32];
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   const int lane = threadIdx.x & (lpn - 1);
-  residual_item<float, V, SPL, false>(L, e, cview(r), r, node, lane, lpn, 1.0f);
+  residual_item<float, V, SPL, false, true>(L, e, cview(r), r, node, lane, lpn, 1.0f);
   const int N = L.N;
   const size_t ld = (size_t)L.ld;
   float sq = 0.f;
