@@ -299,3 +299,33 @@ def test_solve_does_not_read_stale_work_buffers(H, precision, method, gamma):
     finally:
         h1.close()
         h2.close()
+
+
+@pytest.mark.parametrize("drop,amax", [("0.5", "1"), ("1e-2", "5"), ("1e-6", "1000")])
+def test_refinement_anchor_policy_overrides(H, drop, amax):
+    """CMG_ANCHOR_DROP / CMG_ANCHOR_MAX change only when the FP64 anchors are
+    taken: from an anchor every cycle to anchors only at the tolerance, the
+    solve stops on a true residual below the tolerance."""
+    import os
+
+    h, P, pr = H
+    f = rhs(h, pr)
+    os.environ["CMG_ANCHOR_DROP"], os.environ["CMG_ANCHOR_MAX"] = drop, amax
+    try:
+        h2 = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp)
+    finally:
+        os.environ.pop("CMG_ANCHOR_DROP", None)
+        os.environ.pop("CMG_ANCHOR_MAX", None)
+    try:
+        x = h2.zeros(0)
+        st, status = h2.solve(P.CycleOptions(precision=P.FP32), f, x, tol=1e-10, maxit=60)
+        assert status == 0
+        r = h2.zeros(0)
+        h2.residual(0, x, f, r)
+        w = float(pr.N)
+        num = torch.sqrt((w * r[0]).square().sum() + r[1].square().sum() + r[2].square().sum())
+        den = torch.sqrt((w * f[0]).square().sum() + f[1].square().sum() + f[2].square().sum())
+        assert float(num / den) <= 1e-10
+        assert abs(float(num / den) - st.relres) <= 1e-3 * st.relres
+    finally:
+        h2.close()
