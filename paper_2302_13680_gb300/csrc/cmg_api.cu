@@ -520,6 +520,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   h->coarse.N = P.N;
   h->coarse.blocks = (P.N + 31) / 32;
   AL(h->coarse.Ainv, N * h->coarse.m * h->coarse.m);
+  AL(h->coarse.Ainv32, N * h->coarse.m * h->coarse.m);
   AL(h->coarse.Minv, (size_t)h->coarse.m * h->coarse.m);
   AL(h->coarse.wz, std::max(2 * N * h->coarse.m, (size_t)h->coarse.m * h->coarse.m));
   AL(h->coarse.partial, (size_t)h->coarse.blocks * h->coarse.m);
@@ -529,6 +530,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     h->coarse32.N = h->coarse.N;
     h->coarse32.blocks = h->coarse.blocks;
     AL(h->coarse32.Ainv, N * h->coarse.m * h->coarse.m);
+    AL(h->coarse32.Ainv32, N * h->coarse.m * h->coarse.m);
     AL(h->coarse32.Minv, (size_t)h->coarse.m * h->coarse.m);
     AL(h->coarse32.wz, std::max(2 * N * h->coarse.m, (size_t)h->coarse.m * h->coarse.m));
     AL(h->coarse32.partial, (size_t)h->coarse.blocks * h->coarse.m);

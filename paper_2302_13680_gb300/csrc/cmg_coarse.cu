@@ -9,6 +9,9 @@
 // Schur matrix once per hierarchy; each solve is two launches: per-sample
 // products with a fixed-order reduction of the control right side, then the
 // control solve and per-sample back substitution.
+#include <algorithm>
+#include <type_traits>
+
 #include "cmg_common.cuh"
 
 namespace cmg {
@@ -219,38 +222,45 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_b(int m, int N, i
 // (sample j, row r) for the products.  The two-kernel form above gives each
 // thread a whole sample (81 strided loads of A_j^{-1} per product) and is
 // latency-bound.  Same block elimination; the control right side is summed
-// over the samples in sample order.
+// over the samples in sample order, in FP64, and the m x m control solve is
+// FP64.  The per-sample products run in the cycle's precision C: FP64 for
+// FP64 cycles, FP32 for FP32 cycles (GB300's FP64 pipe made them ~6 us of
+// the FP32 cycle's single-CTA critical path).
 constexpr int kCoarseCtaThreads = 512;
 
-inline size_t coarse_cta_smem(int N, int m) { return ((size_t)N * m * m + 4 * (size_t)N * m + 2 * 64) * 8; }
+template <typename C>
+size_t coarse_cta_smem(int N, int m) {
+  return 2 * 64 * sizeof(double) + ((size_t)N * m * m + 4 * (size_t)N * m) * sizeof(C);
+}
 
-template <typename T>
-__global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int N, const double* __restrict__ Ainv,
+template <typename T, typename C>
+__global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int N, const C* __restrict__ Ainv,
                                                                      const double* __restrict__ Minv, double c,
                                                                      double d, double e, Vec3c<T> f, Vec3<T> x,
                                                                      int freeze_u) {
   pdl_enter();
   extern __shared__ __align__(16) double sm[];
   const int mm = m * m, nm = N * m;
-  double* A = sm;                    // [N][m][m]
-  double* by = A + (size_t)N * mm;   // [N][m] f_y, later y
-  double* bp = by + nm;              // [N][m] f_p, later w - c A^{-1} z
-  double* w = bp + nm;               // [N][m] A^{-1} f_y
-  double* z = w + nm;                // [N][m] A^{-1} f_p
-  double* rhs = z + nm;              // [m] control right side
+  double* rhs = sm;                  // [m] control right side
   double* us = rhs + 64;             // [m] control
+  C* A = reinterpret_cast<C*>(us + 64);   // [N][m][m]
+  C* by = A + (size_t)N * mm;        // [N][m] f_y, later y
+  C* bp = by + nm;                   // [N][m] f_p, later w - c A^{-1} z
+  C* w = bp + nm;                    // [N][m] A^{-1} f_y
+  C* z = w + nm;                     // [N][m] A^{-1} f_p
+  const C cc = (C)c, ec = (C)e;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < N * mm; i += nt) A[i] = Ainv[i];
   for (int i = tid; i < nm; i += nt) {   // f.y, f.p are [node r][sample j]
     const int r = i / N, j = i - r * N;
-    by[j * m + r] = (double)f.y[i];
-    bp[j * m + r] = (double)f.p[i];
+    by[j * m + r] = (C)f.y[i];
+    bp[j * m + r] = (C)f.p[i];
   }
   __syncthreads();
   for (int i = tid; i < nm; i += nt) {
     const int j = i / m, r = i - j * m;
-    const double* Ar = A + (size_t)j * mm + r * m;
-    double sw = 0.0, sz = 0.0;
+    const C* Ar = A + (size_t)j * mm + r * m;
+    C sw = 0, sz = 0;
     for (int k = 0; k < m; ++k) {
       sw += Ar[k] * by[j * m + k];
       sz += Ar[k] * bp[j * m + k];
@@ -261,15 +271,15 @@ __global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int
   __syncthreads();
   for (int i = tid; i < nm; i += nt) {   // w - c A^{-1} z, into bp (f_p no longer needed)
     const int j = i / m, r = i - j * m;
-    const double* Ar = A + (size_t)j * mm + r * m;
-    double v = 0.0;
+    const C* Ar = A + (size_t)j * mm + r * m;
+    C v = 0;
     for (int k = 0; k < m; ++k) v += Ar[k] * z[j * m + k];
-    bp[i] = w[i] - c * v;
+    bp[i] = w[i] - cc * v;
   }
   __syncthreads();
   for (int r = tid; r < m; r += nt) {
     double q = 0.0;
-    for (int j = 0; j < N; ++j) q += bp[j * m + r];
+    for (int j = 0; j < N; ++j) q += (double)bp[j * m + r];
     rhs[r] = (double)f.u[r] - d * q;
   }
   __syncthreads();
@@ -283,37 +293,47 @@ __global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int
   __syncthreads();
   for (int i = tid; i < nm; i += nt) {   // y = z - e A^{-1} u, into by
     const int j = i / m, r = i - j * m;
-    const double* Ar = A + (size_t)j * mm + r * m;
-    double t = 0.0;
-    for (int k = 0; k < m; ++k) t += Ar[k] * us[k];
-    const double yv = z[i] - e * t;
+    const C* Ar = A + (size_t)j * mm + r * m;
+    C t = 0;
+    for (int k = 0; k < m; ++k) t += Ar[k] * (C)us[k];
+    const C yv = z[i] - ec * t;
     by[i] = yv;
     x.y[(size_t)r * N + j] = (T)yv;
   }
   __syncthreads();
   for (int i = tid; i < nm; i += nt) {   // p = w - c A^{-1} y
     const int j = i / m, r = i - j * m;
-    const double* Ar = A + (size_t)j * mm + r * m;
-    double t = 0.0;
+    const C* Ar = A + (size_t)j * mm + r * m;
+    C t = 0;
     for (int k = 0; k < m; ++k) t += Ar[k] * by[j * m + k];
-    x.p[(size_t)r * N + j] = (T)(w[i] - c * t);
+    x.p[(size_t)r * N + j] = (T)(w[i] - cc * t);
   }
+}
+
+// FP32 copy of the A_j^{-1} for the FP32 coarse solve.
+__global__ void cast_ainv_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
 }
 
 template <typename T, int MM>
 cudaError_t coarse_solve_mm(const CoarseData& C, double c, double d, double e, Vec3c<T> f, Vec3<T> x,
                             cudaStream_t s, int freeze_u) {
-  if (MM <= 9 && coarse_cta_smem(C.N, C.m) <= 200 * 1024) {
+  using Cm = std::conditional_t<sizeof(T) == 4, float, double>;   // precision of the per-sample products
+  const Cm* ainv = nullptr;
+  if constexpr (sizeof(T) == 4) ainv = C.Ainv32;
+  else ainv = C.Ainv;
+  if (MM <= 9 && ainv && coarse_cta_smem<Cm>(C.N, C.m) <= 200 * 1024) {
     static bool attr = false;
     if (!attr) {
-      const cudaError_t ea = cudaFuncSetAttribute(coarse_solve_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  200 * 1024);
+      const cudaError_t ea = cudaFuncSetAttribute(coarse_solve_cta<T, Cm>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (ea != cudaSuccess) return ea;
       attr = true;
     }
-    const cudaError_t ek = launch_k(coarse_solve_cta<T>, dim3(1), dim3(kCoarseCtaThreads), coarse_cta_smem(C.N, C.m),
-                                    s, C.m, C.N, (const double*)C.Ainv, (const double*)C.Minv, c, d, e, f, x,
-                                    freeze_u);
+    const cudaError_t ek = launch_k(coarse_solve_cta<T, Cm>, dim3(1), dim3(kCoarseCtaThreads),
+                                    coarse_cta_smem<Cm>(C.N, C.m), s, C.m, C.N, ainv, (const double*)C.Minv, c, d, e,
+                                    f, x, freeze_u);
     count_launches(1);
     return ek != cudaSuccess ? ek : cudaGetLastError();
   }
@@ -344,6 +364,11 @@ cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const dou
   coarse_schur_kernel<<<C.m * C.m, 128, 0, s>>>(C.m, C.N, C.Ainv, G, d * c * e, M);
   invert_kernel<<<1, 256, 0, s>>>(C.m, M, C.Minv);
   count_launches(3);
+  if (C.Ainv32) {
+    const size_t cnt = (size_t)C.N * C.m * C.m;
+    cast_ainv_kernel<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 1024), 256, 0, s>>>(C.Ainv, C.Ainv32, cnt);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 

@@ -74,6 +74,7 @@ SampleMap choose_map(int N, int elem_bytes, long items, int spl_target = 0);
 struct CoarseData {
   int n, m, N;
   double* Ainv;      // [N][m][m]
+  float* Ainv32;     // [N][m][m] FP32 copy for the FP32 cycle's coarse solve (may be null)
   double* Minv;      // [m][m]   inverse of the control Schur system
   double* wz;        // scratch [2][N][m] (A_j^{-1} f_y,j and A_j^{-1} f_p,j)
   double* partial;   // scratch [blocks][m]
