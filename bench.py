@@ -108,13 +108,26 @@ class ClockSampler:
         self.path = os.path.join("/tmp", f"cmg_clocks_{os.getpid()}.csv")
 
     def start(self):
+        """Start sampling every 50 ms and wait (up to 3 s) for the first sample,
+        so that the samples counted are those taken inside the timed region."""
+        self.skip = 0
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            self.fh.flush()
+            with open(self.path) as fh:
+                lines = fh.read().count("\n")
+            if lines > 0:
+                self.skip = lines
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -127,7 +140,7 @@ class ClockSampler:
         self.fh.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in open(self.path).read().splitlines()[self.skip:]:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue

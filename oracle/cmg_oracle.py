@@ -28,7 +28,11 @@ It computes, slowly and in the order the paper states them:
 * the coarsest-grid direct solve and the V/W-cycle of Algorithm 1;
 * the V-cycle used stationary and as right preconditioner of flexible
   GMRES, stopped on the relative unpreconditioned residual of the paper's
-  own (unsymmetric) system (Sec. 3.2; see paper_norm).
+  own (unsymmetric) system (Sec. 3.2; see paper_norm);
+* local control (Sec. 3.1 after Eq. (13), and the local-control
+  experiment of Sec. 3.2): the control has a basis function only at the
+  nodes of a control region (indicator chi); at the other nodes u_i = 0,
+  the control row is absent and the smoother takes Eq. (14) with u_i = 0.
 
 Readings where the paper is silent are listed in the design doc under
 "Readings of the paper"; the code follows them.
@@ -86,6 +90,8 @@ class Level:
     a     [n, n, N]    diag(A_j) at each node (sum of its four faces)
     c, G, d, e        the scalar diagonal blocks of Eq. (12) on this grid:
           c = h^2/N, G = nu h^2, d = e = -h^2
+    chi   [n, n]       1.0 where the node carries a control basis function,
+          0.0 where it does not (local control); all ones by default
     """
 
     n: int
@@ -99,6 +105,10 @@ class Level:
     G: float
     d: float
     e: float
+    chi: np.ndarray | None = None
+
+    def control(self) -> np.ndarray:
+        return np.ones((self.n, self.n)) if self.chi is None else self.chi
 
     @property
     def sigma(self) -> np.ndarray:
@@ -151,12 +161,30 @@ def averaged_coarse_level(fine: Level) -> Level:
     return level_from_faces(nc, N, fine.nu, kx, ky)
 
 
-def make_hierarchy(n: int, N: int, nu: float, kappa_fn, coarsest_n: int = 3, coarse: str = "averaged"):
+def control_indicator(n: int, box) -> np.ndarray:
+    """chi of the n x n grid for the closed control region box = (x0, x1, y0,
+    y1): 1 at interior nodes (x, y) = ((ix+1) h, (iy+1) h) with x0 <= x <= x1
+    and y0 <= y <= y1 (compared in integer arithmetic on the grid index:
+    x0 (n+1) <= ix+1 <= x1 (n+1), within a rounding tolerance)."""
+    x0, x1, y0, y1 = box
+    t = np.arange(1, n + 1, dtype=np.float64)           # (ix + 1)
+    s = float(n + 1)
+    eps = 1e-9
+    inx = (t >= x0 * s - eps) & (t <= x1 * s + eps)
+    iny = (t >= y0 * s - eps) & (t <= y1 * s + eps)
+    return (iny[:, None] & inx[None, :]).astype(np.float64)
+
+
+def make_hierarchy(n: int, N: int, nu: float, kappa_fn, coarsest_n: int = 3, coarse: str = "averaged",
+                   control_box=None):
     """Nested grids n_l = 2^l - 1 from n down to coarsest_n (finest first).
 
     coarse = "averaged": coarse face coefficients from the next finer grid
     (averaged_coarse_level); "nodal": every grid samples the field at its
-    own nodes and takes harmonic means of endpoint values (make_level)."""
+    own nodes and takes harmonic means of endpoint values (make_level).
+    control_box = (x0, x1, y0, y1): local control on that closed region,
+    each grid with its own indicator (control_indicator); None = control
+    everywhere."""
     if n < coarsest_n or (n + 1) & n or (coarsest_n + 1) & coarsest_n:
         raise ValueError("grid sizes must be 2^l - 1 with n >= coarsest_n")
     if coarse not in ("averaged", "nodal"):
@@ -168,6 +196,9 @@ def make_hierarchy(n: int, N: int, nu: float, kappa_fn, coarsest_n: int = 3, coa
             levels.append(make_level(m, N, nu, kappa_fn))
         else:
             levels.append(averaged_coarse_level(levels[-1]))
+    if control_box is not None:
+        for lev in levels:
+            lev.chi = control_indicator(lev.n, control_box)
     return levels
 
 
@@ -203,10 +234,15 @@ def apply_A(level: Level, v: np.ndarray) -> np.ndarray:
 
 
 def apply_S(level: Level, y, u, p):
-    """S x for the block matrix of Eq. (2) with the blocks of this problem."""
+    """S x for the block matrix of Eq. (2) with the blocks of this problem.
+
+    With local control the control enters only through chi u, and the
+    control row exists only where chi = 1 (0 elsewhere)."""
+    chi = level.control()
+    cu = chi * u
     sy = level.c * y + apply_A(level, p)
-    su = level.G * u + level.d * np.sum(p, axis=-1)
-    sp = apply_A(level, y) + level.e * u[:, :, None]
+    su = chi * (level.G * cu + level.d * np.sum(p, axis=-1))
+    sp = apply_A(level, y) + level.e * cu[:, :, None]
     return sy, su, sp
 
 
@@ -296,6 +332,12 @@ def rbgs_half_sweep(level: Level, x, f, colour: int, freeze_u: bool = False):
         y[m], p[m] = yn, pn
         return y, u, p
     yn, un, pn = local_solve(b_p, b_u, b_y, level.a[m], level.c, level.G, level.d, level.e)
+    # nodes without a control basis function: Eq. (14) with u_i = 0
+    off = level.control()[m] == 0.0
+    if np.any(off):
+        y0, p0 = local_solve_fixed_u(b_p[off], np.zeros(int(off.sum())), b_y[off], level.a[m][off], level.c,
+                                     level.e)
+        yn[off], pn[off], un[off] = y0, p0, 0.0
     y[m], u[m], p[m] = yn, un, pn
     return y, u, p
 
@@ -331,8 +373,13 @@ def lexgs_sweep(level: Level, x, f):
             if iy < n - 1:
                 off_p += ky[iy + 1, ix] * p[iy + 1, ix]
                 off_y += ky[iy + 1, ix] * y[iy + 1, ix]
-            yi, ui, pi = local_solve(fy[iy, ix] + off_p, fu[iy, ix], fp[iy, ix] + off_y,
-                                     level.a[iy, ix], level.c, level.G, level.d, level.e)
+            if level.control()[iy, ix] == 0.0:   # Eq. (14) with u_i = 0
+                yi, pi = local_solve_fixed_u(fy[iy, ix] + off_p, np.float64(0.0), fp[iy, ix] + off_y,
+                                             level.a[iy, ix], level.c, level.e)
+                ui = 0.0
+            else:
+                yi, ui, pi = local_solve(fy[iy, ix] + off_p, fu[iy, ix], fp[iy, ix] + off_y,
+                                         level.a[iy, ix], level.c, level.G, level.d, level.e)
             y[iy, ix], u[iy, ix], p[iy, ix] = yi, ui, pi
     return y, u, p
 
@@ -344,6 +391,12 @@ def jacobi_sweep(level: Level, x, f, theta: float, freeze_u: bool = False):
         dy, dp = local_solve_fixed_u(ry, np.zeros_like(ru), rp, level.a, level.c, level.e)
         return x[0] + theta * dy, x[1], x[2] + theta * dp
     dy, du, dp = local_solve(ry, ru, rp, level.a, level.c, level.G, level.d, level.e)
+    off = level.control() == 0.0
+    if np.any(off):   # nodes without a control basis function: Eq. (14) with a zero control update
+        y0, p0 = local_solve_fixed_u(ry, np.zeros_like(ru), rp, level.a, level.c, level.e)
+        dy = np.where(off[:, :, None], y0, dy)
+        dp = np.where(off[:, :, None], p0, dp)
+        du = np.where(off, 0.0, du)
     return x[0] + theta * dy, x[1] + theta * du, x[2] + theta * dp
 
 
@@ -401,10 +454,16 @@ def _apply_2d(P1, v, transpose: bool):
     return np.swapaxes(t, 0, 1)
 
 
-def prolong(nf: int, e):
-    """Bilinear prolongation P e of a coarse full-space vector (all three blocks)."""
+def prolong(nf: int, e, chi_f=None):
+    """Bilinear prolongation P e of a coarse full-space vector (all three blocks).
+
+    chi_f: the fine grid's control indicator; the control block of P e is
+    kept only where the fine grid has a control basis function."""
     P1 = prolongation_1d(nf)
-    return tuple(_apply_2d(P1, np.asarray(b), transpose=False) for b in e)
+    out = tuple(_apply_2d(P1, np.asarray(b), transpose=False) for b in e)
+    if chi_f is not None:
+        out = (out[0], chi_f * out[1], out[2])
+    return out
 
 
 def restrict(nf: int, r):
@@ -466,7 +525,10 @@ def coarse_solve(level: Level, f):
         A2 = Ainv[j] @ Ainv[j]
         schur += d * c * e * A2
         rhs -= d * (Ainv[j] @ fy[:, j] - c * (A2 @ fp[:, j]))
-    u = np.linalg.solve(schur, rhs)
+    # local control: the control rows and unknowns exist only where chi = 1
+    on = level.control().reshape(m) != 0.0
+    u = np.zeros(m)
+    u[on] = np.linalg.solve(schur[np.ix_(on, on)], rhs[on])
     y = np.zeros((m, N))
     p = np.zeros((m, N))
     for j in range(N):
@@ -526,7 +588,7 @@ def cycle(levels, l: int, x, f, opts: CycleOptions):
     ec = zeros_like_level(levels[l + 1])
     for _ in range(opts.gamma):
         ec = cycle(levels, l + 1, ec, fc, opts)
-    e = prolong(level.n, ec)
+    e = prolong(level.n, ec, level.chi)
     x = (x[0] + e[0], x[1] + e[1], x[2] + e[2])
     return smooth(level, x, f, opts.n2, opts)
 

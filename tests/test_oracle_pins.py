@@ -625,3 +625,75 @@ def test_residual_vanishes_on_the_last_swept_colour():
     rf = O.residual(lv, xf, f)
     assert np.abs(rf[0][c1]).max() <= 1e-12 * scale and np.abs(rf[2][c1]).max() <= 1e-12 * scale
     assert np.abs(rf[1][c1]).max() > 1e-6 * scale
+
+
+# --------------------------------------------------------------------------
+# Local control (the control acts on a subregion; Eq. (14) at the other nodes)
+# --------------------------------------------------------------------------
+
+LOCAL_BOX = (0.25, 0.75, 0.25, 0.75)   # the control region D_0 = (0.25, 0.75)^2 of Sec. 3.2
+
+
+def local_kkt_solution(level, f):
+    """Dense solution of the local-control optimality system assembled from
+    its definition: the distributed system of assemble_S_blocks with the
+    control unknowns (rows and columns) of the nodes outside the control
+    region deleted; u = 0 there."""
+    S = assemble_S_blocks(level)
+    n, N = level.n, level.N
+    m = n * n
+    chi = level.chi.reshape(m)
+    drop = [m * N + i for i in range(m) if chi[i] == 0.0]
+    keep = np.setdiff1d(np.arange(S.shape[0]), drop)
+    z = np.zeros(S.shape[0])
+    z[keep] = np.linalg.solve(S[np.ix_(keep, keep)], O.pack(f)[keep])
+    return z
+
+
+def test_control_indicator_of_the_local_region():
+    # n = 7, h = 1/8: nodes at 1/8 .. 7/8; the closed region [1/4, 3/4] holds columns 2/8 .. 6/8
+    chi = O.control_indicator(7, LOCAL_BOX)
+    expected = np.zeros((7, 7))
+    expected[1:6, 1:6] = 1.0
+    assert np.array_equal(chi, expected)
+    assert np.array_equal(O.control_indicator(3, LOCAL_BOX), np.ones((3, 3)))     # 1/4, 1/2, 3/4
+    assert np.array_equal(O.control_indicator(5, (0.0, 1.0, 0.0, 1.0)), np.ones((5, 5)))
+
+
+@pytest.mark.parametrize("n,N", [(7, 2), (15, 2)])
+@pytest.mark.parametrize("method", ["rbgs-V", "rbgs-W", "jacobi-V", "lexgs-V", "fgmres"])
+def test_local_control_solvers_converge_to_dense_kkt(n, N, method):
+    xi = inputs.draw_xi(40 + n + N, N, 3)
+    levels = O.make_hierarchy(n, N, 1e-3, O.sine_mode_field(xi, 0.7), control_box=LOCAL_BOX)
+    assert 0.0 < levels[0].chi.mean() < 1.0
+    yd = inputs.target_modes(n, 6)
+    f = O.fine_rhs(levels[0], yd)
+    ref = local_kkt_solution(levels[0], f)
+    if method == "fgmres":
+        res = O.fgmres(levels, f, O.CycleOptions(), tol=1e-12)
+    else:
+        sm, cyc = method.split("-")
+        opts = O.CycleOptions(smoother=sm, gamma=1 if cyc == "V" else 2)
+        res = O.solve_stationary(levels, f, opts, tol=1e-12, maxit=300)
+    assert res.relres <= 1e-12
+    got = O.pack(res.x)
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+    # no control outside the region, and some inside
+    u = res.x[1]
+    assert np.all(u[levels[0].chi == 0.0] == 0.0)
+    assert np.abs(u[levels[0].chi == 1.0]).max() > 0.0
+
+
+def test_local_control_on_the_whole_square_is_the_distributed_problem():
+    xi = inputs.draw_xi(7, 3, 3)
+    field = O.sine_mode_field(xi, 0.6)
+    a = O.make_hierarchy(15, 3, 1e-4, field)
+    b = O.make_hierarchy(15, 3, 1e-4, field, control_box=(0.0, 1.0, 0.0, 1.0))
+    assert all(np.all(lev.chi == 1.0) for lev in b)
+    f = O.fine_rhs(a[0], inputs.target_modes(15, 2))
+    xa = xb = O.zeros_like_level(a[0])
+    for _ in range(2):
+        xa = O.cycle(a, 0, xa, f, O.CycleOptions())
+        xb = O.cycle(b, 0, xb, f, O.CycleOptions())
+    for u, v in zip(xa, xb):
+        assert np.array_equal(u, v)
