@@ -85,8 +85,10 @@ def workload_config(name, n_gpus):
                 "parallelism": f"replicas x{n_gpus} (independent batches, no collective)",
                 "l2": "working set far larger than L2"}
     c = dict(inputs.CONFIGS[name])
+    box = c.get("control_box")
+    ctl = "" if box is None else f", local control on [{box[0]:g},{box[1]:g}]x[{box[2]:g},{box[3]:g}]"
     return {"workload": f"collective MG, n={c['n']} ({c['n'] ** 2} nodes), N={c['N']}, K={c['K']}, "
-                        f"amp={c['amp']}, nu={c['nu']:g}, V(2,2) red-black to 3x3, tol {tolerance(name):g}",
+                        f"amp={c['amp']}, nu={c['nu']:g}, V(2,2) red-black to 3x3, tol {tolerance(name):g}{ctl}",
             "n": c["n"], "N": c["N"], "K": c["K"], "nu": c["nu"], "amp": c["amp"],
             "unknowns": (2 * c["N"] + 1) * c["n"] ** 2, "instances_per_gpu": 1,
             "parallelism": f"replicas x{n_gpus} (independent instances, no collective)",
@@ -169,7 +171,8 @@ class OracleWorkload:
 
         self.O = O
         pr = inputs.make_problem(**inputs.CONFIGS[cfg_name])
-        self.levels = O.make_hierarchy(pr.n, pr.N, pr.nu, O.sine_mode_field(pr.xi, pr.amp))
+        self.levels = O.make_hierarchy(pr.n, pr.N, pr.nu, O.sine_mode_field(pr.xi, pr.amp),
+                                       control_box=pr.control_box)
         self.f = O.fine_rhs(self.levels[0], pr.yd)
         self.x = O.zeros_like_level(self.levels[0])
         self.unknowns = (2 * pr.N + 1) * pr.n ** 2
@@ -310,7 +313,7 @@ def run_cmg(args, world, rank, local):
     n, N = pr.n, pr.N
     unknowns = (2 * N + 1) * n * n
     stream = torch.cuda.current_stream()
-    H = P.Hierarchy(n, N, pr.xi, pr.nu, pr.amp, stream=stream)
+    H = P.Hierarchy(n, N, pr.xi, pr.nu, pr.amp, stream=stream, control_box=pr.control_box)
     dev = torch.device("cuda", local)
     xi_d = torch.tensor(pr.xi, device=dev)
     yd_d = torch.tensor(pr.yd.reshape(-1), device=dev)

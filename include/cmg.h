@@ -73,6 +73,14 @@ typedef struct {
                        arithmetic across it (weights 1/4, 1/2, 1/4);
                        CMG_COARSE_NODAL: the field is sampled at each grid's own nodes and
                        faces are harmonic means of the two endpoint values */
+  double ctl_box[4]; /* local control (Sec. 3.1 after Eq. (13); the local-control test case of
+                       Sec. 3.2): the closed region [x0, x1] x [y0, y1] = {ctl_box[0], ctl_box[1],
+                       ctl_box[2], ctl_box[3]} inside the unit square.  Nodes of every grid inside
+                       it carry a control basis function; at the others u_i = 0, the control row
+                       is absent (its residual is zero) and the smoothers use Eq. (14) with
+                       u_i = 0.  All four zero = control everywhere (distributed control).
+                       Other values with x1 <= x0 or y1 <= y0, or outside [0, 1]:
+                       CMG_ERR_INVALID_ARG. */
 } cmg_problem;
 
 /* Cycle options (Algorithm 1). */

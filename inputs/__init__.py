@@ -78,10 +78,11 @@ class ProblemSpec:
     xi: np.ndarray = field(repr=False)
     yd: np.ndarray = field(repr=False)          # [n, n]
     f: np.ndarray = field(repr=False)           # [n, n]
+    control_box: tuple | None = None            # local control region (x0, x1, y0, y1); None = everywhere
 
 
 def make_problem(n: int, N: int, K: int, nu: float, amp: float, seed: int,
-                 target: str = "sinsin", target_seed: int | None = None) -> ProblemSpec:
+                 target: str = "sinsin", target_seed: int | None = None, control_box=None) -> ProblemSpec:
     xi = draw_xi(seed, N, K)
     if target == "sinsin":
         yd = target_sinsin(n)
@@ -90,7 +91,7 @@ def make_problem(n: int, N: int, K: int, nu: float, amp: float, seed: int,
     else:
         raise ValueError(f"unknown target {target!r}")
     return ProblemSpec(n=n, N=N, K=K, nu=nu, amp=amp, seed=seed, xi=xi, yd=yd,
-                       f=np.zeros((n, n)))
+                       f=np.zeros((n, n)), control_box=control_box)
 
 
 # The five workloads (sizes, field, regularisation, seeds) used by the
@@ -102,6 +103,8 @@ CONFIGS = {
     "n255_N64": dict(n=255, N=64, K=16, nu=1e-6, amp=1.0, seed=2),
     # large mixed-precision instance, n=1023, N=256, 32 modes, nu=1e-5
     "n1023_N256": dict(n=1023, N=256, K=32, nu=1e-5, amp=1.0, seed=3),
+    # the n=255, N=64 instance with the control acting on (0.25, 0.75)^2 only
+    "n255_N64_local": dict(n=255, N=64, K=16, nu=1e-6, amp=1.0, seed=2, control_box=(0.25, 0.75, 0.25, 0.75)),
 }
 
 

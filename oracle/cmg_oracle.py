@@ -247,9 +247,10 @@ def apply_S(level: Level, y, u, p):
 
 
 def residual(level: Level, x, f):
-    """r = f - S x, block by block."""
+    """r = f - S x, block by block.  With local control the control row is
+    absent at nodes without a control basis function: its residual is 0."""
     sy, su, sp = apply_S(level, *x)
-    return f[0] - sy, f[1] - su, f[2] - sp
+    return f[0] - sy, level.control() * (f[1] - su), f[2] - sp
 
 
 def norm(v) -> float:

@@ -34,7 +34,16 @@ class CMGError(RuntimeError):
 
 class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int), ("nu", ctypes.c_double),
-                ("amp", ctypes.c_double), ("coarsest_n", ctypes.c_int), ("coarse_coeff", ctypes.c_int)]
+                ("amp", ctypes.c_double), ("coarsest_n", ctypes.c_int), ("coarse_coeff", ctypes.c_int),
+                ("ctl_box", ctypes.c_double * 4)]
+
+
+def _box(control_box):
+    """cmg_problem.ctl_box from (x0, x1, y0, y1), or all zero (control everywhere)."""
+    b = (0.0, 0.0, 0.0, 0.0) if control_box is None else tuple(float(v) for v in control_box)
+    if len(b) != 4:
+        raise ValueError("control_box must be (x0, x1, y0, y1)")
+    return (ctypes.c_double * 4)(*b)
 
 
 class Cycle(ctypes.Structure):
@@ -137,7 +146,7 @@ class Hierarchy:
     """
 
     def __init__(self, n: int, N: int, xi, nu: float, amp: float, coarsest_n: int = 3, stream=None,
-                 coarse: str = "averaged"):
+                 coarse: str = "averaged", control_box=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -152,7 +161,8 @@ class Hierarchy:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if coarse not in COARSE:
             raise ValueError(f"coarse must be one of {sorted(COARSE)}")
-        prob = Problem(self.n, self.N, self.K, self.nu, self.amp, coarsest_n, COARSE[coarse])
+        prob = Problem(self.n, self.N, self.K, self.nu, self.amp, coarsest_n, COARSE[coarse], _box(control_box))
+        self.control_box = control_box
         h = ctypes.c_void_p()
         st = self._lib.cmg_create(ctypes.byref(prob), xi.ctypes.data_as(ctypes.c_void_p),
                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
@@ -340,7 +350,8 @@ class Batch:
         for i, pr in enumerate(problems):
             xi = np.ascontiguousarray(np.asarray(pr.xi, dtype=np.float64))
             self._xi.append(xi)
-            probs[i] = Problem(pr.n, pr.N, xi.shape[1], pr.nu, pr.amp, coarsest_n, COARSE[coarse])
+            probs[i] = Problem(pr.n, pr.N, xi.shape[1], pr.nu, pr.amp, coarsest_n, COARSE[coarse],
+                               _box(getattr(pr, "control_box", None)))
         ptrs = (ctypes.c_void_p * self.count)(*[x.ctypes.data for x in self._xi])
         b = ctypes.c_void_p()
         st = self._lib.cmg_batch_create(probs, ptrs, self.count, ctypes.c_void_p(self.stream.cuda_stream),

@@ -25,6 +25,7 @@ namespace {
 
 struct Lev {
   int n = 0;
+  CtlBox ctl;                            // nodes with a control basis function (local control)
   int spl_target[2] = {0, 0};            // autotuned chunks per lane: [FP64, FP32]
   double h = 0, c = 0, G = 0, d = 0, e = 0;
   size_t nodes = 0;                      // n*n
@@ -148,13 +149,13 @@ template <>
 LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0], freeze_u,
-          nullptr, v.a64};
+          nullptr, v.a64, v.ctl};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1], freeze_u,
-          v.isigma32, nullptr};
+          v.isigma32, nullptr, v.ctl};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -395,7 +396,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   }
   {
     ProfScope ps(h, CMG_KERNEL_PROLONG, l);
-    e = launch_prolong_add<T>(v.n, N, cview(xc), x, h->stream);
+    e = launch_prolong_add<T>(v.n, N, cview(xc), x, h->stream, v.ctl);
   }
   if (e == cudaSuccess) e = smooth<T>(h, o, l, o.n2, x, f);
   return e;
@@ -441,6 +442,28 @@ cudaError_t fetch(cmg_handle* h, const double* dev, int count) {
 // ============================================================================
 extern "C" {
 
+// Local control region: all zero (or x1 <= x0) = control everywhere; else
+// a box inside the unit square.
+bool control_box_full(const double* b) { return !(b[1] > b[0]) || !(b[3] > b[2]); }
+bool control_box_ok(const double* b) {
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(b[i])) return false;
+  if (control_box_full(b)) return b[0] == 0.0 && b[1] == 0.0 && b[2] == 0.0 && b[3] == 0.0;
+  return b[0] >= 0.0 && b[1] <= 1.0 && b[2] >= 0.0 && b[3] <= 1.0;
+}
+// Index box of the n x n grid's nodes ((ix+1) h, (iy+1) h) inside the
+// closed region (a rounding tolerance keeps nodes on its edges).
+CtlBox control_nodes(int n, const double* b) {
+  CtlBox c;
+  if (control_box_full(b)) return c;
+  const double s = n + 1.0, eps = 1e-9;
+  c.x0 = std::max(0, (int)std::ceil(b[0] * s - eps) - 1);
+  c.x1 = std::min(n - 1, (int)std::floor(b[1] * s + eps) - 1);
+  c.y0 = std::max(0, (int)std::ceil(b[2] * s - eps) - 1);
+  c.y1 = std::min(n - 1, (int)std::floor(b[3] * s + eps) - 1);
+  return c;
+}
+
 cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stream, cmg_handle** out) {
   if (!out) return CMG_ERR_INVALID_ARG;
   *out = nullptr;
@@ -452,6 +475,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   if (P.N < 1 || P.K < 0 || P.K > 64 || !(P.nu > 0.0) || !std::isfinite(P.amp)) return CMG_ERR_INVALID_ARG;
   if (P.coarse_coeff != CMG_COARSE_AVERAGED && P.coarse_coeff != CMG_COARSE_NODAL) return CMG_ERR_INVALID_ARG;
   if (P.K > 0 && !xi_host) return CMG_ERR_INVALID_ARG;
+  if (!control_box_ok(P.ctl_box)) return CMG_ERR_INVALID_ARG;
   const SampleMap m64 = choose_map(P.N, 8, 0), m32 = choose_map(P.N, 4, 0);   // most chunks per lane
   if (m64.spl > kMaxSPL || m32.spl > kMaxSPL) return CMG_ERR_UNSUPPORTED;
 
@@ -479,6 +503,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     v.G = P.nu * v.h * v.h;
     v.d = -v.h * v.h;
     v.e = -v.h * v.h;
+    v.ctl = control_nodes(n, P.ctl_box);
     ++L;
     if (n == P.coarsest_n) break;
     n = (n - 1) / 2;
@@ -519,6 +544,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   h->coarse.m = cn * cn;
   h->coarse.N = P.N;
   h->coarse.blocks = (P.N + 31) / 32;
+  h->coarse.ctl = h->lv[L - 1].ctl;
   AL(h->coarse.Ainv, N * h->coarse.m * h->coarse.m);
   AL(h->coarse.Ainv32, N * h->coarse.m * h->coarse.m);
   AL(h->coarse.Minv, (size_t)h->coarse.m * h->coarse.m);
@@ -529,6 +555,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     h->coarse32.m = h->coarse.m;
     h->coarse32.N = h->coarse.N;
     h->coarse32.blocks = h->coarse.blocks;
+    h->coarse32.ctl = h->coarse.ctl;
     AL(h->coarse32.Ainv, N * h->coarse.m * h->coarse.m);
     AL(h->coarse32.Ainv32, N * h->coarse.m * h->coarse.m);
     AL(h->coarse32.Minv, (size_t)h->coarse.m * h->coarse.m);
@@ -631,7 +658,8 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
     if (!level_ok(h, level) || level == h->L - 1) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");   \
     if (!vec_ok(ey, eu, ep) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
-    CK(launch_prolong_add<T>(h->lv[level].n, h->prob.N, Vec3c<T>{ey, eu, ep}, Vec3<T>{y, u, p}, h->stream));   \
+    CK(launch_prolong_add<T>(h->lv[level].n, h->prob.N, Vec3c<T>{ey, eu, ep}, Vec3<T>{y, u, p}, h->stream,          \
+                             h->lv[level].ctl));   \
     return CMG_OK;                                                                                              \
   }                                                                                                             \
   cmg_status cmg_coarse_solve##SUF(cmg_handle* h, const T* fy, const T* fu, const T* fp, T* y, T* u, T* p) {    \

@@ -38,6 +38,16 @@ __host__ __device__ inline Vec3c<T> cview(const Vec3<T>& v) { return {v.y, v.u, 
 // Read-only view of one grid's operator for the kernels.  Face arrays:
 // kx[iy][f][j], f = 0..n (face f separates columns f-1 and f; f = 0 and n
 // touch the boundary); ky[f][ix][j], f = 0..n likewise for rows.
+// Nodes of a grid that carry a control basis function (local control, the
+// paper's control on a subregion): the inclusive index box [x0, x1] x
+// [y0, y1] of (ix, iy); an empty box (x1 < x0) means no control node.  The
+// default covers every node (distributed control).
+struct CtlBox {
+  int x0 = 0, x1 = 1 << 30, y0 = 0, y1 = 1 << 30;
+  __host__ __device__ bool inside(int iy, int ix) const { return ix >= x0 && ix <= x1 && iy >= y0 && iy <= y1; }
+  __host__ __device__ bool full(int n) const { return x0 <= 0 && y0 <= 0 && x1 >= n - 1 && y1 >= n - 1; }
+};
+
 template <typename T>
 struct LevelView {
   int n;            // nodes per side
@@ -52,6 +62,7 @@ struct LevelView {
   int freeze_u;         // 1: keep u fixed (local solves of the state and adjoint rows only)
   const float* isigma32;  // 1/sigma rounded to FP32 (FP32 path: the control update runs in FP32)
   const double* a64;      // diag(A_j) = sum of the four faces per node-sample (FP64, finest grid only, else null)
+  CtlBox ctl{};           // nodes with a control basis function (elsewhere u_i = 0, no control row)
 };
 
 // Sample mapping of a node's N samples: lanes-per-node (power of two <= 32),
@@ -73,6 +84,7 @@ SampleMap choose_map(int N, int elem_bytes, long items, int spl_target = 0);
 // Coarsest-grid factors (FP64).
 struct CoarseData {
   int n, m, N;
+  CtlBox ctl;        // control nodes of the coarsest grid (the control Schur system lives on them)
   double* Ainv;      // [N][m][m]
   float* Ainv32;     // [N][m][m] FP32 copy for the FP32 cycle's coarse solve (may be null)
   double* Minv;      // [m][m]   inverse of the control Schur system
@@ -139,7 +151,7 @@ template <typename T>
 cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s,
                             Vec3<T> zx = Vec3<T>{nullptr, nullptr, nullptr}, int colour0 = 0);
 template <typename T>
-cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t s);
+cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t s, CtlBox ctl = CtlBox{});
 
 // ---- cluster-resident coarse-grid cycle (cmg_tail.cuh, cmg_tail_f32/f64.cu) ----
 constexpr int kTailMax = 8;        // grids handled inside one cluster launch

@@ -92,13 +92,16 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
   const bool apply = f.y == nullptr;
   using A = acc_t<T>;
   T pacc = T(0);   // this lane's part of sum_j p_j
+  // local control: the control enters as chi_i u_i and its row exists only
+  // where chi_i = 1
+  const int iy = valid ? (int)(node / n) : 0, ix = valid ? (int)(node - (long)iy * n) : 0;
+  const bool ctl = L.ctl.inside(iy, ix);
   if (valid) {
-    const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
     const size_t o = (size_t)node * ld;
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
     const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
-    const T uu = ld1<T, CG>(x.u + node);
+    const T uu = ctl ? ld1<T, CG>(x.u + node) : T(0);
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {
       const int j = (lane + s * lpn) * V;
@@ -160,8 +163,12 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
   }
   const A psum = group_sum((A)pacc, lpn);
   if (valid && lane == 0) {
-    const A su = (A)L.G * (A)ld1<T, CG>(x.u + node) + (A)L.d * psum;   // control row: G u + d sum_j p_j
-    r.u[node] = (T)(apply ? su : (A)ld1<T, CG>(f.u + node) - su);
+    if (ctl) {
+      const A su = (A)L.G * (A)ld1<T, CG>(x.u + node) + (A)L.d * psum;   // control row: G u + d sum_j p_j
+      r.u[node] = (T)(apply ? su : (A)ld1<T, CG>(f.u + node) - su);
+    } else {
+      r.u[node] = T(0);
+    }
   }
 }
 
@@ -271,8 +278,10 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
   const A tsum = group_sum((A)tacc, lpn);
   if (valid) {
     // frozen control: u_i keeps its value and only the state and adjoint
-    // rows are solved (Eq. (14) with u_i given instead of zero)
-    const A uu = L.freeze_u ? bu : (bu + (A)L.d * tsum) * isg;
+    // rows are solved (Eq. (14) with u_i given instead of zero); a node
+    // without a control basis function (local control) takes Eq. (14) with
+    // u_i = 0
+    const A uu = L.freeze_u ? bu : (L.ctl.inside(iy, ix) ? (bu + (A)L.d * tsum) * isg : A(0));
     if (lane == 0 && !L.freeze_u) x.u[node] = (T)uu;
     const T uT = (T)uu, e = (T)L.e;
 #pragma unroll
@@ -305,11 +314,11 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   using A = acc_t<T>;
   T tacc = T(0);
   A ru = A(0), xu = A(0), isg = A(0);   // loaded with the rest, ahead of the group sum
+  const int iy = valid ? (int)(node / n) : 0, ix = valid ? (int)(node - (long)iy * n) : 0;
   if (valid) {
     ru = (A)ld1<T, CG>(r.u + node);
     xu = (A)ld1<T, CG>(x.u + node);
     isg = isigma_of<T>(L, node);
-    const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
 #pragma unroll
@@ -330,7 +339,7 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   }
   const A tsum = group_sum((A)tacc, lpn);
   if (valid) {
-    const A du = L.freeze_u ? A(0) : (ru + (A)L.d * tsum) * isg;
+    const A du = (L.freeze_u || !L.ctl.inside(iy, ix)) ? A(0) : (ru + (A)L.d * tsum) * isg;
     if (lane == 0) x.u[node] = (T)(xu + (A)theta * du);
     const T duT = (T)du, e = (T)L.e, th = (T)theta;
 #pragma unroll
@@ -410,9 +419,11 @@ __device__ __forceinline__ void restrict_item(int nf, int N, const Vec3c<T>& r, 
 
 // x += P e at one fine node: 1 x coinciding coarse node, 1/2 x each of two
 // edge neighbours, 1/4 x each of four cell corners (zero outside the grid).
+// With local control the control block is corrected only at fine nodes that
+// carry a control basis function (ctl).
 template <typename T, int V, int SPL, bool CG>
 __device__ __forceinline__ void prolong_item(int nf, int N, const Vec3c<T>& e, const Vec3<T>& x, long node,
-                                             int lane, int lpn) {
+                                             int lane, int lpn, const CtlBox& ctl = CtlBox{}) {
   const int nc = (nf - 1) / 2;
   if (node >= (long)nf * nf) return;   // no shuffles below
   const int iy = (int)(node / nf), ix = (int)(node - (long)iy * nf);
@@ -447,7 +458,7 @@ __device__ __forceinline__ void prolong_item(int nf, int N, const Vec3c<T>& e, c
       stv<T, V>(x.p + (size_t)node * ld + j, vp);
     }
   }
-  if (lane == 0) {
+  if (lane == 0 && ctl.inside(iy, ix)) {
     T vu = ld1<T, CG>(x.u + node);
     for (int a = 0; a < ny; ++a) {
       if (Jr[a] < 0 || Jr[a] >= nc) continue;
@@ -498,13 +509,14 @@ __device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, 
   T pacc = 0.0;
   float sq = 0.f;
   const float sf = (float)s;
+  const int iy = valid ? (int)(node / n) : 0, ix = valid ? (int)(node - (long)iy * n) : 0;
+  const bool ctl = L.ctl.inside(iy, ix);   // local control: chi_i
   if (valid) {
-    const int iy = (int)(node / n), ix = (int)(node - (long)iy * n);
     const size_t o = (size_t)node * ld;
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
     const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
-    const T xu = x.u[node];
+    const T xu = ctl ? x.u[node] : 0.0;
     const unsigned long long xu_bits = dbits(xu);
     const T eu = e * xu;
 #pragma unroll
@@ -571,7 +583,7 @@ __device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, 
   }
   const double psum = group_sum(pacc, lpn);
   if (valid && lane == 0) {
-    const float ru = (float)((f.u[node] - (L.G * x.u[node] + L.d * psum)) * s);
+    const float ru = ctl ? (float)((f.u[node] - (L.G * x.u[node] + L.d * psum)) * s) : 0.f;
     r.u[node] = ru;
     sq = fmaf(ru, ru, sq);
   }

@@ -85,10 +85,11 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(int nf, int N, Vec3c<T
 }
 
 template <typename T, int V, int SPL>
-__global__ void __launch_bounds__(kBlock) prolong_add_kernel(int nf, int N, Vec3c<T> e, Vec3<T> x, int lpn) {
+__global__ void __launch_bounds__(kBlock) prolong_add_kernel(int nf, int N, Vec3c<T> e, Vec3<T> x, int lpn,
+                                                             CtlBox ctl) {
   pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
-  prolong_item<T, V, SPL, false>(nf, N, e, x, node, threadIdx.x & (lpn - 1), lpn);
+  prolong_item<T, V, SPL, false>(nf, N, e, x, node, threadIdx.x & (lpn - 1), lpn, ctl);
 }
 
 // One pass of FP64 refinement: r32 = s (f - S x) and per-CTA partial sums
@@ -335,11 +336,11 @@ cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t st) {
+cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t st, CtlBox ctl) {
   const SampleMap m = choose_map(N, sizeof(T), (long)nf * nf);
   const unsigned grid = grid_for((long)nf * nf, m.lpn);
   cudaError_t e_ = cudaSuccess;
-  CMG_DISPATCH(T, m, (e_ = launch_k(prolong_add_kernel<T, V, SPL>, grid, kBlock, 0, st, nf, N, e, x, m.lpn)));
+  CMG_DISPATCH(T, m, (e_ = launch_k(prolong_add_kernel<T, V, SPL>, grid, kBlock, 0, st, nf, N, e, x, m.lpn, ctl)));
   count_launches(1);
   return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
@@ -419,7 +420,7 @@ cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<doub
   template cudaError_t launch_restrict<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t, Vec3<T>, int);         \
   template cudaError_t launch_residual_c0<T>(const LevelView<T>&, Vec3c<T>, Vec3c<T>, Vec3<T>, cudaStream_t);       \
   template cudaError_t launch_rbgs_prolong<T>(const LevelView<T>&, Vec3<T>, Vec3c<T>, Vec3c<T>, int, cudaStream_t);                     \
-  template cudaError_t launch_prolong_add<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t);
+  template cudaError_t launch_prolong_add<T>(int, int, Vec3c<T>, Vec3<T>, cudaStream_t, CtlBox);
 
 CMG_INST(double)
 CMG_INST(float)

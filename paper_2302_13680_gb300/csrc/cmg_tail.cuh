@@ -85,10 +85,11 @@ __device__ void coarse_cta(const TailParams<T>& P, const Vec3<T>& x, const Vec3<
     if (lane == 0) red[warp][r] = v;
   }
   __syncthreads();
+  const LevelView<T>& cl = P.lev[P.nlev - 1].L;   // coarsest grid: control rows only at its control nodes
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][r];
-    rhs[r] = (double)ld1<T, true>(f.u + r) - d * s;
+    rhs[r] = cl.ctl.inside(r / cl.n, r % cl.n) ? (double)ld1<T, true>(f.u + r) - d * s : 0.0;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_cycle_kernel(const __grid_c
       }
       const TailLevel<T>& cv = P.lev[k + 1];
       const long nn = (long)lv.L.n * lv.L.n;
-      CMG_TAIL_FOR(nn, (prolong_item<T, V, SPL, true>(lv.L.n, N, cview(cv.x), lv.x, g, lane, lpn)));
+      CMG_TAIL_FOR(nn, (prolong_item<T, V, SPL, true>(lv.L.n, N, cview(cv.x), lv.x, g, lane, lpn, lv.L.ctl)));
       barrier(cl);
       smooth(k, P.n2);
       if (--k < 0) break;

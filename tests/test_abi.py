@@ -50,7 +50,10 @@ def test_binding_loads_and_rejects_bad_sizes(lib):
                 cmg.Problem(31, 8, 4, -1.0, 0.5, 3, 0),      # nu <= 0
                 cmg.Problem(31, 8, 4, 1e-4, 0.5, 5, 0),      # coarsest not 1, 3, 7
                 cmg.Problem(3, 8, 4, 1e-4, 0.5, 7, 0),       # coarsest > n
-                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 2)]:     # unknown coarse-coefficient rule
+                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 2),      # unknown coarse-coefficient rule
+                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 0, cmg._box((0.5, 0.25, 0.0, 1.0))),   # control box x1 < x0
+                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 0, cmg._box((0.0, 1.5, 0.0, 1.0))),    # outside the square
+                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 0, cmg._box((0.2, 0.8, 0.3, float("nan"))))]:
         assert L.cmg_create(ctypes.byref(bad), None, None, ctypes.byref(h)) == 1
     assert L.cmg_create(ctypes.byref(cmg.Problem(31, 4096, 0, 1e-4, 0.5, 3, 0)), None, None,
                         ctypes.byref(h)) == 7        # N above the kernels' limit

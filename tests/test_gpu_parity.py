@@ -66,29 +66,38 @@ def rand_level_vec(n, N, seed, dtype=np.float64):
     return tuple(np.asarray(b, dtype=dtype).astype(np.float64) for b in v)
 
 
-# (n, N, K, nu, amp, seed, coarsest, coarse rule): the small configuration,
-# ragged sample counts (scalar and 2-wide vector paths, partial lane
-# groups), all three coarsest grids, a sample count that spans several
-# chunks per lane, and both coarse-coefficient rules.
+# (n, N, K, nu, amp, seed, coarsest, coarse rule, control region): the small
+# configuration, ragged sample counts (scalar and 2-wide vector paths,
+# partial lane groups), all three coarsest grids, a sample count that spans
+# several chunks per lane, both coarse-coefficient rules, and local control
+# (the paper's region (0.25, 0.75)^2, and an off-centre box) including a
+# coarsest 7 x 7 grid with nodes outside the region.
+LOCAL = (0.25, 0.75, 0.25, 0.75)
 CASES = [
-    (31, 8, 4, 1e-4, 0.5, 1, 3, "averaged"),
-    (31, 8, 4, 1e-4, 0.5, 1, 3, "nodal"),
-    (15, 5, 3, 1e-3, 0.8, 7, 3, "averaged"),
-    (15, 6, 3, 1e-3, 0.8, 8, 1, "averaged"),
-    (31, 3, 2, 1e-5, 1.0, 9, 7, "nodal"),
-    (15, 1, 2, 1e-2, 0.6, 10, 3, "averaged"),
-    (63, 64, 16, 1e-6, 1.0, 2, 3, "averaged"),
-    (15, 130, 4, 1e-4, 1.0, 11, 3, "averaged"),
+    (31, 8, 4, 1e-4, 0.5, 1, 3, "averaged", None),
+    (31, 8, 4, 1e-4, 0.5, 1, 3, "nodal", None),
+    (15, 5, 3, 1e-3, 0.8, 7, 3, "averaged", None),
+    (15, 6, 3, 1e-3, 0.8, 8, 1, "averaged", None),
+    (31, 3, 2, 1e-5, 1.0, 9, 7, "nodal", None),
+    (15, 1, 2, 1e-2, 0.6, 10, 3, "averaged", None),
+    (63, 64, 16, 1e-6, 1.0, 2, 3, "averaged", None),
+    (15, 130, 4, 1e-4, 1.0, 11, 3, "averaged", None),
+    (31, 8, 4, 1e-4, 0.5, 1, 3, "averaged", LOCAL),
+    (15, 5, 3, 1e-3, 0.8, 7, 3, "averaged", LOCAL),
+    (15, 6, 3, 1e-3, 0.8, 8, 1, "averaged", (0.3, 0.7, 0.1, 0.6)),
+    (31, 3, 2, 1e-5, 1.0, 9, 7, "nodal", LOCAL),
+    (63, 64, 16, 1e-6, 1.0, 2, 3, "averaged", LOCAL),
 ]
-IDS = [f"n{c[0]}_N{c[1]}_c{c[6]}_{c[7][:3]}" for c in CASES]
+IDS = [f"n{c[0]}_N{c[1]}_c{c[6]}_{c[7][:3]}" + ("" if c[8] is None else "_local") for c in CASES]
 
 
 @pytest.fixture(scope="module", params=CASES, ids=IDS)
 def case(request, cmg):
-    n, N, K, nu, amp, seed, coarsest, coarse = request.param
+    n, N, K, nu, amp, seed, coarsest, coarse, box = request.param
     xi = inputs.draw_xi(seed, N, K)
-    H = cmg.Hierarchy(n, N, xi, nu, amp, coarsest_n=coarsest, coarse=coarse)
-    levels = O.make_hierarchy(n, N, nu, O.sine_mode_field(xi, amp), coarsest_n=coarsest, coarse=coarse)
+    H = cmg.Hierarchy(n, N, xi, nu, amp, coarsest_n=coarsest, coarse=coarse, control_box=box)
+    levels = O.make_hierarchy(n, N, nu, O.sine_mode_field(xi, amp), coarsest_n=coarsest, coarse=coarse,
+                              control_box=box)
     yield H, levels
     H.close()
 
@@ -170,7 +179,7 @@ def test_transfers(case, prec):
         x = rand_level_vec(nf, N, 700 + l, npdt)
         xd = to_dev(x, dt)
         H.prolong_add(l, to_dev(e, dt), xd)
-        pe = O.prolong(nf, e)
+        pe = O.prolong(nf, e, levels[l].chi)
         assert_close(to_host(xd, nf), tuple(a + b for a, b in zip(x, pe)), tol, f"prolong {l}")
 
 
