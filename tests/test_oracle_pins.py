@@ -697,3 +697,85 @@ def test_local_control_on_the_whole_square_is_the_distributed_problem():
         xb = O.cycle(b, 0, xb, f, O.CycleOptions())
     for u, v in zip(xa, xb):
         assert np.array_equal(u, v)
+
+
+# --------------------------------------------------------------------------
+# Two-level analysis in 1D (Sec. 3.1, Lemma 2, Theorem 1, Fig. 1)
+# --------------------------------------------------------------------------
+
+def two_level_1d(Nh, N, nu, eta, theta, n1, n2):
+    """The 1D model of Sec. 3.1 in the node-collected ordering z: S = I (x) Bt
+    + H (x) B with Bt = [[I/N, D], [D, -1 1^T / (nu N^2)]], B = [[0, -D/2],
+    [-D/2, 0]], d_j = 2 eta_j / (h^2 N); collective Jacobi G = I - (I (x)
+    Bt^-1) S, damped G_theta = (1 - theta) I + theta G; full weighting with
+    rows (1/4, 1/2, 1/4) and linear interpolation 2 R^T (the reading whose
+    action on the Fourier modes is the one the paper states); Galerkin coarse
+    matrix S_c = R S P.  Returns T = G^n2 (I - P S_c^-1 R S) G^n1."""
+    h = 1.0 / (Nh + 1)
+    D = np.diag(2.0 * eta / (h * h * N))
+    I_N, one = np.eye(N), np.ones((N, 1))
+    Bt = np.block([[I_N / N, D], [D, -(one @ one.T) / (nu * N * N)]])
+    B = np.block([[np.zeros((N, N)), -D / 2], [-D / 2, np.zeros((N, N))]])
+    H = np.diag(np.ones(Nh - 1), 1) + np.diag(np.ones(Nh - 1), -1)
+    S = np.kron(np.eye(Nh), Bt) + np.kron(H, B)
+    G = np.eye(S.shape[0]) - np.kron(np.eye(Nh), np.linalg.inv(Bt)) @ S
+    G = (1 - theta) * np.eye(S.shape[0]) + theta * G
+    Nc = (Nh - 1) // 2
+    Rt = np.zeros((Nc, Nh))
+    for I in range(Nc):
+        Rt[I, 2 * I: 2 * I + 3] = (0.25, 0.5, 0.25)
+    R = np.kron(Rt, np.eye(2 * N))
+    P = np.kron(2 * Rt.T, np.eye(2 * N))
+    Sc = R @ S @ P
+    CGC = np.eye(S.shape[0]) - P @ np.linalg.solve(Sc, R @ S)
+    return np.linalg.matrix_power(G, n2) @ CGC @ np.linalg.matrix_power(G, n1)
+
+
+def theorem1_spectrum(Nh, N, nu, eta, theta, n1, n2):
+    """Theorem 1 with Lemma 1's sigma(C):
+        kappa_ji = (c_j^4 (1 - d_ji) d^_jt,i^n + s_j^4 (1 - d_jt,i) d^_ji^n)
+                   / (c_j^4 (1 - d_ji) + s_j^4 (1 - d_jt,i)),
+    d_ji = -mu_j lambda_i, mu_j = 2 cos(j pi h), jt = Nh + 1 - j, c_j, s_j =
+    cos, sin(j pi h / 2), n = n1 + n2, j = 1 .. (Nh+1)/2 - 1, i = 1 .. 2N,
+    and zeros.  Damping (the remark after Corollary 2: G_theta = (1 - theta) I
+    + theta G): the powers take d^ = 1 - theta + theta d, the weights keep the
+    undamped d, and the modes j = (Nh+1)/2 (mu = 0, annihilated by R) add
+    (1 - theta)^n, 2N times."""
+    h = 1.0 / (Nh + 1)
+    dt = 2.0 * eta / (h * h)
+    E = np.mean(dt ** -2.0)
+    r = E / (nu + E)
+    lam = np.concatenate([[-0.5] * (2 * N - 2),
+                          -0.5 * np.array([1 - r + 1j * np.sqrt((1 - r) * r), 1 - r - 1j * np.sqrt((1 - r) * r)])])
+    n = n1 + n2
+    out = []
+    for j in range(1, (Nh + 1) // 2):
+        jt = Nh + 1 - j
+        mu, mut = 2 * np.cos(j * np.pi * h), 2 * np.cos(jt * np.pi * h)
+        c2, s2 = np.cos(j * np.pi * h / 2) ** 2, np.sin(j * np.pi * h / 2) ** 2
+        for li in lam:
+            d, dtl = -mu * li, -mut * li
+            dh, dth = 1 - theta + theta * d, 1 - theta + theta * dtl
+            num = c2 * c2 * (1 - d) * dth ** n + s2 * s2 * (1 - dtl) * dh ** n
+            out.append(num / (c2 * c2 * (1 - d) + s2 * s2 * (1 - dtl)))
+    out += [(1 - theta) ** n] * (2 * N)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("theta,n1,n2", [(1.0, 1, 1), (1.0, 2, 2), (0.5, 1, 1), (0.5, 2, 2)])
+def test_two_level_spectrum_matches_theorem1(theta, n1, n2):
+    """Fig. 1's setting (N_h = 31, N = 10, nu = 1e-2, n1 = n2 = 1) and V(2,2),
+    undamped and with theta = 0.5: the eigenvalues of the assembled
+    two-level operator are Theorem 1's kappa_ji, the damped correction and
+    zeros (2N N_h in all); the spectral radius agrees to rounding."""
+    Nh, N, nu = 31, 10, 1e-2
+    eta = inputs.draw_xi(12, N, 1)[:, 0] * 0.3 + 1.5        # positive samples of eta
+    assert np.all(eta > 0)
+    ev = np.linalg.eigvals(two_level_1d(Nh, N, nu, eta, theta, n1, n2))
+    pred = theorem1_spectrum(Nh, N, nu, eta, theta, n1, n2)
+    pred = np.concatenate([pred, np.zeros(ev.size - pred.size)])
+    assert ev.size == 2 * N * Nh
+    # defective (Jordan) eigenvalues of the smoother are only accurate to ~sqrt(eps) in eig
+    assert _match_spectra(ev, pred) < 1e-6
+    assert np.isclose(np.abs(ev).max(), np.abs(pred).max(), rtol=1e-8, atol=1e-12)
+    assert np.abs(ev).max() < 1.0
