@@ -92,6 +92,9 @@ class Level:
           c = h^2/N, G = nu h^2, d = e = -h^2
     chi   [n, n]       1.0 where the node carries a control basis function,
           0.0 where it does not (local control); all ones by default
+    dw    [n, n]       per-node factor on d (the control row's coupling to the
+          adjoint), all ones by default; the semismooth Newton systems of
+          Sec. 4 set it to the indicator of the active sets
     """
 
     n: int
@@ -106,14 +109,19 @@ class Level:
     d: float
     e: float
     chi: np.ndarray | None = None
+    dw: np.ndarray | None = None
 
     def control(self) -> np.ndarray:
         return np.ones((self.n, self.n)) if self.chi is None else self.chi
 
+    def dnode(self) -> np.ndarray:
+        """d_i per node: d times dw_i."""
+        return self.d * (np.ones((self.n, self.n)) if self.dw is None else self.dw)
+
     @property
     def sigma(self) -> np.ndarray:
-        """Schur denominator of Eq. (13): G + d^T diag(a)^-1 diag(c) diag(a)^-1 e."""
-        return self.G + np.sum(self.d * self.c * self.e / self.a ** 2, axis=-1)
+        """Schur denominator of Eq. (13): G + d_i^T diag(a)^-1 diag(c) diag(a)^-1 e."""
+        return self.G + self.dnode() * np.sum(self.c * self.e / self.a ** 2, axis=-1)
 
 
 def make_level(n: int, N: int, nu: float, kappa_fn) -> Level:
@@ -241,7 +249,7 @@ def apply_S(level: Level, y, u, p):
     chi = level.control()
     cu = chi * u
     sy = level.c * y + apply_A(level, p)
-    su = chi * (level.G * cu + level.d * np.sum(p, axis=-1))
+    su = chi * (level.G * cu + level.dnode() * np.sum(p, axis=-1))
     sp = apply_A(level, y) + level.e * cu[:, :, None]
     return sy, su, sp
 
@@ -332,7 +340,7 @@ def rbgs_half_sweep(level: Level, x, f, colour: int, freeze_u: bool = False):
         yn, pn = local_solve_fixed_u(b_p, u[m], b_y, level.a[m], level.c, level.e)
         y[m], p[m] = yn, pn
         return y, u, p
-    yn, un, pn = local_solve(b_p, b_u, b_y, level.a[m], level.c, level.G, level.d, level.e)
+    yn, un, pn = local_solve(b_p, b_u, b_y, level.a[m], level.c, level.G, level.dnode()[m][:, None], level.e)
     # nodes without a control basis function: Eq. (14) with u_i = 0
     off = level.control()[m] == 0.0
     if np.any(off):
@@ -380,7 +388,7 @@ def lexgs_sweep(level: Level, x, f):
                 ui = 0.0
             else:
                 yi, ui, pi = local_solve(fy[iy, ix] + off_p, fu[iy, ix], fp[iy, ix] + off_y,
-                                         level.a[iy, ix], level.c, level.G, level.d, level.e)
+                                         level.a[iy, ix], level.c, level.G, level.dnode()[iy, ix], level.e)
             y[iy, ix], u[iy, ix], p[iy, ix] = yi, ui, pi
     return y, u, p
 
@@ -391,7 +399,7 @@ def jacobi_sweep(level: Level, x, f, theta: float, freeze_u: bool = False):
     if freeze_u:
         dy, dp = local_solve_fixed_u(ry, np.zeros_like(ru), rp, level.a, level.c, level.e)
         return x[0] + theta * dy, x[1], x[2] + theta * dp
-    dy, du, dp = local_solve(ry, ru, rp, level.a, level.c, level.G, level.d, level.e)
+    dy, du, dp = local_solve(ry, ru, rp, level.a, level.c, level.G, level.dnode()[:, :, None], level.e)
     off = level.control() == 0.0
     if np.any(off):   # nodes without a control basis function: Eq. (14) with a zero control update
         y0, p0 = local_solve_fixed_u(ry, np.zeros_like(ru), rp, level.a, level.c, level.e)
@@ -520,12 +528,13 @@ def coarse_solve(level: Level, f):
     fy, fu, fp = (np.asarray(b).reshape(m, -1) if np.asarray(b).ndim == 3 else np.asarray(b).reshape(m) for b in f)
     c, G, d, e = level.c, level.G, level.d, level.e
     Ainv = [np.linalg.inv(dense_A(level, j)) for j in range(N)]
+    dn = level.dnode().reshape(m)          # d_i, row i of the control system
     schur = G * np.eye(m)
     rhs = fu.copy()
     for j in range(N):
         A2 = Ainv[j] @ Ainv[j]
-        schur += d * c * e * A2
-        rhs -= d * (Ainv[j] @ fy[:, j] - c * (A2 @ fp[:, j]))
+        schur += (dn * c * e)[:, None] * A2
+        rhs -= dn * (Ainv[j] @ fy[:, j] - c * (A2 @ fp[:, j]))
     # local control: the control rows and unknowns exist only where chi = 1
     on = level.control().reshape(m) != 0.0
     u = np.zeros(m)
@@ -687,3 +696,114 @@ def fgmres(levels, f, opts: CycleOptions, tol: float = 1e-10, maxit: int = 100,
         beta = np.linalg.norm(r)
         hist[-1] = beta / fnorm
     return SolveResult(x=unpack(x, n, N), iters=total, relres=hist[-1], history=hist)
+
+
+# ---------------------------------------------------------------------------
+# L1 + box constrained problem: globalised semismooth Newton (Sec. 4, Alg. 2)
+# ---------------------------------------------------------------------------
+#
+# In the symmetric scaling used here the paper's adjoint is N times ours, so
+# E[p_paper] = sum_j zeta_j p_paper,j = sum_j p_j.  The Newton system of
+# Sec. 4 (its control row multiplied by nu) is the linear-quadratic system
+# with the control row's coupling d restricted to the active sets
+# (d_i = d chi_i, chi = indicator of I+ u I-) and right side (0, -nu M F, 0):
+#     (h^2/N) dy_j + A_j dp_j = 0
+#     nu h^2 du - h^2 chi sum_j dp_j = -nu h^2 F(u)
+#     A_j dy_j - h^2 du = 0.
+# Coarse grids take the active-set indicator at their coinciding fine node.
+
+
+def expected_adjoint(p) -> np.ndarray:
+    """E[p] of the paper's adjoint = sum over samples of ours (T u, Sec. 4)."""
+    return np.sum(np.asarray(p), axis=-1)
+
+
+def ssn_F(u, Tu, nu: float, beta: float, a: float, b: float) -> np.ndarray:
+    """The nonlinear optimality map F(u) of Sec. 4 (componentwise)."""
+    mx = lambda v: np.maximum(0.0, v)
+    mn = lambda v: np.minimum(0.0, v)
+    return u - (mx(Tu - beta) + mn(Tu + beta) - mx(Tu - beta - nu * b) - mn(Tu + beta - nu * a)) / nu
+
+
+def ssn_active(Tu, nu: float, beta: float, a: float, b: float) -> np.ndarray:
+    """Indicator of I+ = {0 <= Tu - beta <= nu b} union I- = {nu a <= Tu + beta <= 0}."""
+    ip = (Tu - beta >= 0.0) & (Tu - beta <= nu * b)
+    im = (Tu + beta <= 0.0) & (Tu + beta >= nu * a)
+    return (ip | im).astype(np.float64)
+
+
+def set_active(levels, chi_fine):
+    """dw on every grid: the active-set indicator, injected to coarse grids."""
+    w = np.asarray(chi_fine, dtype=np.float64)
+    for lev in levels:
+        lev.dw = w
+        w = w[1::2, 1::2]
+
+
+def pde_states(levels, u, yd, f=None):
+    """y_j = A_j^-1 M (f + u), p_j = A_j^-1 (M/N)(y_d - y_j) for every sample:
+    the frozen-control cycle solves these 2N PDEs for the given u (first line
+    of Alg. 2; dense solves on the grids used here)."""
+    lev = levels[0]
+    n, N, h = lev.n, lev.N, lev.h
+    m = n * n
+    src = (u if f is None else u + f) * h * h
+    y = np.zeros((n, n, N))
+    p = np.zeros((n, n, N))
+    for j in range(N):
+        A = dense_A(lev, j)
+        y[:, :, j] = np.linalg.solve(A, src.reshape(m)).reshape(n, n)
+        p[:, :, j] = np.linalg.solve(A, (h * h / N * (yd - y[:, :, j])).reshape(m)).reshape(n, n)
+    return y, p
+
+
+@dataclass
+class SSNResult:
+    u: np.ndarray
+    y: np.ndarray
+    p: np.ndarray
+    newton: int
+    inner: list
+    merit: list
+
+
+def semismooth_newton(levels, yd, beta: float, a: float, b: float, tol: float = 1e-9, inner_tol: float = 1e-10,
+                      sigma_ls: float = 1e-4, rho_ls: float = 0.5, maxit: int = 50, opts=None,
+                      inner: str = "cycle", u0=None) -> SSNResult:
+    """Algorithm 2: semismooth Newton on F(u) = 0 with a backtracking line
+    search on phi(u) = sqrt(F^T M F); each Newton system is solved by the
+    collective multigrid (stationary cycles or FGMRES) to inner_tol."""
+    lev = levels[0]
+    n, N, nu, h = lev.n, lev.N, lev.nu, lev.h
+    opts = opts or CycleOptions()
+    u = np.zeros((n, n)) if u0 is None else np.array(u0, dtype=np.float64)
+    y, p = pde_states(levels, u, yd)
+    phi = lambda F: float(h * np.linalg.norm(F))
+    Tu = expected_adjoint(p)
+    F = ssn_F(u, Tu, nu, beta, a, b)
+    merits = [phi(F)]
+    inners = []
+    k = 0
+    while merits[-1] > tol and k < maxit:
+        set_active(levels, ssn_active(Tu, nu, beta, a, b))
+        rhs = (np.zeros((n, n, N)), -nu * h * h * F, np.zeros((n, n, N)))
+        if inner == "fgmres":
+            res = fgmres(levels, rhs, opts, tol=inner_tol)
+        else:
+            res = solve_stationary(levels, rhs, opts, tol=inner_tol, maxit=200)
+        inners.append(res.iters)
+        dy, du, dp = res.x
+        gamma = 1.0
+        Tdp = expected_adjoint(dp)
+        while True:
+            Fn = ssn_F(u + gamma * du, Tu + gamma * Tdp, nu, beta, a, b)
+            if phi(Fn) - merits[-1] <= -sigma_ls * merits[-1] or gamma < 1e-8:
+                break
+            gamma *= rho_ls
+        u, y, p = u + gamma * du, y + gamma * dy, p + gamma * dp
+        Tu = Tu + gamma * Tdp
+        F = ssn_F(u, Tu, nu, beta, a, b)
+        merits.append(phi(F))
+        k += 1
+    set_active(levels, np.ones((n, n)))
+    return SSNResult(u=u, y=y, p=p, newton=k, inner=inners, merit=merits)
