@@ -252,6 +252,33 @@ cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method, double to
                      const double* fy, const double* fu, const double* fp,
                      double* y, double* u, double* p, cmg_stats* stats);
 
+/* L1 + box constrained problem (Sec. 4): minimise
+ *   1/2 E[||y(u) - y_d||^2] + nu/2 ||u||^2 + beta ||u||_1  over  a <= u <= b
+ * (the handle's field, samples and nu; forcing f = 0) by the globalised
+ * semismooth Newton method of Algorithm 2: F(u) = 0 with the optimality map
+ * of Sec. 4, active sets I+ u I-, each Newton system solved by cmg_solve
+ * (opts, method; stopping at inner_tol, at most 200 cycles / iterations)
+ * with the control row's coupling restricted to the active sets, a
+ * backtracking line search on phi(u) = sqrt(F' M F) (sigma = 1e-4,
+ * rho = 1/2), stop when phi <= tol or after maxit Newton steps.  Algorithm
+ * 2's initial states y0, p0 for u0 come from one solve of the same system
+ * with no control coupling.
+ * yd [n*n]: target at the finest grid's nodes (DEVICE, 16-byte aligned);
+ * u [n*n]: u0 in, control out; y, p [n*n][N]: states out (the adjoint in this
+ * library's symmetric scaling, 1/N times the paper's).  All DEVICE pointers.
+ * Requires a < 0 < b, beta >= 0, tol > 0, inner_tol > 0, opts->freeze_u = 0.
+ * The handle's operators are back to the linear-quadratic problem on return.
+ * Returns CMG_ERR_NOT_CONVERGED if phi > tol after maxit steps. */
+typedef struct {
+  int newton;        /* Newton steps taken */
+  int inner_total;   /* cycles / FGMRES iterations over all linear solves (initial states included) */
+  double merit0;     /* phi(u0) */
+  double merit;      /* phi at return */
+} cmg_ssn_stats;
+cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int method, double beta, double a, double b,
+                         double tol, double inner_tol, int maxit, const double* yd, double* y, double* u,
+                         double* p, cmg_ssn_stats* stats);
+
 /* ||(y,u,p)||_2 over all (2N+1) n_l^2 entries of a level vector, written to
  * *out_host.  Synchronises. */
 cmg_status cmg_norm(cmg_handle* h, int level, const double* y, const double* u,

@@ -57,6 +57,11 @@ class Stats(ctypes.Structure):
                 ("relres", ctypes.c_double)]
 
 
+class SSNStats(ctypes.Structure):
+    _fields_ = [("newton", ctypes.c_int), ("inner_total", ctypes.c_int), ("merit0", ctypes.c_double),
+                ("merit", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -98,6 +103,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                             + [ctypes.POINTER(Stats)]),
         "cmg_solve": (_I, [H, ctypes.POINTER(Cycle), _I, _D, _I, _I, _P, _P, _P, _P, _P, _P,
                            ctypes.POINTER(Stats)]),
+        "cmg_ssn_solve": (_I, [H, ctypes.POINTER(Cycle), _I, _D, _D, _D, _D, _D, _I, _P, _P, _P, _P,
+                               ctypes.POINTER(SSNStats)]),
     }
     for suf in ("", "_f32"):
         sig["cmg_residual" + suf] = (_I, [H, _I] + [_P] * 9)
@@ -283,6 +290,27 @@ class Hierarchy:
         if raise_on_fail:
             self._check(status)
         return st, status
+
+    def ssn_solve(self, opts: CycleOptions, yd, u, beta: float, a: float, b: float, method=METHOD_CYCLE,
+                  tol=1e-9, inner_tol=1e-10, maxit=50, raise_on_fail=True):
+        """L1 + box problem by semismooth Newton (cmg_ssn_solve).  yd [n*n],
+        u [n*n] (u0 in, control out) CUDA float64; returns (stats, status, y, p)."""
+        import torch
+
+        m = self.n * self.n
+        for t, name in ((yd, "yd"), (u, "u")):
+            if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float64 \
+                    or tuple(t.shape) != (m,) or not t.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous CUDA float64 tensor of shape ({m},)")
+        y = torch.empty(m, self.N, dtype=torch.float64, device=self.device)
+        p = torch.empty(m, self.N, dtype=torch.float64, device=self.device)
+        c = opts.c()
+        st = SSNStats()
+        status = self._lib.cmg_ssn_solve(self._h, ctypes.byref(c), method, beta, a, b, tol, inner_tol, maxit,
+                                         _ptr(yd), _ptr(y), _ptr(u), _ptr(p), ctypes.byref(st))
+        if raise_on_fail:
+            self._check(status)
+        return st, status, y, p
 
     def norm(self, level, v):
         import torch

@@ -38,6 +38,7 @@ struct Lev {
   double* r64[3] = {nullptr, nullptr, nullptr};
   float* x32[3] = {nullptr, nullptr, nullptr};
   float* d32[3] = {nullptr, nullptr, nullptr};   // finest grid: FP32 correction since the last refinement anchor
+  float* dw = nullptr;                   // per-node factor on d (1; semismooth Newton: active-set indicator)
   float* f32[3] = {nullptr, nullptr, nullptr};
   float* r32[3] = {nullptr, nullptr, nullptr};
 };
@@ -76,6 +77,7 @@ struct cmg_handle {
   double* hsc = nullptr;      // pinned host scalars
   double* part = nullptr;     // per-CTA partial sums of the fused refinement pass
   int part_cap = 0;
+  double* ssn = nullptr;      // semismooth Newton work vectors (allocated on first use)
   // FP32 refinement loop as a CUDA graph with a device-side while node
   cudaStream_t cap = nullptr;            // non-blocking stream used for capture
   cudaGraph_t ir_graph = nullptr;
@@ -149,13 +151,13 @@ template <>
 LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0], freeze_u,
-          nullptr, v.a64, v.ctl};
+          nullptr, v.a64, v.ctl, v.dw};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1], freeze_u,
-          v.isigma32, nullptr, v.ctl};
+          v.isigma32, nullptr, v.ctl, v.dw};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -199,7 +201,8 @@ cudaError_t setup_coefficients(cmg_handle* h) {
       const Lev& f = h->lv[l - 1];
       e = launch_coarse_faces32(f.n, P.N, f.kx32, f.ky32, v.kx32, v.ky32, h->stream);
     }
-    if (e == cudaSuccess) e = launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G, h->stream);
+    if (e == cudaSuccess)
+      e = launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G, h->stream, v.dw);
   }
   if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
@@ -224,12 +227,42 @@ cudaError_t ensure_fp64(cmg_handle* h) {
       const Lev& f = h->lv[l - 1];
       e = launch_coarse_faces64(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, h->stream);
     }
-    if (e == cudaSuccess) e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, v.G, h->stream);
+    if (e == cudaSuccess)
+      e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, v.G, h->stream, v.dw);
   }
   if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
   e = launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
   if (e == cudaSuccess) h->fp64_ready = true;
+  return e;
+}
+
+// After the finest grid's per-node factor on d changed: inject it to the
+// coarse grids and rebuild what depends on it (1/sigma on every grid, the
+// coarsest control Schur inverse), for the FP32 operators and, where built,
+// the FP64 ones.
+cudaError_t refresh_dw(cmg_handle* h) {
+  const cmg_problem& P = h->prob;
+  const bool nodal = P.coarse_coeff == CMG_COARSE_NODAL;
+  cudaError_t e = cudaSuccess;
+  for (int l = 1; l < h->L && e == cudaSuccess; ++l)
+    e = launch_inject32(h->lv[l - 1].n, h->lv[l - 1].dw, h->lv[l].dw, h->stream);
+  for (int l = 0; l < h->L && e == cudaSuccess; ++l) {
+    Lev& v = h->lv[l];
+    if (nodal || h->fp64_ready)
+      e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, v.G, h->stream, v.dw);
+    if (e != cudaSuccess) break;
+    e = nodal ? launch_scale_cast<double, float>(1.0, v.isigma, v.isigma32, v.nodes, h->stream)
+              : launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G, h->stream, v.dw);
+  }
+  if (e != cudaSuccess) return e;
+  const Lev& cl = h->lv[h->L - 1];
+  if (!nodal) {
+    const size_t cf = (size_t)cl.n * (cl.n + 1) * P.N;
+    e = launch_coarse_setup(h->coarse32, h->cface64, h->cface64 + cf, cl.c, cl.G, cl.d, cl.e, h->stream);
+  }
+  if (e == cudaSuccess && (nodal || h->fp64_ready))
+    e = launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
   return e;
 }
 
@@ -545,6 +578,9 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   h->coarse.N = P.N;
   h->coarse.blocks = (P.N + 31) / 32;
   h->coarse.ctl = h->lv[L - 1].ctl;
+  for (int l = 0; l < L; ++l) AL(h->lv[l].dw, h->lv[l].nodes);
+  for (int l = 0; l < L && e == cudaSuccess; ++l) e = launch_fill32((long)h->lv[l].nodes, 1.f, h->lv[l].dw, h->stream);
+  h->coarse.dw = h->lv[L - 1].dw;
   AL(h->coarse.Ainv, N * h->coarse.m * h->coarse.m);
   AL(h->coarse.Ainv32, N * h->coarse.m * h->coarse.m);
   AL(h->coarse.Minv, (size_t)h->coarse.m * h->coarse.m);
@@ -556,6 +592,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     h->coarse32.N = h->coarse.N;
     h->coarse32.blocks = h->coarse.blocks;
     h->coarse32.ctl = h->coarse.ctl;
+    h->coarse32.dw = h->coarse.dw;
     AL(h->coarse32.Ainv, N * h->coarse.m * h->coarse.m);
     AL(h->coarse32.Ainv32, N * h->coarse.m * h->coarse.m);
     AL(h->coarse32.Minv, (size_t)h->coarse.m * h->coarse.m);
@@ -1373,6 +1410,129 @@ extern "C" cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method
   if (opts->precision == CMG_FP64) CK(ensure_fp64(h));
   if (method == CMG_METHOD_CYCLE) return solve_cycle(h, *opts, tol, maxit, f, x, fnorm, st);
   return solve_fgmres(h, *opts, tol, maxit, restart, f, x, fnorm, st);
+}
+
+// L1 + box constrained problem: globalised semismooth Newton (Sec. 4,
+// Algorithm 2).  In the symmetric scaling E[p_paper] = sum_j p_j; each Newton
+// system is the linear-quadratic system with the control row's coupling
+// restricted to the active sets (per-node factor dw on d, injected to coarse
+// grids) and right side (0, -G F, 0), G = nu h^2, solved by cmg_solve.
+extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int method, double beta, double a,
+                                    double b, double tol, double inner_tol, int maxit, const double* yd, double* y,
+                                    double* u, double* p, cmg_ssn_stats* stats) {
+  if (!h) return CMG_ERR_INVALID_ARG;
+  cmg_status s = check_cycle(h, opts);
+  if (s != CMG_OK) return s;
+  if (!yd || !vec_ok(y, u, p) || (reinterpret_cast<uintptr_t>(yd) & 15))
+    return fail(h, CMG_ERR_INVALID_ARG, "null or misaligned vector");
+  if (!(a < 0.0 && b > 0.0 && beta >= 0.0 && tol > 0.0 && inner_tol > 0.0 && maxit >= 0) || !std::isfinite(a) ||
+      !std::isfinite(b) || !std::isfinite(beta))
+    return fail(h, CMG_ERR_INVALID_ARG, "need a < 0 < b, beta >= 0, tol > 0, inner_tol > 0, maxit >= 0");
+  if (opts->freeze_u) return fail(h, CMG_ERR_INVALID_ARG, "the Newton systems need the control update");
+  if (method != CMG_METHOD_CYCLE && method != CMG_METHOD_FGMRES) return fail(h, CMG_ERR_INVALID_ARG, "unknown method");
+  cmg_ssn_stats local{};
+  cmg_ssn_stats* st = stats ? stats : &local;
+  *st = cmg_ssn_stats{};
+  Lev& l0 = h->lv[0];
+  const int N = h->prob.N;
+  const size_t ny = l0.nodes * N, nu = l0.nodes;
+  const double nuc = h->prob.nu, hh = l0.h;
+  // work vectors, each segment on a 256-byte boundary
+  const size_t sy = pad32(ny), su = pad32(nu);
+  if (!h->ssn) {
+    void* q = nullptr;
+    CK(cudaMalloc(&q, (4 * sy + 6 * su) * sizeof(double) + su * sizeof(float)));
+    h->allocs.push_back(q);
+    h->ssn = static_cast<double*>(q);
+  }
+  double* fy = h->ssn;
+  double* fp = fy + sy;
+  double* dy = fp + sy;
+  double* dp = dy + sy;
+  double* fu = dp + sy;
+  double* du = fu + su;
+  double* Tu = du + su;
+  double* Tdp = Tu + su;
+  double* F = Tdp + su;
+  double* spare = F + su;
+  float* chi = reinterpret_cast<float*>(spare + su);
+  (void)spare;
+  const long nodes = (long)nu;
+  auto merit = [&](const double* uu, const double* duu, const double* tu, const double* tdp, double g, double* Fout,
+                   float* chio, double* out) -> cmg_status {
+    const int cnt = launch_ssn_map(nodes, uu, duu, tu, tdp, g, nuc, beta, a, b, Fout, chio, h->part, h->part_cap,
+                                   h->stream);
+    if (cnt < 0) return fail(h, CMG_ERR_CUDA, "optimality map launch failed");
+    CK(launch_finish_sum(h->part, cnt, h->dsc, h->stream));
+    CK(fetch(h, h->dsc, 1));
+    *out = hh * std::sqrt(h->hsc[0]);   // phi = sqrt(F' M F), M = h^2 I
+    return CMG_OK;
+  };
+  auto inner = [&](double* xy, double* xu, double* xp) -> cmg_status {
+    cmg_stats is{};
+    const cmg_status r = cmg_solve(h, opts, method, inner_tol, 200, 30, fy, fu, fp, xy, xu, xp, &is);
+    st->inner_total += is.iters;
+    return r == CMG_ERR_NOT_CONVERGED ? CMG_OK : r;   // at the rounding floor the last iterate is kept
+  };
+  cmg_status res = CMG_OK;
+  // (1) y0, p0 for u0: the Newton system's form with no control coupling
+  //     (dw = 0) and right side (c y_d, G u0, 0) leaves u = u0 and solves the
+  //     2N PDEs of Algorithm 2's first line
+  for (int l = 0; l < h->L && res == CMG_OK; ++l)
+    if (launch_fill32((long)h->lv[l].nodes, 0.f, h->lv[l].dw, h->stream) != cudaSuccess) res = CMG_ERR_CUDA;
+  if (res == CMG_OK && refresh_dw(h) != cudaSuccess) res = CMG_ERR_CUDA;
+  if (res == CMG_OK) {
+    CK(launch_spread(nodes, N, l0.c, yd, fy, h->stream));
+    CK(launch_scale64(nodes, l0.G, u, fu, h->stream));
+    CK(cudaMemsetAsync(fp, 0, ny * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(y, 0, ny * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(p, 0, ny * sizeof(double), h->stream));
+    res = inner(y, u, p);
+  }
+  double phi = 0.0;
+  if (res == CMG_OK) {
+    CK(launch_sum_samples(nodes, N, p, Tu, h->stream));
+    res = merit(u, nullptr, Tu, nullptr, 0.0, F, chi, &phi);
+    st->merit0 = phi;
+  }
+  const double sigma_ls = 1e-4, rho_ls = 0.5;
+  while (res == CMG_OK && phi > tol && st->newton < maxit) {
+    // (2) active sets -> dw on every grid; Newton system with right side (0, -G F, 0)
+    CK(cudaMemcpyAsync(l0.dw, chi, nu * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    if (refresh_dw(h) != cudaSuccess) { res = fail(h, CMG_ERR_CUDA, "active-set update failed"); break; }
+    CK(cudaMemsetAsync(fy, 0, ny * sizeof(double), h->stream));
+    CK(launch_scale64(nodes, -l0.G, F, fu, h->stream));
+    CK(cudaMemsetAsync(dy, 0, ny * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(du, 0, nu * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(dp, 0, ny * sizeof(double), h->stream));
+    res = inner(dy, du, dp);
+    if (res != CMG_OK) break;
+    // (3) backtracking line search on phi; T(u + g du) = Tu + g T(du) is linear
+    CK(launch_sum_samples(nodes, N, dp, Tdp, h->stream));
+    double g = 1.0, trial = 0.0;
+    for (int k = 0; k < 40; ++k) {
+      res = merit(u, du, Tu, Tdp, g, nullptr, nullptr, &trial);
+      if (res != CMG_OK || trial - phi <= -sigma_ls * phi) break;
+      g *= rho_ls;
+    }
+    if (res != CMG_OK) break;
+    // (4) x += g dx; active sets and phi at the new iterate
+    CK(launch_axpy64((long)ny, g, dy, y, h->stream));
+    CK(launch_axpy64(nodes, g, du, u, h->stream));
+    CK(launch_axpy64((long)ny, g, dp, p, h->stream));
+    CK(launch_axpy64(nodes, g, Tdp, Tu, h->stream));
+    res = merit(u, nullptr, Tu, nullptr, 0.0, F, chi, &phi);
+    ++st->newton;
+  }
+  st->merit = phi;
+  // back to the linear-quadratic operators (dw = 1)
+  for (int l = 0; l < h->L; ++l) (void)launch_fill32((long)h->lv[l].nodes, 1.f, h->lv[l].dw, h->stream);
+  const cudaError_t er = refresh_dw(h);
+  if (res != CMG_OK) return res;
+  if (er != cudaSuccess) return cuda_fail(h, er, "restoring the operators");
+  if (!std::isfinite(phi)) return fail(h, CMG_ERR_NONFINITE, "merit function is not finite");
+  if (phi > tol) return fail(h, CMG_ERR_NOT_CONVERGED, "maximum Newton iterations reached");
+  return CMG_OK;
 }
 
 // ============================================================================

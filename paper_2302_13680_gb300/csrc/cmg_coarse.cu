@@ -76,7 +76,7 @@ __global__ void coarse_inv_kernel(int n, int N, const double* __restrict__ kx, c
 // and columns of the other nodes are those of the identity (their right
 // sides are zero, so their u is zero).
 __global__ void coarse_schur_kernel(int m, int N, const double* __restrict__ Ainv, double G, double dce,
-                                    double* __restrict__ M, int n, CtlBox ctl) {
+                                    double* __restrict__ M, int n, CtlBox ctl, const float* __restrict__ dw) {
   __shared__ double red[128];
   const int r = blockIdx.x / m, c = blockIdx.x - (blockIdx.x / m) * m;
   double s = 0.0;
@@ -94,7 +94,8 @@ __global__ void coarse_schur_kernel(int m, int N, const double* __restrict__ Ain
   }
   if (threadIdx.x == 0) {
     const bool on = ctl.inside(r / n, r % n) && ctl.inside(c / n, c % n);
-    M[blockIdx.x] = on ? (r == c ? G : 0.0) + dce * red[0] : (r == c ? 1.0 : 0.0);
+    const double dcer = dw ? dce * (double)dw[r] : dce;   // row r couples through d_r
+    M[blockIdx.x] = on ? (r == c ? G : 0.0) + dcer * red[0] : (r == c ? 1.0 : 0.0);
   }
 }
 
@@ -179,12 +180,13 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_b(int m, int N, i
                                                                 const double* __restrict__ wz,
                                                                 const double* __restrict__ partial, T* __restrict__ y,
                                                                 T* __restrict__ u, T* __restrict__ p, int freeze_u,
-                                                                int n, CtlBox ctl) {
+                                                                int n, CtlBox ctl, const float* __restrict__ dw) {
   __shared__ double rhs[MM], us[MM];
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * m + r];
-    rhs[r] = ctl.inside(r / n, r % n) ? (double)fu[r] - d * s : 0.0;   // control rows only at control nodes
+    const double dr = dw ? d * (double)dw[r] : d;
+    rhs[r] = ctl.inside(r / n, r % n) ? (double)fu[r] - dr * s : 0.0;   // control rows only at control nodes
   }
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
@@ -244,7 +246,8 @@ template <typename T, typename C>
 __global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int N, const C* __restrict__ Ainv,
                                                                      const double* __restrict__ Minv, double c,
                                                                      double d, double e, Vec3c<T> f, Vec3<T> x,
-                                                                     int freeze_u, int nside, CtlBox ctl) {
+                                                                     int freeze_u, int nside, CtlBox ctl,
+                                                                     const float* __restrict__ dw) {
   pdl_enter();
   extern __shared__ __align__(16) double sm[];
   const int mm = m * m, nm = N * m;
@@ -287,7 +290,8 @@ __global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int
   for (int r = tid; r < m; r += nt) {
     double q = 0.0;
     for (int j = 0; j < N; ++j) q += (double)bp[j * m + r];
-    rhs[r] = ctl.inside(r / nside, r % nside) ? (double)f.u[r] - d * q : 0.0;   // control rows only at control nodes
+    const double dr = dw ? d * (double)dw[r] : d;   // d_r (active-set factor)
+    rhs[r] = ctl.inside(r / nside, r % nside) ? (double)f.u[r] - dr * q : 0.0;   // control rows only at control nodes
   }
   __syncthreads();
   for (int r = tid; r < m; r += nt) {
@@ -340,14 +344,14 @@ cudaError_t coarse_solve_mm(const CoarseData& C, double c, double d, double e, V
     }
     const cudaError_t ek = launch_k(coarse_solve_cta<T, Cm>, dim3(1), dim3(kCoarseCtaThreads),
                                     coarse_cta_smem<Cm>(C.N, C.m), s, C.m, C.N, ainv, (const double*)C.Minv, c, d, e,
-                                    f, x, freeze_u, C.n, C.ctl);
+                                    f, x, freeze_u, C.n, C.ctl, C.dw);
     count_launches(1);
     return ek != cudaSuccess ? ek : cudaGetLastError();
   }
   const int nblk = (C.N + kCoarseThreads - 1) / kCoarseThreads;
   coarse_solve_a<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, C.Ainv, c, f.y, f.p, C.wz, C.partial);
   coarse_solve_b<T, MM><<<nblk, kCoarseThreads, 0, s>>>(C.m, C.N, nblk, C.Ainv, C.Minv, c, d, e, f.u, C.wz,
-                                                         C.partial, x.y, x.u, x.p, freeze_u, C.n, C.ctl);
+                                                         C.partial, x.y, x.u, x.p, freeze_u, C.n, C.ctl, C.dw);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -368,7 +372,7 @@ cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const dou
   coarse_inv_kernel<<<C.N, 64, 0, s>>>(C.n, C.N, kx, ky, C.Ainv);
   // M is staged in the wz scratch (2 N m >= m^2 is not guaranteed, so use partial-free space):
   double* M = C.wz;   // wz holds at least max(2 N m, m m) doubles (allocated so)
-  coarse_schur_kernel<<<C.m * C.m, 128, 0, s>>>(C.m, C.N, C.Ainv, G, d * c * e, M, C.n, C.ctl);
+  coarse_schur_kernel<<<C.m * C.m, 128, 0, s>>>(C.m, C.N, C.Ainv, G, d * c * e, M, C.n, C.ctl, C.dw);
   invert_kernel<<<1, 256, 0, s>>>(C.m, M, C.Minv);
   count_launches(3);
   if (C.Ainv32) {

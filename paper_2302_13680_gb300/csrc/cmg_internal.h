@@ -63,7 +63,14 @@ struct LevelView {
   const float* isigma32;  // 1/sigma rounded to FP32 (FP32 path: the control update runs in FP32)
   const double* a64;      // diag(A_j) = sum of the four faces per node-sample (FP64, finest grid only, else null)
   CtlBox ctl{};           // nodes with a control basis function (elsewhere u_i = 0, no control row)
+  const float* dw = nullptr;   // per-node factor on d (semismooth Newton active sets); null = 1
 };
+
+// d_i = d * dw[node] (the control row's coupling to the adjoint at node i).
+template <typename T>
+__host__ __device__ inline double d_of(const LevelView<T>& L, long node) {
+  return L.dw ? L.d * (double)L.dw[node] : L.d;
+}
 
 // Sample mapping of a node's N samples: lanes-per-node (power of two <= 32),
 // vector width V (elements per 16-byte or narrower load), chunks per lane.
@@ -85,6 +92,7 @@ SampleMap choose_map(int N, int elem_bytes, long items, int spl_target = 0);
 struct CoarseData {
   int n, m, N;
   CtlBox ctl;        // control nodes of the coarsest grid (the control Schur system lives on them)
+  const float* dw;   // per-node factor on d of the coarsest grid (null = 1)
   double* Ainv;      // [N][m][m]
   float* Ainv32;     // [N][m][m] FP32 copy for the FP32 cycle's coarse solve (may be null)
   double* Minv;      // [m][m]   inverse of the control Schur system
@@ -152,6 +160,21 @@ cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s
                             Vec3<T> zx = Vec3<T>{nullptr, nullptr, nullptr}, int colour0 = 0);
 template <typename T>
 cudaError_t launch_prolong_add(int nf, int N, Vec3c<T> e, Vec3<T> x, cudaStream_t s, CtlBox ctl = CtlBox{});
+
+// ---- semismooth Newton for the L1 + box problem (cmg_ssn.cu) ----
+// out[i] = sum_j p[i][j] (FP64, fixed order)
+cudaError_t launch_sum_samples(long nodes, int N, const double* p, double* out, cudaStream_t s);
+// F = the optimality map of Sec. 4 at (u + g du, Tu + g Tdp) (du, Tdp may be
+// null), chi = the active-set indicator there (may be null), per-CTA
+// partial sums of F^2; returns the number of partials (<= max_partials) or -1.
+int launch_ssn_map(long nodes, const double* u, const double* du, const double* Tu, const double* Tdp, double g,
+                   double nu, double beta, double a, double b, double* F, float* chi, double* partial,
+                   int max_partials, cudaStream_t s);
+cudaError_t launch_axpy64(long n, double g, const double* x, double* y, cudaStream_t s);       // y += g x
+cudaError_t launch_scale64(long n, double sc, const double* x, double* y, cudaStream_t s);     // y = sc x
+cudaError_t launch_spread(long nodes, int N, double c, const double* yd, double* fy, cudaStream_t s);  // fy[i][j] = c yd[i]
+cudaError_t launch_fill32(long n, float v, float* x, cudaStream_t s);
+cudaError_t launch_inject32(int nf, const float* fine, float* coarse, cudaStream_t s);  // coarse = fine at coinciding nodes
 
 // ---- cluster-resident coarse-grid cycle (cmg_tail.cuh, cmg_tail_f32/f64.cu) ----
 constexpr int kTailMax = 8;        // grids handled inside one cluster launch
@@ -236,13 +259,13 @@ cudaError_t launch_coarse_level_setup(int nf, int N, const double* kxf, const do
 cudaError_t launch_field_faces(int n, int N, int K, double amp, const double* xi, double* kap, double* kx64,
                                double* ky64, float* kx32, float* ky32, cudaStream_t s);
 cudaError_t launch_diag64(int n, int N, const double* kx64, const double* ky64, double* inva, double* isigma,
-                          double dce, double G, cudaStream_t s);
+                          double dce, double G, cudaStream_t s, const float* dw = nullptr);
 cudaError_t launch_coarse_faces64(int nf, int N, const double* kxf, const double* kyf, double* kx64, double* ky64,
                                   cudaStream_t s);
 cudaError_t launch_coarse_faces32(int nf, int N, const float* kxf, const float* kyf, float* kx32, float* ky32,
                                   cudaStream_t s);
 cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double dce, double G,
-                          cudaStream_t s);
+                          cudaStream_t s, const float* dw = nullptr);
 
 // ---- vector kernels (cmg_blas.cu) ----
 constexpr int kRedBlocks = 304;    // fixed partial count: deterministic reductions

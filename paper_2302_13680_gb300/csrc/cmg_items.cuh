@@ -164,7 +164,7 @@ __device__ __forceinline__ void residual_item(const LevelView<T>& L, const Vec3c
   const A psum = group_sum((A)pacc, lpn);
   if (valid && lane == 0) {
     if (ctl) {
-      const A su = (A)L.G * (A)ld1<T, CG>(x.u + node) + (A)L.d * psum;   // control row: G u + d sum_j p_j
+      const A su = (A)L.G * (A)ld1<T, CG>(x.u + node) + (A)d_of(L, node) * psum;   // control row: G u + d_i sum_j p_j
       r.u[node] = (T)(apply ? su : (A)ld1<T, CG>(f.u + node) - su);
     } else {
       r.u[node] = T(0);
@@ -281,7 +281,7 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
     // rows are solved (Eq. (14) with u_i given instead of zero); a node
     // without a control basis function (local control) takes Eq. (14) with
     // u_i = 0
-    const A uu = L.freeze_u ? bu : (L.ctl.inside(iy, ix) ? (bu + (A)L.d * tsum) * isg : A(0));
+    const A uu = L.freeze_u ? bu : (L.ctl.inside(iy, ix) ? (bu + (A)d_of(L, node) * tsum) * isg : A(0));
     if (lane == 0 && !L.freeze_u) x.u[node] = (T)uu;
     const T uT = (T)uu, e = (T)L.e;
 #pragma unroll
@@ -339,7 +339,7 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   }
   const A tsum = group_sum((A)tacc, lpn);
   if (valid) {
-    const A du = (L.freeze_u || !L.ctl.inside(iy, ix)) ? A(0) : (ru + (A)L.d * tsum) * isg;
+    const A du = (L.freeze_u || !L.ctl.inside(iy, ix)) ? A(0) : (ru + (A)d_of(L, node) * tsum) * isg;
     if (lane == 0) x.u[node] = (T)(xu + (A)theta * du);
     const T duT = (T)du, e = (T)L.e, th = (T)theta;
 #pragma unroll
@@ -583,7 +583,7 @@ __device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, 
   }
   const double psum = group_sum(pacc, lpn);
   if (valid && lane == 0) {
-    const float ru = ctl ? (float)((f.u[node] - (L.G * x.u[node] + L.d * psum)) * s) : 0.f;
+    const float ru = ctl ? (float)((f.u[node] - (L.G * x.u[node] + d_of(L, node) * psum)) * s) : 0.f;
     r.u[node] = ru;
     sq = fmaf(ru, ru, sq);
   }

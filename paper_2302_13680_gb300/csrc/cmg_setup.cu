@@ -75,7 +75,8 @@ __global__ void faces_kernel(int n, int N, const double* __restrict__ kap, doubl
 // (Schur denominator), its sum over samples reduced by one warp per node in
 // a fixed order.
 __global__ void diag_kernel(int n, int N, const double* __restrict__ kx, const double* __restrict__ ky,
-                            double* __restrict__ inva, double* __restrict__ isigma, double dce, double G) {
+                            double* __restrict__ inva, double* __restrict__ isigma, double dce, double G,
+                            const float* __restrict__ dw = nullptr) {
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (long)n * n) return;
@@ -90,7 +91,7 @@ __global__ void diag_kernel(int n, int N, const double* __restrict__ kx, const d
     s += ia * ia;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) isigma[warp] = 1.0 / (G + dce * s);
+  if (lane == 0) isigma[warp] = 1.0 / (G + (dw ? dce * (double)dw[warp] : dce) * s);   // d_i = d dw_i
 }
 
 // Coarse faces averaged from the next finer grid (nf = 2 nc + 1): a coarse
@@ -165,7 +166,7 @@ __global__ void coarse_faces32_kernel(int nf, int N, const float* __restrict__ k
 // isigma32[node] = 1 / (G + dce sum_j 1/a_j^2) from the FP32 faces (sum in
 // FP32 over a warp per node, the quotient in FP64).
 __global__ void diag32_kernel(int n, int N, const float* __restrict__ kx, const float* __restrict__ ky,
-                              float* __restrict__ isigma32, double dce, double G) {
+                              float* __restrict__ isigma32, double dce, double G, const float* __restrict__ dw) {
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (long)n * n) return;
@@ -178,7 +179,7 @@ __global__ void diag32_kernel(int n, int N, const float* __restrict__ kx, const 
     s += ia * ia;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) isigma32[warp] = (float)(1.0 / (G + dce * (double)s));
+  if (lane == 0) isigma32[warp] = (float)(1.0 / (G + (dw ? dce * (double)dw[warp] : dce) * (double)s));
 }
 
 inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
@@ -264,8 +265,8 @@ cudaError_t launch_field_faces(int n, int N, int K, double amp, const double* xi
 }
 
 cudaError_t launch_diag64(int n, int N, const double* kx64, const double* ky64, double* inva, double* isigma,
-                          double dce, double G, cudaStream_t s) {
-  diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, isigma, dce, G);
+                          double dce, double G, cudaStream_t s, const float* dw) {
+  diag_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx64, ky64, inva, isigma, dce, G, dw);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -288,8 +289,8 @@ cudaError_t launch_coarse_faces32(int nf, int N, const float* kxf, const float* 
 }
 
 cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double dce, double G,
-                          cudaStream_t s) {
-  diag32_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx32, ky32, isigma32, dce, G);
+                          cudaStream_t s, const float* dw) {
+  diag32_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx32, ky32, isigma32, dce, G, dw);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) rbgs_staged_kernel(LevelView
     const float tsum = group_sum(tacc, lpn);
     if (!valid) return;
     const float bu = ws[(b * 2 + 0) * 32 + lane], isg = ws[(b * 2 + 1) * 32 + lane];
-    const float uu = L.freeze_u ? bu : (L.ctl.inside(iy, ix) ? (bu + (float)L.d * tsum) * isg : 0.f);
+    const float uu = L.freeze_u ? bu : (L.ctl.inside(iy, ix) ? (bu + (float)d_of(L, (long)node) * tsum) * isg : 0.f);
     if (ln == 0 && !L.freeze_u) x.u[node] = uu;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {

@@ -89,7 +89,8 @@ __device__ void coarse_cta(const TailParams<T>& P, const Vec3<T>& x, const Vec3<
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][r];
-    rhs[r] = cl.ctl.inside(r / cl.n, r % cl.n) ? (double)ld1<T, true>(f.u + r) - d * s : 0.0;
+    const double dr = cl.dw ? d * (double)cl.dw[r] : d;   // d_i of the coarsest grid's row r
+    rhs[r] = cl.ctl.inside(r / cl.n, r % cl.n) ? (double)ld1<T, true>(f.u + r) - dr * s : 0.0;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
