@@ -704,12 +704,16 @@ def fgmres(levels, f, opts: CycleOptions, tol: float = 1e-10, maxit: int = 100,
 #
 # In the symmetric scaling used here the paper's adjoint is N times ours, so
 # E[p_paper] = sum_j zeta_j p_paper,j = sum_j p_j.  The Newton system of
-# Sec. 4 (its control row multiplied by nu) is the linear-quadratic system
-# with the control row's coupling d restricted to the active sets
-# (d_i = d chi_i, chi = indicator of I+ u I-) and right side (0, -nu M F, 0):
+# Sec. 4 is the linear-quadratic system with the control row as the paper
+# writes it, M du - M H sum_j zeta_j dp_paper,j = -M F, i.e. G = h^2 (nu h^2
+# divided by nu) and the coupling d / nu restricted to the active sets
+# (d_i = (d / nu) chi_i, chi = indicator of I+ u I-), right side (0, -M F, 0):
 #     (h^2/N) dy_j + A_j dp_j = 0
-#     nu h^2 du - h^2 chi sum_j dp_j = -nu h^2 F(u)
+#     h^2 du - (h^2/nu) chi sum_j dp_j = -h^2 F(u)
 #     A_j dy_j - h^2 du = 0.
+# (The same system with its control row multiplied by nu gives the same
+# iterates, Eq. (13) being invariant to that row's scale, but a right side
+# nu times smaller, whose relative residual stalls at the rounding floor.)
 # Coarse grids take the active-set indicator at their coinciding fine node.
 
 
@@ -732,12 +736,20 @@ def ssn_active(Tu, nu: float, beta: float, a: float, b: float) -> np.ndarray:
     return (ip | im).astype(np.float64)
 
 
-def set_active(levels, chi_fine):
-    """dw on every grid: the active-set indicator, injected to coarse grids."""
-    w = np.asarray(chi_fine, dtype=np.float64)
+def set_active(levels, chi_fine, scale: float = 1.0):
+    """dw on every grid: scale times the active-set indicator, injected to
+    coarse grids."""
+    w = np.asarray(chi_fine, dtype=np.float64) * scale
     for lev in levels:
         lev.dw = w
         w = w[1::2, 1::2]
+
+
+def newton_form(levels, on: bool):
+    """Switch every grid's control row between the linear-quadratic form
+    (G = nu h^2) and the Newton systems' form (G = h^2)."""
+    for lev in levels:
+        lev.G = lev.h * lev.h * (1.0 if on else lev.nu)
 
 
 def pde_states(levels, u, yd, f=None):
@@ -784,9 +796,10 @@ def semismooth_newton(levels, yd, beta: float, a: float, b: float, tol: float = 
     merits = [phi(F)]
     inners = []
     k = 0
+    newton_form(levels, True)
     while merits[-1] > tol and k < maxit:
-        set_active(levels, ssn_active(Tu, nu, beta, a, b))
-        rhs = (np.zeros((n, n, N)), -nu * h * h * F, np.zeros((n, n, N)))
+        set_active(levels, ssn_active(Tu, nu, beta, a, b), 1.0 / nu)
+        rhs = (np.zeros((n, n, N)), -h * h * F, np.zeros((n, n, N)))
         if inner == "fgmres":
             res = fgmres(levels, rhs, opts, tol=inner_tol)
         else:
@@ -805,5 +818,6 @@ def semismooth_newton(levels, yd, beta: float, a: float, b: float, tol: float = 
         F = ssn_F(u, Tu, nu, beta, a, b)
         merits.append(phi(F))
         k += 1
+    newton_form(levels, False)
     set_active(levels, np.ones((n, n)))
     return SSNResult(u=u, y=y, p=p, newton=k, inner=inners, merit=merits)

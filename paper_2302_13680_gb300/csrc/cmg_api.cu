@@ -78,11 +78,13 @@ struct cmg_handle {
   double* part = nullptr;     // per-CTA partial sums of the fused refinement pass
   int part_cap = 0;
   double* ssn = nullptr;      // semismooth Newton work vectors (allocated on first use)
+  double gscale = 1.0;        // factor on every grid's G (1/nu: the Newton systems' control row form)
   // FP32 refinement loop as a CUDA graph with a device-side while node
   cudaStream_t cap = nullptr;            // non-blocking stream used for capture
   cudaGraph_t ir_graph = nullptr;
   cudaGraphExec_t ir_exec = nullptr;
   const void* ir_key[6] = {};
+  double ir_gscale = 1.0;                // gscale the captured loop was built with (its kernels hold G by value)
   cmg_cycle ir_opts{};
   double* ir_state = nullptr;            // device refinement state, see IrState
   double anchor_drop = 1e-3;             // anchor policy of FP32 refinement (see IrState)
@@ -150,14 +152,14 @@ LevelView<T> view(const cmg_handle* h, int l, int freeze_u = 0);
 template <>
 LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[0], freeze_u,
-          nullptr, v.a64, v.ctl, v.dw};
+  return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G * h->gscale, v.d, v.e,
+          v.spl_target[0], freeze_u, nullptr, v.a64, v.ctl, v.dw};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G, v.d, v.e, v.spl_target[1], freeze_u,
-          v.isigma32, nullptr, v.ctl, v.dw};
+  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G * h->gscale, v.d, v.e,
+          v.spl_target[1], freeze_u, v.isigma32, nullptr, v.ctl, v.dw};
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -202,7 +204,7 @@ cudaError_t setup_coefficients(cmg_handle* h) {
       e = launch_coarse_faces32(f.n, P.N, f.kx32, f.ky32, v.kx32, v.ky32, h->stream);
     }
     if (e == cudaSuccess)
-      e = launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G, h->stream, v.dw);
+      e = launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G * h->gscale, h->stream, v.dw);
   }
   if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
@@ -210,7 +212,8 @@ cudaError_t setup_coefficients(cmg_handle* h) {
   e = launch_scale_cast<float, double>(1.0, cl.kx32, h->cface64, cf, h->stream);
   if (e == cudaSuccess) e = launch_scale_cast<float, double>(1.0, cl.ky32, h->cface64 + cf, cf, h->stream);
   if (e != cudaSuccess) return e;
-  return launch_coarse_setup(h->coarse32, h->cface64, h->cface64 + cf, cl.c, cl.G, cl.d, cl.e, h->stream);
+  return launch_coarse_setup(h->coarse32, h->cface64, h->cface64 + cf, cl.c, cl.G * h->gscale, cl.d, cl.e,
+                             h->stream);
 }
 
 // The FP64 operators below the finest faces (1/diag, 1/sigma on every grid,
@@ -228,11 +231,12 @@ cudaError_t ensure_fp64(cmg_handle* h) {
       e = launch_coarse_faces64(f.n, P.N, f.kx64, f.ky64, v.kx64, v.ky64, h->stream);
     }
     if (e == cudaSuccess)
-      e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, v.G, h->stream, v.dw);
+      e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, v.G * h->gscale, h->stream,
+                        v.dw);
   }
   if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
-  e = launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
+  e = launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G * h->gscale, cl.d, cl.e, h->stream);
   if (e == cudaSuccess) h->fp64_ready = true;
   return e;
 }
@@ -249,20 +253,22 @@ cudaError_t refresh_dw(cmg_handle* h) {
     e = launch_inject32(h->lv[l - 1].n, h->lv[l - 1].dw, h->lv[l].dw, h->stream);
   for (int l = 0; l < h->L && e == cudaSuccess; ++l) {
     Lev& v = h->lv[l];
+    const double G = v.G * h->gscale;
     if (nodal || h->fp64_ready)
-      e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, v.G, h->stream, v.dw);
+      e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, G, h->stream, v.dw);
     if (e != cudaSuccess) break;
     e = nodal ? launch_scale_cast<double, float>(1.0, v.isigma, v.isigma32, v.nodes, h->stream)
-              : launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G, h->stream, v.dw);
+              : launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, G, h->stream, v.dw);
   }
   if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
   if (!nodal) {
     const size_t cf = (size_t)cl.n * (cl.n + 1) * P.N;
-    e = launch_coarse_setup(h->coarse32, h->cface64, h->cface64 + cf, cl.c, cl.G, cl.d, cl.e, h->stream);
+    e = launch_coarse_setup(h->coarse32, h->cface64, h->cface64 + cf, cl.c, cl.G * h->gscale, cl.d, cl.e,
+                            h->stream);
   }
   if (e == cudaSuccess && (nodal || h->fp64_ready))
-    e = launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
+    e = launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G * h->gscale, cl.d, cl.e, h->stream);
   return e;
 }
 
@@ -1147,7 +1153,8 @@ void count_replay(const cmg_handle* h, int iterations) {
 // pointers or the cycle options change.
 cmg_status build_ir_graph(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3<double> x) {
   const void* key[6] = {f.y, f.u, f.p, x.y, x.u, x.p};
-  if (h->ir_exec && same_cycle(h->ir_opts, o) && std::equal(key, key + 6, h->ir_key)) return CMG_OK;
+  if (h->ir_exec && same_cycle(h->ir_opts, o) && std::equal(key, key + 6, h->ir_key) && h->ir_gscale == h->gscale)
+    return CMG_OK;
   if (h->ir_exec) {
     CK(cudaGraphExecDestroy(h->ir_exec));
     h->ir_exec = nullptr;
@@ -1165,6 +1172,7 @@ cmg_status build_ir_graph(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Ve
   CK(cudaGraphInstantiate(&ex, g, 0));
   h->ir_exec = ex;
   h->ir_opts = o;
+  h->ir_gscale = h->gscale;
   std::copy(key, key + 6, h->ir_key);
   return CMG_OK;
 }
@@ -1414,9 +1422,12 @@ extern "C" cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method
 
 // L1 + box constrained problem: globalised semismooth Newton (Sec. 4,
 // Algorithm 2).  In the symmetric scaling E[p_paper] = sum_j p_j; each Newton
-// system is the linear-quadratic system with the control row's coupling
-// restricted to the active sets (per-node factor dw on d, injected to coarse
-// grids) and right side (0, -G F, 0), G = nu h^2, solved by cmg_solve.
+// system is the linear-quadratic system with the control row as the paper
+// writes it (G = h^2, coupling d / nu restricted to the active sets: per-node
+// factor dw = chi / nu on d, injected to coarse grids) and right side
+// (0, -h^2 F, 0), solved by cmg_solve.  (Multiplying that row by nu gives
+// the same iterates but a right side nu times smaller, whose relative
+// residual stalls at the rounding floor.)
 extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int method, double beta, double a,
                                     double b, double tol, double inner_tol, int maxit, const double* yd, double* y,
                                     double* u, double* p, cmg_ssn_stats* stats) {
@@ -1476,14 +1487,16 @@ extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int me
   };
   cmg_status res = CMG_OK;
   // (1) y0, p0 for u0: the Newton system's form with no control coupling
-  //     (dw = 0) and right side (c y_d, G u0, 0) leaves u = u0 and solves the
-  //     2N PDEs of Algorithm 2's first line
+  //     (dw = 0) and right side (c y_d, h^2 u0, 0) leaves u = u0 and solves
+  //     the 2N PDEs of Algorithm 2's first line
+  h->gscale = 1.0 / nuc;
+  const double hh2 = hh * hh;
   for (int l = 0; l < h->L && res == CMG_OK; ++l)
     if (launch_fill32((long)h->lv[l].nodes, 0.f, h->lv[l].dw, h->stream) != cudaSuccess) res = CMG_ERR_CUDA;
   if (res == CMG_OK && refresh_dw(h) != cudaSuccess) res = CMG_ERR_CUDA;
   if (res == CMG_OK) {
     CK(launch_spread(nodes, N, l0.c, yd, fy, h->stream));
-    CK(launch_scale64(nodes, l0.G, u, fu, h->stream));
+    CK(launch_scale64(nodes, hh2, u, fu, h->stream));
     CK(cudaMemsetAsync(fp, 0, ny * sizeof(double), h->stream));
     CK(cudaMemsetAsync(y, 0, ny * sizeof(double), h->stream));
     CK(cudaMemsetAsync(p, 0, ny * sizeof(double), h->stream));
@@ -1497,11 +1510,11 @@ extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int me
   }
   const double sigma_ls = 1e-4, rho_ls = 0.5;
   while (res == CMG_OK && phi > tol && st->newton < maxit) {
-    // (2) active sets -> dw on every grid; Newton system with right side (0, -G F, 0)
-    CK(cudaMemcpyAsync(l0.dw, chi, nu * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    // (2) active sets -> dw = chi / nu on every grid; right side (0, -h^2 F, 0)
+    CK(launch_scale32(nodes, (float)(1.0 / nuc), chi, l0.dw, h->stream));
     if (refresh_dw(h) != cudaSuccess) { res = fail(h, CMG_ERR_CUDA, "active-set update failed"); break; }
     CK(cudaMemsetAsync(fy, 0, ny * sizeof(double), h->stream));
-    CK(launch_scale64(nodes, -l0.G, F, fu, h->stream));
+    CK(launch_scale64(nodes, -hh2, F, fu, h->stream));
     CK(cudaMemsetAsync(dy, 0, ny * sizeof(double), h->stream));
     CK(cudaMemsetAsync(du, 0, nu * sizeof(double), h->stream));
     CK(cudaMemsetAsync(dp, 0, ny * sizeof(double), h->stream));
@@ -1525,7 +1538,8 @@ extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int me
     ++st->newton;
   }
   st->merit = phi;
-  // back to the linear-quadratic operators (dw = 1)
+  // back to the linear-quadratic operators (G = nu h^2, dw = 1)
+  h->gscale = 1.0;
   for (int l = 0; l < h->L; ++l) (void)launch_fill32((long)h->lv[l].nodes, 1.f, h->lv[l].dw, h->stream);
   const cudaError_t er = refresh_dw(h);
   if (res != CMG_OK) return res;

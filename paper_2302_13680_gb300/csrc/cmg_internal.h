@@ -174,6 +174,7 @@ cudaError_t launch_axpy64(long n, double g, const double* x, double* y, cudaStre
 cudaError_t launch_scale64(long n, double sc, const double* x, double* y, cudaStream_t s);     // y = sc x
 cudaError_t launch_spread(long nodes, int N, double c, const double* yd, double* fy, cudaStream_t s);  // fy[i][j] = c yd[i]
 cudaError_t launch_fill32(long n, float v, float* x, cudaStream_t s);
+cudaError_t launch_scale32(long n, float sc, const float* x, float* y, cudaStream_t s);    // y = sc x
 cudaError_t launch_inject32(int nf, const float* fine, float* coarse, cudaStream_t s);  // coarse = fine at coinciding nodes
 
 // ---- cluster-resident coarse-grid cycle (cmg_tail.cuh, cmg_tail_f32/f64.cu) ----

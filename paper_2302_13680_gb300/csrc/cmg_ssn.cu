@@ -78,6 +78,10 @@ __global__ void spread_kernel(long nodes, int N, double c, const double* __restr
     fy[t] = c * yd[t / N];
 }
 
+__global__ void scale32_kernel(long n, float sc, const float* __restrict__ x, float* __restrict__ y) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) y[i] = sc * x[i];
+}
+
 __global__ void fill32_kernel(long n, float v, float* __restrict__ x) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) x[i] = v;
 }
@@ -131,6 +135,12 @@ cudaError_t launch_scale64(long n, double sc, const double* x, double* y, cudaSt
 
 cudaError_t launch_spread(long nodes, int N, double c, const double* yd, double* fy, cudaStream_t s) {
   spread_kernel<<<grid_of(nodes * N), kSsnBlock, 0, s>>>(nodes, N, c, yd, fy);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale32(long n, float sc, const float* x, float* y, cudaStream_t s) {
+  scale32_kernel<<<grid_of(n), kSsnBlock, 0, s>>>(n, sc, x, y);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -42,6 +42,10 @@ def test_semismooth_newton_matches_oracle(P, case, form):
     try:
         prec = P.FP32 if form == "fp32-ir" else P.FP64
         method = P.METHOD_FGMRES if form == "fp64-fgmres" else P.METHOD_CYCLE
+        # a linear-quadratic solve first: its captured refinement loop must not
+        # be reused for the Newton systems (their control row differs)
+        f = H.rhs(torch.tensor(inputs.target_sinsin(n).reshape(-1), device="cuda"))
+        H.solve(P.CycleOptions(precision=prec), f, H.zeros(0), tol=1e-10)
         u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
         ydd = torch.tensor(yd.reshape(-1), dtype=torch.float64, device="cuda")
         st, status, y, p = H.ssn_solve(P.CycleOptions(precision=prec), ydd, u, beta, a, b, method=method)
