@@ -79,6 +79,7 @@ struct cmg_handle {
   int part_cap = 0;
   double* ssn = nullptr;      // semismooth Newton work vectors (allocated on first use)
   double gscale = 1.0;        // factor on every grid's G (1/nu: the Newton systems' control row form)
+  bool dw_on = false;         // the per-node factors on d are in use (else the views carry none: factor 1)
   // FP32 refinement loop as a CUDA graph with a device-side while node
   cudaStream_t cap = nullptr;            // non-blocking stream used for capture
   cudaGraph_t ir_graph = nullptr;
@@ -153,13 +154,22 @@ template <>
 LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G * h->gscale, v.d, v.e,
-          v.spl_target[0], freeze_u, nullptr, v.a64, v.ctl, v.dw};
+          v.spl_target[0], freeze_u, nullptr, v.a64, v.ctl, h->dw_on ? v.dw : nullptr};
 }
 template <>
 LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G * h->gscale, v.d, v.e,
-          v.spl_target[1], freeze_u, v.isigma32, nullptr, v.ctl, v.dw};
+          v.spl_target[1], freeze_u, v.isigma32, nullptr, v.ctl, h->dw_on ? v.dw : nullptr};
+}
+
+// The coarsest-grid data for a cycle of precision T; its per-node factor on d
+// is passed only while the factors are in use (else the kernels skip it).
+template <typename T>
+CoarseData coarse_for(cmg_handle* h) {
+  CoarseData c = sizeof(T) == 4 ? h->c32() : h->coarse;
+  if (!h->dw_on) c.dw = nullptr;
+  return c;
 }
 
 bool level_ok(const cmg_handle* h, int l) { return h && l >= 0 && l < h->L; }
@@ -377,7 +387,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   }
   if (l == h->L - 1) {
     ProfScope ps(h, CMG_KERNEL_COARSE, l);
-    return launch_coarse_solve<T>(sizeof(T) == 4 ? h->c32() : h->coarse, v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
+    return launch_coarse_solve<T>(coarse_for<T>(h), v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
   }
   cudaError_t e = cudaSuccess;
   if (zg) {
@@ -710,7 +720,7 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!vec_ok(fy, fu, fp) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
     const Lev& v = h->lv[h->L - 1];                                                                             \
     if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
-    CK(launch_coarse_solve<T>(sizeof(T) == 4 ? h->c32() : h->coarse, v.c, v.d, v.e, Vec3c<T>{fy, fu, fp},      \
+    CK(launch_coarse_solve<T>(coarse_for<T>(h), v.c, v.d, v.e, Vec3c<T>{fy, fu, fp},                           \
                               Vec3<T>{y, u, p}, h->stream));                                                    \
     return CMG_OK;                                                                                              \
   }                                                                                                             \
@@ -1490,6 +1500,7 @@ extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int me
   //     (dw = 0) and right side (c y_d, h^2 u0, 0) leaves u = u0 and solves
   //     the 2N PDEs of Algorithm 2's first line
   h->gscale = 1.0 / nuc;
+  h->dw_on = true;
   const double hh2 = hh * hh;
   for (int l = 0; l < h->L && res == CMG_OK; ++l)
     if (launch_fill32((long)h->lv[l].nodes, 0.f, h->lv[l].dw, h->stream) != cudaSuccess) res = CMG_ERR_CUDA;
@@ -1540,6 +1551,7 @@ extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int me
   st->merit = phi;
   // back to the linear-quadratic operators (G = nu h^2, dw = 1)
   h->gscale = 1.0;
+  h->dw_on = false;
   for (int l = 0; l < h->L; ++l) (void)launch_fill32((long)h->lv[l].nodes, 1.f, h->lv[l].dw, h->stream);
   const cudaError_t er = refresh_dw(h);
   if (res != CMG_OK) return res;

@@ -229,14 +229,17 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
   int iy = 0, ix = 0;
   if (valid) colour_node(g, n, colour, iy, ix);
   const long node = (long)iy * n + ix;
+  const bool ctl = L.ctl.inside(iy, ix);   // taken here so (iy, ix) need not stay live
   const size_t o = (size_t)node * ld;
   vec<T, V> bp[SPL], by[SPL], ia[SPL];
   using A = acc_t<T>;
   T tacc = T(0);   // this lane's part of the sum over samples
   A bu = A(0), isg = A(0);   // control-row right side (or the frozen u) and 1/sigma, loaded with the rest
+  A dwv = A(1);              // per-node factor on d (semismooth Newton systems only), loaded with them
   if (valid) {
     bu = L.freeze_u ? (A)ld1<T, CG>(x.u + node) : (A)ld1<T, CG>(f.u + node);
     isg = isigma_of<T>(L, node);
+    if (L.dw) dwv = (A)L.dw[node];
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
     const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
@@ -281,7 +284,7 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
     // rows are solved (Eq. (14) with u_i given instead of zero); a node
     // without a control basis function (local control) takes Eq. (14) with
     // u_i = 0
-    const A uu = L.freeze_u ? bu : (L.ctl.inside(iy, ix) ? (bu + (A)d_of(L, node) * tsum) * isg : A(0));
+    const A uu = L.freeze_u ? bu : (ctl ? (bu + (A)L.d * dwv * tsum) * isg : A(0));
     if (lane == 0 && !L.freeze_u) x.u[node] = (T)uu;
     const T uT = (T)uu, e = (T)L.e;
 #pragma unroll
@@ -315,10 +318,12 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   T tacc = T(0);
   A ru = A(0), xu = A(0), isg = A(0);   // loaded with the rest, ahead of the group sum
   const int iy = valid ? (int)(node / n) : 0, ix = valid ? (int)(node - (long)iy * n) : 0;
+  A dwv = A(1);   // per-node factor on d (semismooth Newton systems only)
   if (valid) {
     ru = (A)ld1<T, CG>(r.u + node);
     xu = (A)ld1<T, CG>(x.u + node);
     isg = isigma_of<T>(L, node);
+    if (L.dw) dwv = (A)L.dw[node];
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
 #pragma unroll
@@ -339,7 +344,7 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   }
   const A tsum = group_sum((A)tacc, lpn);
   if (valid) {
-    const A du = (L.freeze_u || !L.ctl.inside(iy, ix)) ? A(0) : (ru + (A)d_of(L, node) * tsum) * isg;
+    const A du = (L.freeze_u || !L.ctl.inside(iy, ix)) ? A(0) : (ru + (A)L.d * dwv * tsum) * isg;
     if (lane == 0) x.u[node] = (T)(xu + (A)theta * du);
     const T duT = (T)du, e = (T)L.e, th = (T)theta;
 #pragma unroll

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) rbgs_staged_kernel(LevelView
     int iy = 0, ix = 0;
     if (valid) colour_node(g, n, colour, iy, ix);
     const size_t node = (size_t)iy * n + ix, o = node * ld;
+    const bool ctl = L.ctl.inside(iy, ix);
     const float4* d = wv + (size_t)b * VEC * 32 + lane;
     const float c = (float)L.c, e = (float)L.e;
     float bp[SPL][4], by[SPL][4], ia[SPL][4];
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) rbgs_staged_kernel(LevelView
     const float tsum = group_sum(tacc, lpn);
     if (!valid) return;
     const float bu = ws[(b * 2 + 0) * 32 + lane], isg = ws[(b * 2 + 1) * 32 + lane];
-    const float uu = L.freeze_u ? bu : (L.ctl.inside(iy, ix) ? (bu + (float)d_of(L, (long)node) * tsum) * isg : 0.f);
+    const float uu = L.freeze_u ? bu : (ctl ? (bu + (float)d_of(L, (long)node) * tsum) * isg : 0.f);
     if (ln == 0 && !L.freeze_u) x.u[node] = uu;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {
