@@ -323,18 +323,24 @@ cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, double tol, int 
  * (CMG_FP64 or CMG_FP32): how many sample chunks one lane takes (1, 2 or 4,
  * which fixes how many lanes share a node) and, for CMG_FP32 with N a
  * multiple of 4, whether the red-black half-sweep stages its loads through
- * shared memory (CMG_TUNE_STAGED | 1 or 2 chunks).  Each candidate is timed
+ * shared memory (CMG_TUNE_STAGED | 1 or 2 chunks), and for CMG_FP32 with N
+ * even and at most 64 the layout with two samples per lane and N/2 lanes
+ * (rounded up to a power of two) per node (CMG_TUNE_WIDE | 1), which applies
+ * to every node kernel of that grid.  Each candidate is timed
  * with CUDA events on a few red+black half-sweep pairs on the handle's own
- * work vectors, and the fastest is kept in the handle.  chosen (host, may
+ * work vectors, three times in turn, and the one with the fastest median
+ * time is kept in the handle.  chosen (host, may
  * be NULL) receives the target per grid (num_levels entries; the coarsest
  * is not tuned: 0).  Synchronises.  Numerical results do not depend on the
  * choice except for the order of the sample sums (rounding). */
 cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
 /* Set the per-grid targets directly (e.g. from a cache of earlier
  * cmg_autotune runs): num_levels entries of 0 (size heuristic), 1, 2 or 4,
- * and for CMG_FP32 also CMG_TUNE_STAGED | 1 or CMG_TUNE_STAGED | 2; NULL
- * resets all to 0.  Other values return CMG_ERR_INVALID_ARG. */
+ * and for CMG_FP32 also CMG_TUNE_STAGED | 1, CMG_TUNE_STAGED | 2 or
+ * CMG_TUNE_WIDE | 1 (ignored where N is odd or above 64); NULL resets all to
+ * 0.  Other values return CMG_ERR_INVALID_ARG. */
 #define CMG_TUNE_STAGED 16
+#define CMG_TUNE_WIDE 32
 cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets);
 
 /* cmg_autotune on every instance of a batch (the batch graph is re-captured

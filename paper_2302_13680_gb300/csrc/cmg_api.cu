@@ -834,24 +834,33 @@ cmg_status autotune_levels(cmg_handle* h, int* chosen) {
     Lev& v = h->lv[l];
     CK(zero_vec<T>(h, l, Work<T>::x(v)));
     CK(zero_vec<T>(h, l, Work<T>::f(v)));
-    const int reps = v.n >= 255 ? 4 : 16;
-    float best = 1e30f;
-    int best_t = 0;
+    const int reps = v.n >= 255 ? 8 : 16;
     // direct-load sweeps with 1, 2, 4 chunks per lane; FP32 also the staged
-    // sweep with 1 or 2 (kTuneStaged)
-    int cand[5] = {1, 2, 4, 0, 0}, nc = 3;
+    // sweep with 1 or 2 (kTuneStaged) and the two-sample layout (kTuneWide).
+    // Three rounds over all candidates in turn; each candidate is judged by
+    // its median round (one timing per candidate was at the mercy of clock
+    // ramps and L2 state).
+    int cand[6] = {1, 2, 4, 0, 0, 0}, nc = 3;
     if (sizeof(T) == 4 && staged_supported(h->prob.N, 1)) {
       cand[nc++] = kTuneStaged | 1;
       cand[nc++] = kTuneStaged | 2;
     }
+    if (sizeof(T) == 4 && wide_supported(h->prob.N)) cand[nc++] = kTuneWide | 1;
+    constexpr int kRounds = 3;
+    float t_ms[kRounds][6] = {};
+    for (int r = 0; r < kRounds; ++r)
+      for (int ci = 0; ci < nc; ++ci) {
+        const cmg_status s = time_sweeps<T>(h, l, cand[ci], reps, &t_ms[r][ci]);
+        if (s != CMG_OK) return s;
+      }
+    float best = 1e30f;
+    int best_t = 0;
     for (int ci = 0; ci < nc; ++ci) {
-      const int t = cand[ci];
-      float ms = 0.f;
-      const cmg_status s = time_sweeps<T>(h, l, t, reps, &ms);
-      if (s != CMG_OK) return s;
-      if (ms < best) {
-        best = ms;
-        best_t = t;
+      float a = t_ms[0][ci], b = t_ms[1][ci], c = t_ms[2][ci];
+      const float med = std::max(std::min(a, b), std::min(std::max(a, b), c));
+      if (med < best) {
+        best = med;
+        best_t = cand[ci];
       }
     }
     v.spl_target[k] = best_t;
@@ -881,9 +890,12 @@ cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets) 
   const int k = precision == CMG_FP64 ? 0 : 1;
   for (int l = 0; l < h->L; ++l) {
     const int t = spl_targets ? spl_targets[l] : 0;
-    const int c = t & ~kTuneStaged;
-    if ((c != 0 && c != 1 && c != 2 && c != 4) || ((t & kTuneStaged) && (k == 0 || (c != 1 && c != 2))))
-      return fail(h, CMG_ERR_INVALID_ARG, "target must be 0, 1, 2 or 4 (FP32: or CMG_TUNE_STAGED | 1 or 2)");
+    const int c = t & ~(kTuneStaged | kTuneWide);
+    const bool staged = t & kTuneStaged, wide = t & kTuneWide;
+    if ((c != 0 && c != 1 && c != 2 && c != 4) || ((staged || wide) && k == 0) || (staged && c != 1 && c != 2) ||
+        (wide && (staged || c != 1)))
+      return fail(h, CMG_ERR_INVALID_ARG,
+                  "target must be 0, 1, 2 or 4 (FP32: or CMG_TUNE_STAGED | 1 or 2, or CMG_TUNE_WIDE | 1)");
   }
   for (int l = 0; l < h->L; ++l) h->lv[l].spl_target[k] = spl_targets ? spl_targets[l] : 0;
   h->ir_opts.n1 = -1;   // captured graphs bake the launch shapes: force a re-capture

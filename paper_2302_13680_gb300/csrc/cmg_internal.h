@@ -130,6 +130,12 @@ cudaError_t launch_residual(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Vec3<
 // Tuning target flag (FP32): the half-sweep stages its loads through
 // shared memory (cmg_staged.cu); the low bits are the chunks per lane.
 constexpr int kTuneStaged = 16;
+// Tuning target flag (FP32, N even and at most 64): two samples per lane
+// (8-byte loads), so a node takes N/2 lanes rounded up to a power of two and
+// a warp holds one node at N = 64 -- twice the warps of the 16-byte layout,
+// finer work for the last wave of a grid.  Low bits must be 1.
+constexpr int kTuneWide = 32;
+inline bool wide_supported(int N) { return N % 2 == 0 && N <= 64; }
 bool staged_supported(int N, int spl);
 cudaError_t launch_rbgs_half_staged(const LevelView<float>& L, Vec3<float> x, Vec3c<float> f, int colour,
                                     const SampleMap& m, cudaStream_t s);

@@ -486,10 +486,16 @@ __device__ __forceinline__ void prolong_item(int nf, int N, const Vec3c<T>& e, c
     default: return cudaErrorInvalidValue;                                     \
   }
 
+// FP32 with V = 2 is the wide layout (kTuneWide): one chunk per lane only.
 #define CMG_DISPATCH(T, MAP, ...)                                              \
   do {                                                                         \
     if ((MAP).V == 1) { CMG_SPL_SWITCH((MAP).spl, 1, __VA_ARGS__) }            \
     else if constexpr (sizeof(T) == 8) { CMG_SPL_SWITCH((MAP).spl, 2, __VA_ARGS__) } \
+    else if ((MAP).V == 2) {                                                   \
+      if ((MAP).spl != 1) return cudaErrorInvalidValue;                        \
+      constexpr int V = 2, SPL = 1;                                            \
+      __VA_ARGS__;                                                             \
+    }                                                                          \
     else { CMG_SPL_SWITCH((MAP).spl, 4, __VA_ARGS__) }                         \
   } while (0)
 

@@ -236,12 +236,19 @@ bool pdl_enabled() {
 
 SampleMap choose_map(int N, int elem_bytes, long items, int spl_target) {
   SampleMap m;
+  if ((spl_target & kTuneWide) && elem_bytes == 4 && wide_supported(N)) {
+    m.V = 2;
+    m.spl = 1;
+    m.lpn = 1;
+    while (m.lpn < N / 2) m.lpn <<= 1;
+    return m;
+  }
   const int vmax = 16 / elem_bytes;     // 2 for double, 4 for float
   m.V = (N % vmax == 0) ? vmax : 1;
   const int chunks = (N + m.V - 1) / m.V;
   int target = 4;
   while (target > 1 && items * chunks / target < kMinLanes) target >>= 1;
-  if ((spl_target & 15) > 0) target = spl_target & 15;   // the staged flag is not part of the map
+  if ((spl_target & 15) > 0) target = spl_target & 15;   // the staged and wide flags are not part of it
   const int want = (chunks + target - 1) / target;   // lanes needed at `target` chunks each
   int lpn = 1;
   while (lpn < want && lpn < 32) lpn <<= 1;

@@ -166,7 +166,7 @@ def test_autotune_keeps_results_and_validates(H, tmp_path):
     st0, _ = h.solve(opts, f, x0)
     chosen = tuning.apply_or_tune(h, P.FP32, str(tmp_path / "tune.json"))
     assert len(chosen) == h.levels and chosen[-1] == 0
-    assert all(t in (1, 2, 4, 16 | 1, 16 | 2) for t in chosen[:-1])   # 16: staged FP32 sweep
+    assert all(t in (1, 2, 4, 16 | 1, 16 | 2, 32 | 1) for t in chosen[:-1])   # 16: staged sweep, 32: wide layout
     again = tuning.apply_or_tune(h, P.FP32, str(tmp_path / "tune.json"))   # from the cache
     assert again == chosen
     x1 = h.zeros(0)
@@ -188,7 +188,14 @@ def test_set_tuning_validates_targets(H):
         h.set_tuning(P.FP64, [16 | 1] + [0] * (L - 1))      # FP32 only
     with pytest.raises(P.CMGError):
         h.set_tuning(P.FP32, [3] + [0] * (L - 1))
+    with pytest.raises(P.CMGError):
+        h.set_tuning(P.FP32, [32 | 2] + [0] * (L - 1))      # wide layout: one chunk per lane
+    with pytest.raises(P.CMGError):
+        h.set_tuning(P.FP32, [32 | 16 | 1] + [0] * (L - 1))  # not with the staged sweep
+    with pytest.raises(P.CMGError):
+        h.set_tuning(P.FP64, [32 | 1] + [0] * (L - 1))      # FP32 only
     h.set_tuning(P.FP32, [16 | 2] + [0] * (L - 1))
+    h.set_tuning(P.FP32, [32 | 1] * (L - 1) + [0])
     h.set_tuning(P.FP32, None)
 
 

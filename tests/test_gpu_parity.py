@@ -318,6 +318,43 @@ def test_staged_half_sweep_matches_direct(case, spl, freeze):
             assert torch.equal(ta, tb)
 
 
+def test_wide_layout_matches_oracle(case):
+    """FP32 node kernels in the two-samples-per-lane layout (CMG_TUNE_WIDE;
+    ignored where N is odd or above 64): residual, one sweep of each
+    smoother and a refinement solve against the FP64 oracle, as for the
+    default layout."""
+    H, levels = case
+    import paper_2302_13680_gb300 as P
+
+    wide = 32
+    H.set_tuning(P.FP32, [wide | 1] * (H.levels - 1) + [0])
+    try:
+        for l, lv in enumerate(levels[:-1]):
+            x = rand_level_vec(lv.n, lv.N, 700 + l, np.float32)
+            f = rand_level_vec(lv.n, lv.N, 750 + l, np.float32)
+            r = H.zeros(l, torch.float32)
+            H.residual(l, to_dev(x, torch.float32), to_dev(f, torch.float32), r)
+            assert_close(to_host(r, lv.n), O.residual(lv, x, f), TOL32, f"wide residual level {l}")
+            fs = tuple(np.asarray(b * s, dtype=np.float32).astype(np.float64) for b, s in zip(f, (lv.c, lv.G, lv.h ** 2)))
+            for sm in ("rbgs", "jacobi"):
+                opts = P.CycleOptions(precision=P.FP32, theta=0.5,
+                                      smoother=P.SMOOTH_RBGS if sm == "rbgs" else P.SMOOTH_JACOBI)
+                xd = to_dev(x, torch.float32)
+                H.smooth(l, opts, 1, xd, to_dev(fs, torch.float32))
+                ref = O.rbgs_sweep(lv, x, fs) if sm == "rbgs" else O.jacobi_sweep(lv, x, fs, 0.5)
+                assert_close(to_host(xd, lv.n), ref, TOL32, f"wide {sm} level {l}")
+        lv = levels[0]
+        f = O.fine_rhs(lv, inputs.target_sinsin(lv.n))
+        ref = O.fgmres(levels, f, O.CycleOptions(), tol=1e-12)
+        xd = H.zeros(0)
+        st, _ = H.solve(P.CycleOptions(precision=P.FP32), to_dev(f), xd, method=P.METHOD_CYCLE, tol=1e-10, maxit=60)
+        assert st.relres <= 1e-10
+        for name, g, r in zip("yup", to_host(xd, lv.n), ref.x):
+            assert relerr(g, r) <= 1e-6, name
+    finally:
+        H.set_tuning(P.FP32, None)
+
+
 @pytest.mark.parametrize("gamma", [1, 2])
 @pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
 def test_fp32_cycle_cluster_matches_per_launch(case, gamma, smoother):
