@@ -1,0 +1,163 @@
+"""Galerkin coarse operators for the collective multigrid: plain sparse-matrix oracle.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference legs of ``bench.py`` may import this module; it
+shares no code with the CUDA library.
+
+Sec. 3 (after the collective smoothing iteration, Eq. (11)) defines the
+coarse matrices recursively from the finest one, S_l = R S_{l+1} P with
+R = P^T, and its experiments (Sec. 3.2) smooth with the damped collective
+Jacobi iteration, theta = 0.5, n1 = n2 = 2.  This module computes exactly
+that, from the definitions and nothing else:
+
+* the finest system matrix S assembled as a sparse matrix from the block
+  definition of the full-space optimality system (Eq. (2) with this
+  problem's blocks; ordering (y, u, p), y and p node-major with the
+  sample index fastest, as ``cmg_oracle.pack``);
+* the block prolongation P (the bilinear interpolation of every block) as
+  a sparse matrix, and S_c = P^T S P by sparse products, level by level;
+* collective Jacobi, Eq. (11): x += theta sum_i P_i S_ii^{-1} R_i (f - S x),
+  with S_ii the (2N+1) x (2N+1) block of S on node i's unknowns, solved
+  densely (no use of its arrow structure);
+* Algorithm 1 with that smoother, the residual f - S x by a sparse
+  product, the transfers by P and P^T, and a sparse direct solve on the
+  coarsest grid.
+
+Distributed control only (chi = 1, dw = 1 on every grid).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import cmg_oracle as O
+
+
+def stiffness_matrix(level: O.Level, j: int) -> sp.csr_matrix:
+    """A_j of the grid: row i holds the sum of node i's four face
+    coefficients on the diagonal and minus the face coefficient towards
+    each interior neighbour (a neighbour on the boundary is a zero
+    Dirichlet value and has no column)."""
+    n = level.n
+    rows, cols, vals = [], [], []
+    for iy in range(n):
+        for ix in range(n):
+            i = iy * n + ix
+            kW, kE = level.kx[iy, ix, j], level.kx[iy, ix + 1, j]
+            kS, kN = level.ky[iy, ix, j], level.ky[iy + 1, ix, j]
+            rows.append(i)
+            cols.append(i)
+            vals.append(kW + kE + kS + kN)
+            for (ny, nx), k in (((iy, ix - 1), kW), ((iy, ix + 1), kE), ((iy - 1, ix), kS), ((iy + 1, ix), kN)):
+                if 0 <= ny < n and 0 <= nx < n:
+                    rows.append(i)
+                    cols.append(ny * n + nx)
+                    vals.append(-k)
+    m = n * n
+    return sp.csr_matrix((vals, (rows, cols)), shape=(m, m))
+
+
+def system_matrix(level: O.Level) -> sp.csr_matrix:
+    """The full-space system of the symmetric form on this grid:
+
+        [ c I_m (x) I_N      0          blkdiag(A_j) ]   y
+        [ 0                  G I_m      d (I_m (x) 1_N^T) ]   u
+        [ blkdiag(A_j)       e (I_m (x) 1_N)   0      ]   p
+
+    with y, p ordered [node][sample] (I_m (x) B puts B on every node)."""
+    if level.chi is not None or level.dw is not None:
+        raise ValueError("Galerkin hierarchy: distributed control only")
+    n, N = level.n, level.N
+    m = n * n
+    # blkdiag over samples of A_j in the node-major, sample-fastest ordering:
+    # entry (i N + j, k N + j) = (A_j)_{ik}
+    rows, cols, vals = [], [], []
+    for j in range(N):
+        A = stiffness_matrix(level, j).tocoo()
+        rows.append(A.row * N + j)
+        cols.append(A.col * N + j)
+        vals.append(A.data)
+    Ablk = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(m * N, m * N))
+    Im = sp.identity(m, format="csr")
+    ones_col = sp.csr_matrix(np.ones((N, 1)))
+    Y = level.c * sp.identity(m * N, format="csr")
+    U = level.G * Im
+    D = level.d * sp.kron(Im, ones_col.T, format="csr")      # u-row, p columns: d sum_j p_ij
+    E = level.e * sp.kron(Im, ones_col, format="csr")        # p-rows, u column: e u_i
+    return sp.bmat([[Y, None, Ablk], [None, U, D], [Ablk, E, None]], format="csr")
+
+
+def prolongation_matrix(nf: int, N: int) -> sp.csr_matrix:
+    """Block prolongation of a full-space vector from the (nf-1)/2 grid to
+    the nf grid: the bilinear interpolation P2 = P1 (x) P1 (row index
+    iy nf + ix, the 1D operator along y outside) on every sample of y and
+    p and on u."""
+    P1 = sp.csr_matrix(O.prolongation_1d(nf))
+    P2 = sp.kron(P1, P1, format="csr")
+    PN = sp.kron(P2, sp.identity(N, format="csr"), format="csr")
+    return sp.block_diag([PN, P2, PN], format="csr")
+
+
+def hierarchy(levels) -> list[sp.csr_matrix]:
+    """S_0 from the finest grid's definition, S_{l+1} = P^T S_l P (the
+    grids of ``levels`` fix only the sizes below the finest)."""
+    N = levels[0].N
+    S = [system_matrix(levels[0])]
+    for l in range(1, len(levels)):
+        P = prolongation_matrix(levels[l - 1].n, N)
+        S.append((P.T @ S[-1] @ P).tocsr())
+    return S
+
+
+def node_indices(n: int, N: int, i: int) -> np.ndarray:
+    """Positions of node i's 2N+1 unknowns (y_i, u_i, p_i) in a packed vector."""
+    m = n * n
+    return np.concatenate([i * N + np.arange(N), [m * N + i], m * N + m + i * N + np.arange(N)])
+
+
+def jacobi_sweep(S: sp.csr_matrix, n: int, N: int, z: np.ndarray, f: np.ndarray, theta: float) -> np.ndarray:
+    """One collective Jacobi step (Eq. (11)) on packed vectors."""
+    r = f - S @ z
+    out = z.copy()
+    for i in range(n * n):
+        idx = node_indices(n, N, i)
+        Sii = S[idx][:, idx].toarray()
+        out[idx] += theta * np.linalg.solve(Sii, r[idx])
+    return out
+
+
+def cycle(S, ns, N: int, l: int, z: np.ndarray, f: np.ndarray, n1: int = 2, n2: int = 2, theta: float = 0.5,
+          gamma: int = 1) -> np.ndarray:
+    """Algorithm 1 on packed vectors with the Galerkin matrices S[l] on the
+    grids ns[l] (finest first); gamma = 2 gives the W-cycle."""
+    if l == len(S) - 1:
+        return spla.spsolve(S[l].tocsc(), f)
+    for _ in range(n1):
+        z = jacobi_sweep(S[l], ns[l], N, z, f, theta)
+    P = prolongation_matrix(ns[l], N)
+    fc = P.T @ (f - S[l] @ z)
+    ec = np.zeros(S[l + 1].shape[0])
+    for _ in range(gamma):
+        ec = cycle(S, ns, N, l + 1, ec, fc, n1, n2, theta, gamma)
+    z = z + P @ ec
+    for _ in range(n2):
+        z = jacobi_sweep(S[l], ns[l], N, z, f, theta)
+    return z
+
+
+def solve_stationary(S, ns, N: int, f: np.ndarray, tol: float = 1e-10, maxit: int = 100, **kw):
+    """Repeated cycles from zero until the relative residual of the paper's
+    system, ||W (f - S z)|| / ||W f|| (``cmg_oracle.paper_norm``), is <= tol;
+    returns (z, cycles, history of relative residuals, the first entry for
+    z = 0)."""
+    n = ns[0]
+    z = np.zeros_like(f)
+    fnorm = O.paper_norm(O.unpack(f, n, N), N)
+    hist = [1.0]
+    it = 0
+    while hist[-1] > tol and it < maxit:
+        z = cycle(S, ns, N, 0, z, f, **kw)
+        it += 1
+        hist.append(O.paper_norm(O.unpack(f - S[0] @ z, n, N), N) / fnorm)
+    return z, it, hist
