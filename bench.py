@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cmg", choices=["cmg", "reference"])
-    ap.add_argument("--config", default="n255_N64", choices=sorted(inputs.CONFIGS) + ["batch96", "n255_N64_l1box"])
+    ap.add_argument("--config", default="n255_N64", choices=sorted(inputs.CONFIGS) + ["batch96", "n255_N64_l1box", "n255_N64_galerkin"])
     ap.add_argument("--form", default="auto", choices=["auto", "fp64-fgmres", "fp64-cycle", "fp32-ir",
                                                         "fp32-ir-launches", "fp32-fgmres"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -667,6 +667,100 @@ def run_ssn(args, world, rank, local):
     H.close()
 
 
+GALERKIN_CONFIGS = {"n255_N64_galerkin": dict(base="n255_N64")}
+
+
+def run_galerkin(args, world, rank, local):
+    """The paper's own coarse operators (Sec. 3: S_l = P^T S_{l-1} P) against
+    rediscretised ones, both with FP64 collective Jacobi V(2,2), theta = 0.5
+    (the smoother of the paper's experiments), stationary and as FGMRES
+    preconditioner; a step = coefficient set-up for the sample set (the
+    Galerkin triple products included) + solve to 1e-10.  Units = unknowns
+    x cycles."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2302_13680_gb300 as P
+    from paper_2302_13680_gb300 import cmg as C
+
+    torch.cuda.set_device(local)
+    base = dict(inputs.CONFIGS[GALERKIN_CONFIGS[args.config]["base"]])
+    base["seed"] = base["seed"] + 1000 * rank
+    pr = inputs.make_problem(**base)
+    n, N = pr.n, pr.N
+    unknowns = (2 * N + 1) * n * n
+    hier = {"galerkin": P.Hierarchy(n, N, pr.xi, pr.nu, pr.amp, coarse="galerkin"),
+            "rediscretised": P.Hierarchy(n, N, pr.xi, pr.nu, pr.amp)}
+    xi_dev = torch.tensor(pr.xi, dtype=torch.float64, device="cuda")
+    fs = {k: H.rhs(torch.tensor(pr.yd.reshape(-1), device="cuda")) for k, H in hier.items()}
+    xs = {k: H.zeros(0) for k, H in hier.items()}
+    opts = P.CycleOptions(smoother=P.SMOOTH_JACOBI, theta=0.5, precision=P.FP64)
+    forms = {f"{k}-{m}": (k, P.METHOD_CYCLE if m == "cycle" else P.METHOD_FGMRES)
+             for k in hier for m in ("cycle", "fgmres")}
+
+    def step(form):
+        k, method = forms[form]
+        H = hier[k]
+        H.set_samples(xi_dev)
+        for t in xs[k]:
+            t.zero_()
+        st, _ = H.solve(opts, fs[k], xs[k], method=method, tol=TOL, maxit=200, restart=30)
+        return st
+
+    def timed(form, k):
+        ts, sts = [], []
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = step(form)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            sts.append(st)
+        return ts, sts
+
+    survey = {}
+    for form in forms:
+        for _ in range(2):
+            step(form)
+        ts, sts = timed(form, 3)
+        survey[form] = {"time_to_tol_ms": statistics.median(ts), "cycles": sts[-1].cycles,
+                        "iters": sts[-1].iters, "relres": sts[-1].relres}
+    chosen = min((f for f in forms if f.startswith("galerkin")), key=lambda f: survey[f]["time_to_tol_ms"])
+    for _ in range(args.warmup):
+        step(chosen)
+    clocks = ClockSampler(local)
+    launches0 = C.kernel_launches()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, sts = timed(chosen, args.steps)
+    clk = clocks.stop()
+    launches = C.kernel_launches() - launches0
+    value = sum(unknowns * s.cycles for s in sts) / (sum(times) / 1e3)
+    redis = min((f for f in forms if f.startswith("rediscretised")), key=lambda f: survey[f]["time_to_tol_ms"])
+    if rank == 0:
+        line = {"metric": "time-to-1e-10 residual & unknowns*cycles/s: Galerkin coarse operators (Sec. 3) "
+                          "vs rediscretised, FP64 collective Jacobi V(2,2)",
+                "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"collective MG with Galerkin coarse operators, n={n}, N={N}, K={pr.K}, "
+                                       f"amp={pr.amp}, nu={pr.nu:g}, FP64 Jacobi V(2,2) theta=0.5 to 3x3, "
+                                       f"tol {TOL:g}, set-up per step",
+                           "n": n, "N": N, "unknowns": unknowns, "instances_per_gpu": 1,
+                           "parallelism": f"replicas x{world} (independent instances, no collective)"},
+                "form": chosen, "forms": survey,
+                "time_to_tol_ms": {"chosen": statistics.median(times),
+                                   "rediscretised": survey[redis]["time_to_tol_ms"]},
+                "speedup_vs_rediscretised": survey[redis]["time_to_tol_ms"] / statistics.median(times),
+                "cycles_per_step": sts[-1].cycles, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    for H in hier.values():
+        H.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -678,6 +772,9 @@ def main():
         return
     if args.config in SSN_CONFIGS:
         run_ssn(args, world, rank, local)
+        return
+    if args.config in GALERKIN_CONFIGS:
+        run_galerkin(args, world, rank, local)
         return
     run_cmg(args, world, rank, local)
 

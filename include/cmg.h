@@ -57,7 +57,7 @@ typedef enum {
 enum { CMG_SMOOTH_RBGS = 0, CMG_SMOOTH_JACOBI = 1 };
 enum { CMG_FP64 = 0, CMG_FP32 = 1 };
 enum { CMG_METHOD_CYCLE = 0, CMG_METHOD_FGMRES = 1 };
-enum { CMG_COARSE_AVERAGED = 0, CMG_COARSE_NODAL = 1 };
+enum { CMG_COARSE_AVERAGED = 0, CMG_COARSE_NODAL = 1, CMG_COARSE_GALERKIN = 2 };
 
 /* Problem description (Sec. 2; field of Sec. 3.2). */
 typedef struct {
@@ -72,7 +72,15 @@ typedef struct {
                        grid's faces, harmonic along it (two fine faces in series) and
                        arithmetic across it (weights 1/4, 1/2, 1/4);
                        CMG_COARSE_NODAL: the field is sampled at each grid's own nodes and
-                       faces are harmonic means of the two endpoint values */
+                       faces are harmonic means of the two endpoint values;
+                       CMG_COARSE_GALERKIN: no rediscretisation -- the coarse matrices are the
+                       Galerkin products S_l = P^T S_{l-1} P of Sec. 3 (the operator of the
+                       paper's experiments): 9-point A_j and a 9-point mass M_l on every grid
+                       below the finest.  FP64 cycles with the collective Jacobi smoother only
+                       (cmg_cycle.precision = CMG_FP64, smoother = CMG_SMOOTH_JACOBI, freeze_u = 0;
+                       tail_n is ignored), distributed control only (ctl_box all zero), no
+                       semismooth Newton and no batches: those return CMG_ERR_UNSUPPORTED, as do
+                       the _f32 level operations on such a handle */
   double ctl_box[4]; /* local control (Sec. 3.1 after Eq. (13); the local-control test case of
                        Sec. 3.2): the closed region [x0, x1] x [y0, y1] = {ctl_box[0], ctl_box[1],
                        ctl_box[2], ctl_box[3]} inside the unit square.  Nodes of every grid inside

@@ -23,7 +23,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5:
 SMOOTH_RBGS, SMOOTH_JACOBI = 0, 1
 FP64, FP32 = 0, 1
 METHOD_CYCLE, METHOD_FGMRES = 0, 1
-COARSE = {"averaged": 0, "nodal": 1}
+COARSE = {"averaged": 0, "nodal": 1, "galerkin": 2}
 
 
 class CMGError(RuntimeError):

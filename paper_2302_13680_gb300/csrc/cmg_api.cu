@@ -39,6 +39,12 @@ struct Lev {
   float* x32[3] = {nullptr, nullptr, nullptr};
   float* d32[3] = {nullptr, nullptr, nullptr};   // finest grid: FP32 correction since the last refinement anchor
   float* dw = nullptr;                   // per-node factor on d (1; semismooth Newton: active-set indicator)
+  // Galerkin coarse operators (grids below the finest): 9-point A_j planes
+  // [9][n*n][N], the mass stencil M_l, and a scratch [n*n] for sample sums.
+  // c, G, d, e above then hold the diagonal entries (times M_l's centre).
+  double* a9 = nullptr;
+  double* psum = nullptr;
+  Stencil9 m9{};
   float* f32[3] = {nullptr, nullptr, nullptr};
   float* r32[3] = {nullptr, nullptr, nullptr};
 };
@@ -70,6 +76,7 @@ struct cmg_handle {
   double* cface64 = nullptr;   // coarsest FP32 faces promoted to FP64 for coarse32's set-up
   bool fp64_ready = false;     // FP64 operators below the finest faces are current
   CoarseData& c32() { return prob.coarse_coeff == CMG_COARSE_NODAL ? coarse : coarse32; }
+  bool galerkin() const { return prob.coarse_coeff == CMG_COARSE_GALERKIN; }
   double* xi = nullptr;       // [N][K] device
   double* kap = nullptr;      // setup scratch
   double* red = nullptr;      // reduction partials
@@ -234,6 +241,22 @@ cudaError_t ensure_fp64(cmg_handle* h) {
   if (h->fp64_ready) return cudaSuccess;
   const cmg_problem& P = h->prob;
   cudaError_t e = cudaSuccess;
+  if (h->galerkin()) {
+    // finest grid as for the rediscretised hierarchy; below it S_l = P^T S_{l-1} P
+    const Lev& f0 = h->lv[0];
+    e = launch_diag64(f0.n, P.N, f0.kx64, f0.ky64, f0.inva, f0.isigma, f0.d * f0.c * f0.e, f0.G, h->stream);
+    for (int l = 1; l < h->L && e == cudaSuccess; ++l) {
+      Lev& v = h->lv[l];
+      const Lev& f = h->lv[l - 1];
+      e = launch_galerkin_setup(f.n, P.N, f0.kx64, f0.ky64, l == 1 ? nullptr : f.a9, v.a9, h->stream);
+      if (e == cudaSuccess) e = launch_galerkin_diag(v.n, P.N, v.a9, v.inva, v.isigma, v.d * v.c * v.e, v.G, h->stream);
+    }
+    if (e != cudaSuccess) return e;
+    const Lev& cl = h->lv[h->L - 1];
+    e = launch_galerkin_coarse_setup(h->coarse, cl.a9, cl.m9, f0.c, f0.G, f0.d, f0.e, h->stream);
+    if (e == cudaSuccess) h->fp64_ready = true;
+    return e;
+  }
   for (int l = 0; l < h->L && e == cudaSuccess; ++l) {
     Lev& v = h->lv[l];
     if (l > 0) {
@@ -284,6 +307,20 @@ cudaError_t refresh_dw(cmg_handle* h) {
 
 // ---- smoothing and cycles --------------------------------------------------
 
+// r = f - S_l x (r = S_l x when f.y == nullptr): the 9-point Galerkin
+// operator on the coarse grids of a Galerkin hierarchy, else the 5-point one.
+template <typename T>
+cudaError_t level_residual(cmg_handle* h, int l, Vec3c<T> x, Vec3c<T> f, Vec3<T> r) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->galerkin() && l > 0) {
+      const Lev& v = h->lv[l];
+      const Lev& f0 = h->lv[0];
+      return launch_residual9(v.n, h->prob.N, v.a9, v.m9, f0.c, f0.G, f0.d, f0.e, x, f, r, v.psum, h->stream);
+    }
+  }
+  return launch_residual<T>(view<T>(h, l), x, f, r, h->stream);
+}
+
 template <typename T>
 cudaError_t smooth(cmg_handle* h, const cmg_cycle& o, int l, int sweeps, Vec3<T> x, Vec3c<T> f) {
   const LevelView<T> L = view<T>(h, l, o.freeze_u);
@@ -299,7 +336,7 @@ cudaError_t smooth(cmg_handle* h, const cmg_cycle& o, int l, int sweeps, Vec3<T>
       cudaError_t e;
       {
         ProfScope ps(h, CMG_KERNEL_RESIDUAL, l);
-        e = launch_residual<T>(L, cview(x), f, r, h->stream);
+        e = level_residual<T>(h, l, cview(x), f, r);
       }
       if (e != cudaSuccess) return e;
       ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
@@ -381,12 +418,18 @@ template <typename T>
 cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> f, bool zg = false) {
   Lev& v = h->lv[l];
   const int N = h->prob.N;
-  if (o.tail_n > 0 && v.n <= o.tail_n) {
+  if (o.tail_n > 0 && v.n <= o.tail_n && !h->galerkin()) {
     const cudaError_t e = tail_cycle<T>(h, o, l, x, f);
     if (e != cudaErrorNotSupported) return e;
   }
   if (l == h->L - 1) {
     ProfScope ps(h, CMG_KERNEL_COARSE, l);
+    if constexpr (sizeof(T) == 8) {
+      if (h->galerkin()) {
+        const Lev& f0 = h->lv[0];
+        return launch_galerkin_coarse_solve(h->coarse, v.m9, f0.c, f0.d, f0.e, f, x, h->stream);
+      }
+    }
     return launch_coarse_solve<T>(coarse_for<T>(h), v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
   }
   cudaError_t e = cudaSuccess;
@@ -413,7 +456,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   {
     ProfScope ps(h, CMG_KERNEL_RESIDUAL, l);
     e = c0 ? launch_residual_c0<T>(view<T>(h, l), cview(x), f, r, h->stream)
-           : launch_residual<T>(view<T>(h, l), cview(x), f, r, h->stream);
+           : level_residual<T>(h, l, cview(x), f, r);
   }
   if (e != cudaSuccess) return e;
   Lev& cl = h->lv[l + 1];
@@ -463,6 +506,9 @@ cmg_status check_cycle(cmg_handle* h, const cmg_cycle* o) {
   if (o->freeze_u && h && h->L < 2) return fail(h, CMG_ERR_INVALID_ARG, "freeze_u needs at least two grids");
   if (o->smoother == CMG_SMOOTH_JACOBI && !(o->theta > 0.0 && o->theta <= 1.0))
     return fail(h, CMG_ERR_INVALID_ARG, "theta must be in (0, 1]");
+  if (h && h->galerkin() && (o->precision != CMG_FP64 || o->smoother != CMG_SMOOTH_JACOBI || o->freeze_u))
+    return fail(h, CMG_ERR_UNSUPPORTED,
+                "Galerkin coarse operators: FP64 cycles with the collective Jacobi smoother, control updated");
   return CMG_OK;
 }
 
@@ -522,9 +568,12 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   if (!pow2m1(P.n) || P.n < 3 || P.n > 4095) return CMG_ERR_INVALID_ARG;
   if (!(P.coarsest_n == 1 || P.coarsest_n == 3 || P.coarsest_n == 7) || P.coarsest_n > P.n) return CMG_ERR_INVALID_ARG;
   if (P.N < 1 || P.K < 0 || P.K > 64 || !(P.nu > 0.0) || !std::isfinite(P.amp)) return CMG_ERR_INVALID_ARG;
-  if (P.coarse_coeff != CMG_COARSE_AVERAGED && P.coarse_coeff != CMG_COARSE_NODAL) return CMG_ERR_INVALID_ARG;
+  if (P.coarse_coeff != CMG_COARSE_AVERAGED && P.coarse_coeff != CMG_COARSE_NODAL &&
+      P.coarse_coeff != CMG_COARSE_GALERKIN)
+    return CMG_ERR_INVALID_ARG;
   if (P.K > 0 && !xi_host) return CMG_ERR_INVALID_ARG;
   if (!control_box_ok(P.ctl_box)) return CMG_ERR_INVALID_ARG;
+  if (P.coarse_coeff == CMG_COARSE_GALERKIN && !control_box_full(P.ctl_box)) return CMG_ERR_UNSUPPORTED;
   const SampleMap m64 = choose_map(P.N, 8, 0), m32 = choose_map(P.N, 4, 0);   // most chunks per lane
   if (m64.spl > kMaxSPL || m32.spl > kMaxSPL) return CMG_ERR_UNSUPPORTED;
 
@@ -558,6 +607,19 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     n = (n - 1) / 2;
   }
   h->L = L;
+  h->lv[0].m9.w[4] = 1.0;   // fine mass: the identity (times c, G, d, e)
+  if (P.coarse_coeff == CMG_COARSE_GALERKIN) {
+    const Lev& f0 = h->lv[0];
+    for (int l = 1; l < L; ++l) {
+      Lev& v = h->lv[l];
+      v.m9 = galerkin_mass(h->lv[l - 1].m9);
+      const double mii = v.m9.w[4];
+      v.c = f0.c * mii;
+      v.G = f0.G * mii;
+      v.d = f0.d * mii;
+      v.e = f0.e * mii;
+    }
+  }
   const size_t N = (size_t)P.N;
   cudaError_t e = cudaSuccess;
 #define AL(ptr, cnt)                        \
@@ -576,6 +638,11 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     }
   }
   AL(h->lv[0].a64, h->lv[0].nodes * N);
+  if (P.coarse_coeff == CMG_COARSE_GALERKIN)
+    for (int l = 1; l < L; ++l) {
+      AL(h->lv[l].a9, 9 * h->lv[l].nodes * N);
+      AL(h->lv[l].psum, h->lv[l].nodes);
+    }
   const size_t g = (size_t)P.n + 2;
   AL(h->kap, g * g * N + g * N);
   AL(h->xi, (size_t)N * (P.K > 0 ? P.K : 1));
@@ -679,9 +746,9 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!level_ok(h, level)) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");                        \
     if (!vec_ok(y, u, p) || !vec_ok(ry, ru, rp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
     if ((fy || fu || fp) && !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "partial rhs");           \
+    if (sizeof(T) == 4 && h->galerkin()) return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin operators are FP64");   \
     if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
-    CK(launch_residual<T>(view<T>(h, level), Vec3c<T>{y, u, p}, Vec3c<T>{fy, fu, fp}, Vec3<T>{ry, ru, rp},     \
-                          h->stream));                                                                          \
+    CK(level_residual<T>(h, level, Vec3c<T>{y, u, p}, Vec3c<T>{fy, fu, fp}, Vec3<T>{ry, ru, rp}));             \
     return CMG_OK;                                                                                              \
   }                                                                                                             \
   cmg_status cmg_smooth##SUF(cmg_handle* h, int level, const cmg_cycle* opts, int sweeps, T* y, T* u, T* p,     \
@@ -719,6 +786,15 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!h) return CMG_ERR_INVALID_ARG;                                                                         \
     if (!vec_ok(fy, fu, fp) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
     const Lev& v = h->lv[h->L - 1];                                                                             \
+    if (h->galerkin()) {                                                                                        \
+      if (sizeof(T) == 4) return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin operators are FP64");                  \
+      CK(ensure_fp64(h));                                                                                       \
+      const Lev& f0 = h->lv[0];                                                                                 \
+      CK(launch_galerkin_coarse_solve(h->coarse, v.m9, f0.c, f0.d, f0.e,                                        \
+                                      Vec3c<double>{(const double*)fy, (const double*)fu, (const double*)fp},   \
+                                      Vec3<double>{(double*)y, (double*)u, (double*)p}, h->stream));            \
+      return CMG_OK;                                                                                            \
+    }                                                                                                           \
     if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
     CK(launch_coarse_solve<T>(coarse_for<T>(h), v.c, v.d, v.e, Vec3c<T>{fy, fu, fp},                           \
                               Vec3<T>{y, u, p}, h->stream));                                                    \
@@ -1462,6 +1538,7 @@ extern "C" cmg_status cmg_ssn_solve(cmg_handle* h, const cmg_cycle* opts, int me
       !std::isfinite(b) || !std::isfinite(beta))
     return fail(h, CMG_ERR_INVALID_ARG, "need a < 0 < b, beta >= 0, tol > 0, inner_tol > 0, maxit >= 0");
   if (opts->freeze_u) return fail(h, CMG_ERR_INVALID_ARG, "the Newton systems need the control update");
+  if (h->galerkin()) return fail(h, CMG_ERR_UNSUPPORTED, "semismooth Newton: rediscretised coarse grids only");
   if (method != CMG_METHOD_CYCLE && method != CMG_METHOD_FGMRES) return fail(h, CMG_ERR_INVALID_ARG, "unknown method");
   cmg_ssn_stats local{};
   cmg_ssn_stats* st = stats ? stats : &local;
@@ -1609,6 +1686,8 @@ extern "C" cmg_status cmg_batch_create(const cmg_problem* probs, const double* c
   if (!out) return CMG_ERR_INVALID_ARG;
   *out = nullptr;
   if (!probs || !xi_host || count < 1 || count > 4096) return CMG_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (probs[i].coarse_coeff == CMG_COARSE_GALERKIN) return CMG_ERR_UNSUPPORTED;   // the batch runs FP32 cycles
   cmg_batch* b = new (std::nothrow) cmg_batch();
   if (!b) return CMG_ERR_OOM;
   b->stream = static_cast<cudaStream_t>(stream);

@@ -383,6 +383,206 @@ cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const dou
   return cudaGetLastError();
 }
 
+// ---- Galerkin coarsest grid ------------------------------------------------
+// With the non-diagonal mass M (9-point, constant) the elimination reads
+//     y_j = A_j^{-1} (f_p,j - e M u),   p_j = A_j^{-1} (f_y,j - c M y_j),
+//     (G M + d c e M Q M) u = f_u - d M sum_j z_j,   Q = sum_j A_j^{-1} M A_j^{-1},
+// with w_j = A_j^{-1} f_p,j and z_j = A_j^{-1} (f_y,j - c M w_j).
+namespace {
+
+// (M v)_r on the n x n grid (zero outside).
+__device__ __forceinline__ double mass_apply(const Stencil9& M, const double* v, int n, int r) {
+  const int ry = r / n, rx = r - (r / n) * n;
+  double s = 0.0;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int y = ry + dy, x = rx + dx;
+      if (y < 0 || y >= n || x < 0 || x >= n) continue;
+      s = fma(M.w[(dy + 1) * 3 + dx + 1], v[y * n + x], s);
+    }
+  return s;
+}
+
+// M[r][c] of the n x n grid.
+__device__ __forceinline__ double mass_entry(const Stencil9& M, int n, int r, int c) {
+  const int dy = c / n - r / n, dx = c % n - r % n;
+  return (dy < -1 || dy > 1 || dx < -1 || dx > 1) ? 0.0 : M.w[(dy + 1) * 3 + dx + 1];
+}
+
+// One CTA per sample: A_j from its 9-point stencil, inverted.
+__global__ void galerkin_coarse_inv_kernel(int n, int N, const double* __restrict__ a9, double* __restrict__ Ainv) {
+  __shared__ double aug[kMaxCoarseM * 2 * kMaxCoarseM];
+  __shared__ double fac[kMaxCoarseM];
+  const int j = blockIdx.x;
+  const int m = n * n, w = 2 * m;
+  for (int idx = threadIdx.x; idx < m * w; idx += blockDim.x) {
+    const int r = idx / w, c = idx - r * w;
+    double v = 0.0;
+    if (c >= m) {
+      v = (c - m == r) ? 1.0 : 0.0;
+    } else {
+      const int dy = c / n - r / n, dx = c % n - r % n;
+      if (dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1)
+        v = a9[((size_t)((dy + 1) * 3 + dx + 1) * m + r) * N + j];
+    }
+    aug[idx] = v;
+  }
+  gauss_jordan(aug, fac, m);
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx / m, c = idx - r * m;
+    Ainv[(size_t)j * m * m + idx] = aug[r * w + m + c];
+  }
+}
+
+// One CTA per entry (r, c): Q[r][c] = sum_j sum_k A_j^{-1}[r][k] (M A_j^{-1})[k][c],
+// fixed-order reduction over the samples.
+__global__ void galerkin_q_kernel(int n, int N, const double* __restrict__ Ainv, Stencil9 M, double* __restrict__ Q) {
+  __shared__ double red[128];
+  const int m = n * n;
+  const int r = blockIdx.x / m, c = blockIdx.x - (blockIdx.x / m) * m;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double* A = Ainv + (size_t)j * m * m;
+    double t = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const int ky = k / n, kx = k - (k / n) * n;
+      double mk = 0.0;   // (M A^{-1})[k][c]
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int y = ky + dy, x = kx + dx;
+          if (y < 0 || y >= n || x < 0 || x >= n) continue;
+          mk = fma(M.w[(dy + 1) * 3 + dx + 1], A[(y * n + x) * m + c], mk);
+        }
+      t = fma(A[r * m + k], mk, t);
+    }
+    s += t;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Q[blockIdx.x] = red[0];
+}
+
+// One CTA: S_u = G M + dce M Q M, inverted into Minv.
+__global__ void galerkin_schur_inv_kernel(int n, const double* __restrict__ Q, Stencil9 M, double G, double dce,
+                                          double* __restrict__ Minv) {
+  __shared__ double aug[kMaxCoarseM * 2 * kMaxCoarseM];
+  __shared__ double fac[kMaxCoarseM];
+  const int m = n * n, w = 2 * m;
+  // right half: T = Q M
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx / m, c = idx - r * m;
+    double t = 0.0;
+    for (int k = 0; k < m; ++k) t = fma(Q[r * m + k], mass_entry(M, n, k, c), t);
+    aug[r * w + m + c] = t;
+  }
+  __syncthreads();
+  // left half: G M + dce M T
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx / m, c = idx - r * m;
+    double t = 0.0;
+    for (int k = 0; k < m; ++k) t = fma(mass_entry(M, n, r, k), aug[k * w + m + c], t);
+    aug[r * w + c] = G * mass_entry(M, n, r, c) + dce * t;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx / m, c = idx - r * m;
+    aug[r * w + m + c] = (r == c) ? 1.0 : 0.0;
+  }
+  gauss_jordan(aug, fac, m);
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx / m, c = idx - r * m;
+    Minv[idx] = aug[r * w + m + c];
+  }
+}
+
+// One CTA, a thread per sample for the per-sample products and a thread per
+// node for the control system.  wz: [2][N][m] scratch (w_j, then y_j; z_j).
+__global__ void galerkin_coarse_solve_kernel(int n, int N, const double* __restrict__ Ainv,
+                                             const double* __restrict__ Minv, Stencil9 M, double c, double d,
+                                             double e, Vec3c<double> f, Vec3<double> x, double* __restrict__ wz) {
+  __shared__ double s_sum[kMaxCoarseM], s_rhs[kMaxCoarseM], s_u[kMaxCoarseM];
+  const int m = n * n;
+  double* W = wz;
+  double* Z = wz + (size_t)N * m;
+  double t[kMaxCoarseM];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double* A = Ainv + (size_t)j * m * m;
+    double* w = W + (size_t)j * m;
+    double* z = Z + (size_t)j * m;
+    for (int r = 0; r < m; ++r) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(A[r * m + k], f.p[(size_t)k * N + j], s);
+      w[r] = s;
+    }
+    for (int r = 0; r < m; ++r) t[r] = f.y[(size_t)r * N + j] - c * mass_apply(M, w, n, r);
+    for (int r = 0; r < m; ++r) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(A[r * m + k], t[k], s);
+      z[r] = s;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) s += Z[(size_t)j * m + r];
+    s_sum[r] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += blockDim.x) s_rhs[r] = f.u[r] - d * mass_apply(M, s_sum, n, r);
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s = fma(Minv[r * m + k], s_rhs[k], s);
+    s_u[r] = s;
+    x.u[r] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += blockDim.x) s_rhs[r] = mass_apply(M, s_u, n, r);   // M u
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double* A = Ainv + (size_t)j * m * m;
+    double* w = W + (size_t)j * m;   // becomes y_j
+    for (int r = 0; r < m; ++r) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(A[r * m + k], s_rhs[k], s);
+      w[r] -= e * s;
+      x.y[(size_t)r * N + j] = w[r];
+    }
+    for (int r = 0; r < m; ++r) t[r] = f.y[(size_t)r * N + j] - c * mass_apply(M, w, n, r);
+    for (int r = 0; r < m; ++r) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(A[r * m + k], t[k], s);
+      x.p[(size_t)r * N + j] = s;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_galerkin_coarse_setup(const CoarseData& C, const double* a9, const Stencil9& M, double c,
+                                         double G, double d, double e, cudaStream_t s) {
+  if (C.m > kMaxCoarseM) return cudaErrorInvalidValue;
+  galerkin_coarse_inv_kernel<<<C.N, 64, 0, s>>>(C.n, C.N, a9, C.Ainv);
+  double* Q = C.wz;   // at least m^2 doubles
+  galerkin_q_kernel<<<C.m * C.m, 128, 0, s>>>(C.n, C.N, C.Ainv, M, Q);
+  galerkin_schur_inv_kernel<<<1, 256, 0, s>>>(C.n, Q, M, G, d * c * e, C.Minv);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_coarse_solve(const CoarseData& C, const Stencil9& M, double c, double d, double e,
+                                         Vec3c<double> f, Vec3<double> x, cudaStream_t s) {
+  if (C.m > kMaxCoarseM || C.N > 1024) return cudaErrorInvalidValue;
+  const int threads = std::max(32, std::min(1024, (std::max(C.N, C.m) + 31) / 32 * 32));
+  galerkin_coarse_solve_kernel<<<1, threads, 0, s>>>(C.n, C.N, C.Ainv, C.Minv, M, c, d, e, f, x, C.wz);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_coarse_solve<double>(const CoarseData&, double, double, double, Vec3c<double>,
                                                  Vec3<double>, cudaStream_t, int);
 template cudaError_t launch_coarse_solve<float>(const CoarseData&, double, double, double, Vec3c<float>,

@@ -1,0 +1,215 @@
+// Galerkin coarse operators (Sec. 3: S_l = P^T S_{l-1} P with the bilinear
+// prolongation P and R = P^T), the operator the paper's experiments use.
+//
+// With P bilinear, the product of a 5- or 9-point stencil is a 9-point
+// stencil on the coarse grid, so every coarse grid stores A_j as nine planes
+// [9][n*n][N] (offset k = (dy+1)*3 + (dx+1), sample index fastest).  The
+// mass blocks (fine: the identity times the scalars c, G, d, e) become
+// c M_l, G M_l, d M_l, e M_l with one constant 9-point stencil M_l per grid:
+// both the fine and the coarse nodes that enter an entry (C, D) of the
+// product are interior, so the constant fine stencil gives a constant coarse
+// one.
+#include "cmg_common.cuh"
+
+namespace cmg {
+
+namespace {
+
+constexpr int kGBlock = 256;
+
+// The coarse nodes that a fine node 2C+1+g (one axis, g in [-2, 2]) takes
+// its bilinear interpolant from, as offsets from C, with their weights: g
+// even sits on the coarse node C + g/2 (weight 1); g odd lies halfway
+// between C + (g-1)/2 and C + (g+1)/2 (1/2 each).
+__host__ __device__ inline int coarse_targets(int g, int* off, double* wt) {
+  if ((g & 1) == 0) {
+    off[0] = g / 2;
+    wt[0] = 1.0;
+    return 1;
+  }
+  off[0] = (g - 1) / 2;
+  off[1] = (g + 1) / 2;
+  wt[0] = wt[1] = 0.5;
+  return 2;
+}
+
+// One thread per (coarse node C, sample j): entry (C, C+o) of P^T A P is
+// the sum over the fine nodes f of C's interpolation stencil (weight
+// P(f, C)) and the fine neighbours g of f (operator entry A(f, g)) of
+// P(f, C) A(f, g) P(g, C + o).  Fine nodes outside the grid are Dirichlet
+// (no entry); coarse nodes outside the grid receive nothing.
+__global__ void galerkin_setup_kernel(int nf, int N, const double* __restrict__ kx, const double* __restrict__ ky,
+                                      const double* __restrict__ in9, double* __restrict__ out9) {
+  const int nc = (nf - 1) / 2;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)nc * nc * N) return;
+  const int j = (int)(t % N);
+  const long C = t / N;
+  const int cy = (int)(C / nc), cx = (int)(C - (long)cy * nc);
+  const size_t fnodes = (size_t)nf * nf, cnodes = (size_t)nc * nc;
+  const double w1[3] = {0.5, 1.0, 0.5};
+  double acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+  for (int a = -1; a <= 1; ++a)
+    for (int b = -1; b <= 1; ++b) {
+      const int fy = 2 * cy + 1 + a, fx = 2 * cx + 1 + b;   // in [0, nf): nf = 2 nc + 1
+      const double wf = w1[a + 1] * w1[b + 1];
+      const long fnode = (long)fy * nf + fx;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int gy = fy + dy, gx = fx + dx;
+          if (gy < 0 || gy >= nf || gx < 0 || gx >= nf) continue;
+          double v;
+          if (in9) {
+            v = in9[((size_t)((dy + 1) * 3 + dx + 1) * fnodes + fnode) * N + j];
+          } else {
+            // the finest grid's 5-point stencil from its face coefficients
+            const double kW = kx[((size_t)fy * (nf + 1) + fx) * N + j];
+            const double kE = kx[((size_t)fy * (nf + 1) + fx + 1) * N + j];
+            const double kS = ky[((size_t)fy * nf + fx) * N + j];
+            const double kN = ky[((size_t)(fy + 1) * nf + fx) * N + j];
+            if (dy == 0 && dx == 0) v = (kW + kE) + (kS + kN);
+            else if (dy == 0) v = dx < 0 ? -kW : -kE;
+            else if (dx == 0) v = dy < 0 ? -kS : -kN;
+            else continue;   // corners: no entry
+          }
+          int oy[2], ox[2];
+          double wy[2], wx[2];
+          const int ny = coarse_targets(a + dy, oy, wy), nx = coarse_targets(b + dx, ox, wx);
+          for (int p = 0; p < ny; ++p)
+            for (int q = 0; q < nx; ++q) {
+              const int Dy = cy + oy[p], Dx = cx + ox[q];
+              if (Dy < 0 || Dy >= nc || Dx < 0 || Dx >= nc) continue;
+              acc[(oy[p] + 1) * 3 + (ox[q] + 1)] += wf * v * (wy[p] * wx[q]);
+            }
+        }
+    }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out9[((size_t)k * cnodes + C) * N + j] = acc[k];
+}
+
+// One warp per node, lanes over samples: inva = 1 / (A_j)_ii and
+// isigma = 1 / (G + dce sum_j inva^2) (fixed-order shuffle reduction).
+__global__ void galerkin_diag_kernel(long nodes, int N, const double* __restrict__ a9, double* __restrict__ inva,
+                                     double* __restrict__ isigma, double dce, double G) {
+  const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (node >= nodes) return;   // whole warp
+  const double* centre = a9 + (size_t)4 * nodes * N;
+  double s = 0.0;
+  for (int j = lane; j < N; j += 32) {
+    const double ia = 1.0 / centre[(size_t)node * N + j];
+    inva[(size_t)node * N + j] = ia;
+    s += ia * ia;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) isigma[node] = 1.0 / (G + dce * s);
+}
+
+// State and adjoint rows, one thread per (node, sample):
+//   r_y = f_y - (c (M y_j)_i + (A_j p_j)_i),  r_p = f_p - ((A_j y_j)_i + e (M u)_i).
+__global__ void residual9_yp_kernel(int n, int N, const double* __restrict__ a9, Stencil9 M, double c, double e,
+                                    Vec3c<double> x, Vec3c<double> f, Vec3<double> r) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nodes = (size_t)n * n;
+  if (t >= (long)nodes * N) return;
+  const int j = (int)(t % N);
+  const long i = t / N;
+  const int iy = (int)(i / n), ix = (int)(i - (long)iy * n);
+  double Ap = 0.0, Ay = 0.0, My = 0.0, Mu = 0.0;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int ny = iy + dy, nx = ix + dx;
+      if (ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
+      const int k = (dy + 1) * 3 + (dx + 1);
+      const size_t nb = (size_t)ny * n + nx;
+      const double a = a9[((size_t)k * nodes + i) * N + j];
+      const double yv = x.y[nb * N + j], pv = x.p[nb * N + j];
+      Ap = fma(a, pv, Ap);
+      Ay = fma(a, yv, Ay);
+      My = fma(M.w[k], yv, My);
+      Mu = fma(M.w[k], x.u[nb], Mu);
+    }
+  const double sy = c * My + Ap, sp = Ay + e * Mu;
+  const size_t o = (size_t)i * N + j;
+  r.y[o] = f.y ? f.y[o] - sy : sy;
+  r.p[o] = f.y ? f.p[o] - sp : sp;
+}
+
+// Control row, one thread per node: r_u = f_u - (G (M u)_i + d (M sum_j p_j)_i).
+__global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stencil9 M, double G, double d,
+                                   Vec3c<double> x, Vec3c<double> f, Vec3<double> r) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)n * n) return;
+  const int iy = (int)(i / n), ix = (int)(i - (long)iy * n);
+  double Mu = 0.0, Mp = 0.0;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int ny = iy + dy, nx = ix + dx;
+      if (ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
+      const int k = (dy + 1) * 3 + (dx + 1);
+      const size_t nb = (size_t)ny * n + nx;
+      Mu = fma(M.w[k], x.u[nb], Mu);
+      Mp = fma(M.w[k], psum[nb], Mp);
+    }
+  const double su = G * Mu + d * Mp;
+  r.u[i] = f.y ? f.u[i] - su : su;
+}
+
+unsigned blocks_for(long threads) { return (unsigned)((threads + kGBlock - 1) / kGBlock); }
+
+}  // namespace
+
+Stencil9 galerkin_mass(const Stencil9& fine) {
+  // the setup kernel's triple product with a constant stencil and no grid
+  // boundary (every node entering an interior entry is interior)
+  Stencil9 out{};
+  const double w1[3] = {0.5, 1.0, 0.5};
+  for (int a = -1; a <= 1; ++a)
+    for (int b = -1; b <= 1; ++b)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const double v = fine.w[(dy + 1) * 3 + dx + 1];
+          if (v == 0.0) continue;
+          int oy[2], ox[2];
+          double wy[2], wx[2];
+          const int ny = coarse_targets(a + dy, oy, wy), nx = coarse_targets(b + dx, ox, wx);
+          for (int p = 0; p < ny; ++p)
+            for (int q = 0; q < nx; ++q)
+              out.w[(oy[p] + 1) * 3 + (ox[q] + 1)] += w1[a + 1] * w1[b + 1] * v * (wy[p] * wx[q]);
+        }
+  return out;
+}
+
+cudaError_t launch_galerkin_setup(int nf, int N, const double* kx, const double* ky, const double* in9, double* out9,
+                                  cudaStream_t s) {
+  const int nc = (nf - 1) / 2;
+  const long threads = (long)nc * nc * N;
+  if (threads == 0) return cudaSuccess;
+  galerkin_setup_kernel<<<blocks_for(threads), kGBlock, 0, s>>>(nf, N, kx, ky, in9, out9);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_diag(int n, int N, const double* a9, double* inva, double* isigma, double dce, double G,
+                                 cudaStream_t s) {
+  const long nodes = (long)n * n;
+  galerkin_diag_kernel<<<blocks_for(nodes * 32), kGBlock, 0, s>>>(nodes, N, a9, inva, isigma, dce, G);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
+                             double e, Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* psum,
+                             cudaStream_t s) {
+  const long nodes = (long)n * n;
+  cudaError_t err = launch_sum_samples(nodes, N, x.p, psum, s);
+  if (err != cudaSuccess) return err;
+  residual9_yp_kernel<<<blocks_for(nodes * N), kGBlock, 0, s>>>(n, N, a9, M, c, e, x, f, r);
+  residual9_u_kernel<<<blocks_for(nodes), kGBlock, 0, s>>>(n, psum, M, G, d, x, f, r);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace cmg

@@ -297,6 +297,39 @@ cudaError_t launch_scale_cast(double a, const Tx* x, Ty* y, size_t n, cudaStream
 cudaError_t launch_rhs(int n, int N, double h, const double* yd, const double* fsrc, double* fy,
                        double* fu, double* fp, cudaStream_t s);
 
+// ---- Galerkin coarse operators (cmg_galerkin.cu, cmg_coarse.cu) ----
+// Sec. 3 builds the coarse matrices as S_l = P^T S_{l-1} P with the bilinear
+// P.  On a coarse grid every block is then a 9-point stencil: A_j variable
+// ([9][n*n][N], offset k = (dy+1)*3 + (dx+1)) and the mass M_l constant
+// (Stencil9; M_0 = I), the blocks c M_l, G M_l, d M_l, e M_l with the finest
+// grid's c, G, d, e.
+struct Stencil9 {
+  double w[9];
+};
+// M_l from M_{l-1} (the same triple product with a constant stencil).
+Stencil9 galerkin_mass(const Stencil9& fine);
+// out9 = P^T A P on the (nf-1)/2 grid, from the finest grid's faces (in9 ==
+// nullptr) or from the 9-point A of the nf grid.
+cudaError_t launch_galerkin_setup(int nf, int N, const double* kx, const double* ky, const double* in9, double* out9,
+                                  cudaStream_t s);
+// inva = 1 / (A_j)_ii, isigma = 1 / (G + dce sum_j inva^2) (the Schur
+// denominator of Eq. (13) with the diagonal entries of the blocks).
+cudaError_t launch_galerkin_diag(int n, int N, const double* a9, double* inva, double* isigma, double dce, double G,
+                                 cudaStream_t s);
+// r = f - S_l x (r = S_l x when f.y == nullptr) with 9-point blocks; psum:
+// scratch [n*n] for the sums over samples of x.p.
+cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
+                             double e, Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* psum,
+                             cudaStream_t s);
+// Coarsest grid: A_j^{-1} per sample from the 9-point stencil, and the
+// inverse of the control Schur matrix G M + d c e M (sum_j A_j^{-1} M A_j^{-1}) M.
+cudaError_t launch_galerkin_coarse_setup(const CoarseData& C, const double* a9, const Stencil9& M, double c,
+                                         double G, double d, double e, cudaStream_t s);
+// x = S_L^{-1} f on the coarsest grid by block elimination with the
+// non-diagonal mass (x and f must not overlap).
+cudaError_t launch_galerkin_coarse_solve(const CoarseData& C, const Stencil9& M, double c, double d, double e,
+                                         Vec3c<double> f, Vec3<double> x, cudaStream_t s);
+
 // ---- warm-start network kernels (cmg_nn_*.cu) ----
 // mean over samples of log kappa_j at the n x n interior nodes of the finest grid.
 cudaError_t launch_mean_log_kappa(int n, int N, int K, double amp, const double* xi, double* out, cudaStream_t s);
