@@ -40,7 +40,8 @@ struct Lev {
   float* d32[3] = {nullptr, nullptr, nullptr};   // finest grid: FP32 correction since the last refinement anchor
   float* dw = nullptr;                   // per-node factor on d (1; semismooth Newton: active-set indicator)
   // Galerkin coarse operators (grids below the finest): 9-point A_j planes
-  // [9][n*n][N], the mass stencil M_l, and a scratch [n*n] for sample sums.
+  // [9][n*n][N], the mass stencil M_l, and a scratch [2 n*n] for the
+  // 9-point residual (sums over samples, then M u).
   // c, G, d, e above then hold the diagonal entries (times M_l's centre).
   double* a9 = nullptr;
   double* psum = nullptr;
@@ -641,7 +642,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
   if (P.coarse_coeff == CMG_COARSE_GALERKIN)
     for (int l = 1; l < L; ++l) {
       AL(h->lv[l].a9, 9 * h->lv[l].nodes * N);
-      AL(h->lv[l].psum, h->lv[l].nodes);
+      AL(h->lv[l].psum, 2 * h->lv[l].nodes);
     }
   const size_t g = (size_t)P.n + 2;
   AL(h->kap, g * g * N + g * N);

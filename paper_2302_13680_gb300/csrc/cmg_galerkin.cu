@@ -107,17 +107,36 @@ __global__ void galerkin_diag_kernel(long nodes, int N, const double* __restrict
   if (lane == 0) isigma[node] = 1.0 / (G + dce * s);
 }
 
+// The three kernels of the 9-point residual run as a programmatic-dependent
+// chain: the sums over samples of p, then the control row (which also leaves
+// (M u)_i for the others), then the state and adjoint rows.
+
+// psum[i] = sum_j p[i][j]: one warp per node, fixed-order shuffle reduction.
+__global__ void galerkin_psum_kernel(long nodes, int N, const double* __restrict__ p, double* __restrict__ psum) {
+  pdl_enter();
+  const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (node >= nodes) return;   // whole warp
+  double s = 0.0;
+  for (int j = lane; j < N; j += 32) s += p[(size_t)node * N + j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) psum[node] = s;
+}
+
 // State and adjoint rows, one thread per (node, sample):
-//   r_y = f_y - (c (M y_j)_i + (A_j p_j)_i),  r_p = f_p - ((A_j y_j)_i + e (M u)_i).
+//   r_y = f_y - (c (M y_j)_i + (A_j p_j)_i),  r_p = f_p - ((A_j y_j)_i + e (M u)_i),
+// with (M u)_i from the control-row kernel (mu).
 __global__ void residual9_yp_kernel(int n, int N, const double* __restrict__ a9, Stencil9 M, double c, double e,
-                                    Vec3c<double> x, Vec3c<double> f, Vec3<double> r) {
+                                    const double* __restrict__ mu, Vec3c<double> x, Vec3c<double> f,
+                                    Vec3<double> r) {
+  pdl_enter();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nodes = (size_t)n * n;
   if (t >= (long)nodes * N) return;
   const int j = (int)(t % N);
   const long i = t / N;
   const int iy = (int)(i / n), ix = (int)(i - (long)iy * n);
-  double Ap = 0.0, Ay = 0.0, My = 0.0, Mu = 0.0;
+  double Ap = 0.0, Ay = 0.0, My = 0.0;
   for (int dy = -1; dy <= 1; ++dy)
     for (int dx = -1; dx <= 1; ++dx) {
       const int ny = iy + dy, nx = ix + dx;
@@ -129,17 +148,18 @@ __global__ void residual9_yp_kernel(int n, int N, const double* __restrict__ a9,
       Ap = fma(a, pv, Ap);
       Ay = fma(a, yv, Ay);
       My = fma(M.w[k], yv, My);
-      Mu = fma(M.w[k], x.u[nb], Mu);
     }
-  const double sy = c * My + Ap, sp = Ay + e * Mu;
+  const double sy = c * My + Ap, sp = Ay + e * mu[i];
   const size_t o = (size_t)i * N + j;
   r.y[o] = f.y ? f.y[o] - sy : sy;
   r.p[o] = f.y ? f.p[o] - sp : sp;
 }
 
-// Control row, one thread per node: r_u = f_u - (G (M u)_i + d (M sum_j p_j)_i).
+// Control row, one thread per node: r_u = f_u - (G (M u)_i + d (M sum_j p_j)_i);
+// (M u)_i is also left in mu.
 __global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stencil9 M, double G, double d,
-                                   Vec3c<double> x, Vec3c<double> f, Vec3<double> r) {
+                                   Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* __restrict__ mu) {
+  pdl_enter();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)n * n) return;
   const int iy = (int)(i / n), ix = (int)(i - (long)iy * n);
@@ -155,6 +175,7 @@ __global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stenc
     }
   const double su = G * Mu + d * Mp;
   r.u[i] = f.y ? f.u[i] - su : su;
+  mu[i] = Mu;
 }
 
 unsigned blocks_for(long threads) { return (unsigned)((threads + kGBlock - 1) / kGBlock); }
@@ -204,12 +225,15 @@ cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, 
                              double e, Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* psum,
                              cudaStream_t s) {
   const long nodes = (long)n * n;
-  cudaError_t err = launch_sum_samples(nodes, N, x.p, psum, s);
-  if (err != cudaSuccess) return err;
-  residual9_yp_kernel<<<blocks_for(nodes * N), kGBlock, 0, s>>>(n, N, a9, M, c, e, x, f, r);
-  residual9_u_kernel<<<blocks_for(nodes), kGBlock, 0, s>>>(n, psum, M, G, d, x, f, r);
-  count_launches(2);
-  return cudaGetLastError();
+  double* mu = psum + nodes;
+  cudaError_t err = launch_k(galerkin_psum_kernel, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N, x.p, psum);
+  if (err == cudaSuccess)
+    err = launch_k(residual9_u_kernel, blocks_for(nodes), kGBlock, 0, s, n, (const double*)psum, M, G, d, x, f, r, mu);
+  if (err == cudaSuccess)
+    err = launch_k(residual9_yp_kernel, blocks_for(nodes * N), kGBlock, 0, s, n, N, a9, M, c, e, (const double*)mu,
+                   x, f, r);
+  count_launches(3);
+  return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 }  // namespace cmg

@@ -317,7 +317,7 @@ cudaError_t launch_galerkin_setup(int nf, int N, const double* kx, const double*
 cudaError_t launch_galerkin_diag(int n, int N, const double* a9, double* inva, double* isigma, double dce, double G,
                                  cudaStream_t s);
 // r = f - S_l x (r = S_l x when f.y == nullptr) with 9-point blocks; psum:
-// scratch [n*n] for the sums over samples of x.p.
+// scratch [2 n*n] (the sums over samples of x.p, then (M u)_i).
 cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
                              double e, Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* psum,
                              cudaStream_t s);
