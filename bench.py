@@ -69,6 +69,25 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of the instance a rank solves: every rank an independent problem
+    (replicas; the units shard with no collective on the data path)."""
+    return seed + 1000 * rank
+
+
+def job_throughput(total_s: float, units: float, dist=None, device=None):
+    """Whole-job (value, time, units): the slowest rank's timed seconds (MAX)
+    and the units every rank processed (SUM); dist = torch.distributed or None."""
+    import torch
+
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+
+
 def tolerance(name: str) -> float:
     """Relative residual target: 1e-10, except at n = 1023 where the FP64
     rounding floor of the relative residual (about 5e-16 (n+1)^2 kappa) lies
@@ -308,7 +327,7 @@ def run_cmg(args, world, rank, local):
         torch.cuda.synchronize()
 
     base = dict(inputs.CONFIGS[args.config])
-    base["seed"] = base["seed"] + 1000 * rank          # one independent instance per rank
+    base["seed"] = rank_seed(base["seed"], rank)          # one independent instance per rank
     pr = inputs.make_problem(**base)
     n, N = pr.n, pr.N
     unknowns = (2 * N + 1) * n * n
@@ -404,14 +423,7 @@ def run_cmg(args, world, rank, local):
     # events around its launches (an open profiling window runs the
     # refinement loop eagerly instead of as a graph; kernels are identical)
     _, _, (dom_ms, dom_cnt), _ = timed_steps(chosen, max(2, min(args.steps, 10)), profile_kind=dom)
-    total_s = sum(times) / 1e3
-    t_local = torch.tensor([total_s], dtype=torch.float64, device=dev)
-    units_local = torch.tensor([float(unknowns * sum(cycles))], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        dist.all_reduce(units_local, op=dist.ReduceOp.SUM)
-    total_s = float(t_local.item())
-    value = float(units_local.item()) / total_s
+    value, total_s, _ = job_throughput(sum(times) / 1e3, unknowns * sum(cycles), dist, dev)
 
     # --- end to end through the public API with host buffers
     xi_h = torch.tensor(pr.xi).pin_memory()
@@ -497,7 +509,7 @@ def run_batch(args, world, rank, local):
     from paper_2302_13680_gb300 import cmg as C
 
     torch.cuda.set_device(local)
-    probs = inputs.batch_problems(seed=4 + 1000 * rank)
+    probs = inputs.batch_problems(seed=rank_seed(4, rank))
     B = P.Batch(probs)
     B.autotune(P.FP32)
     fs = []
@@ -592,7 +604,7 @@ def run_ssn(args, world, rank, local):
     torch.cuda.set_device(local)
     sc = SSN_CONFIGS[args.config]
     base = dict(inputs.CONFIGS[sc["base"]])
-    base["seed"] = base["seed"] + 1000 * rank
+    base["seed"] = rank_seed(base["seed"], rank)
     base["nu"] = sc["nu"]
     pr = inputs.make_problem(**base)
     n, N = pr.n, pr.N
@@ -687,7 +699,7 @@ def run_galerkin(args, world, rank, local):
 
     torch.cuda.set_device(local)
     base = dict(inputs.CONFIGS[GALERKIN_CONFIGS[args.config]["base"]])
-    base["seed"] = base["seed"] + 1000 * rank
+    base["seed"] = rank_seed(base["seed"], rank)
     pr = inputs.make_problem(**base)
     n, N = pr.n, pr.N
     unknowns = (2 * N + 1) * n * n

@@ -909,6 +909,12 @@ cmg_status autotune_levels(cmg_handle* h, int* chosen) {
   const int k = sizeof(T) == 8 ? 0 : 1;
   for (int l = 0; l + 1 < h->L; ++l) {
     Lev& v = h->lv[l];
+    if (sizeof(T) == 8 && h->galerkin() && l > 0) {
+      // Galerkin grids have no face arrays and never run the timed sweeps
+      v.spl_target[k] = 0;
+      if (chosen) chosen[l] = 0;
+      continue;
+    }
     CK(zero_vec<T>(h, l, Work<T>::x(v)));
     CK(zero_vec<T>(h, l, Work<T>::f(v)));
     const int reps = v.n >= 255 ? 8 : 16;

@@ -183,3 +183,21 @@ def test_unsupported_combinations_are_refused(P):
         H.close()
     with pytest.raises(P.CMGError):
         P.Hierarchy(15, 4, xi, 1e-3, 0.8, coarse="galerkin", control_box=(0.25, 0.75, 0.25, 0.75))
+
+
+def test_fp64_autotune_skips_galerkin_grids(P):
+    """The FP64 autotuner times red-black sweeps; Galerkin grids below the
+    finest run the Jacobi path only and are left at the size heuristic."""
+    xi = inputs.draw_xi(7, 5, 3)
+    H = P.Hierarchy(15, 5, xi, 1e-3, 0.8, coarse="galerkin")
+    try:
+        chosen = H.autotune(P.FP64)
+        assert chosen[0] in (1, 2, 4) and all(t == 0 for t in chosen[1:])
+        levels = O.make_hierarchy(15, 5, 1e-3, O.sine_mode_field(xi, 0.8))
+        S = G.hierarchy(levels)
+        f = O.pack(O.fine_rhs(levels[0], inputs.target_sinsin(15)))
+        x = H.zeros(0)
+        st, _ = H.solve(jacobi(), dev(f, 15, 5), x, tol=1e-12, maxit=100)
+        assert_blocks(host(x), spla.spsolve(S[0].tocsc(), f), 15, 5, 1e-7, "solution after autotune")
+    finally:
+        H.close()
