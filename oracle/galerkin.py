@@ -18,7 +18,10 @@ that, from the definitions and nothing else:
   a sparse matrix, and S_c = P^T S P by sparse products, level by level;
 * collective Jacobi, Eq. (11): x += theta sum_i P_i S_ii^{-1} R_i (f - S x),
   with S_ii the (2N+1) x (2N+1) block of S on node i's unknowns, solved
-  densely (no use of its arrow structure);
+  densely (no use of its arrow structure); and the Gauss-Seidel variant the
+  paper names after Eq. (11): node groups in turn, each node's block row
+  solved with the current values of the others (red-black on the 5-point
+  finest grid, four colours (iy mod 2, ix mod 2) on the 9-point grids);
 * Algorithm 1 with that smoother, the residual f - S x by a sparse
   product, the transfers by P and P^T, and a sparse direct solve on the
   coarsest grid.
@@ -142,22 +145,58 @@ def jacobi_sweep(S: sp.csr_matrix, n: int, N: int, z: np.ndarray, f: np.ndarray,
     return out
 
 
+def colour_sweep(S: sp.csr_matrix, n: int, N: int, z: np.ndarray, f: np.ndarray, colours) -> np.ndarray:
+    """Collective block Gauss-Seidel (the variant named after Eq. (11)): the
+    groups of nodes in `colours` (lists of node indices, no two nodes of a
+    group coupled) in turn, each node's unknowns replaced by the solution of
+    its block row with the current values of all other unknowns."""
+    idx_all, B = node_blocks(S, n, N)
+    z = z.copy()
+    for nodes in colours:
+        idx = idx_all[nodes]
+        r = f - S @ z
+        z[idx] += np.linalg.solve(B[nodes], r[idx][..., None])[..., 0]
+    return z
+
+
+def four_colours(n: int):
+    """Nodes by (iy mod 2, ix mod 2), in the order (0,0), (0,1), (1,0), (1,1):
+    a 9-point stencil couples no two nodes of one group."""
+    iy, ix = np.divmod(np.arange(n * n), n)
+    return [np.flatnonzero((iy % 2 == a) & (ix % 2 == b)) for a in (0, 1) for b in (0, 1)]
+
+
+def red_black(n: int):
+    """Red ((ix + iy) even) then black: the 5-point finest grid's ordering."""
+    iy, ix = np.divmod(np.arange(n * n), n)
+    return [np.flatnonzero((iy + ix) % 2 == c) for c in (0, 1)]
+
+
+def smooth(S, ns, N: int, l: int, z, f, smoother: str, theta: float):
+    """One sweep on grid l: damped collective Jacobi, or Gauss-Seidel in
+    red-black order on the finest (5-point) grid and in four colours on the
+    Galerkin (9-point) grids."""
+    if smoother == "jacobi":
+        return jacobi_sweep(S[l], ns[l], N, z, f, theta)
+    return colour_sweep(S[l], ns[l], N, z, f, red_black(ns[l]) if l == 0 else four_colours(ns[l]))
+
+
 def cycle(S, ns, N: int, l: int, z: np.ndarray, f: np.ndarray, n1: int = 2, n2: int = 2, theta: float = 0.5,
-          gamma: int = 1) -> np.ndarray:
+          gamma: int = 1, smoother: str = "jacobi") -> np.ndarray:
     """Algorithm 1 on packed vectors with the Galerkin matrices S[l] on the
     grids ns[l] (finest first); gamma = 2 gives the W-cycle."""
     if l == len(S) - 1:
         return spla.spsolve(S[l].tocsc(), f)
     for _ in range(n1):
-        z = jacobi_sweep(S[l], ns[l], N, z, f, theta)
+        z = smooth(S, ns, N, l, z, f, smoother, theta)
     P = prolongation_matrix(ns[l], N)
     fc = P.T @ (f - S[l] @ z)
     ec = np.zeros(S[l + 1].shape[0])
     for _ in range(gamma):
-        ec = cycle(S, ns, N, l + 1, ec, fc, n1, n2, theta, gamma)
+        ec = cycle(S, ns, N, l + 1, ec, fc, n1, n2, theta, gamma, smoother)
     z = z + P @ ec
     for _ in range(n2):
-        z = jacobi_sweep(S[l], ns[l], N, z, f, theta)
+        z = smooth(S, ns, N, l, z, f, smoother, theta)
     return z
 
 

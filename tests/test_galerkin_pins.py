@@ -183,3 +183,61 @@ def test_galerkin_cycle_converges_to_the_direct_solution(gamma):
     # scaling from x = 0, for every coarse-operator rule), about 0.3 per cycle
     assert all(b < a for a, b in zip(hist[1:], hist[2:]))
     assert (hist[-1] / hist[3]) ** (1.0 / (len(hist) - 4)) < 0.4
+
+
+def test_four_colour_sweep_is_block_gauss_seidel_in_colour_order():
+    """One four-colour sweep on a Galerkin grid equals the textbook block
+    Gauss-Seidel step (D + L) z' = f - U z in the node order the colours
+    give (L, U: couplings to earlier / later nodes of that order), solved
+    as one sparse triangular-block system; and no two nodes of a colour
+    are coupled."""
+    N = 2
+    levels = hier(15, N)
+    S = G.hierarchy(levels)
+    l, n = 1, levels[1].n
+    m = n * n
+    cols = G.four_colours(n)
+    for c in cols:
+        for i in c:
+            for k in c:
+                if i != k:
+                    assert S[l][G.node_indices(n, N, i)][:, G.node_indices(n, N, k)].nnz == 0
+    order = np.concatenate(cols)                       # node order of the sweep
+    rank = np.empty(m, dtype=int)
+    rank[order] = np.arange(m)
+    perm = np.concatenate([G.node_indices(n, N, i) for i in order])
+    A = S[l].toarray()[np.ix_(perm, perm)]
+    blk = np.repeat(rank[order], 2 * N + 1)            # sweep position of every permuted unknown
+    lower = blk[:, None] >= blk[None, :]               # block lower triangle, diagonal blocks included
+    rng = np.random.default_rng(31)
+    z = rng.standard_normal(S[l].shape[0])
+    f = rng.standard_normal(S[l].shape[0])
+    zp, fp = z[perm], f[perm]
+    DL, U = np.where(lower, A, 0.0), np.where(lower, 0.0, A)
+    ref = np.empty_like(z)
+    ref[perm] = np.linalg.solve(DL, fp - U @ zp)
+    got = G.colour_sweep(S[l], n, N, z, f, cols)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_red_black_sweep_on_the_finest_grid_matches_eq13_sweep():
+    N = 3
+    lv = hier(7, N)[0]
+    rng = np.random.default_rng(33)
+    x = (rng.standard_normal((7, 7, N)), rng.standard_normal((7, 7)), rng.standard_normal((7, 7, N)))
+    f = tuple(b * s for b, s in zip((rng.standard_normal((7, 7, N)), rng.standard_normal((7, 7)),
+                                     rng.standard_normal((7, 7, N))), (lv.c, lv.G, lv.h ** 2)))
+    got = G.colour_sweep(G.system_matrix(lv), 7, N, O.pack(x), O.pack(f), G.red_black(7))
+    ref = O.pack(O.rbgs_sweep(lv, x, f))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_gauss_seidel_galerkin_cycle_converges_to_the_direct_solution():
+    N = 3
+    levels = hier(15, N, nu=1e-4)
+    S = G.hierarchy(levels)
+    f = O.pack(O.fine_rhs(levels[0], inputs.target_sinsin(15)))
+    z, it, hist = G.solve_stationary(S, [lv.n for lv in levels], N, f, tol=1e-10, maxit=60, smoother="gs")
+    assert hist[-1] <= 1e-10 and it < 20
+    ref = spla.spsolve(S[0].tocsc(), f)
+    assert np.abs(z - ref).max() <= 1e-7 * np.abs(ref).max()
