@@ -691,11 +691,12 @@ GALERKIN_CONFIGS = {"n255_N64_galerkin": dict(base="n255_N64")}
 
 def run_galerkin(args, world, rank, local):
     """The paper's own coarse operators (Sec. 3: S_l = P^T S_{l-1} P) against
-    rediscretised ones, both with FP64 collective Jacobi V(2,2), theta = 0.5
-    (the smoother of the paper's experiments), stationary and as FGMRES
-    preconditioner; a step = coefficient set-up for the sample set (the
-    Galerkin triple products included) + solve to 1e-10.  Units = unknowns
-    x cycles."""
+    rediscretised ones, FP64 V(2,2) with collective Jacobi, theta = 0.5 (the
+    smoother of the paper's experiments) or collective Gauss-Seidel (red-black
+    on the finest grid, four colours on the 9-point Galerkin grids),
+    stationary and as FGMRES preconditioner; a step = coefficient set-up for
+    the sample set (the Galerkin triple products included) + solve to 1e-10.
+    Units = unknowns x cycles."""
     import torch
 
     import __graft_entry__
@@ -715,16 +716,17 @@ def run_galerkin(args, world, rank, local):
     xi_dev = torch.tensor(pr.xi, dtype=torch.float64, device="cuda")
     fs = {k: H.rhs(torch.tensor(pr.yd.reshape(-1), device="cuda")) for k, H in hier.items()}
     xs = {k: H.zeros(0) for k, H in hier.items()}
-    opts = P.CycleOptions(smoother=P.SMOOTH_JACOBI, theta=0.5, precision=P.FP64)
-    forms = {f"{k}-{m}": (k, P.METHOD_CYCLE if m == "cycle" else P.METHOD_FGMRES)
-             for k in hier for m in ("cycle", "fgmres")}
+    smoothers = {"jacobi": P.SMOOTH_JACOBI, "gs": P.SMOOTH_RBGS}
+    forms = {f"{k}-{sm}-{m}": (k, smoothers[sm], P.METHOD_CYCLE if m == "cycle" else P.METHOD_FGMRES)
+             for k in hier for sm in smoothers for m in ("cycle", "fgmres")}
 
     def step(form):
-        k, method = forms[form]
+        k, smoother, method = forms[form]
         H = hier[k]
         H.set_samples(xi_dev)
         for t in xs[k]:
             t.zero_()
+        opts = P.CycleOptions(smoother=smoother, theta=0.5, precision=P.FP64)
         st, _ = H.solve(opts, fs[k], xs[k], method=method, tol=TOL, maxit=200, restart=30)
         return st
 
@@ -761,13 +763,13 @@ def run_galerkin(args, world, rank, local):
     redis = min((f for f in forms if f.startswith("rediscretised")), key=lambda f: survey[f]["time_to_tol_ms"])
     if rank == 0:
         line = {"metric": "time-to-1e-10 residual & unknowns*cycles/s: Galerkin coarse operators (Sec. 3) "
-                          "vs rediscretised, FP64 collective Jacobi V(2,2)",
+                          "vs rediscretised, FP64 collective V(2,2)",
                 "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": statistics.mean(times), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"collective MG with Galerkin coarse operators, n={n}, N={N}, K={pr.K}, "
-                                       f"amp={pr.amp}, nu={pr.nu:g}, FP64 Jacobi V(2,2) theta=0.5 to 3x3, "
-                                       f"tol {TOL:g}, set-up per step",
+                                       f"amp={pr.amp}, nu={pr.nu:g}, FP64 V(2,2) (Jacobi theta=0.5 or "
+                                       f"Gauss-Seidel) to 3x3, tol {TOL:g}, set-up per step",
                            "n": n, "N": N, "unknowns": unknowns, "instances_per_gpu": 1,
                            "parallelism": f"replicas x{world} (independent instances, no collective)"},
                 "form": chosen, "forms": survey,

@@ -76,9 +76,11 @@ typedef struct {
                        CMG_COARSE_GALERKIN: no rediscretisation -- the coarse matrices are the
                        Galerkin products S_l = P^T S_{l-1} P of Sec. 3 (the operator of the
                        paper's experiments): 9-point A_j and a 9-point mass M_l on every grid
-                       below the finest.  FP64 cycles with the collective Jacobi smoother only
-                       (cmg_cycle.precision = CMG_FP64, smoother = CMG_SMOOTH_JACOBI, freeze_u = 0;
-                       tail_n is ignored), distributed control only (ctl_box all zero), no
+                       below the finest.  FP64 cycles only (cmg_cycle.precision = CMG_FP64,
+                       freeze_u = 0; tail_n is ignored); CMG_SMOOTH_JACOBI as on any grid, and
+                       CMG_SMOOTH_RBGS = red-black Gauss-Seidel on the finest grid and four-colour
+                       (iy mod 2, ix mod 2) collective Gauss-Seidel on the 9-point grids;
+                       distributed control only (ctl_box all zero), no
                        semismooth Newton and no batches: those return CMG_ERR_UNSUPPORTED, as do
                        the _f32 level operations on such a handle */
   double ctl_box[4]; /* local control (Sec. 3.1 after Eq. (13); the local-control test case of

@@ -324,6 +324,20 @@ cudaError_t level_residual(cmg_handle* h, int l, Vec3c<T> x, Vec3c<T> f, Vec3<T>
 
 template <typename T>
 cudaError_t smooth(cmg_handle* h, const cmg_cycle& o, int l, int sweeps, Vec3<T> x, Vec3c<T> f) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->galerkin() && l > 0 && o.smoother == CMG_SMOOTH_RBGS) {
+      // Gauss-Seidel on a 9-point grid: four colours instead of two
+      const Lev& v = h->lv[l];
+      const Lev& f0 = h->lv[0];
+      for (int s = 0; s < sweeps; ++s) {
+        ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+        const cudaError_t e = launch_gs4_sweep(v.n, h->prob.N, v.a9, v.m9, f0.c, f0.G, f0.d, f0.e, v.inva, v.isigma,
+                                               x, f, v.psum, h->stream);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+  }
   const LevelView<T> L = view<T>(h, l, o.freeze_u);
   for (int s = 0; s < sweeps; ++s) {
     if (o.smoother == CMG_SMOOTH_RBGS) {
@@ -408,6 +422,7 @@ cudaError_t tail_cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3
 // the direct solve read u) nor for grids handed to the cluster tail.
 bool zero_guess_ok(const cmg_handle* h, const cmg_cycle& o, int l) {
   if (o.freeze_u) return false;
+  if (h->galerkin() && l > 0 && l < h->L - 1) return false;   // the zero-guess sweep is the 5-point red-black one
   if (o.tail_n > 0 && h->lv[l].n <= o.tail_n) return false;
   if (l == h->L - 1) return true;
   return o.smoother == CMG_SMOOTH_RBGS && o.n1 >= 1;
@@ -453,7 +468,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   Vec3<T> r = Work<T>::r(v);
   // after red-black pre-smoothing (last half-sweep: colour 1) with the control
   // updated, the residual vanishes at colour 1: compute and restrict colour 0
-  const int c0 = (o.smoother == CMG_SMOOTH_RBGS && o.n1 >= 1 && !o.freeze_u) ? 1 : 0;
+  const int c0 = (o.smoother == CMG_SMOOTH_RBGS && o.n1 >= 1 && !o.freeze_u && !(h->galerkin() && l > 0)) ? 1 : 0;
   {
     ProfScope ps(h, CMG_KERNEL_RESIDUAL, l);
     e = c0 ? launch_residual_c0<T>(view<T>(h, l), cview(x), f, r, h->stream)
@@ -507,9 +522,8 @@ cmg_status check_cycle(cmg_handle* h, const cmg_cycle* o) {
   if (o->freeze_u && h && h->L < 2) return fail(h, CMG_ERR_INVALID_ARG, "freeze_u needs at least two grids");
   if (o->smoother == CMG_SMOOTH_JACOBI && !(o->theta > 0.0 && o->theta <= 1.0))
     return fail(h, CMG_ERR_INVALID_ARG, "theta must be in (0, 1]");
-  if (h && h->galerkin() && (o->precision != CMG_FP64 || o->smoother != CMG_SMOOTH_JACOBI || o->freeze_u))
-    return fail(h, CMG_ERR_UNSUPPORTED,
-                "Galerkin coarse operators: FP64 cycles with the collective Jacobi smoother, control updated");
+  if (h && h->galerkin() && (o->precision != CMG_FP64 || o->freeze_u))
+    return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin coarse operators: FP64 cycles, control updated");
   return CMG_OK;
 }
 

@@ -178,6 +178,84 @@ __global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stenc
   mu[i] = Mu;
 }
 
+// Collective Gauss-Seidel on a 9-point grid, one colour (iy mod 2, ix mod 2)
+// = (cy, cx): no two nodes of a colour are coupled, so each node's block
+// row is solved with its neighbours' current values (Eq. (13) with the
+// diagonal entries of the Galerkin blocks; the variant named after Eq. (11)).
+// One warp per node, lanes over samples.  Pass 1 forms the local right sides
+//   B_y = f_y - sum_{k != centre} (c m_k y_k + A_k p_k),
+//   B_p = f_p - sum_{k != centre} (A_k y_k + e m_k u_k),
+//   B_u = f_u - sum_{k != centre} m_k (G u_k + d psum_k)
+// and parks B_p, B_y in the node's own y, p slots (read by no other thread
+// during this colour); pass 2 writes the solution and the node's new sum
+// over samples of p.  c, G, d, e: the finest grid's; the diagonal entries are
+// these times m_centre, a = (A_j)_ii; inva, isigma from galerkin_diag_kernel.
+__global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const double* __restrict__ a9, Stencil9 M, double c,
+                                  double G, double d, double e, const double* __restrict__ inva,
+                                  const double* __restrict__ isigma, Vec3<double> x, Vec3c<double> f,
+                                  double* __restrict__ psum) {
+  pdl_enter();
+  const int nbx = (n - cx + 1) / 2, nby = (n - cy + 1) / 2;
+  const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= (long)nbx * nby) return;   // whole warp
+  const int iy = cy + 2 * (int)(g / nbx), ix = cx + 2 * (int)(g % nbx);
+  const size_t nodes = (size_t)n * n;
+  const size_t i = (size_t)iy * n + ix;
+  const double mc = M.w[4];
+  const double cd = c * mc, dd = d * mc, ed = e * mc;   // diagonal entries of the mass blocks
+  double Bu = 0.0;
+  if (lane == 0) {
+    double s = f.u[i];
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ny = iy + dy, nx = ix + dx;
+        if ((dy == 0 && dx == 0) || ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
+        const size_t nb = (size_t)ny * n + nx;
+        const double mk = M.w[(dy + 1) * 3 + dx + 1];
+        s -= mk * (G * x.u[nb] + d * psum[nb]);
+      }
+    Bu = s;
+  }
+  double tacc = 0.0;
+  for (int j = lane; j < N; j += 32) {
+    double By = f.y[i * N + j], Bp = f.p[i * N + j];
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ny = iy + dy, nx = ix + dx;
+        if ((dy == 0 && dx == 0) || ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
+        const int k = (dy + 1) * 3 + dx + 1;
+        const size_t nb = (size_t)ny * n + nx;
+        const double a = a9[((size_t)k * nodes + i) * N + j];
+        const double yv = x.y[nb * N + j], pv = x.p[nb * N + j];
+        By -= c * M.w[k] * yv + a * pv;
+        Bp -= a * yv + e * M.w[k] * x.u[nb];
+      }
+    const double ia = inva[i * N + j];
+    tacc += (cd * ia) * (ia * Bp) - ia * By;
+    x.y[i * N + j] = Bp;   // parked until pass 2
+    x.p[i * N + j] = By;
+  }
+  for (int o = 16; o > 0; o >>= 1) tacc += __shfl_xor_sync(0xffffffffu, tacc, o);
+  Bu = __shfl_sync(0xffffffffu, Bu, 0);
+  const double u = (Bu + dd * tacc) * isigma[i];
+  double ps = 0.0;
+  for (int j = lane; j < N; j += 32) {
+    const double ia = inva[i * N + j];
+    const double Bp = x.y[i * N + j], By = x.p[i * N + j];
+    const double y = ia * (Bp - ed * u);
+    const double p = ia * (By - cd * y);
+    x.y[i * N + j] = y;
+    x.p[i * N + j] = p;
+    ps += p;
+  }
+  for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
+  if (lane == 0) {
+    x.u[i] = u;
+    psum[i] = ps;
+  }
+}
+
 unsigned blocks_for(long threads) { return (unsigned)((threads + kGBlock - 1) / kGBlock); }
 
 }  // namespace
@@ -233,6 +311,23 @@ cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, 
     err = launch_k(residual9_yp_kernel, blocks_for(nodes * N), kGBlock, 0, s, n, N, a9, M, c, e, (const double*)mu,
                    x, f, r);
   count_launches(3);
+  return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+cudaError_t launch_gs4_sweep(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
+                             double e, const double* inva, const double* isigma, Vec3<double> x, Vec3c<double> f,
+                             double* psum, cudaStream_t s) {
+  const long nodes = (long)n * n;
+  cudaError_t err = launch_k(galerkin_psum_kernel, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N,
+                             (const double*)x.p, psum);
+  for (int col = 0; col < 4 && err == cudaSuccess; ++col) {
+    const int cy = col >> 1, cx = col & 1;
+    const long groups = (long)((n - cx + 1) / 2) * ((n - cy + 1) / 2);
+    if (groups == 0) continue;
+    err = launch_k(gs4_colour_kernel, blocks_for(groups * 32), kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva,
+                   isigma, x, f, psum);
+  }
+  count_launches(5);
   return err != cudaSuccess ? err : cudaGetLastError();
 }
 

@@ -321,6 +321,12 @@ cudaError_t launch_galerkin_diag(int n, int N, const double* a9, double* inva, d
 cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
                              double e, Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* psum,
                              cudaStream_t s);
+// One collective Gauss-Seidel sweep in four colours (iy mod 2, ix mod 2) on
+// a 9-point grid (Eq. (13) per node with the Galerkin diagonal entries);
+// psum: scratch [n*n] (sums over samples of p, kept current by the sweep).
+cudaError_t launch_gs4_sweep(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
+                             double e, const double* inva, const double* isigma, Vec3<double> x, Vec3c<double> f,
+                             double* psum, cudaStream_t s);
 // Coarsest grid: A_j^{-1} per sample from the 9-point stencil, and the
 // inverse of the control Schur matrix G M + d c e M (sum_j A_j^{-1} M A_j^{-1}) M.
 cudaError_t launch_galerkin_coarse_setup(const CoarseData& C, const double* a9, const Stencil9& M, double c,

@@ -5,7 +5,9 @@ The oracle assembles S_0 from the block definition, forms the coarse
 matrices by sparse products, smooths with dense node-block solves and
 solves the coarsest grid with a sparse direct solver; the GPU builds 9-point
 stencils by a triple-product kernel and runs Eq. (13) with the Galerkin
-diagonal entries.  FP64 bars: operators within 1e-12 relative (max-norm per
+diagonal entries.  Both smoothers: damped collective Jacobi, and collective
+Gauss-Seidel (red-black on the 5-point finest grid, four colours on the
+9-point grids).  FP64 bars: operators within 1e-12 relative (max-norm per
 block), the coarsest direct solve within 1e-11; one Jacobi sweep within 1e-10 (the oracle's
 dense block solve and Eq. (13) round differently, amplified by the local
 condition); cycle iterates within 1e-9; solutions converged to 1e-12 within 1e-7
@@ -74,10 +76,19 @@ def assert_blocks(got, ref, n, N, tol, what):
         assert e <= tol, f"{what} block {name}: rel err {e:.3e} > {tol:.1e}"
 
 
-def jacobi():
+def opts(smoother="jacobi", gamma=1):
+    """Jacobi (theta = 1/2), or Gauss-Seidel: red-black on the finest grid, four colours below."""
     import paper_2302_13680_gb300 as P
 
-    return P.CycleOptions(smoother=P.SMOOTH_JACOBI, theta=0.5, precision=P.FP64)
+    sm = P.SMOOTH_JACOBI if smoother == "jacobi" else P.SMOOTH_RBGS
+    return P.CycleOptions(smoother=sm, theta=0.5, precision=P.FP64, gamma=gamma)
+
+
+def jacobi():
+    return opts("jacobi")
+
+
+SMOOTHERS = ["jacobi", "gs"]
 
 
 def test_residual_every_level(case):
@@ -94,8 +105,10 @@ def test_residual_every_level(case):
         assert_blocks(host(r), S[l] @ z, lv.n, N, 1e-12, f"apply level {l}")
 
 
-def test_one_jacobi_sweep_every_grid(case):
+@pytest.mark.parametrize("smoother", SMOOTHERS)
+def test_one_sweep_every_grid(case, smoother):
     H, levels, S = case
+    ns = [lv.n for lv in levels]
     N = levels[0].N
     fine = levels[0]
     rng = np.random.default_rng(22)
@@ -108,9 +121,9 @@ def test_one_jacobi_sweep_every_grid(case):
         f[m * N: m * N + m] *= fine.G
         f[m * N + m:] *= fine.h ** 2
         x = dev(z, lv.n, N)
-        H.smooth(l, jacobi(), 1, x, dev(f, lv.n, N))
-        ref = G.jacobi_sweep(S[l], lv.n, N, z, f, 0.5)
-        assert_blocks(host(x), ref, lv.n, N, 1e-10, f"jacobi level {l}")
+        H.smooth(l, opts(smoother), 1, x, dev(f, lv.n, N))
+        ref = G.smooth(S, ns, N, l, z, f, smoother, 0.5)
+        assert_blocks(host(x), ref, lv.n, N, 1e-10, f"{smoother} level {l}")
 
 
 def test_coarse_solve(case):
@@ -125,8 +138,9 @@ def test_coarse_solve(case):
     assert_blocks(host(x), spla.spsolve(S[-1].tocsc(), f), lv.n, N, 1e-11, "coarse solve")
 
 
+@pytest.mark.parametrize("smoother", SMOOTHERS)
 @pytest.mark.parametrize("gamma", [1, 2])
-def test_cycle_iterates(case, gamma):
+def test_cycle_iterates(case, gamma, smoother):
     H, levels, S = case
     N, n = levels[0].N, levels[0].n
     ns = [lv.n for lv in levels]
@@ -134,17 +148,15 @@ def test_cycle_iterates(case, gamma):
     z = rng.standard_normal(S[0].shape[0])
     f = O.pack(O.fine_rhs(levels[0], inputs.target_sinsin(n)))
     x = dev(z, n, N)
-    import paper_2302_13680_gb300 as P
-
-    opts = P.CycleOptions(smoother=P.SMOOTH_JACOBI, theta=0.5, precision=P.FP64, gamma=gamma)
     for k in range(2):
-        H.cycle(opts, x, dev(f, n, N))
-        z = G.cycle(S, ns, N, 0, z, f, n1=2, n2=2, theta=0.5, gamma=gamma)
+        H.cycle(opts(smoother, gamma), x, dev(f, n, N))
+        z = G.cycle(S, ns, N, 0, z, f, n1=2, n2=2, theta=0.5, gamma=gamma, smoother=smoother)
         assert_blocks(host(x), z, n, N, 1e-9, f"cycle {k}")
 
 
+@pytest.mark.parametrize("smoother", SMOOTHERS)
 @pytest.mark.parametrize("method", ["cycle", "fgmres"])
-def test_converged_solution(case, method):
+def test_converged_solution(case, method, smoother):
     H, levels, S = case
     import paper_2302_13680_gb300 as P
 
@@ -155,13 +167,13 @@ def test_converged_solution(case, method):
     # to 1e-12; the sparse direct solution's own residual is 1e-13 .. 5e-12 on these systems, and
     # the oracle's converged iterate lies within 1.1e-8 of it (the control block, u = sum_j p_j / nu,
     # is the sensitive one): the bar is 1e-7
-    st, _ = H.solve(jacobi(), dev(f, n, N), x, method=m, tol=1e-12, maxit=100, restart=30)
+    st, _ = H.solve(opts(smoother), dev(f, n, N), x, method=m, tol=1e-12, maxit=100, restart=30)
     assert st.relres <= 1e-12
     ref = spla.spsolve(S[0].tocsc(), f)
     assert_blocks(host(x), ref, n, N, 1e-7, f"{method} solution")
     if method == "cycle":
         # the same stationary iteration as the oracle's: the same number of cycles
-        _, it, _ = G.solve_stationary(S, [lv.n for lv in levels], N, f, tol=1e-12, maxit=100)
+        _, it, _ = G.solve_stationary(S, [lv.n for lv in levels], N, f, tol=1e-12, maxit=100, smoother=smoother)
         assert abs(st.iters - it) <= 1
 
 
@@ -170,11 +182,11 @@ def test_unsupported_combinations_are_refused(P):
     H = P.Hierarchy(15, 4, xi, 1e-3, 0.8, coarse="galerkin")
     try:
         f = H.zeros(0)
-        for opts in (P.CycleOptions(smoother=P.SMOOTH_RBGS, precision=P.FP64),
-                     P.CycleOptions(smoother=P.SMOOTH_JACOBI, precision=P.FP32),
-                     P.CycleOptions(smoother=P.SMOOTH_JACOBI, precision=P.FP64, freeze_u=1)):
+        for o in (P.CycleOptions(smoother=P.SMOOTH_RBGS, precision=P.FP32),
+                  P.CycleOptions(smoother=P.SMOOTH_JACOBI, precision=P.FP32),
+                  P.CycleOptions(smoother=P.SMOOTH_JACOBI, precision=P.FP64, freeze_u=1)):
             with pytest.raises(P.CMGError) as ei:
-                H.solve(opts, f, H.zeros(0))
+                H.solve(o, f, H.zeros(0))
             assert ei.value.status == 7
         with pytest.raises(P.CMGError) as ei:
             H.residual(1, H.zeros(1, torch.float32), H.zeros(1, torch.float32), H.zeros(1, torch.float32))
