@@ -137,18 +137,17 @@ __global__ void residual9_yp_kernel(int n, int N, const double* __restrict__ a9,
   const long i = t / N;
   const int iy = (int)(i / n), ix = (int)(i - (long)iy * n);
   double Ap = 0.0, Ay = 0.0, My = 0.0;
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int ny = iy + dy, nx = ix + dx;
-      if (ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
-      const int k = (dy + 1) * 3 + (dx + 1);
-      const size_t nb = (size_t)ny * n + nx;
-      const double a = a9[((size_t)k * nodes + i) * N + j];
-      const double yv = x.y[nb * N + j], pv = x.p[nb * N + j];
-      Ap = fma(a, pv, Ap);
-      Ay = fma(a, yv, Ay);
-      My = fma(M.w[k], yv, My);
-    }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ny = iy + k / 3 - 1, nx = ix + k % 3 - 1;
+    if (ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
+    const size_t nb = (size_t)ny * n + nx;
+    const double a = a9[((size_t)k * nodes + i) * N + j];
+    const double yv = x.y[nb * N + j], pv = x.p[nb * N + j];
+    Ap = fma(a, pv, Ap);
+    Ay = fma(a, yv, Ay);
+    My = fma(M.w[k], yv, My);
+  }
   const double sy = c * My + Ap, sp = Ay + e * mu[i];
   const size_t o = (size_t)i * N + j;
   r.y[o] = f.y ? f.y[o] - sy : sy;
@@ -204,33 +203,38 @@ __global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const double* __
   const size_t i = (size_t)iy * n + ix;
   const double mc = M.w[4];
   const double cd = c * mc, dd = d * mc, ed = e * mc;   // diagonal entries of the mass blocks
+  // the eight neighbours (unrolled, predicated: all loads of a sample issue together)
+  bool ok[9];
+  size_t nbr[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ny = iy + k / 3 - 1, nx = ix + k % 3 - 1;
+    ok[k] = k != 4 && ny >= 0 && ny < n && nx >= 0 && nx < n;
+    nbr[k] = ok[k] ? (size_t)ny * n + nx : i;
+  }
   double Bu = 0.0;
   if (lane == 0) {
     double s = f.u[i];
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ny = iy + dy, nx = ix + dx;
-        if ((dy == 0 && dx == 0) || ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
-        const size_t nb = (size_t)ny * n + nx;
-        const double mk = M.w[(dy + 1) * 3 + dx + 1];
-        s -= mk * (G * x.u[nb] + d * psum[nb]);
-      }
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      if (ok[k]) s -= M.w[k] * (G * x.u[nbr[k]] + d * psum[nbr[k]]);
     Bu = s;
   }
+  double eMu = 0.0;   // e (M u)_i off the centre: the same for every sample
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    if (ok[k]) eMu += e * M.w[k] * x.u[nbr[k]];
   double tacc = 0.0;
   for (int j = lane; j < N; j += 32) {
-    double By = f.y[i * N + j], Bp = f.p[i * N + j];
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ny = iy + dy, nx = ix + dx;
-        if ((dy == 0 && dx == 0) || ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
-        const int k = (dy + 1) * 3 + dx + 1;
-        const size_t nb = (size_t)ny * n + nx;
-        const double a = a9[((size_t)k * nodes + i) * N + j];
-        const double yv = x.y[nb * N + j], pv = x.p[nb * N + j];
-        By -= c * M.w[k] * yv + a * pv;
-        Bp -= a * yv + e * M.w[k] * x.u[nb];
-      }
+    double By = f.y[i * N + j], Bp = f.p[i * N + j] - eMu;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      if (!ok[k]) continue;
+      const double a = a9[((size_t)k * nodes + i) * N + j];
+      const double yv = x.y[nbr[k] * N + j], pv = x.p[nbr[k] * N + j];
+      By -= c * M.w[k] * yv + a * pv;
+      Bp -= a * yv;
+    }
     const double ia = inva[i * N + j];
     tacc += (cd * ia) * (ia * Bp) - ia * By;
     x.y[i * N + j] = Bp;   // parked until pass 2
