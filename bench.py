@@ -264,7 +264,8 @@ FORMS = {
 
 def algorithmic_bytes(kind: int, n: int, N: int, s: int) -> float:
     """Minimum DRAM bytes one launch of `kind` must move on an n x n grid
-    with N samples and element size s (per-unit figures in the design doc)."""
+    with N samples and element size s: every operand the launch needs read
+    once and every result written once."""
     nodes = n * n
     faces = 2 * n * (n + 1) * N * s
     if kind == 1:   # red-black half-sweep (average of the red and black launches)

@@ -34,8 +34,8 @@ It computes, slowly and in the order the paper states them:
   nodes of a control region (indicator chi); at the other nodes u_i = 0,
   the control row is absent and the smoother takes Eq. (14) with u_i = 0.
 
-Readings where the paper is silent are listed in the design doc under
-"Readings of the paper"; the code follows them.
+Where the paper is silent the code takes one reading and states it in the
+docstring of the function it concerns.
 
 Storage: node arrays are [n, n, ...] indexed [iy, ix]; y and p carry a
 trailing sample axis [n, n, N]; u is [n, n].  The lexicographic node index
