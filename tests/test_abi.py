@@ -41,21 +41,59 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_binding_loads_and_rejects_bad_sizes(lib):
+    """Every problem below is rejected before any device call, each for its
+    own defect (a valid xi is passed, so a missing one is not the reason)."""
+    import numpy as np
+
     from paper_2302_13680_gb300 import cmg
 
     L = cmg.load_library()
     h = ctypes.c_void_p()
+    xi = np.zeros((4096, 4))
+    xp = xi.ctypes.data_as(ctypes.c_void_p)
+    local = cmg._box((0.25, 0.75, 0.25, 0.75))
     for bad in [cmg.Problem(30, 8, 4, 1e-4, 0.5, 3, 0),      # n not 2^l - 1
                 cmg.Problem(31, 0, 4, 1e-4, 0.5, 3, 0),      # N < 1
                 cmg.Problem(31, 8, 4, -1.0, 0.5, 3, 0),      # nu <= 0
                 cmg.Problem(31, 8, 4, 1e-4, 0.5, 5, 0),      # coarsest not 1, 3, 7
                 cmg.Problem(3, 8, 4, 1e-4, 0.5, 7, 0),       # coarsest > n
-                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 2),      # unknown coarse-coefficient rule
+                cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 3),      # unknown coarse-operator rule
                 cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 0, cmg._box((0.5, 0.25, 0.0, 1.0))),   # control box x1 < x0
                 cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 0, cmg._box((0.0, 1.5, 0.0, 1.0))),    # outside the square
                 cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 0, cmg._box((0.2, 0.8, 0.3, float("nan"))))]:
-        assert L.cmg_create(ctypes.byref(bad), None, None, ctypes.byref(h)) == 1
-    assert L.cmg_create(ctypes.byref(cmg.Problem(31, 4096, 0, 1e-4, 0.5, 3, 0)), None, None,
+        assert L.cmg_create(ctypes.byref(bad), xp, None, ctypes.byref(h)) == 1
+    assert L.cmg_create(ctypes.byref(cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, 0)), None, None,
+                        ctypes.byref(h)) == 1        # K > 0 and no xi
+    assert L.cmg_create(ctypes.byref(cmg.Problem(31, 4096, 4, 1e-4, 0.5, 3, 0)), xp, None,
                         ctypes.byref(h)) == 7        # N above the kernels' limit
+    assert L.cmg_create(ctypes.byref(cmg.Problem(31, 8, 4, 1e-4, 0.5, 3, cmg.COARSE["galerkin"], local)), xp, None,
+                        ctypes.byref(h)) == 7        # Galerkin operators with local control
     assert L.cmg_num_levels(None) == 0
     assert L.cmg_level_n(None, 0) == -1
+
+
+def header_constants():
+    text = open(os.path.join(ROOT, "include", "cmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    vals = {k: int(v) for k, v in re.findall(r"\b(CMG_\w+)\s*=\s*(\d+)", text)}
+    vals.update({k: int(v) for k, v in re.findall(r"#define\s+(CMG_\w+)\s+(\d+)", text)})
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    from paper_2302_13680_gb300 import cmg
+
+    c = header_constants()
+    assert cmg.STATUS == {c["CMG_OK"]: "OK", c["CMG_ERR_INVALID_ARG"]: "INVALID_ARG", c["CMG_ERR_CUDA"]: "CUDA",
+                          c["CMG_ERR_OOM"]: "OOM", c["CMG_ERR_NOT_CONVERGED"]: "NOT_CONVERGED",
+                          c["CMG_ERR_NONFINITE"]: "NONFINITE", c["CMG_ERR_TIMEOUT"]: "TIMEOUT",
+                          c["CMG_ERR_UNSUPPORTED"]: "UNSUPPORTED"}
+    assert (cmg.SMOOTH_RBGS, cmg.SMOOTH_JACOBI) == (c["CMG_SMOOTH_RBGS"], c["CMG_SMOOTH_JACOBI"])
+    assert (cmg.FP64, cmg.FP32) == (c["CMG_FP64"], c["CMG_FP32"])
+    assert (cmg.METHOD_CYCLE, cmg.METHOD_FGMRES) == (c["CMG_METHOD_CYCLE"], c["CMG_METHOD_FGMRES"])
+    assert cmg.COARSE == {"averaged": c["CMG_COARSE_AVERAGED"], "nodal": c["CMG_COARSE_NODAL"],
+                          "galerkin": c["CMG_COARSE_GALERKIN"]}
+    assert (cmg.KERNEL_SMOOTH, cmg.KERNEL_RESIDUAL, cmg.KERNEL_RESTRICT, cmg.KERNEL_PROLONG, cmg.KERNEL_COARSE,
+            cmg.KERNEL_TAIL) == tuple(c["CMG_KERNEL_" + k] for k in ("SMOOTH", "RESIDUAL", "RESTRICT", "PROLONG",
+                                                                       "COARSE", "TAIL"))
+    assert (c["CMG_TUNE_STAGED"], c["CMG_TUNE_WIDE"]) == (16, 32)   # the flags the tests and tuning cache use
