@@ -59,14 +59,13 @@ def test_invalid_arguments(H):
     with pytest.raises(P.CMGError) as e:
         h.residual(h.levels, x, f, r)
     assert e.value.status == 1
-    with pytest.raises(P.CMGError):
-        h.solve(P.CycleOptions(gamma=3), f, x)
-    with pytest.raises(P.CMGError):
-        h.solve(P.CycleOptions(smoother=P.SMOOTH_JACOBI, theta=0.0), f, x)
-    with pytest.raises(P.CMGError):
-        h.solve(P.CycleOptions(), f, x, method=P.METHOD_FGMRES, restart=0)
-    with pytest.raises(P.CMGError):
-        h.cycle(P.CycleOptions(precision=P.FP32), x, f)        # FP64 vectors, FP32 cycle
+    for bad in (lambda: h.solve(P.CycleOptions(gamma=3), f, x),
+                lambda: h.solve(P.CycleOptions(smoother=P.SMOOTH_JACOBI, theta=0.0), f, x),
+                lambda: h.solve(P.CycleOptions(), f, x, method=P.METHOD_FGMRES, restart=0),
+                lambda: h.cycle(P.CycleOptions(precision=P.FP32), x, f)):     # FP64 vectors, FP32 cycle
+        with pytest.raises(P.CMGError) as e:
+            bad()
+        assert e.value.status == 1
     with pytest.raises(TypeError):
         h.residual(0, tuple(t.float() for t in x), f, r)       # mixed dtypes
     st, status = h.solve(P.CycleOptions(), f, x, maxit=50)
@@ -182,18 +181,15 @@ def test_autotune_keeps_results_and_validates(H, tmp_path):
 def test_set_tuning_validates_targets(H):
     h, P, pr = H
     L = h.levels
-    with pytest.raises(P.CMGError):
-        h.set_tuning(P.FP32, [16 | 4] + [0] * (L - 1))      # staged sweep takes 1 or 2 chunks per lane
-    with pytest.raises(P.CMGError):
-        h.set_tuning(P.FP64, [16 | 1] + [0] * (L - 1))      # FP32 only
-    with pytest.raises(P.CMGError):
-        h.set_tuning(P.FP32, [3] + [0] * (L - 1))
-    with pytest.raises(P.CMGError):
-        h.set_tuning(P.FP32, [32 | 2] + [0] * (L - 1))      # wide layout: one chunk per lane
-    with pytest.raises(P.CMGError):
-        h.set_tuning(P.FP32, [32 | 16 | 1] + [0] * (L - 1))  # not with the staged sweep
-    with pytest.raises(P.CMGError):
-        h.set_tuning(P.FP64, [32 | 1] + [0] * (L - 1))      # FP32 only
+    for prec, targets in ((P.FP32, [16 | 4]),        # staged sweep takes 1 or 2 chunks per lane
+                          (P.FP64, [16 | 1]),        # FP32 only
+                          (P.FP32, [3]),
+                          (P.FP32, [32 | 2]),        # wide layout: one chunk per lane
+                          (P.FP32, [32 | 16 | 1]),   # not with the staged sweep
+                          (P.FP64, [32 | 1])):       # FP32 only
+        with pytest.raises(P.CMGError) as e:
+            h.set_tuning(prec, targets + [0] * (L - 1))
+        assert e.value.status == 1
     h.set_tuning(P.FP32, [16 | 2] + [0] * (L - 1))
     h.set_tuning(P.FP32, [32 | 1] * (L - 1) + [0])
     h.set_tuning(P.FP32, None)
