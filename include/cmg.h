@@ -62,7 +62,10 @@ enum { CMG_COARSE_AVERAGED = 0, CMG_COARSE_NODAL = 1, CMG_COARSE_GALERKIN = 2 };
 /* Problem description (Sec. 2; field of Sec. 3.2). */
 typedef struct {
   int n;            /* interior nodes per side, finest grid: 2^L - 1, 3 <= n <= 4095 */
-  int N;            /* samples (quadrature nodes, Monte Carlo weights 1/N): 1 <= N <= 512 */
+  int N;            /* samples (quadrature nodes, Monte Carlo weights 1/N): 1 <= N <= 256, or up
+                       to 512 when N is a multiple of 4 (a lane holds at most 8 chunks of the
+                       16-byte, or for other N 1-sample, vectors: see cmg_sample_map); other N
+                       return CMG_ERR_UNSUPPORTED */
   int K;            /* field modes, 0 <= K <= 64 */
   double nu;        /* control cost nu > 0 */
   double amp;       /* field amplitude */
@@ -351,6 +354,17 @@ cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
  * 0.  Other values return CMG_ERR_INVALID_ARG. */
 #define CMG_TUNE_STAGED 16
 #define CMG_TUNE_WIDE 32
+/* The launch shape the node kernels use for N samples of elem_bytes (4 or 8)
+ * over `items` nodes (0: as many lanes per node as allowed) with a tuning
+ * target as above: *lanes_per_node (a power of two <= 32, consecutive lanes of
+ * one warp), *vec_width (samples per vector load: 16 / elem_bytes when it
+ * divides N, else 1; 2 for CMG_TUNE_WIDE in FP32) and *chunks_per_lane (a
+ * power of two; lanes x chunks x width >= N).  Host arithmetic only (no
+ * device call, no handle).  CMG_ERR_INVALID_ARG for N < 1, elem_bytes not 4
+ * or 8, or a null output; CMG_ERR_UNSUPPORTED when the chunks per lane exceed
+ * the kernels' limit of 8 (the outputs are still written). */
+cmg_status cmg_sample_map(int N, int elem_bytes, long long items, int target, int* lanes_per_node, int* vec_width,
+                          int* chunks_per_lane);
 cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets);
 
 /* cmg_autotune on every instance of a batch (the batch graph is re-captured

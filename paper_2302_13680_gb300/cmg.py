@@ -352,6 +352,20 @@ class Hierarchy:
 KERNEL_SMOOTH, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_COARSE, KERNEL_TAIL = 1, 2, 4, 8, 16, 32
 
 
+def sample_map(N: int, elem_bytes: int, items: int = 0, target: int = 0):
+    """(lanes per node, vector width, chunks per lane) of the node kernels
+    (cmg_sample_map; host arithmetic, no GPU needed)."""
+    lib = load_library()
+    fn = lib.cmg_sample_map
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    out = [ctypes.c_int() for _ in range(3)]
+    st = fn(N, elem_bytes, items, target, *[ctypes.byref(o) for o in out])
+    if st not in (CMG_OK, 7):
+        raise CMGError(st, "bad sample-map arguments")
+    return tuple(o.value for o in out)
+
+
 def kernel_launches() -> int:
     """Kernels launched by libcmg in this process so far."""
     return int(load_library().cmg_kernel_launches())

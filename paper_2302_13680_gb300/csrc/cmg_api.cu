@@ -981,6 +981,17 @@ cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen) {
   return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");
 }
 
+cmg_status cmg_sample_map(int N, int elem_bytes, long long items, int target, int* lanes_per_node, int* vec_width,
+                          int* chunks_per_lane) {
+  if (N < 1 || (elem_bytes != 4 && elem_bytes != 8) || items < 0 || !lanes_per_node || !vec_width || !chunks_per_lane)
+    return CMG_ERR_INVALID_ARG;
+  const SampleMap m = choose_map(N, elem_bytes, (long)items, target);
+  *lanes_per_node = m.lpn;
+  *vec_width = m.V;
+  *chunks_per_lane = m.spl;
+  return m.spl > kMaxSPL ? CMG_ERR_UNSUPPORTED : CMG_OK;
+}
+
 cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets) {
   if (!h) return CMG_ERR_INVALID_ARG;
   if (precision != CMG_FP64 && precision != CMG_FP32) return fail(h, CMG_ERR_INVALID_ARG, "unknown precision");

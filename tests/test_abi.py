@@ -97,3 +97,43 @@ def test_binding_constants_match_the_header():
             cmg.KERNEL_TAIL) == tuple(c["CMG_KERNEL_" + k] for k in ("SMOOTH", "RESIDUAL", "RESTRICT", "PROLONG",
                                                                        "COARSE", "TAIL"))
     assert (c["CMG_TUNE_STAGED"], c["CMG_TUNE_WIDE"]) == (16, 32)   # the flags the tests and tuning cache use
+
+
+def test_sample_map_covers_every_sample_and_matches_the_stated_limits(lib):
+    """The node kernels' launch shape (cmg_sample_map, host arithmetic):
+    every sample of a node is covered by its lanes x chunks x vector width,
+    lanes and chunks are powers of two, vectors divide N and fit 16 bytes;
+    the wide FP32 layout takes 2 samples a lane; and the shapes the kernels
+    cannot take are exactly the N the header excludes (N > 256 not a
+    multiple of 4, N > 512), which cmg_create refuses before any device call."""
+    import numpy as np
+
+    from paper_2302_13680_gb300 import cmg
+
+    L = cmg.load_library()
+    fn = L.cmg_sample_map
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    lpn, V, spl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    pow2 = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512}
+    for N in range(1, 521):
+        for eb in (4, 8):
+            for items in (0, 1, 961, 65025, 10 ** 6):
+                for target in (0, 1, 2, 4, 16 | 1, 16 | 2, 32 | 1):
+                    st = fn(N, eb, items, target, ctypes.byref(lpn), ctypes.byref(V), ctypes.byref(spl))
+                    l, v, c = lpn.value, V.value, spl.value
+                    assert l in pow2 and l <= 32 and c in pow2
+                    assert v in (1, 2, 4) and v * eb <= 16 and N % v == 0
+                    assert l * c * v >= N
+                    if target & 32 and eb == 4 and N % 2 == 0 and N <= 64:
+                        assert (v, c) == (2, 1) and 2 * l >= N
+                    assert st == (0 if c <= 8 else 7)
+        ok = all(fn(N, eb, 0, 0, ctypes.byref(lpn), ctypes.byref(V), ctypes.byref(spl)) == 0 for eb in (4, 8))
+        assert ok == (N <= 256 or (N % 4 == 0 and N <= 512)), N
+        if not ok:
+            xi = np.zeros((N, 1))
+            h = ctypes.c_void_p()
+            assert L.cmg_create(ctypes.byref(cmg.Problem(31, N, 1, 1e-4, 0.5, 3, 0)), xi.ctypes.data_as(ctypes.c_void_p),
+                                None, ctypes.byref(h)) == 7
+    assert fn(0, 4, 0, 0, ctypes.byref(lpn), ctypes.byref(V), ctypes.byref(spl)) == 1
+    assert fn(8, 2, 0, 0, ctypes.byref(lpn), ctypes.byref(V), ctypes.byref(spl)) == 1
