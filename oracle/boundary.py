@@ -238,3 +238,40 @@ def reduced_control(n: int, N: int, nu: float, kx, ky, yd: np.ndarray, f: np.nda
         lhs += T.T @ (w[:, None] * T) / N
         rhs_ += T.T @ (w * (yd - Ainv @ mf)) / N
     return np.linalg.solve(lhs, rhs_)
+
+
+def fgmres(S, ns, N: int, f, tol: float = 1e-10, maxit: int = 60, **kw):
+    """Flexible GMRES without restarts, right-preconditioned by one cycle, on
+    the paper's row scaling W S z = W f (W = diag(N I, 1, 1) on the state,
+    control and adjoint rows; the relative residual it minimises is the one
+    the paper reports).  Arnoldi with Gram-Schmidt applied twice; the small
+    least-squares problem is solved afresh at every step.  Returns
+    (z, iterations, history of relative residuals)."""
+    n = ns[0]
+    m = (n + 1) * n
+    w = np.concatenate([np.full(m * N, float(N)), np.ones(S[0].shape[0] - m * N)])
+    b = w * f
+    beta = np.linalg.norm(b)
+    V = [b / beta]
+    Z, H = [], np.zeros((maxit + 1, maxit))
+    hist = [1.0]
+    y = np.zeros(0)
+    for k in range(maxit):
+        z = cycle(S, ns, N, 0, np.zeros_like(f), V[k] / w, **kw)
+        Z.append(z)
+        v = w * (S[0] @ z)
+        for _ in range(2):
+            for i in range(k + 1):
+                c = V[i] @ v
+                H[i, k] += c
+                v = v - c * V[i]
+        H[k + 1, k] = np.linalg.norm(v)
+        V.append(v / H[k + 1, k])
+        e1 = np.zeros(k + 2)
+        e1[0] = beta
+        y, *_ = np.linalg.lstsq(H[: k + 2, : k + 1], e1, rcond=None)
+        hist.append(np.linalg.norm(e1 - H[: k + 2, : k + 1] @ y) / beta)
+        if hist[-1] <= tol:
+            break
+    z = np.array(Z).T @ y
+    return z, len(Z), hist

@@ -120,3 +120,20 @@ def test_vcycle_converges_h_robustly_to_the_direct_solution():
         assert np.abs(z - ref).max() <= 1e-6 * np.abs(ref).max()
         its.append(it)
     assert max(its) <= 1.3 * min(its) + 2      # the cycle count does not grow with 1/h
+
+
+def test_fgmres_converges_to_the_direct_solution_in_fewer_iterations():
+    """FGMRES with the V-cycle as right preconditioner reaches the direct
+    solution; its residual estimate equals the true weighted residual; it
+    needs fewer iterations than the stationary cycle (the paper's Table 3
+    pattern)."""
+    n, N, nu = 15, 4, 1e-4
+    ns, S = Bd.hierarchy(n, N, nu, field(N))
+    f = Bd.rhs(n, N, Bd.node_values(n, lambda x, y: np.sin(np.pi * x) * np.sin(np.pi * y)))
+    z, it, hist = Bd.fgmres(S, ns, N, f, tol=1e-10)
+    true = Bd.paper_norm(f - S[0] @ z, n, N) / Bd.paper_norm(f, n, N)
+    assert hist[-1] <= 1e-10 and true <= 2e-10
+    ref = spla.spsolve(S[0].tocsc(), f)
+    assert np.abs(z - ref).max() <= 1e-6 * np.abs(ref).max()
+    _, it_stat, _ = Bd.solve_stationary(S, ns, N, f, tol=1e-10, maxit=80)
+    assert it < it_stat
