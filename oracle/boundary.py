@@ -43,7 +43,8 @@ from . import cmg_oracle as O
 
 
 def faces(n: int, N: int, kappa_fn):
-    """Face coefficients (harmonic means of the endpoint values of kappa).
+    """Face coefficients (harmonic means of the endpoint values of kappa;
+    the field of Sec. 3.2 sampled on this grid, as on the square).
 
     kx [n+1, n+1, N]: row r, face f between columns f-1 and f (f = 0 and
     f = n touch x = 0 and x = 1).  ky [n+1, n, N]: face between rows r and
@@ -58,6 +59,8 @@ def faces(n: int, N: int, kappa_fn):
 
 
 def stiffness_matrix(n: int, kx, ky, j: int) -> sp.csr_matrix:
+    """A_j of the state equation (Sec. 2, Eq. (2)'s stiffness block) with the
+    Neumann edge: dual-cell fluxes, row 0's x-faces halved, no south face."""
     rows, cols, vals = [], [], []
     for r in range(n + 1):
         s = 0.5 if r == 0 else 1.0
@@ -79,7 +82,7 @@ def stiffness_matrix(n: int, kx, ky, j: int) -> sp.csr_matrix:
 
 
 def mass(n: int) -> np.ndarray:
-    """Lumped mass per node: h^2, h^2/2 on row 0."""
+    """Lumped mass per node (Sec. 2's M): h^2, h^2/2 on row 0."""
     h = 1.0 / (n + 1)
     w = np.full((n + 1, n), h * h)
     w[0] *= 0.5
@@ -87,7 +90,9 @@ def mass(n: int) -> np.ndarray:
 
 
 def system_matrix(n: int, N: int, nu: float, kx, ky) -> sp.csr_matrix:
-    """Ordering (y [node][sample], u [row-0 node], p [node][sample])."""
+    """The full-space optimality system (Sec. 2, Eq. (2)) with B the Neumann
+    control on the row-0 nodes; ordering (y [node][sample], u [row-0 node],
+    p [node][sample])."""
     h = 1.0 / (n + 1)
     m = (n + 1) * n
     rows, cols, vals = [], [], []
@@ -105,7 +110,7 @@ def system_matrix(n: int, N: int, nu: float, kx, ky) -> sp.csr_matrix:
 
 
 def rhs(n: int, N: int, yd: np.ndarray, f: np.ndarray | None = None) -> np.ndarray:
-    """(M y_d / N, 0, M f) with yd, f [(n+1) n] node values."""
+    """Right side of Eq. (2): (M y_d / N, 0, M f) with yd, f [(n+1) n] node values."""
     w = mass(n)
     fy = np.repeat(w * yd / N, N)
     fp = np.zeros(w.size * N) if f is None else np.repeat(w * f, N)
@@ -140,7 +145,8 @@ def prolongation_matrix(n: int, N: int) -> sp.csr_matrix:
 
 
 def hierarchy(n: int, N: int, nu: float, kappa_fn, coarsest_n: int = 3):
-    """(grid sizes finest first, S_l): S_0 from the definition, S_{l+1} = P^T S_l P."""
+    """(grid sizes finest first, S_l): S_0 from the definition, S_{l+1} = P^T S_l P
+    (the Galerkin coarse matrices of Sec. 3)."""
     kx, ky = faces(n, N, kappa_fn)
     ns = [n]
     while ns[-1] != coarsest_n:
@@ -184,6 +190,8 @@ def jacobi_sweep(S, n: int, N: int, z: np.ndarray, f: np.ndarray, theta: float) 
 
 
 def cycle(S, ns, N: int, l: int, z, f, n1: int = 2, n2: int = 2, theta: float = 0.5, gamma: int = 1):
+    """Algorithm 1 (gamma = 2: W-cycle) with collective Jacobi and a direct
+    solve on the coarsest grid."""
     if l == len(S) - 1:
         return spla.spsolve(S[l].tocsc(), f)
     for _ in range(n1):
@@ -206,6 +214,8 @@ def paper_norm(v: np.ndarray, n: int, N: int) -> float:
 
 
 def solve_stationary(S, ns, N: int, f, tol: float = 1e-10, maxit: int = 100, **kw):
+    """Repeated cycles from zero until the relative residual of the paper's
+    system (Sec. 3.2) is <= tol; returns (z, cycles, history)."""
     n = ns[0]
     z = np.zeros_like(f)
     fn = paper_norm(f, n, N)
