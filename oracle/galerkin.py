@@ -38,7 +38,7 @@ from . import cmg_oracle as O
 
 
 def stiffness_matrix(level: O.Level, j: int) -> sp.csr_matrix:
-    """A_j of the grid: row i holds the sum of node i's four face
+    """A_j of the grid (the stiffness block of Eq. (2)): row i holds the sum of node i's four face
     coefficients on the diagonal and minus the face coefficient towards
     each interior neighbour (a neighbour on the boundary is a zero
     Dirichlet value and has no column)."""
@@ -62,7 +62,7 @@ def stiffness_matrix(level: O.Level, j: int) -> sp.csr_matrix:
 
 
 def system_matrix(level: O.Level) -> sp.csr_matrix:
-    """The full-space system of the symmetric form on this grid:
+    """The full-space system (Sec. 2, Eq. (2)) in the symmetric form on this grid:
 
         [ c I_m (x) I_N      0          blkdiag(A_j) ]   y
         [ 0                  G I_m      d (I_m (x) 1_N^T) ]   u
@@ -92,7 +92,7 @@ def system_matrix(level: O.Level) -> sp.csr_matrix:
 
 
 def prolongation_matrix(nf: int, N: int) -> sp.csr_matrix:
-    """Block prolongation of a full-space vector from the (nf-1)/2 grid to
+    """Block prolongation (Algorithm 1's P) of a full-space vector from the (nf-1)/2 grid to
     the nf grid: the bilinear interpolation P2 = P1 (x) P1 (row index
     iy nf + ix, the 1D operator along y outside) on every sample of y and
     p and on u."""
@@ -103,7 +103,7 @@ def prolongation_matrix(nf: int, N: int) -> sp.csr_matrix:
 
 
 def hierarchy(levels) -> list[sp.csr_matrix]:
-    """S_0 from the finest grid's definition, S_{l+1} = P^T S_l P (the
+    """S_0 from the finest grid's definition, S_{l+1} = P^T S_l P (Sec. 3; the
     grids of ``levels`` fix only the sizes below the finest)."""
     N = levels[0].N
     S = [system_matrix(levels[0])]
@@ -124,7 +124,8 @@ _BLOCKS: dict = {}
 
 def node_blocks(S: sp.csr_matrix, n: int, N: int):
     """The positions [n^2, 2N+1] of every node's unknowns and the dense
-    diagonal blocks S_ii [n^2, 2N+1, 2N+1] (extracted once per matrix)."""
+    diagonal blocks S_ii [n^2, 2N+1, 2N+1] (the node systems of Eq. (12);
+    extracted once per matrix)."""
     hit = _BLOCKS.get(id(S))
     if hit is None or hit[0] is not S:
         idx = np.stack([node_indices(n, N, i) for i in range(n * n)])
