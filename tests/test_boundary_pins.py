@@ -137,3 +137,40 @@ def test_fgmres_converges_to_the_direct_solution_in_fewer_iterations():
     assert np.abs(z - ref).max() <= 1e-6 * np.abs(ref).max()
     _, it_stat, _ = Bd.solve_stationary(S, ns, N, f, tol=1e-10, maxit=80)
     assert it < it_stat
+
+
+def test_galerkin_coarse_structure_the_gpu_path_relies_on():
+    """On every coarse grid of the boundary hierarchy: the control rows couple
+    only to row-0 adjoints; the control-control block is a constant 3-point
+    stencil along Gamma; the mass (state-state block of a sample) is one
+    constant 9-point stencil on rows >= 1 and another on row 0, where the
+    centre and side weights are halved and there is no south neighbour."""
+    N = 2
+    ns, S = Bd.hierarchy(31, N, 1e-4, field(N))
+    for l in range(1, len(ns)):
+        n = ns[l]
+        m = (n + 1) * n
+        A = S[l].toarray()
+        D = A[m * N: m * N + n, m * N + n:]                     # control rows x adjoint columns
+        cols = np.nonzero(D)[1] // N
+        assert np.all(cols < n)                                # row-0 nodes only
+        U = A[m * N: m * N + n, m * N: m * N + n]
+        assert np.allclose(U, np.diag(np.diag(U)) + np.diag(np.diag(U, 1), 1) + np.diag(np.diag(U, -1), -1))
+        if n > 1:
+            assert np.allclose(np.diag(U), U[0, 0]) and np.allclose(np.diag(U, 1), U[0, 1])
+        Y = A[: m * N: N, : m * N: N]                          # sample 0's state-state block
+
+        def stencil(r, ix):
+            i = r * n + ix
+            return {(k // n - r, k % n - ix): v for k, v in enumerate(Y[i]) if v != 0.0}
+
+        if n >= 3:
+            ref = stencil(1, 1)                                # an interior row's stencil
+            for r in range(1, n):                              # rows away from the top boundary
+                for ix in range(1, n - 1):
+                    st = stencil(r, ix)
+                    assert st.keys() == ref.keys() and all(np.isclose(st[k], ref[k]) for k in ref)
+            top = stencil(0, 1)
+            assert all(dy >= 0 for dy, _ in top)               # no south neighbour on Gamma
+            assert np.isclose(top[(0, 0)], ref[(0, 0)] / 2) and np.isclose(top[(0, 1)], ref[(0, 1)] / 2)
+            assert np.isclose(top[(1, 0)], ref[(1, 0)]) and np.isclose(top[(1, 1)], ref[(1, 1)])
