@@ -216,3 +216,100 @@ def solve_stationary(S, ns, N: int, f: np.ndarray, tol: float = 1e-10, maxit: in
         it += 1
         hist.append(O.paper_norm(O.unpack(f - S[0] @ z, n, N), N) / fnorm)
     return z, it, hist
+
+
+# ---------------------------------------------------------------------------
+# Local control (Sec. 3.1 after Eq. (13)): the control exists only at the nodes
+# with a control basis function (chi = 1); the Galerkin products then act on
+# the unknowns that exist.
+# ---------------------------------------------------------------------------
+
+def system_matrix_local(level: O.Level) -> sp.csr_matrix:
+    """Eq. (2) with u only at the control nodes (ordering y, u on the control
+    nodes in node order, p): the control block and its couplings are the
+    distributed ones restricted to those nodes."""
+    if level.dw is not None:
+        raise ValueError("per-node factors on d are not part of this form")
+    n, N = level.n, level.N
+    m = n * n
+    full = system_matrix(O.Level(level.n, level.N, level.nu, level.h, level.kx, level.ky, level.a, level.c,
+                                 level.G, level.d, level.e))
+    ctl = np.flatnonzero(level.control().ravel() != 0.0)
+    keep = np.concatenate([np.arange(m * N), m * N + ctl, m * N + m + np.arange(m * N)])
+    return full[keep][:, keep].tocsr()
+
+
+def prolongation_matrix_local(nf: int, N: int, ctl_f: np.ndarray, ctl_c: np.ndarray) -> sp.csr_matrix:
+    """The block prolongation with the control block restricted to the fine
+    and coarse control nodes (flat index arrays)."""
+    P1 = sp.csr_matrix(O.prolongation_1d(nf))
+    P2 = sp.kron(P1, P1, format="csr")
+    PN = sp.kron(P2, sp.identity(N, format="csr"), format="csr")
+    return sp.block_diag([PN, P2[ctl_f][:, ctl_c], PN], format="csr")
+
+
+def hierarchy_local(levels):
+    """(S_l, control node indices per grid) with S_{l+1} = P^T S_l P."""
+    N = levels[0].N
+    ctls = [np.flatnonzero(lv.control().ravel() != 0.0) for lv in levels]
+    S = [system_matrix_local(levels[0])]
+    for l in range(1, len(levels)):
+        P = prolongation_matrix_local(levels[l - 1].n, N, ctls[l - 1], ctls[l])
+        S.append((P.T @ S[-1] @ P).tocsr())
+    return S, ctls
+
+
+def _local_groups(n: int, N: int, ctl: np.ndarray):
+    m = n * n
+    pos = -np.ones(m, dtype=int)
+    pos[ctl] = np.arange(ctl.size)
+    nu_ = ctl.size
+    ar = np.arange(N)
+    on = [np.concatenate([i * N + ar, [m * N + pos[i]], m * N + nu_ + i * N + ar]) for i in range(m) if pos[i] >= 0]
+    off = [np.concatenate([i * N + ar, m * N + nu_ + i * N + ar]) for i in range(m) if pos[i] < 0]
+    return [np.stack(g) for g in (on, off) if g]
+
+
+_LBLOCKS: dict = {}
+
+
+def jacobi_sweep_local(S, n: int, N: int, ctl: np.ndarray, z, f, theta: float):
+    """Collective Jacobi (Eq. (11)) with dense node blocks: 2N+1 unknowns at
+    control nodes (Eq. (13)), 2N elsewhere (Eq. (14))."""
+    hit = _LBLOCKS.get(id(S))
+    if hit is None or hit[0] is not S:
+        hit = (S, [(idx, np.stack([S[row][:, row].toarray() for row in idx])) for idx in _local_groups(n, N, ctl)])
+        _LBLOCKS[id(S)] = hit
+    r = f - S @ z
+    out = z.copy()
+    for idx, B in hit[1]:
+        out[idx] += theta * np.linalg.solve(B, r[idx][..., None])[..., 0]
+    return out
+
+
+def cycle_local(S, ctls, ns, N: int, l: int, z, f, n1: int = 2, n2: int = 2, theta: float = 0.5):
+    """Algorithm 1 (V-cycle) on the local-control Galerkin hierarchy."""
+    if l == len(S) - 1:
+        return spla.spsolve(S[l].tocsc(), f)
+    for _ in range(n1):
+        z = jacobi_sweep_local(S[l], ns[l], N, ctls[l], z, f, theta)
+    P = prolongation_matrix_local(ns[l], N, ctls[l], ctls[l + 1])
+    ec = cycle_local(S, ctls, ns, N, l + 1, np.zeros(S[l + 1].shape[0]), P.T @ (f - S[l] @ z), n1, n2, theta)
+    z = z + P @ ec
+    for _ in range(n2):
+        z = jacobi_sweep_local(S[l], ns[l], N, ctls[l], z, f, theta)
+    return z
+
+
+def solve_stationary_local(S, ctls, ns, N: int, f, tol: float = 1e-10, maxit: int = 100, **kw):
+    """Repeated V-cycles until the paper's relative residual (state rows
+    weighted by N) is <= tol; returns (z, cycles, history)."""
+    m = ns[0] ** 2
+    w = np.concatenate([np.full(m * N, float(N)), np.ones(S[0].shape[0] - m * N)])
+    z = np.zeros_like(f)
+    fn = np.linalg.norm(w * f)
+    hist = [1.0]
+    while hist[-1] > tol and len(hist) <= maxit:
+        z = cycle_local(S, ctls, ns, N, 0, z, f, **kw)
+        hist.append(np.linalg.norm(w * (f - S[0] @ z)) / fn)
+    return z, len(hist) - 1, hist

@@ -241,3 +241,24 @@ def test_gauss_seidel_galerkin_cycle_converges_to_the_direct_solution():
     assert hist[-1] <= 1e-10 and it < 20
     ref = spla.spsolve(S[0].tocsc(), f)
     assert np.abs(z - ref).max() <= 1e-7 * np.abs(ref).max()
+
+
+def test_local_control_galerkin_hierarchy():
+    """Local control (u only at the control nodes): a region covering the
+    square gives the distributed system; the finest matrix equals the level
+    oracle's local-control system on the unknowns that exist; the Galerkin
+    V-cycle with Eq. (13) / Eq. (14) node blocks reaches the direct solution."""
+    N, n = 3, 15
+    field_ = O.sine_mode_field(inputs.draw_xi(1, N, 3), 0.5)
+    full = O.make_hierarchy(n, N, 1e-4, field_, control_box=(0.0, 1.0, 0.0, 1.0))
+    assert abs(G.system_matrix_local(full[0]) - G.system_matrix(O.make_hierarchy(n, N, 1e-4, field_)[0])).max() == 0
+    lv = O.make_hierarchy(n, N, 1e-4, field_, control_box=(0.25, 0.75, 0.25, 0.75))
+    S, ctls = G.hierarchy_local(lv)
+    m = n * n
+    keep = np.concatenate([np.arange(m * N), m * N + ctls[0], m * N + m + np.arange(m * N)])
+    assert np.array_equal(S[0].toarray(), O.dense_S(lv[0])[np.ix_(keep, keep)])
+    f = O.pack(O.fine_rhs(lv[0], inputs.target_sinsin(n)))[keep]
+    z, it, hist = G.solve_stationary_local(S, ctls, [l.n for l in lv], N, f, tol=1e-10)
+    assert hist[-1] <= 1e-10 and it < 40
+    ref = spla.spsolve(S[0].tocsc(), f)
+    assert np.abs(z - ref).max() <= 1e-7 * np.abs(ref).max()
