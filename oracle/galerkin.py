@@ -313,3 +313,35 @@ def solve_stationary_local(S, ctls, ns, N: int, f, tol: float = 1e-10, maxit: in
         z = cycle_local(S, ctls, ns, N, 0, z, f, **kw)
         hist.append(np.linalg.norm(w * (f - S[0] @ z)) / fn)
     return z, len(hist) - 1, hist
+
+
+def fgmres_packed(S0, precondition, f, N: int, m: int, tol: float = 1e-10, maxit: int = 60):
+    """Flexible GMRES without restarts on the paper's row scaling W S z = W f
+    (W = N on the m N state rows, 1 elsewhere), right-preconditioned by
+    `precondition(v)` (one cycle applied to W^{-1} v); Gram-Schmidt applied
+    twice, the small least-squares problem solved afresh at every step.
+    Returns (z, iterations, history of relative residuals)."""
+    w = np.concatenate([np.full(m * N, float(N)), np.ones(S0.shape[0] - m * N)])
+    b = w * f
+    beta = np.linalg.norm(b)
+    V, Z = [b / beta], []
+    H = np.zeros((maxit + 1, maxit))
+    hist, y = [1.0], np.zeros(0)
+    for k in range(maxit):
+        z = precondition(V[k] / w)
+        Z.append(z)
+        v = w * (S0 @ z)
+        for _ in range(2):
+            for i in range(k + 1):
+                c = V[i] @ v
+                H[i, k] += c
+                v = v - c * V[i]
+        H[k + 1, k] = np.linalg.norm(v)
+        V.append(v / H[k + 1, k])
+        e1 = np.zeros(k + 2)
+        e1[0] = beta
+        y, *_ = np.linalg.lstsq(H[: k + 2, : k + 1], e1, rcond=None)
+        hist.append(np.linalg.norm(e1 - H[: k + 2, : k + 1] @ y) / beta)
+        if hist[-1] <= tol:
+            break
+    return np.array(Z).T @ y, len(Z), hist
