@@ -169,7 +169,9 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc,
 /* ---- level operators (FP64; *_f32 take float vectors) ------------------ */
 
 /* r = f - S x on grid `level` (Eq. (2) with this problem's blocks).  With
- * fy, fu, fp all NULL the call computes r = S x (operator apply). */
+ * fy, fu, fp all NULL the call computes r = S x (operator apply).  On a
+ * CMG_COARSE_GALERKIN handle S on the grids below the finest is the Galerkin
+ * product P^T S P (9-point blocks); the _f32 variant is refused there. */
 cmg_status cmg_residual(cmg_handle* h, int level,
                         const double* y, const double* u, const double* p,
                         const double* fy, const double* fu, const double* fp,
@@ -183,7 +185,8 @@ cmg_status cmg_residual_f32(cmg_handle* h, int level,
  * red-black collective Gauss-Seidel (each node solves its reduced system
  * Eq. (12) by Eq. (13) with current neighbour values; all red nodes, then
  * all black) or damped collective Jacobi Eq. (11).  Only opts->smoother and
- * opts->theta are read. */
+ * opts->theta are read.  On the Galerkin grids of a CMG_COARSE_GALERKIN
+ * handle CMG_SMOOTH_RBGS sweeps in four colours (iy mod 2, ix mod 2). */
 cmg_status cmg_smooth(cmg_handle* h, int level, const cmg_cycle* opts, int sweeps,
                       double* y, double* u, double* p,
                       const double* fy, const double* fu, const double* fp);
@@ -214,7 +217,9 @@ cmg_status cmg_prolong_add_f32(cmg_handle* h, int level,
 /* x = S^{-1} f on the coarsest grid (Algorithm 1, direct solver): the
  * per-sample PDE blocks are eliminated with precomputed A_j^{-1} and the
  * n_c^2 x n_c^2 Schur system for u is solved with its precomputed inverse.
- * Always computed in FP64 (the f32 variant converts on load and store). */
+ * Always computed in FP64 (the f32 variant converts on load and store).  On
+ * a CMG_COARSE_GALERKIN handle the elimination carries the non-diagonal
+ * Galerkin mass (FP64 only; x and f must not overlap). */
 cmg_status cmg_coarse_solve(cmg_handle* h, const double* fy, const double* fu, const double* fp,
                             double* y, double* u, double* p);
 cmg_status cmg_coarse_solve_f32(cmg_handle* h, const float* fy, const float* fu, const float* fp,
