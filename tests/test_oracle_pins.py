@@ -851,3 +851,36 @@ def test_semismooth_newton_matches_proximal_gradient(inner):
     # F(u_ref) = 0 with T u from the per-sample PDE solves
     _, p = O.pde_states(levels, ref, yd)
     assert np.abs(O.ssn_F(ref, O.expected_adjoint(p), nu, beta, a, b)).max() <= 1e-8
+
+
+def test_row_wavefront_order_equals_the_red_black_sweep():
+    """An implementation identity for a one-pass sweep: updating the red
+    nodes of row r and then the black nodes of row r - 1, for r = 0 .. n,
+    gives the red-black sweep (all red, then all black) bit for bit -- a
+    black node of row r - 1 couples only to red nodes of rows r - 2 .. r,
+    all of them final by then, and nodes of one colour never couple."""
+    import inputs
+
+    n, N = 15, 4
+    lv = O.make_hierarchy(n, N, 1e-4, O.sine_mode_field(inputs.draw_xi(3, N, 3), 0.7),
+                          control_box=(0.2, 0.7, 0.3, 0.9))[0]
+    rng = np.random.default_rng(41)
+    x = (rng.standard_normal((n, n, N)), rng.standard_normal((n, n)), rng.standard_normal((n, n, N)))
+    f = tuple(rng.standard_normal(b.shape) * s for b, s in zip(x, (lv.c, lv.G, lv.h ** 2)))
+    ref = O.rbgs_sweep(lv, x, f)
+    cur = tuple(np.array(b, copy=True) for b in x)
+
+    def update_row(colour, r):
+        # a half-sweep computes every node of the colour from the current
+        # values; keep row r of it (same-colour nodes do not interact)
+        nxt = O.rbgs_half_sweep(lv, cur, f, colour)
+        for b, nb in zip(cur, nxt):
+            b[r] = nb[r]
+
+    for r in range(n + 1):
+        if r < n:
+            update_row(0, r)
+        if r >= 1:
+            update_row(1, r - 1)
+    for a, b in zip(cur, ref):
+        assert np.array_equal(a, b)
