@@ -1,22 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the collective multigrid solver on one GB300 (per rank).
 
-Workload (default): n = 255 interior nodes per side (65,025 nodes), N = 64
-samples, 16 field modes of amplitude 1.0, nu = 1e-6, y_d = sin(pi x)
-sin(pi y), f = 0, V(2,2) red-black collective Gauss-Seidel cycles down to
-3 x 3, solved to a relative residual of 1e-10 (paper's system, see
-include/cmg.h).  One step is the whole path on one synthetic instance:
-coefficients of every grid from the field draws (device), right-hand side,
-and the solve from a zero initial guess.
+Workload (default): the largest single instance, n = 1023 interior nodes
+per side (1,046,529 nodes), N = 256 samples (536.9M unknowns), 32 field
+modes of amplitude 1.0, nu = 1e-5, y_d = sin(pi x) sin(pi y), f = 0,
+red-black collective Gauss-Seidel cycles down to 3 x 3, V(2,2) and W(1,1),
+solved to the paper's relative residual 2e-9 (the FP64 rounding floor of
+that residual at n = 1023 lies near 1e-9, include/cmg.h).  One step is the
+whole path on one synthetic instance: coefficients of every grid from the
+field draws (device), right-hand side, and the solve from a zero initial
+guess.  --config n255_N64 runs the n = 255, N = 64, nu = 1e-6 instance to
+1e-10; the default line also carries that instance's times and the errors
+of its solutions against the oracle's (key "n255_N64").
 
-Forms timed: plain FP64 (FGMRES with an FP64 V-cycle, and FP64 stationary
-cycles) and mixed precision (FP32 V-cycle inside FP64 iterative refinement
-or FP64 FGMRES).  The fastest form to the tolerance is the chosen form; its
-throughput in unknowns*cycles/s, (2N+1) n^2 * fine-grid cycles / time, is
-`value`.
+Forms timed: plain FP64 (FP64 stationary V(2,2) cycles; FGMRES with an FP64
+V-cycle where the Krylov basis fits) and mixed precision (FP32 cycles, with
+Eq. (13)'s per-node Schur scalar in FP64, inside FP64 iterative refinement
+or FP64 FGMRES; V(2,2) and W(1,1); and the all-FP32 option).  The fastest
+form to the tolerance is the chosen form; its throughput in
+unknowns*cycles/s, (2N+1) n^2 * fine-grid cycles / time, is `value`.
 
---impl reference times the CPU oracle (FP64 numpy) on the same workload:
-each step is one oracle V(2,2) cycle on the full grid.
+--impl reference times the CPU oracle (FP64 numpy) on a bounded sample of
+the same workload: each step is one oracle V(2,2) cycle on the full n x n
+grid with the first few of the N samples.
 """
 from __future__ import annotations
 
@@ -46,15 +52,36 @@ UNIT = "unknowns*cycles/s"
 TOL = 1e-10
 
 
+FORMS = {
+    "fp64-fgmres": dict(precision=0, method=1),
+    "fp64-cycle": dict(precision=0, method=0),
+    "fp32-ir": dict(precision=1, method=0),
+    # the same with every coarse grid run one launch per step (tail_n = 0)
+    # instead of the cluster kernel for n <= 31
+    "fp32-ir-launches": dict(precision=1, method=0, tail_n=0),
+    "fp32-fgmres": dict(precision=1, method=1),
+    # W(1,1) cycles (gamma = 2): the coarse grids n <= 31 in the cluster kernel
+    "fp32-ir-w11": dict(precision=1, method=0, gamma=2, n1=1, n2=1, tail_n=31),
+    # the all-FP32 option: Eq. (13)'s per-node Schur scalar in FP32 as well
+    "fp32-ir-ctl32": dict(precision=1, method=0, tail_n=0, ctl32=1),
+}
+
+
+def cycle_options(P, spec):
+    return P.CycleOptions(precision=spec["precision"], tail_n=spec.get("tail_n", 31), gamma=spec.get("gamma", 1),
+                          n1=spec.get("n1", 2), n2=spec.get("n2", 2), ctl32=spec.get("ctl32", 0))
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cmg", choices=["cmg", "reference"])
-    ap.add_argument("--config", default="n255_N64", choices=sorted(inputs.CONFIGS) + ["batch96", "n255_N64_l1box", "n255_N64_galerkin"])
-    ap.add_argument("--form", default="auto", choices=["auto", "fp64-fgmres", "fp64-cycle", "fp32-ir",
-                                                        "fp32-ir-launches", "fp32-fgmres"])
+    ap.add_argument("--config", default="n1023_N256",
+                    choices=sorted(inputs.CONFIGS) + ["batch96", "n255_N64_l1box", "n255_N64_galerkin"])
+    ap.add_argument("--form", default="auto", choices=["auto"] + sorted(FORMS))
+    ap.add_argument("--no-extra", action="store_true", help="skip the n = 255, N = 64 key of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON file of autotuned targets: used if it holds this hierarchy, else written "
@@ -106,8 +133,10 @@ def workload_config(name, n_gpus):
     c = dict(inputs.CONFIGS[name])
     box = c.get("control_box")
     ctl = "" if box is None else f", local control on [{box[0]:g},{box[1]:g}]x[{box[2]:g},{box[3]:g}]"
+    cyc = "V(2,2) and W(1,1)" if name == "n1023_N256" else "V(2,2)"
     return {"workload": f"collective MG, n={c['n']} ({c['n'] ** 2} nodes), N={c['N']}, K={c['K']}, "
-                        f"amp={c['amp']}, nu={c['nu']:g}, V(2,2) red-black to 3x3, tol {tolerance(name):g}{ctl}",
+                        f"amp={c['amp']}, nu={c['nu']:g}, {cyc} red-black to 3x3, tol {tolerance(name):g} "
+                        f"(paper's relative residual){ctl}",
             "n": c["n"], "N": c["N"], "K": c["K"], "nu": c["nu"], "amp": c["amp"],
             "unknowns": (2 * c["N"] + 1) * c["n"] ** 2, "instances_per_gpu": 1,
             "parallelism": f"replicas x{n_gpus} (independent instances, no collective)",
@@ -182,19 +211,30 @@ class ClockSampler:
 # CPU oracle timing (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-class OracleWorkload:
-    """The oracle's hierarchy and right side for one workload (built once)."""
+# Samples of the workload the oracle takes per bounded CPU sample: the full
+# grid with the first SAMPLE_N[config] of its N samples (one FP64 numpy
+# cycle on all 256 samples of the n = 1023 grid would take minutes and tens
+# of GB of host memory).
+SAMPLE_N = {"n1023_N256": 2}
 
-    def __init__(self, cfg_name: str):
+
+class OracleWorkload:
+    """The oracle's hierarchy and right side for one workload (built once);
+    `samples` keeps the first samples of the workload's N."""
+
+    def __init__(self, cfg_name: str, samples: int | None = None):
         import oracle.cmg_oracle as O
 
         self.O = O
         pr = inputs.make_problem(**inputs.CONFIGS[cfg_name])
-        self.levels = O.make_hierarchy(pr.n, pr.N, pr.nu, O.sine_mode_field(pr.xi, pr.amp),
+        N = pr.N if samples is None else min(samples, pr.N)
+        xi = pr.xi[:N]
+        self.levels = O.make_hierarchy(pr.n, N, pr.nu, O.sine_mode_field(xi, pr.amp),
                                        control_box=pr.control_box)
         self.f = O.fine_rhs(self.levels[0], pr.yd)
         self.x = O.zeros_like_level(self.levels[0])
-        self.unknowns = (2 * pr.N + 1) * pr.n ** 2
+        self.unknowns = (2 * N + 1) * pr.n ** 2
+        self.desc = f"n={pr.n}, {N} of the N={pr.N} samples" if N < pr.N else f"n={pr.n}, N={pr.N}"
 
     def cycles(self, seconds: float, max_cycles: int):
         """Run V(2,2) red-black oracle cycles until `seconds` have passed or
@@ -211,11 +251,63 @@ class OracleWorkload:
 
 
 def oracle_cycle_rate(cfg_name: str, seconds: float = 12.0, max_cycles: int = 100):
-    """unknowns*cycles/s of the oracle on the full workload over a bounded
-    sample of about `seconds`; returns (rate, cycles, seconds)."""
-    w = OracleWorkload(cfg_name)
+    """unknowns*cycles/s of the oracle on one host core over a bounded sample
+    of about `seconds`; returns (rate, cycles, seconds, description)."""
+    w = OracleWorkload(cfg_name, SAMPLE_N.get(cfg_name))
     cyc, dt = w.cycles(seconds, max_cycles)
-    return w.unknowns * cyc / dt, cyc, dt
+    return w.unknowns * cyc / dt, cyc, dt, w.desc
+
+
+def _oracle_worker(args):
+    cfg_name, seconds = args
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    w = OracleWorkload(cfg_name, SAMPLE_N.get(cfg_name))
+    cyc, dt = w.cycles(seconds, 100)
+    return w.unknowns * cyc, dt, w.desc
+
+
+def oracle_rate_all_cores(cfg_name: str, seconds: float = 10.0):
+    """The same bounded sample run at once in one process per host core
+    (spawned, independent copies; the oracle itself is single-threaded):
+    the summed unknowns*cycles of all processes over the longest process's
+    time.  Returns (rate, processes, description) or None."""
+    import multiprocessing as mp
+
+    procs = os.cpu_count() or 1
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [(cfg_name, seconds)] * procs)
+    except Exception:   # noqa: BLE001 - the baseline is context; the GPU line does not depend on it
+        return None
+    units = sum(r[0] for r in res)
+    return units / max(r[1] for r in res), procs, res[0][2]
+
+
+def host_cpu():
+    """CPU model and core count of this host (for the baseline record)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                if key == "model name":
+                    break
+    except OSError:
+        pass
+    if model is None or model.startswith("0x"):
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    import platform
+
+    return {"model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "nproc": os.cpu_count()}
 
 
 def run_reference(args, world, rank):
@@ -229,20 +321,20 @@ def run_reference(args, world, rank):
               flush=True)
         return
     cfg = workload_config(args.config, args.gpus)
-    w = OracleWorkload(args.config)
+    w = OracleWorkload(args.config, SAMPLE_N.get(args.config))
     per_step = []
     for i in range(args.warmup + args.steps):
         _, dt = w.cycles(0.0, 1)
         if i >= args.warmup:
             per_step.append(dt)
-    unknowns = cfg["unknowns"]
-    value = unknowns * len(per_step) / sum(per_step)
+    value = w.unknowns * len(per_step) / sum(per_step)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / len(per_step), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one FP64 V(2,2) red-black oracle cycle on the full grid per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+                             "sample": f"one FP64 V(2,2) red-black oracle cycle per step on {w.desc} "
+                                       f"({w.unknowns} unknowns)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -251,28 +343,21 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-FORMS = {
-    "fp64-fgmres": dict(precision=0, method=1),
-    "fp64-cycle": dict(precision=0, method=0),
-    "fp32-ir": dict(precision=1, method=0),
-    # the same with every coarse grid run one launch per step (tail_n = 0)
-    # instead of the cluster kernel for n <= 31
-    "fp32-ir-launches": dict(precision=1, method=0, tail_n=0),
-    "fp32-fgmres": dict(precision=1, method=1),
-}
 
 
 def algorithmic_bytes(kind: int, n: int, N: int, s: int) -> float:
-    """Minimum DRAM bytes one launch of `kind` must move on an n x n grid
-    with N samples and element size s: every operand the launch needs read
-    once and every result written once."""
+    """Algorithmic DRAM bytes of one launch of `kind` on an n x n grid with N
+    samples and element size s.  Red-black half-sweep: the method's minimum
+    for a full red + black sweep (read y and p once, write them once, read
+    the right sides f_y, f_p and the two stored faces per node-sample: 8 s
+    per node-sample), split evenly over its two launches, i.e. 4 s per
+    node-sample per launch; per-node terms (u, f_u, 1/sigma) are left out.
+    Other kinds: every operand the launch needs read once and every result
+    written once."""
     nodes = n * n
     faces = 2 * n * (n + 1) * N * s
-    if kind == 1:   # red-black half-sweep (average of the red and black launches)
-        act = nodes / 2.0
-        inact = nodes / 2.0
-        inva = act * N * 8 if s == 8 else 0.0
-        return (faces + act * N * (2 * s + 2 * s) + inact * N * 2 * s + inva + act * (8 + 8 + s))
+    if kind == 1:   # red-black half-sweep: half of a full sweep's 8 s per node-sample
+        return 4.0 * s * nodes * N
     if kind == 2:   # residual: read x, f, faces; write r
         return 6 * s * nodes * N + faces + 3 * s * nodes
     if kind == 4:   # restriction
@@ -282,6 +367,18 @@ def algorithmic_bytes(kind: int, n: int, N: int, s: int) -> float:
         nc = (n - 1) // 2
         return 4 * s * nodes * N + 2 * s * nc * nc * N + s * (2 * nodes + nc * nc)
     raise ValueError(kind)
+
+
+def unfused_operand_bytes(n: int, N: int, s: int) -> float:
+    """Operands of one unfused red-black half-sweep launch (average of the red
+    and black launches): every face once, the active colour's f_y, f_p read
+    and y, p written, the other colour's y, p read, per-node u, f_u, 1/sigma
+    (and 1/a_j for FP64).  Context for the roofline, not its numerator."""
+    nodes = n * n
+    faces = 2 * n * (n + 1) * N * s
+    act = inact = nodes / 2.0
+    inva = act * N * 8 if s == 8 else 0.0
+    return faces + act * N * (2 * s + 2 * s) + inact * N * 2 * s + inva + act * (8 + 8 + s)
 
 
 KIND_NAMES = {1: "rbgs_half_kernel", 2: "residual_kernel", 4: "restrict_kernel", 8: "prolong_add_kernel"}
@@ -363,8 +460,7 @@ def run_cmg(args, world, rank, local):
             a.copy_(b)
         for t in x:
             t.zero_()
-        st, status = H.solve(P.CycleOptions(precision=spec["precision"], tail_n=spec.get("tail_n", 31)), f, x,
-                             method=spec["method"],
+        st, status = H.solve(cycle_options(P, spec), f, x, method=spec["method"],
                              tol=tol, maxit=200, restart=restart, raise_on_fail=False)
         if status != 0:
             raise RuntimeError(f"form {form} did not reach {tol}: status {status}, relres {st.relres:.3e}")
@@ -392,16 +488,27 @@ def run_cmg(args, world, rank, local):
     # --- compare forms (untimed for the result line, reported as context)
     forms = list(FORMS) if args.form == "auto" else [args.form]
     if args.form == "auto" and n * n * N > 50_000_000:
-        forms = ["fp64-cycle", "fp32-ir", "fp32-ir-launches"]   # the Krylov forms would hold 2 x restart 4 GB vectors
-    survey = {}
+        # the Krylov forms would hold 2 x restart full FP64 vectors (4.3 GB each at n = 1023, N = 256)
+        forms = [f for f in FORMS if FORMS[f]["method"] == 0]
+    survey, solution = {}, {}
     for form in forms:
         for _ in range(2):
             step(form)
         t, c, _, st = timed_steps(form, 3)
         survey[form] = {"time_to_tol_ms": statistics.median(t), "cycles": c[-1], "iters": st.iters,
                         "relres": st.relres}
+        if form in ("fp64-fgmres", "fp64-cycle") and "plain" not in solution:
+            solution["plain"] = [t.clone() for t in x]
     chosen = min(survey, key=lambda k: survey[k]["time_to_tol_ms"])
     plain = "fp64-fgmres" if "fp64-fgmres" in survey else ("fp64-cycle" if "fp64-cycle" in survey else chosen)
+    # every form's solution against the plain FP64 GPU solution (relative max-norm per block)
+    err_vs_plain = {}
+    if "plain" in solution:
+        for form in forms:
+            step(form)
+            err_vs_plain[form] = {nm: float((a - b).abs().max() / b.abs().max())
+                                  for nm, a, b in zip("yup", x, solution["plain"])}
+        del solution
     prec = "f32" if FORMS[chosen]["precision"] == 1 else "f64"
     s_bytes = 4 if prec == "f32" else 8
 
@@ -474,13 +581,28 @@ def run_cmg(args, world, rank, local):
                 "measured": "CUDA events around each launch, instrumented pass of the timed steps",
                 "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_record(kname, prec, n, N), "algorithmic_bytes_per_launch": alg,
+                "algorithmic_bytes_rule": ("half of a full red+black sweep's minimum: read y, p, f_y, f_p and "
+                                           "two faces, write y, p = 8 s per node-sample per sweep"
+                                           if dom == 1 else "every operand read once, every result written once"),
                 "avg_launch_ms": avg_ms, "launches_timed": dom_cnt}
+    if dom == 1:
+        ub = unfused_operand_bytes(n, N, s_bytes)
+        roofline["unfused_operand_bytes_per_launch"] = ub
+        roofline["unfused_operand_gbs"] = ub / (avg_ms * 1e-3) / 1e9
 
-    cpu = None
+    extra = None
+    if rank == 0 and args.config == "n1023_N256" and not args.no_extra:
+        extra = smaller_instance(P, stream, dev, args.tuning_cache)
+
+    cpu, cpu_all = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cyc, dt = oracle_cycle_rate(args.config, seconds=12.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{cyc} FP64 V(2,2) red-black oracle cycles on the full grid ({dt:.1f} s)"}
+        rate, cyc, dt, desc = oracle_cycle_rate(args.config, seconds=15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+               "sample": f"{cyc} FP64 V(2,2) red-black oracle cycles on {desc} ({dt:.1f} s, one core)"}
+        allc = oracle_rate_all_cores(args.config, seconds=10.0)
+        if allc is not None:
+            cpu_all = {"value": allc[0], "unit": UNIT, "cores": allc[1], "kind": "oracle",
+                       "sample": f"the same sample in {allc[1]} independent processes at once (one per core)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -495,9 +617,88 @@ def run_cmg(args, world, rank, local):
                 "kernel_time_share_level0": {KIND_NAMES[k]: v[0] for k, v in kind_time.items()},
                 "tuning_chunks_per_lane": tuned, "tol": tol,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+                "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+                "cpu_baseline_all_cores": cpu_all,
+                "err_vs_plain_fp64_gpu": err_vs_plain}
+        if extra is not None:
+            line["n255_N64"] = extra
         print(json.dumps(line), flush=True)
     H.close()
+
+
+def golden_samples(name: str):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_solution_samples.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def err_vs_samples(x, g):
+    """Relative max-norm error per block of a GPU solution (y, u, p CUDA
+    tensors [n*n][N], [n*n]) at the sampled nodes of the oracle's stored
+    converged solution, scaled by the oracle block's largest magnitude."""
+    import torch
+
+    idx = torch.tensor(g["nodes"], dtype=torch.long, device=x[0].device)
+    out = {}
+    for nm, t in zip("yup", x):
+        ref = torch.tensor(g[nm], dtype=torch.float64, device=t.device)
+        got = t.index_select(0, idx).to(torch.float64)
+        out[nm] = float((got - ref).abs().max()) / g["max_abs"][nm]
+    return out
+
+
+def smaller_instance(P, stream, dev, tuning_cache):
+    """The n = 255, N = 64, nu = 1e-6 instance: chosen mixed form and plain
+    FP64 FGMRES timed to 1e-10 (3 steps each after 2 untimed), and each
+    solution's error against the oracle's converged solution at the stored
+    sampled nodes (tests/golden/n255_N64_solution_samples.json)."""
+    import torch
+
+    from paper_2302_13680_gb300 import tuning as T
+
+    name = "n255_N64"
+    pr = inputs.make_problem(**inputs.CONFIGS[name])
+    H = P.Hierarchy(pr.n, pr.N, pr.xi, pr.nu, pr.amp, stream=stream)
+    T.apply_or_tune(H, P.FP32, tuning_cache)
+    T.apply_or_tune(H, P.FP64, tuning_cache)
+    xi_d = torch.tensor(pr.xi, device=dev)
+    yd_d = torch.tensor(pr.yd.reshape(-1), device=dev)
+    g = golden_samples(name)
+    unknowns = (2 * pr.N + 1) * pr.n ** 2
+    out = {"workload": workload_config(name, 1)["workload"], "forms": {}}
+    for form in ("fp32-ir-launches", "fp32-ir-ctl32", "fp64-fgmres"):
+        spec = FORMS[form]
+        x = H.zeros(0)
+        ts = []
+        for k in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.set_samples(xi_d)
+            f = H.rhs(yd_d)
+            for t in x:
+                t.zero_()
+            st, status = H.solve(cycle_options(P, spec), f, x, method=spec["method"], tol=TOL, maxit=200,
+                                 restart=30, raise_on_fail=False)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                ts.append(e0.elapsed_time(e1))
+        rec = {"time_to_tol_ms": statistics.median(ts), "cycles": st.cycles, "iters": st.iters,
+               "relres": st.relres, "status": status,
+               "unknowns_cycles_per_s": unknowns * st.cycles / (statistics.median(ts) / 1e3)}
+        if g is not None:
+            rec["err_vs_oracle"] = err_vs_samples(x, g)
+        out["forms"][form] = rec
+    out["speedup_vs_plain_fp64"] = (out["forms"]["fp64-fgmres"]["time_to_tol_ms"] /
+                                    out["forms"]["fp32-ir-launches"]["time_to_tol_ms"])
+    if g is not None:
+        out["err_vs_oracle_note"] = (f"relative max-norm per block at {len(g['nodes'])} sampled nodes (all "
+                                     f"{pr.N} samples) of the oracle's converged solution "
+                                     f"(relres {g['relres']:.2e})")
+    H.close()
+    return out
     if dist is not None:
         dist.destroy_process_group()
 

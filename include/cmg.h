@@ -102,9 +102,13 @@ typedef struct {
   double theta;     /* damping of collective Jacobi, Eq. (11); the paper uses 0.5 */
   int n1, n2;       /* pre- and post-smoothing sweeps */
   int gamma;        /* recursive calls per level: 1 = V-cycle, 2 = W-cycle */
-  int precision;    /* arithmetic of the cycle: CMG_FP64, or CMG_FP32 (single-precision
-                       smoothing, control update, residual and transfers; the coarsest
-                       solve in FP64 on FP32-built operators) */
+  int precision;    /* arithmetic of the cycle: CMG_FP64, or CMG_FP32: FP32 vectors and
+                       FP32 per-sample arithmetic in the smoothing, residual and transfer
+                       sweeps, while the per-node Schur scalar of Eq. (13) (the sum over
+                       samples for u_i, 1/sigma_i and u_i) is FP64 from the lanes' FP32
+                       partial sums, 1/sigma_i being computed in FP64 from the FP32 faces;
+                       the coarsest solve takes the per-sample products A_j^{-1} f in FP32
+                       and the sums over samples and the control Schur solve in FP64 */
   int tail_n;       /* grids with at most tail_n nodes per side (and the coarsest solve)
                        run as ONE launch of a thread-block cluster whose phases are
                        separated by cluster barriers; 0 = one launch per step on every
@@ -120,6 +124,9 @@ typedef struct {
                        solve the 2N PDEs for a given control (used to complete a
                        predicted control into a consistent initial iterate); 0 = the
                        collective smoother of Eq. (13). */
+  int ctl32;        /* CMG_FP32 cycles only: 1 = the per-node Schur scalar of Eq. (13) in
+                       FP32 as well (sum over samples, 1/sigma_i rounded to FP32, u_i):
+                       an all-FP32 option, off by default (0); ignored by FP64 cycles. */
 } cmg_cycle;
 
 /* Solve statistics filled by cmg_solve. */

@@ -49,7 +49,7 @@ def _box(control_box):
 class Cycle(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("theta", ctypes.c_double), ("n1", ctypes.c_int),
                 ("n2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
-                ("tail_n", ctypes.c_int), ("freeze_u", ctypes.c_int)]
+                ("tail_n", ctypes.c_int), ("freeze_u", ctypes.c_int), ("ctl32", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -132,10 +132,11 @@ class CycleOptions:
     tail_n: int = 0           # grids with n <= tail_n run as one cluster launch; 0 = one launch per step
                               # (the faster choice inside the refinement graph on GB300)
     freeze_u: int = 0         # 1: keep u fixed, solve the state and adjoint rows only
+    ctl32: int = 0            # FP32 cycles: 1 = Eq. (13)'s per-node Schur scalar in FP32 too (all-FP32 option)
 
     def c(self) -> Cycle:
         return Cycle(self.smoother, self.theta, self.n1, self.n2, self.gamma, self.precision, self.tail_n,
-                     self.freeze_u)
+                     self.freeze_u, self.ctl32)
 
 
 def _ptr(t):

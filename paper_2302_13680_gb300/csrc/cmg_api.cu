@@ -30,7 +30,8 @@ struct Lev {
   double h = 0, c = 0, G = 0, d = 0, e = 0;
   size_t nodes = 0;                      // n*n
   double *kx64 = nullptr, *ky64 = nullptr, *inva = nullptr, *isigma = nullptr;
-  float* isigma32 = nullptr;             // 1/sigma in FP32 for the FP32 cycle
+  float* isigma32 = nullptr;             // 1/sigma in FP32 (the FP32 cycle's all-FP32 option)
+  double* isigd32 = nullptr;             // 1/sigma of the FP32 operator in FP64 (the FP32 cycle's Schur scalar)
   double* a64 = nullptr;                 // finest grid: diag(A_j) for the FP64 refinement residual
   float *kx32 = nullptr, *ky32 = nullptr;
   double* x64[3] = {nullptr, nullptr, nullptr};
@@ -156,19 +157,23 @@ struct ProfScope {
   }
 };
 
+// ctl32: the FP32 cycle's all-FP32 option (cmg_cycle.ctl32); FP64 views ignore it.
 template <typename T>
-LevelView<T> view(const cmg_handle* h, int l, int freeze_u = 0);
+LevelView<T> view(const cmg_handle* h, int l, int freeze_u = 0, int ctl32 = 0);
 template <>
-LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u) {
+LevelView<double> view<double>(const cmg_handle* h, int l, int freeze_u, int) {
   const Lev& v = h->lv[l];
   return {v.n, h->prob.N, h->prob.N, v.kx64, v.ky64, v.inva, v.isigma, v.c, v.G * h->gscale, v.d, v.e,
-          v.spl_target[0], freeze_u, nullptr, v.a64, v.ctl, h->dw_on ? v.dw : nullptr};
+          v.spl_target[0], freeze_u, nullptr, v.a64, v.ctl, h->dw_on ? v.dw : nullptr, 0};
 }
 template <>
-LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u) {
+LevelView<float> view<float>(const cmg_handle* h, int l, int freeze_u, int ctl32) {
   const Lev& v = h->lv[l];
-  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, v.isigma, v.c, v.G * h->gscale, v.d, v.e,
-          v.spl_target[1], freeze_u, v.isigma32, nullptr, v.ctl, h->dw_on ? v.dw : nullptr};
+  // nodal coarse grids round the FP64 operator's 1/sigma; averaged ones have
+  // their own FP32 operator with its FP64 1/sigma
+  const double* isd = h->prob.coarse_coeff == CMG_COARSE_NODAL ? v.isigma : v.isigd32;
+  return {v.n, h->prob.N, h->prob.N, v.kx32, v.ky32, v.inva, isd, v.c, v.G * h->gscale, v.d, v.e,
+          v.spl_target[1], freeze_u, v.isigma32, nullptr, v.ctl, h->dw_on ? v.dw : nullptr, ctl32 ? 1 : 0};
 }
 
 // The coarsest-grid data for a cycle of precision T; its per-node factor on d
@@ -222,7 +227,7 @@ cudaError_t setup_coefficients(cmg_handle* h) {
       e = launch_coarse_faces32(f.n, P.N, f.kx32, f.ky32, v.kx32, v.ky32, h->stream);
     }
     if (e == cudaSuccess)
-      e = launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, v.G * h->gscale, h->stream, v.dw);
+      e = launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.isigd32, v.d * v.c * v.e, v.G * h->gscale, h->stream, v.dw);
   }
   if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
@@ -292,7 +297,7 @@ cudaError_t refresh_dw(cmg_handle* h) {
       e = launch_diag64(v.n, P.N, v.kx64, v.ky64, v.inva, v.isigma, v.d * v.c * v.e, G, h->stream, v.dw);
     if (e != cudaSuccess) break;
     e = nodal ? launch_scale_cast<double, float>(1.0, v.isigma, v.isigma32, v.nodes, h->stream)
-              : launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.d * v.c * v.e, G, h->stream, v.dw);
+              : launch_diag32(v.n, P.N, v.kx32, v.ky32, v.isigma32, v.isigd32, v.d * v.c * v.e, G, h->stream, v.dw);
   }
   if (e != cudaSuccess) return e;
   const Lev& cl = h->lv[h->L - 1];
@@ -338,7 +343,7 @@ cudaError_t smooth(cmg_handle* h, const cmg_cycle& o, int l, int sweeps, Vec3<T>
       return cudaSuccess;
     }
   }
-  const LevelView<T> L = view<T>(h, l, o.freeze_u);
+  const LevelView<T> L = view<T>(h, l, o.freeze_u, o.ctl32);
   for (int s = 0; s < sweeps; ++s) {
     if (o.smoother == CMG_SMOOTH_RBGS) {
       for (int colour = 0; colour < 2; ++colour) {
@@ -384,7 +389,7 @@ cudaError_t tail_cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3
   P.nlev = nlev;
   for (int k = 0; k < nlev; ++k) {
     Lev& v = h->lv[l + k];
-    P.lev[k].L = view<T>(h, l + k, o.freeze_u);
+    P.lev[k].L = view<T>(h, l + k, o.freeze_u, o.ctl32);
     P.lev[k].r = Work<T>::r(v);
     if (k == 0) {
       P.lev[k].x = x;
@@ -451,7 +456,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   cudaError_t e = cudaSuccess;
   if (zg) {
     // first pre-smoothing sweep from the zero iterate
-    const LevelView<T> L = view<T>(h, l, o.freeze_u);
+    const LevelView<T> L = view<T>(h, l, o.freeze_u, o.ctl32);
     {
       ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
       e = launch_rbgs_zero<T>(L, x, f, h->stream);
@@ -490,7 +495,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
     // FP32: prolongation fused into the first post-smoothing half-sweep
     // (colour 0); identical results, one pass over x fewer.  (In FP64 the
     // fused sweep is bound by the FP64 pipe and costs more than the pass.)
-    const LevelView<T> L = view<T>(h, l, o.freeze_u);
+    const LevelView<T> L = view<T>(h, l, o.freeze_u, o.ctl32);
     {
       ProfScope ps(h, CMG_KERNEL_PROLONG, l);
       e = launch_rbgs_prolong<T>(L, x, f, cview(xc), cl.n, h->stream);
@@ -520,6 +525,7 @@ cmg_status check_cycle(cmg_handle* h, const cmg_cycle* o) {
   if (o->tail_n < 0) return fail(h, CMG_ERR_INVALID_ARG, "tail_n must be >= 0");
   if (o->freeze_u != 0 && o->freeze_u != 1) return fail(h, CMG_ERR_INVALID_ARG, "freeze_u must be 0 or 1");
   if (o->freeze_u && h && h->L < 2) return fail(h, CMG_ERR_INVALID_ARG, "freeze_u needs at least two grids");
+  if (o->ctl32 != 0 && o->ctl32 != 1) return fail(h, CMG_ERR_INVALID_ARG, "ctl32 must be 0 or 1");
   if (o->smoother == CMG_SMOOTH_JACOBI && !(o->theta > 0.0 && o->theta <= 1.0))
     return fail(h, CMG_ERR_INVALID_ARG, "theta must be in (0, 1]");
   if (h && h->galerkin() && (o->precision != CMG_FP64 || o->freeze_u))
@@ -645,7 +651,7 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     Lev& v = h->lv[l];
     const size_t faces = (size_t)v.n * (v.n + 1) * N;
     AL(v.kx64, faces); AL(v.ky64, faces); AL(v.kx32, faces); AL(v.ky32, faces);
-    AL(v.inva, v.nodes * N); AL(v.isigma, v.nodes); AL(v.isigma32, v.nodes);
+    AL(v.inva, v.nodes * N); AL(v.isigma, v.nodes); AL(v.isigma32, v.nodes); AL(v.isigd32, v.nodes);
     for (int b = 0; b < 3; ++b) {
       const size_t cnt = (b == 1) ? v.nodes : v.nodes * N;
       AL(v.r64[b], cnt); AL(v.x32[b], cnt); AL(v.f32[b], cnt); AL(v.r32[b], cnt); AL(v.f64[b], cnt);
@@ -1206,7 +1212,7 @@ cmg_status ir_iteration(cmg_handle* h, const cmg_cycle& o, Vec3c<double> f, Vec3
 
 bool same_cycle(const cmg_cycle& a, const cmg_cycle& b) {
   return a.smoother == b.smoother && a.theta == b.theta && a.n1 == b.n1 && a.n2 == b.n2 && a.gamma == b.gamma &&
-         a.precision == b.precision && a.tail_n == b.tail_n && a.freeze_u == b.freeze_u;
+         a.precision == b.precision && a.tail_n == b.tail_n && a.freeze_u == b.freeze_u && a.ctl32 == b.ctl32;
 }
 
 // Sets a loop condition from the state before the first iteration:

@@ -54,17 +54,38 @@ __device__ __forceinline__ A group_sum(A v, int lpn) {
   return v;
 }
 
-// Arithmetic of the per-node control-row work (sums over samples, u): FP32
-// in the FP32 cycle, FP64 in the FP64 one.  On this GPU an FP64 warp
-// instruction holds the narrow FP64 pipe for tens of cycles, and this work
-// sits on every node group's critical path.
+// Arithmetic of the control row of a residual (G u_i + d_i sum_j p_j): the
+// vector's own precision.
 template <typename T>
 using acc_t = typename std::conditional<sizeof(T) == 4, float, double>::type;
 
+// 1/sigma_i of Eq. (13): FP64, except in an FP32 view with the all-FP32
+// option (ctl32), which reads the FP32 copy.
 template <typename T>
-__device__ __forceinline__ acc_t<T> isigma_of(const LevelView<T>& L, long node) {
-  if constexpr (sizeof(T) == 4) return L.isigma32[node];
-  else return L.isigma[node];
+__device__ __forceinline__ double isigma_of(const LevelView<T>& L, long node) {
+  if constexpr (sizeof(T) == 4) {
+    if (L.ctl32) return (double)L.isigma32[node];
+  }
+  return L.isigma[node];
+}
+
+// The per-node Schur scalar of Eq. (13): u_i = (b_u + d_i sum_j t_j) / sigma_i
+// with t_j = c b_y,j / a_j^2 - b_p,j / a_j, from this lane's part `tacc` of
+// the sum over samples (accumulated in the vector's precision).  The lane
+// parts are converted to FP64 once, then the group sum, the product with
+// 1/sigma_i and u_i are FP64: a few FP64 operations per node, not per
+// node-sample.  The all-FP32 option (ctl32, FP32 views) keeps all of it in
+// FP32.  Every lane of the warp must call this (shuffle reduction).
+template <typename T>
+__device__ __forceinline__ double schur_u(const LevelView<T>& L, T tacc, int lpn, double bu, double di, double isg) {
+  if constexpr (sizeof(T) == 4) {
+    if (L.ctl32) {
+      const float ts = group_sum(tacc, lpn);
+      return (double)(((float)bu + (float)di * ts) * (float)isg);
+    }
+  }
+  const double ts = group_sum((double)tacc, lpn);
+  return (bu + di * ts) * isg;
 }
 
 // Red-black ordering: map the g-th node of colour `colour` (red = (ix+iy)

@@ -56,14 +56,18 @@ struct LevelView {
   const T* kx;
   const T* ky;
   const double* inva;   // 1/diag(A_j) per node-sample (FP64 path only)
-  const double* isigma; // 1 / Schur denominator of Eq. (13) per node
+  const double* isigma; // 1 / Schur denominator of Eq. (13) per node, FP64 (for an FP32 view: of the FP32 operator)
   double c, G, d, e;    // scalar blocks of Eq. (12): C_j = c I, G, D_j = d I, E_j = e I
   int spl_target;       // chunks per lane chosen by the autotuner (0 = size heuristic)
   int freeze_u;         // 1: keep u fixed (local solves of the state and adjoint rows only)
-  const float* isigma32;  // 1/sigma rounded to FP32 (FP32 path: the control update runs in FP32)
+  const float* isigma32;  // 1/sigma rounded to FP32 (read only by the all-FP32 option, ctl32)
   const double* a64;      // diag(A_j) = sum of the four faces per node-sample (FP64, finest grid only, else null)
   CtlBox ctl{};           // nodes with a control basis function (elsewhere u_i = 0, no control row)
   const float* dw = nullptr;   // per-node factor on d (semismooth Newton active sets); null = 1
+  // FP32 views: 0 (default) = the per-node Schur scalar of Eq. (13) (the sum
+  // over samples for u_i, 1/sigma_i and u_i) in FP64 from the lanes' FP32
+  // partial sums; 1 = that work in FP32 as well (all-FP32 option)
+  int ctl32 = 0;
 };
 
 // d_i = d * dw[node] (the control row's coupling to the adjoint at node i).
@@ -271,8 +275,10 @@ cudaError_t launch_coarse_faces64(int nf, int N, const double* kxf, const double
                                   cudaStream_t s);
 cudaError_t launch_coarse_faces32(int nf, int N, const float* kxf, const float* kyf, float* kx32, float* ky32,
                                   cudaStream_t s);
-cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double dce, double G,
-                          cudaStream_t s, const float* dw = nullptr);
+// 1/sigma of the FP32 operator (sum over samples in FP64): FP64 isigma_d and
+// its FP32 rounding isigma32.
+cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double* isigma_d,
+                          double dce, double G, cudaStream_t s, const float* dw = nullptr);
 
 // ---- vector kernels (cmg_blas.cu) ----
 constexpr int kRedBlocks = 304;    // fixed partial count: deterministic reductions

@@ -205,8 +205,8 @@ __device__ __forceinline__ vec<T, V> prolonged(const T* xv, const T* ev, int nf,
 // first block row, b_y of the last, b_u of the control row:
 //   u = (b_u + d sum_j (c b_y,j / a_j^2 - b_p,j / a_j)) / sigma
 //   y_j = (b_y,j - e u) / a_j,   p_j = (b_p,j - c y_j) / a_j
-// with 1/sigma stored per node, so u costs one multiply; the control-row
-// work runs in the cycle's own precision (acc_t) and its loads are issued
+// with 1/sigma stored per node, so u costs one multiply; the sum over
+// samples, 1/sigma and u are FP64 (schur_u) and their loads are issued
 // together with the node's other loads, ahead of the group sum.
 // ---------------------------------------------------------------------------
 // PRO: the neighbours are read as x + P e (coarse correction e on the grid
@@ -232,14 +232,13 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
   const bool ctl = L.ctl.inside(iy, ix);   // taken here so (iy, ix) need not stay live
   const size_t o = (size_t)node * ld;
   vec<T, V> bp[SPL], by[SPL], ia[SPL];
-  using A = acc_t<T>;
   T tacc = T(0);   // this lane's part of the sum over samples
-  A bu = A(0), isg = A(0);   // control-row right side (or the frozen u) and 1/sigma, loaded with the rest
-  A dwv = A(1);              // per-node factor on d (semismooth Newton systems only), loaded with them
+  double bu = 0.0, isg = 0.0;   // control-row right side (or the frozen u) and 1/sigma, loaded with the rest
+  double dwv = 1.0;             // per-node factor on d (semismooth Newton systems only), loaded with them
   if (valid) {
-    bu = L.freeze_u ? (A)ld1<T, CG>(x.u + node) : (A)ld1<T, CG>(f.u + node);
+    bu = L.freeze_u ? (double)ld1<T, CG>(x.u + node) : (double)ld1<T, CG>(f.u + node);
     isg = isigma_of<T>(L, node);
-    if (L.dw) dwv = (A)L.dw[node];
+    if (L.dw) dwv = (double)L.dw[node];
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
     const bool hW = ix > 0, hE = ix < n - 1, hS = iy > 0, hN = iy < n - 1;
@@ -278,13 +277,13 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
       }
     }
   }
-  const A tsum = group_sum((A)tacc, lpn);
+  const double su = schur_u<T>(L, tacc, lpn, bu, L.d * dwv, isg);
   if (valid) {
     // frozen control: u_i keeps its value and only the state and adjoint
     // rows are solved (Eq. (14) with u_i given instead of zero); a node
     // without a control basis function (local control) takes Eq. (14) with
     // u_i = 0
-    const A uu = L.freeze_u ? bu : (ctl ? (bu + (A)L.d * dwv * tsum) * isg : A(0));
+    const double uu = L.freeze_u ? bu : (ctl ? su : 0.0);
     if (lane == 0 && !L.freeze_u) x.u[node] = (T)uu;
     const T uT = (T)uu, e = (T)L.e;
 #pragma unroll
@@ -314,16 +313,16 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
   const T c = (T)L.c;
   const size_t o = (size_t)(valid ? node : 0) * ld;
   vec<T, V> bp[SPL], by[SPL], ia[SPL];
-  using A = acc_t<T>;
   T tacc = T(0);
-  A ru = A(0), xu = A(0), isg = A(0);   // loaded with the rest, ahead of the group sum
+  double ru = 0.0, isg = 0.0;   // loaded with the rest, ahead of the group sum
+  T xu = T(0);
   const int iy = valid ? (int)(node / n) : 0, ix = valid ? (int)(node - (long)iy * n) : 0;
-  A dwv = A(1);   // per-node factor on d (semismooth Newton systems only)
+  double dwv = 1.0;   // per-node factor on d (semismooth Newton systems only)
   if (valid) {
-    ru = (A)ld1<T, CG>(r.u + node);
-    xu = (A)ld1<T, CG>(x.u + node);
+    ru = (double)ld1<T, CG>(r.u + node);
+    xu = ld1<T, CG>(x.u + node);
     isg = isigma_of<T>(L, node);
-    if (L.dw) dwv = (A)L.dw[node];
+    if (L.dw) dwv = (double)L.dw[node];
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
     const T* kSp = L.ky + ((size_t)iy * n + ix) * ld;
 #pragma unroll
@@ -342,10 +341,13 @@ __device__ __forceinline__ void jacobi_item(const LevelView<T>& L, const Vec3<T>
       }
     }
   }
-  const A tsum = group_sum((A)tacc, lpn);
+  const double sdu = schur_u<T>(L, tacc, lpn, ru, L.d * dwv, isg);
   if (valid) {
-    const A du = (L.freeze_u || !L.ctl.inside(iy, ix)) ? A(0) : (ru + (A)L.d * dwv * tsum) * isg;
-    if (lane == 0) x.u[node] = (T)(xu + (A)theta * du);
+    const double du = (L.freeze_u || !L.ctl.inside(iy, ix)) ? 0.0 : sdu;
+    if (lane == 0) {
+      if (sizeof(T) == 4 && L.ctl32) x.u[node] = (T)((float)xu + (float)theta * (float)du);
+      else x.u[node] = (T)((double)xu + theta * du);
+    }
     const T duT = (T)du, e = (T)L.e, th = (T)theta;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {

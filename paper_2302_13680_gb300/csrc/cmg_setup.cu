@@ -163,23 +163,30 @@ __global__ void coarse_faces32_kernel(int nf, int N, const float* __restrict__ k
   }
 }
 
-// isigma32[node] = 1 / (G + dce sum_j 1/a_j^2) from the FP32 faces (sum in
-// FP32 over a warp per node, the quotient in FP64).
+// 1/sigma_i = 1 / (G + dce sum_j 1/a_j^2) of the FP32 operator: a_j from the
+// FP32 faces and 1/a_j in FP32 as the FP32 sweeps form them, the sum over
+// samples and the quotient in FP64; written in FP64 (isigma_d, read by the
+// FP32 cycle's Schur scalar) and rounded to FP32 (isigma32, all-FP32 option).
 __global__ void diag32_kernel(int n, int N, const float* __restrict__ kx, const float* __restrict__ ky,
-                              float* __restrict__ isigma32, double dce, double G, const float* __restrict__ dw) {
+                              float* __restrict__ isigma32, double* __restrict__ isigma_d, double dce, double G,
+                              const float* __restrict__ dw) {
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (long)n * n) return;
   const int iy = (int)(warp / n), ix = (int)(warp - (long)iy * n);
   const float* kW = kx + ((size_t)iy * (n + 1) + ix) * N;
   const float* kS = ky + ((size_t)iy * n + ix) * N;
-  float s = 0.f;
+  double s = 0.0;
   for (int j = lane; j < N; j += 32) {
     const float ia = __frcp_rn((kW[j] + kW[N + j]) + (kS[j] + kS[(size_t)n * N + j]));
-    s += ia * ia;
+    s = fma((double)ia, (double)ia, s);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) isigma32[warp] = (float)(1.0 / (G + (dw ? dce * (double)dw[warp] : dce) * (double)s));
+  if (lane == 0) {
+    const double is = 1.0 / (G + (dw ? dce * (double)dw[warp] : dce) * s);
+    isigma_d[warp] = is;
+    isigma32[warp] = (float)is;
+  }
 }
 
 inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
@@ -288,9 +295,9 @@ cudaError_t launch_coarse_faces32(int nf, int N, const float* kxf, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double dce, double G,
-                          cudaStream_t s, const float* dw) {
-  diag32_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx32, ky32, isigma32, dce, G, dw);
+cudaError_t launch_diag32(int n, int N, const float* kx32, const float* ky32, float* isigma32, double* isigma_d,
+                          double dce, double G, cudaStream_t s, const float* dw) {
+  diag32_kernel<<<blocks_for((long)n * n * 32, 256), 256, 0, s>>>(n, N, kx32, ky32, isigma32, isigma_d, dce, G, dw);
   count_launches(1);
   return cudaGetLastError();
 }

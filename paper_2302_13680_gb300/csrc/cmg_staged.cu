@@ -10,7 +10,7 @@
 // group are already landing in the other, costing no registers.  Every lane
 // copies and later reads only its own vectors, so no barrier is needed
 // beyond the copy-group wait.  The arithmetic is that of rbgs_item (same
-// operand order), with Eq. (13) for u.
+// operand order), with Eq. (13) for u (its Schur scalar in FP64).
 #include <cstdint>
 #include <mutex>
 
@@ -32,12 +32,17 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <int SPL>
 constexpr size_t staged_smem_bytes() {
-  return (size_t)kStageWarps * (2 * SPL * kStageVecs * 32 * sizeof(float4) + 2 * 2 * 32 * sizeof(float));
+  return (size_t)kStageWarps * (2 * SPL * kStageVecs * 32 * sizeof(float4) + 2 * 32 * sizeof(double) +
+                                2 * 2 * 32 * sizeof(float));
 }
 
 template <int SPL>
@@ -49,7 +54,11 @@ __global__ void __launch_bounds__(kStageWarps * 32) rbgs_staged_kernel(LevelView
   constexpr int VEC = SPL * kStageVecs;   // vectors per lane per buffer
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4* wv = sbuf + (size_t)warp * 2 * VEC * 32;   // [2][VEC][32]
-  float* ws = reinterpret_cast<float*>(sbuf + (size_t)kStageWarps * 2 * VEC * 32) + warp * 2 * 2 * 32;   // [2][2][32]
+  // per warp: 1/sigma_i in FP64 [2][32], then the control right side and
+  // the FP32 1/sigma_i (all-FP32 option) [2][2][32]
+  double* wd = reinterpret_cast<double*>(sbuf + (size_t)kStageWarps * 2 * VEC * 32) + warp * 2 * 32;
+  float* ws = reinterpret_cast<float*>(reinterpret_cast<double*>(sbuf + (size_t)kStageWarps * 2 * VEC * 32) +
+                                       kStageWarps * 2 * 32) + warp * 2 * 2 * 32;
   const int n = L.n, N = L.N;
   const size_t ld = (size_t)L.ld;
   const int gpw = 32 / lpn, sub = lane / lpn, ln = lane & (lpn - 1);
@@ -86,7 +95,8 @@ __global__ void __launch_bounds__(kStageWarps * 32) rbgs_staged_kernel(LevelView
       for (int t = 0; t < kStageVecs; ++t) cp_async16(d + (s * kStageVecs + t) * 32, use[t] ? src[t] : safe, use[t]);
     }
     cp_async4(ws + (b * 2 + 0) * 32 + lane, (L.freeze_u ? x.u : f.u) + node);
-    cp_async4(ws + (b * 2 + 1) * 32 + lane, L.isigma32 + node);
+    if (L.ctl32) cp_async4(ws + (b * 2 + 1) * 32 + lane, L.isigma32 + node);
+    else cp_async8(wd + b * 32 + lane, L.isigma + node);
     cp_async_commit();
   };
 
@@ -133,10 +143,12 @@ __global__ void __launch_bounds__(kStageWarps * 32) rbgs_staged_kernel(LevelView
         }
       }
     }
-    const float tsum = group_sum(tacc, lpn);
+    // Eq. (13)'s Schur scalar for u in FP64 (schur_u); every lane takes part
+    const float bu = valid ? ws[(b * 2 + 0) * 32 + lane] : 0.f;
+    const double isg = !valid ? 0.0 : (L.ctl32 ? (double)ws[(b * 2 + 1) * 32 + lane] : wd[b * 32 + lane]);
+    const double su = schur_u<float>(L, tacc, lpn, (double)bu, valid ? d_of(L, (long)node) : 0.0, isg);
     if (!valid) return;
-    const float bu = ws[(b * 2 + 0) * 32 + lane], isg = ws[(b * 2 + 1) * 32 + lane];
-    const float uu = L.freeze_u ? bu : (ctl ? (bu + (float)d_of(L, (long)node) * tsum) * isg : 0.f);
+    const float uu = L.freeze_u ? bu : (ctl ? (float)su : 0.f);
     if (ln == 0 && !L.freeze_u) x.u[node] = uu;
 #pragma unroll
     for (int s = 0; s < SPL; ++s) {
@@ -194,7 +206,7 @@ bool staged_supported(int N, int spl) { return N % 4 == 0 && (spl == 1 || spl ==
 
 cudaError_t launch_rbgs_half_staged(const LevelView<float>& L, Vec3<float> x, Vec3c<float> f, int colour,
                                     const SampleMap& m, cudaStream_t st) {
-  if (m.V != 4 || !staged_supported(L.N, m.spl) || !L.isigma32) return cudaErrorNotSupported;
+  if (m.V != 4 || !staged_supported(L.N, m.spl) || (L.ctl32 ? !L.isigma32 : !L.isigma)) return cudaErrorNotSupported;
   const long groups = colour_count(L.n, colour);
   const long items = (groups + (32 / m.lpn) - 1) / (32 / m.lpn);
   const long need = (items + kStageWarps - 1) / kStageWarps;
