@@ -79,7 +79,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cmg", choices=["cmg", "reference"])
     ap.add_argument("--config", default="n1023_N256",
-                    choices=sorted(inputs.CONFIGS) + ["batch96", "n255_N64_l1box", "n255_N64_galerkin"])
+                    choices=sorted(inputs.CONFIGS) + ["batch96", "n255_N64_l1box", "n255_N64_galerkin", "warmstart"])
+    ap.add_argument("--warm-train", type=int, default=4000, help="warmstart: training solves")
+    ap.add_argument("--warm-epochs", type=int, default=20, help="warmstart: training epochs")
     ap.add_argument("--form", default="auto", choices=["auto"] + sorted(FORMS))
     ap.add_argument("--no-extra", action="store_true", help="skip the n = 255, N = 64 key of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -314,8 +316,9 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     if args.config not in inputs.CONFIGS:
-        # batched, semismooth Newton and Galerkin lines: their oracle (96 instances, Newton steps of full solves,
-        # the sparse Galerkin hierarchy at n = 255) has no sample of a few CPU-seconds that keeps the line's metric
+        # batched, semismooth Newton, Galerkin and warm-start lines: their oracle (96 instances, Newton steps of
+        # full solves, the sparse Galerkin hierarchy at n = 255, thousands of training solves) has no sample of a
+        # few CPU-seconds that keeps the line's metric
         print(json.dumps({"impl": "reference", "unavailable": f"no bounded oracle sample for --config {args.config}; "
                                                               "the reference arm times the base workloads"}),
               flush=True)
@@ -984,6 +987,112 @@ def run_galerkin(args, world, rank, local):
         H.close()
 
 
+def run_warmstart(args, world, rank, local):
+    """Learned warm start (n = 255, N = 64, 16 modes, nu = 1e-5, 8-mode
+    targets): the network is trained on --warm-train solves the method
+    generates (seeds 1000...), then each step solves one held-out instance
+    (seeds 5000...) to 1e-10 from the network's control completed by one
+    frozen-control cycle, inference included; the same instances from a zero
+    initial guess are timed alike.  value = unknowns x fine cycles (frozen
+    cycle included) / time of the warm-started solves."""
+    import math
+
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2302_13680_gb300 as P
+    from paper_2302_13680_gb300 import warmstart as W
+    from paper_2302_13680_gb300.learned import WarmStartNet
+
+    torch.cuda.set_device(local)
+    n, N, K, nu, amp = 255, 64, 16, 1e-5, 1.0
+    unknowns = (2 * N + 1) * n * n
+    first = W.make_instance(1000, n, N, K, nu, amp)
+    H = P.Hierarchy(n, N, first.xi, nu, amp)
+    from paper_2302_13680_gb300 import tuning as T
+
+    T.apply_or_tune(H, P.FP32, args.tuning_cache)
+    t0 = time.perf_counter()
+    YD, MLK, U, it_tr = W.generate(H, list(range(1000, 1000 + args.warm_train)), n, N, K, nu, amp)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    S = 1 << int(math.ceil(math.log2(n + 1)))
+    net = WarmStartNet(S=S, batch=8, seed=0)
+    t0 = time.perf_counter()
+    hist = W.train(net, YD, MLK, U, n, epochs=args.warm_epochs, batch=8, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    opts = P.CycleOptions(precision=P.FP32, tail_n=0)
+    frozen = P.CycleOptions(precision=P.FP32, tail_n=0, freeze_u=1)
+    x = H.zeros(0)
+    stream = torch.cuda.current_stream()
+
+    def instance(seed):
+        pr = W.make_instance(seed, n, N, K, nu, amp)
+        H.set_samples(torch.tensor(pr.xi, device="cuda"))
+        yd = torch.tensor(pr.yd.reshape(-1), device="cuda")
+        return yd, H.rhs(yd), H.mean_log_kappa()
+
+    def solve(yd, f, mlk, warm):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in x:
+            t.zero_()
+        extra = 0
+        if warm:
+            x[1].copy_(W.predict(net, yd, mlk, n))
+            H.solve(frozen, f, x, tol=1e-300, maxit=1, raise_on_fail=False)
+            extra = 1
+        st, status = H.solve(opts, f, x, tol=TOL, maxit=200, raise_on_fail=False)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), st.cycles + extra, st.relres, status
+
+    seeds = list(range(5000, 5000 + args.warmup + args.steps))
+    rec = {"zero": [], "warm": []}
+    errs = []
+    for k, seed in enumerate(seeds):
+        yd, f, mlk = instance(seed)
+        for form in ("zero", "warm"):
+            ms, cyc, relres, status = solve(yd, f, mlk, form == "warm")
+            if status != 0:
+                raise RuntimeError(f"{form} solve of seed {seed} missed 1e-10: relres {relres:.3e}")
+            if k >= args.warmup:
+                rec[form].append((ms, cyc))
+        if k >= args.warmup:
+            ustar = x[1].clone()
+            u0 = W.predict(net, yd, mlk, n)
+            errs.append(float(torch.linalg.norm(u0 - ustar) / torch.linalg.norm(ustar)))
+    ms = {f: statistics.mean(v[0] for v in rec[f]) for f in rec}
+    cyc = {f: statistics.mean(v[1] for v in rec[f]) for f in rec}
+    value = unknowns * sum(v[1] for v in rec["warm"]) / (sum(v[0] for v in rec["warm"]) / 1e3)
+    if rank == 0:
+        line = {"metric": "time-to-1e-10 residual: learned warm start (network u0 + 1 frozen-control cycle, "
+                          "inference included) vs zero initial guess, FP32 cycles in FP64 refinement",
+                "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms["warm"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 network, f32+f64 solver", "data": "synthetic",
+                "config": {"workload": f"learned warm start, n={n}, N={N}, K={K}, amp={amp}, nu={nu:g}, 8-mode "
+                                       f"targets; {args.warm_train} training solves, {args.warm_epochs} epochs, "
+                                       f"held-out seeds 5000+, tol 1e-10",
+                           "n": n, "N": N, "unknowns": unknowns, "instances_per_gpu": 1,
+                           "parallelism": f"replicas x{world} (independent instances, no collective)"},
+                "surrogate_rel_err": statistics.mean(errs),
+                "cycles": cyc, "time_to_tol_ms": ms,
+                "cycles_saved": cyc["zero"] - cyc["warm"],
+                "speedup_vs_zero_start": ms["zero"] / ms["warm"],
+                "gain": "positive" if ms["warm"] < ms["zero"] else "negative: the warm start costs more time "
+                                                                   "than it saves",
+                "training": {"solves": args.warm_train, "generation_s": t_gen, "epochs": args.warm_epochs,
+                             "training_s": t_train, "loss_first_last": [hist[0], hist[-1]],
+                             "train_cycles_mean": statistics.mean(it_tr)}}
+        print(json.dumps(line), flush=True)
+    net.close()
+    H.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -998,6 +1107,9 @@ def main():
         return
     if args.config in GALERKIN_CONFIGS:
         run_galerkin(args, world, rank, local)
+        return
+    if args.config == "warmstart":
+        run_warmstart(args, world, rank, local)
         return
     run_cmg(args, world, rank, local)
 

@@ -448,6 +448,96 @@ cmg_status cmg_nn_unpack_output(const float* img, int B, int n, int S, double sc
                                 void* stream);
 cmg_status cmg_nn_pack_target(const double* u, int B, int n, int S, double scale, float* img, void* stream);
 
+/* ---- learned warm start: the network as one handle ------------------------ */
+
+/* The warm-start network (not part of the paper; multigrid always finishes
+ * the solve, Algorithm 1): a BF16 U-Net mapping (y_d, sample mean of
+ * log kappa_j) on an S x S image to a control u0.  Four resolutions S, S/2,
+ * S/4, S/8 with 32, 64, 64, 64 channels; two 3x3 convolutions + ReLU per
+ * encoder level, 2x2 average pooling, nearest upsampling with additive
+ * skips, one 3x3 convolution + ReLU per decoder level, a 1x1 linear head;
+ * input images [B][S][S][8] BF16 NHWC (channels 0, 1 = y_d and mean
+ * log kappa, the rest zero).  Layers 0..10 are the 3x3 convolutions c0a,
+ * c0b, c1a, c1b, c2a, c2b, c3a, c3b, d2, d1, d0 (weights [Cout][9 Cin],
+ * column t*Cin + c for tap t = 3 dy + dx, bias [Cout]); layer 11 is the
+ * head (weights [1][32], bias [1]).
+ *
+ * The handle owns FP32 master weights, their BF16 copies, the AdamW moments,
+ * the gradients, the activations of the last forward pass and the work
+ * buffers of the largest layer, all sized at create for at most max_batch
+ * images; every call enqueues on the stream given at create.  Device
+ * pointers passed in are borrowed for the call (the input X of
+ * cmg_unet_forward until the matching cmg_unet_backward).  Errors are
+ * status codes with a per-handle message (cmg_unet_last_error); a failed
+ * call leaves the handle usable. */
+typedef struct cmg_unet cmg_unet;
+enum {
+  CMG_UNET_W = 0,     /* FP32 master weights */
+  CMG_UNET_B = 1,     /* bias */
+  CMG_UNET_GW = 2,    /* gradient of the weights (last backward pass) */
+  CMG_UNET_GB = 3,    /* gradient of the bias */
+  CMG_UNET_MW = 4,    /* AdamW first moment of the weights */
+  CMG_UNET_VW = 5,    /* AdamW second moment of the weights */
+  CMG_UNET_MB = 6,    /* AdamW moments of the bias */
+  CMG_UNET_VB = 7,
+  CMG_UNET_W16 = 8    /* the BF16 weights the kernels use (read only, widened to FP32) */
+};
+
+/* S: image side, a multiple of 32 in [32, 4096]; max_batch in [1, 1024];
+ * seed: initial weights (He-normal for the convolutions, N(0, 1e-4) for the
+ * head, zero biases and moments) from a host generator.  Synchronises the
+ * stream once.  INVALID_ARG, OOM, CUDA. */
+cmg_status cmg_unet_create(int S, int max_batch, unsigned long long seed, void* stream, cmg_unet** out);
+void cmg_unet_destroy(cmg_unet* net);
+const char* cmg_unet_last_error(const cmg_unet* net);
+/* Input and output normalisation (also stored in checkpoints): network
+ * channels 0 and 1 are in_yd * y_d and in_logk * mean log kappa; the
+ * network predicts u / out. */
+cmg_status cmg_unet_set_scales(cmg_unet* net, float in_yd, float in_logk, double out);
+cmg_status cmg_unet_get_scales(const cmg_unet* net, float* in_yd, float* in_logk, double* out);
+/* Solver grids to images: yd, mlk [B][n*n] FP64 -> X [B][S][S][8] BF16
+ * (zero padded outside the n x n interior, n <= S); u [B][n*n] FP64 ->
+ * T [B][S][S] FP32 normalised targets; pred [B][S][S] FP32 (NULL = the
+ * handle's last prediction) -> out [B][n*n] FP64 controls.  DEVICE. */
+cmg_status cmg_unet_pack_inputs(cmg_unet* net, const double* yd, const double* mlk, int B, int n, void* X);
+cmg_status cmg_unet_pack_targets(cmg_unet* net, const double* u, int B, int n, float* T);
+cmg_status cmg_unet_unpack(cmg_unet* net, const float* pred, int B, int n, double* out);
+/* Forward pass of B <= max_batch images X (DEVICE, 16-byte aligned); the
+ * prediction is kept in the handle and copied to pred [B][S][S] FP32 when
+ * pred is not NULL.  Activations are kept for cmg_unet_backward. */
+cmg_status cmg_unet_forward(cmg_unet* net, const void* X, int B, float* pred);
+/* Masked mean squared error of the last prediction against target
+ * [B][S][S] FP32 over the interior m x m pixels of each image:
+ * *loss (DEVICE double) = sum (pred - target)^2 / (B m^2); its gradient
+ * (BF16) is kept in the handle for cmg_unet_backward. */
+cmg_status cmg_unet_loss(cmg_unet* net, const float* target, int m, double* loss);
+/* Gradients of every weight and bias for the last forward pass, from the
+ * loss gradient dpred [B][S][S] BF16 (DEVICE), or from the one cmg_unet_loss
+ * kept when dpred is NULL. */
+cmg_status cmg_unet_backward(cmg_unet* net, const void* dpred);
+/* One AdamW step on every layer (decoupled weight decay wd on the weights,
+ * none on the biases; bias-corrected moments); refreshes the BF16 weights. */
+cmg_status cmg_unet_step(cmg_unet* net, float lr, float beta1, float beta2, float eps, float wd);
+/* Parameters: cmg_unet_num_params layers; layer i has weights [rows][cols]
+ * and a bias [rows].  cmg_unet_get / cmg_unet_set copy array `which`
+ * (CMG_UNET_*) to / from HOST memory and synchronise; setting CMG_UNET_W
+ * refreshes the BF16 copy; CMG_UNET_W16 can only be read. */
+int cmg_unet_num_params(const cmg_unet* net);
+int cmg_unet_steps_taken(const cmg_unet* net);
+cmg_status cmg_unet_param_shape(const cmg_unet* net, int layer, int* rows, int* cols);
+cmg_status cmg_unet_get(cmg_unet* net, int layer, int which, float* host);
+cmg_status cmg_unet_set(cmg_unet* net, int layer, int which, const float* host);
+/* *host = 1 if a tensor-core completion wait of any layer's GEMM exceeded
+ * its limit since create (results then incomplete), else 0.  Synchronises. */
+cmg_status cmg_unet_status(cmg_unet* net, int* host);
+/* Checkpoints: a binary file with the FP32 weights, biases, both AdamW
+ * moments of each, the AdamW step count and the scales (format 1, checked
+ * with the layer shapes on load; S need not match: the network is fully
+ * convolutional).  Both synchronise.  A failed load leaves the network
+ * unchanged. */
+cmg_status cmg_unet_save(cmg_unet* net, const char* path);
+cmg_status cmg_unet_load(cmg_unet* net, const char* path);
+
 /* ---- measurement ------------------------------------------------------- */
 
 /* Kernel kinds for cmg_profile_begin. */

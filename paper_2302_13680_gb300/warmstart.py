@@ -7,8 +7,9 @@
    the GPU (cmg_set_samples) and the mixed-precision solver solves the
    problem to 1e-10; the network input is (y_d, sample mean of log kappa_j),
    the target the optimal control u*.
-2. Training: the BF16 U-Net of learned.py with AdamW on the masked MSE of
-   normalised u, all on libcmg's kernels.
+2. Training: the BF16 U-Net held by libcmg's network handle (cmg_unet_*,
+   bound in learned.py) with AdamW on the masked MSE of normalised u, all
+   on libcmg's kernels.
 3. Evaluation on held-out seeds, each solved to 1e-10 from
    (a) zero,
    (b) (0, u0, 0) with u0 the network's prediction, and
@@ -63,8 +64,7 @@ def generate(H, seeds, n, N, K, nu, amp, tol=1e-10):
 def train(net, YD, MLK, U, n, epochs=6, batch=8, lr=2e-3, log=None):
     import torch
 
-    net.in_scale = (1.0 / float(YD.std()), 1.0 / float(MLK.std()))
-    net.out_scale = float(U.std())
+    net.set_scales(1.0 / float(YD.std()), 1.0 / float(MLK.std()), float(U.std()))
     X_all = torch.cat([net.pack_inputs(YD[i:i + 256], MLK[i:i + 256], n) for i in range(0, YD.shape[0], 256)])
     T_all = torch.cat([net.pack_targets(U[i:i + 256], n) for i in range(0, U.shape[0], 256)])
     count = YD.shape[0]
@@ -78,9 +78,9 @@ def train(net, YD, MLK, U, n, epochs=6, batch=8, lr=2e-3, log=None):
         for b in range(count // batch):
             idx = perm[b * batch:(b + 1) * batch].cuda()
             X, T = X_all[idx].contiguous(), T_all[idx].contiguous()
-            pred = net.forward(X)
-            loss, grad = net.loss_and_grad(pred, T, n)
-            net.backward(grad)
+            net.forward(X)
+            loss = net.loss(T, n)
+            net.backward()
             cur = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps))
             net.adamw_step(lr=cur)
             step += 1
@@ -126,7 +126,7 @@ def evaluate(net, H, seeds, n, N, K, nu, amp, frozen=(1, 2, 3), tol=1e-10):
             return H.solve(opts, f, x, tol=tol, maxit=200)[0]
 
         st, ms = timed(zero_solve)
-        row["zero"] = {"cycles": st.iters, "ms": ms}
+        row["zero"] = {"cycles": st.iters, "ms": ms, "relres": st.relres}
         ustar = x[1].clone()
         for kf in (0,) + tuple(frozen):
             def warm_solve():
@@ -140,7 +140,7 @@ def evaluate(net, H, seeds, n, N, K, nu, amp, frozen=(1, 2, 3), tol=1e-10):
                 return H.solve(opts, f, x, tol=tol, maxit=200)[0], u0
 
             (st, u0), ms = timed(warm_solve)
-            row[f"warm_k{kf}"] = {"cycles": st.iters + kf, "main_cycles": st.iters, "ms": ms}
+            row[f"warm_k{kf}"] = {"cycles": st.iters + kf, "main_cycles": st.iters, "ms": ms, "relres": st.relres}
         row["surrogate_rel_err"] = float(torch.linalg.norm(u0 - ustar) / torch.linalg.norm(ustar))
         rows.append(row)
     return rows

@@ -137,3 +137,30 @@ def test_sample_map_covers_every_sample_and_matches_the_stated_limits(lib):
                                 None, ctypes.byref(h)) == 7
     assert fn(0, 4, 0, 0, ctypes.byref(lpn), ctypes.byref(V), ctypes.byref(spl)) == 1
     assert fn(8, 2, 0, 0, ctypes.byref(lpn), ctypes.byref(V), ctypes.byref(spl)) == 1
+
+
+def test_unet_create_rejects_bad_sizes_before_any_device_call(lib):
+    """The network handle refuses image sides that are not multiples of 32,
+    batch sizes outside [1, 1024] and a null output, with no GPU present."""
+    create = lib.cmg_unet_create
+    create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p,
+                       ctypes.POINTER(ctypes.c_void_p)]
+    create.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    for S, B in [(30, 2), (16, 2), (8192, 2), (64, 0), (64, 2000)]:
+        assert create(S, B, 0, None, ctypes.byref(h)) == 1, (S, B)
+        assert not h.value
+    assert create(64, 2, 0, None, None) == 1
+
+
+def test_unet_binding_constants_match_the_header():
+    """learned.py's array codes and layer order equal include/cmg.h's."""
+    from paper_2302_13680_gb300 import learned
+
+    text = open(os.path.join(ROOT, "include", "cmg.h")).read()
+    for name, code in learned.ARRAYS.items():
+        m = re.search(rf"CMG_UNET_{name.upper()}\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == code, name
+    order = re.search(r"Layers 0\.\.10 are the 3x3 convolutions (.*?) \(weights", text, flags=re.S).group(1)
+    names = [w.strip(" ,*\n") for w in re.split(r"[,\s]+", order.replace("*", " ")) if w.strip(" ,*\n")]
+    assert names == learned.LAYERS[:11], names

@@ -1,6 +1,7 @@
-"""The warm-start network's forward pass and parameter gradients on the GPU
-(tcgen05 GEMMs + layer kernels) against the CPU float64 reference with
-automatic differentiation.
+"""The warm-start network through its C ABI handle (cmg_unet_*): forward pass
+and parameter gradients (tcgen05 GEMMs + layer kernels) against the CPU
+float64 reference with automatic differentiation, AdamW training, and
+checkpoints (weights and AdamW state) round-tripped bit for bit.
 
 Tolerances follow from BF16: activations, data gradients and GEMM operands
 are rounded to 8 significant bits (relative 2^-9 = 0.2 %) at each of ~12
@@ -15,69 +16,122 @@ import oracle.unet_oracle as U
 
 pytestmark = pytest.mark.gpu
 
+ARRAYS = ("w", "b", "mw", "vw", "mb", "vb", "w16")
+
 
 @pytest.fixture(scope="module")
-def net():
+def mod():
     from paper_2302_13680_gb300 import build
 
     build.build()
-    from paper_2302_13680_gb300.learned import WarmStartNet
+    from paper_2302_13680_gb300 import learned
 
-    return WarmStartNet(S=32, batch=2, seed=3)
+    return learned
+
+
+@pytest.fixture(scope="module")
+def net(mod):
+    n = mod.WarmStartNet(S=32, batch=2, seed=3)
+    yield n
+    n.close()
 
 
 def rel(a, b):
     return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
 
-def test_forward_and_gradients_match_cpu_reference(net):
-    g = torch.Generator().manual_seed(1)
-    B, S, m = 2, 32, 31
+def batch(seed, B=2, S=32):
+    g = torch.Generator().manual_seed(seed)
     X = torch.zeros(B, S, S, 8)
     X[..., :2] = torch.randn(B, S, S, 2, generator=g)
-    X = X.to(torch.bfloat16)
-    tgt = torch.randn(B, S, S, generator=g)
-    # a head large enough that the loss gradient reaches every layer, drawn
-    # from a seeded generator (not the process-wide CUDA one, whose state
-    # depends on which tests ran before)
+    return X.to(torch.bfloat16), torch.randn(B, S, S, generator=g)
+
+
+def test_forward_and_gradients_match_cpu_reference(mod, net):
+    B, S, m = 2, 32, 31
+    X, tgt = batch(1)
+    # a head large enough that the loss gradient reaches every layer, from a
+    # seeded generator (not the process-wide one, whose state depends on
+    # which tests ran before)
     hg = torch.Generator().manual_seed(7)
-    with torch.no_grad():
-        w = net.params["head"].w
-        w.copy_(torch.randn(w.shape, generator=hg) * 0.2)
-    net.refresh_bf16()
+    net.set("head", "w", torch.randn(1, 32, generator=hg).numpy() * 0.2)
     pred = net.forward(X.cuda())
     torch.cuda.synchronize()
-    params = {k: (p.w16.double().cpu().clone().requires_grad_(True), p.b.double().cpu().clone().requires_grad_(True))
-              for k, p in net.params.items()}
+    params = {k: (torch.tensor(net.get(k, "w16"), dtype=torch.float64).requires_grad_(True),
+                  torch.tensor(net.get(k, "b"), dtype=torch.float64).requires_grad_(True)) for k in mod.LAYERS}
     ref = U.forward(params, X.double())
     assert rel(pred.double().cpu(), ref.detach()) <= 3e-2
-    loss, grad = net.loss_and_grad(pred, tgt.cuda(), m)
-    net.backward(grad)
+    loss = float(net.loss(tgt.cuda(), m))
+    net.backward()
     torch.cuda.synchronize()
     net.check_status()
     ref_loss = U.masked_mse(ref, tgt.double(), m)
-    assert abs(float(loss) - float(ref_loss.detach())) <= 3e-2 * float(ref_loss.detach())
+    assert abs(loss - float(ref_loss.detach())) <= 3e-2 * float(ref_loss.detach())
     ref_loss.backward()
-    for k, p in net.params.items():
-        gw_ref, gb_ref = params[k][0].grad, params[k][1].grad
-        assert rel(p.gw.double().cpu(), gw_ref) <= 6e-2, k
-        assert rel(p.gb.double().cpu(), gb_ref) <= 6e-2, k
+    for k in mod.LAYERS:
+        assert rel(torch.tensor(net.get(k, "gw"), dtype=torch.float64), params[k][0].grad) <= 6e-2, k
+        assert rel(torch.tensor(net.get(k, "gb"), dtype=torch.float64), params[k][1].grad) <= 6e-2, k
 
 
 def test_training_steps_reduce_the_loss(net):
     """A few AdamW steps on a fixed batch lower the masked MSE."""
-    g = torch.Generator().manual_seed(2)
     B, S, m = 2, 32, 31
-    X = torch.zeros(B, S, S, 8)
-    X[..., :2] = torch.randn(B, S, S, 2, generator=g)
-    X = X.to(torch.bfloat16).cuda()
-    tgt = (torch.sin(torch.arange(S) * 0.3)[None, :, None] * torch.ones(B, S, S)).cuda()
+    X, _ = batch(2)
+    X = X.cuda()
+    tgt = (torch.sin(torch.arange(S) * 0.3)[None, :, None] * torch.ones(B, S, S)).cuda().contiguous()
     losses = []
     for _ in range(30):
-        pred = net.forward(X)
-        loss, grad = net.loss_and_grad(pred, tgt, m)
-        net.backward(grad)
+        net.forward(X)
+        losses.append(float(net.loss(tgt, m)))
+        net.backward()
         net.adamw_step(lr=3e-3)
-        losses.append(float(loss))
     net.check_status()
     assert losses[-1] < 0.5 * losses[0], losses
+
+
+def test_checkpoint_round_trip_is_bit_exact(mod, net, tmp_path):
+    """save/load carries the weights, biases, both AdamW moments, the step
+    count and the scales; a fresh handle loaded from the file predicts the
+    same bits and takes the same next AdamW step."""
+    X, tgt = batch(3)
+    X, tgt = X.cuda(), tgt.cuda()
+    net.set_scales(0.5, 2.0, 3.0)
+    for _ in range(3):
+        net.forward(X)
+        net.loss(tgt, 31)
+        net.backward()
+        net.adamw_step(lr=1e-3)
+    path = str(tmp_path / "unet.ckpt")
+    net.save(path)
+    other = mod.WarmStartNet(S=32, batch=2, seed=99)
+    try:
+        assert not np.array_equal(other.get("c0a", "w"), net.get("c0a", "w"))
+        other.load(path)
+        assert other.step_count == net.step_count
+        assert other.in_scale == net.in_scale and other.out_scale == net.out_scale
+        for k in mod.LAYERS:
+            for a in ARRAYS:
+                assert np.array_equal(other.get(k, a), net.get(k, a)), (k, a)
+        p1, p2 = net.forward(X), other.forward(X)
+        assert torch.equal(p1, p2)
+        for h in (net, other):
+            h.forward(X)
+            h.loss(tgt, 31)
+            h.backward()
+            h.adamw_step(lr=1e-3)
+        for k in mod.LAYERS:
+            for a in ARRAYS:
+                assert np.array_equal(other.get(k, a), net.get(k, a)), (k, a)
+    finally:
+        other.close()
+
+
+def test_load_rejects_a_foreign_file_and_keeps_the_weights(net, tmp_path):
+    from paper_2302_13680_gb300.cmg import CMGError
+
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"not a checkpoint at all")
+    before = net.get("d0", "w")
+    with pytest.raises(CMGError):
+        net.load(str(bad))
+    assert np.array_equal(net.get("d0", "w"), before)

@@ -1,4 +1,5 @@
-"""The allocation-free norm entry point against cmg_norm, through the C ABI.
+"""The allocation-free norm entry point against cmg_norm and against numpy, through
+the C ABI.
 
 cmg_norm_noalloc serves callers that cannot allocate device memory where
 they need a norm (an embedding application that owns all allocations, or a
@@ -59,6 +60,9 @@ def test_noalloc_norm_matches_cmg_norm_twice(env):
         ref = H.norm(0, vecs[k])
         got = float(outs[k].item())
         assert abs(got - ref) <= TOL64 * ref, (k, got, ref)
+        # and against the norm computed on the host by numpy (FP64)
+        host = float(np.sqrt(sum(np.sum(t.cpu().numpy() ** 2) for t in vecs[k])))
+        assert abs(got - host) <= TOL64 * host, (k, got, host)
     # weighted form: the y segment scaled by wy
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     assert call(fn, vecs[0], float(H.N), out, stream) == 0
@@ -66,6 +70,8 @@ def test_noalloc_norm_matches_cmg_norm_twice(env):
     scaled = (vecs[0][0] * H.N, vecs[0][1], vecs[0][2])
     ref = H.norm(0, scaled)
     assert abs(float(out.item()) - ref) <= TOL64 * ref
+    host = float(np.sqrt(sum(np.sum(t.cpu().numpy() ** 2) for t in scaled)))
+    assert abs(float(out.item()) - host) <= TOL64 * host
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_array(env):
