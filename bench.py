@@ -385,12 +385,32 @@ def unfused_operand_bytes(n: int, N: int, s: int) -> float:
 
 
 KIND_NAMES = {1: "rbgs_half_kernel", 2: "residual_kernel", 4: "restrict_kernel", 8: "prolong_add_kernel"}
+TUNE_FUSED, TUNE_UNFUSED = 128, 64
+
+
+def fused_sweep_bytes(spec, tuned_f32, cycles: int, launches: int, n: int, N: int, s: int):
+    """Algorithmic bytes per launch of the finest grid's smoothing launches
+    when its red-black sweeps run as one launch each (CMG_TUNE_FUSED): a
+    whole sweep, 8 s per node-sample (y, p read and written once, f_y, f_p,
+    two faces), except the first sweep of each correction cycle, which starts
+    from the zero iterate and reads no y, p (6 s).  Per cycle the finest grid
+    runs n1 - 1 + n2 - 1 plain sweeps (n2 if the prolongation is its own
+    pass: the first post-smoothing sweep is then a plain one) and one from
+    zero; returns None when the launches counted do not match that mix."""
+    t0 = tuned_f32[0]
+    n1, n2 = spec.get("n1", 2), spec.get("n2", 2)
+    if not (t0 & TUNE_FUSED) or spec["precision"] != 1 or n1 % 2 or n2 % 2:
+        return None
+    per_cycle = 1 + (n1 - 1) + (n2 if t0 & TUNE_UNFUSED else n2 - 1)
+    if launches != cycles * per_cycle:
+        return None
+    return (cycles * 6 + (launches - cycles) * 8) / launches * s * n * n * N
 
 
 def kernel_source_sha() -> str:
     """Hash of the sources that define the node kernels (items + wrappers)."""
     h = hashlib.sha256()
-    for name in ("cmg_items.cuh", "cmg_stencil.cu", "cmg_common.cuh"):
+    for name in ("cmg_items.cuh", "cmg_stencil.cu", "cmg_common.cuh", "cmg_fused.cu"):
         h.update(open(os.path.join(ROOT, "paper_2302_13680_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -407,9 +427,14 @@ def traffic_record(kernel: str, precision: str, n: int, N: int):
         return None
     sha = kernel_source_sha()
     entry = rec.get(f"{kernel}:{precision}:n{n}_N{N}")
-    if not entry or entry.get("source_sha") != sha:
-        return None
-    return entry.get("dram_bytes_per_launch")
+    if entry and entry.get("source_sha") == sha:
+        return entry.get("dram_bytes_per_launch")
+    # a capture on a smaller grid (a few GB on the device), scaled by the
+    # node-samples one launch processes
+    entry = rec.get(f"{kernel}:{precision}:per_node_sample")
+    if entry and entry.get("source_sha") == sha:
+        return entry["dram_bytes_per_node_sample"] * n * n * N
+    return None
 
 
 def run_cmg(args, world, rank, local):
@@ -540,7 +565,7 @@ def run_cmg(args, world, rank, local):
     # the dominant kernel's launch durations: the same steps again with CUDA
     # events around its launches (an open profiling window runs the
     # refinement loop eagerly instead of as a graph; kernels are identical)
-    _, _, (dom_ms, dom_cnt), _ = timed_steps(chosen, max(2, min(args.steps, 10)), profile_kind=dom)
+    _, prof_cycles, (dom_ms, dom_cnt), _ = timed_steps(chosen, max(2, min(args.steps, 10)), profile_kind=dom)
     value, total_s, _ = job_throughput(sum(times) / 1e3, unknowns * sum(cycles), dist, dev)
 
     # --- end to end through the public API with host buffers
@@ -577,18 +602,23 @@ def run_cmg(args, world, rank, local):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     alg = algorithmic_bytes(dom, n, N, s_bytes)
+    kname = KIND_NAMES[dom]
+    rule = ("half of a full red+black sweep's minimum: read y, p, f_y, f_p and two faces, write y, p = "
+            "8 s per node-sample per sweep" if dom == 1 else "every operand read once, every result written once")
+    fb = fused_sweep_bytes(FORMS[chosen], tuned["f32"], sum(prof_cycles), dom_cnt, n, N, s_bytes) if dom == 1 else None
+    if fb is not None:
+        alg, kname = fb, "rbgs_fused_kernel"
+        rule = ("one launch per whole red+black sweep: read y, p, f_y, f_p and two faces, write y, p = 8 s per "
+                "node-sample; the first sweep of each correction cycle (zero iterate) 6 s; averaged over the "
+                "launches timed")
     avg_ms = dom_ms / max(dom_cnt, 1)
     achieved = alg / (avg_ms * 1e-3) / 1e9
-    kname = KIND_NAMES[dom]
     roofline = {"bound": "hbm", "kernel": f"{kname} ({prec}, finest grid)", "achieved": achieved,
                 "measured": "CUDA events around each launch, instrumented pass of the timed steps",
                 "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_record(kname, prec, n, N), "algorithmic_bytes_per_launch": alg,
-                "algorithmic_bytes_rule": ("half of a full red+black sweep's minimum: read y, p, f_y, f_p and "
-                                           "two faces, write y, p = 8 s per node-sample per sweep"
-                                           if dom == 1 else "every operand read once, every result written once"),
-                "avg_launch_ms": avg_ms, "launches_timed": dom_cnt}
-    if dom == 1:
+                "algorithmic_bytes_rule": rule, "avg_launch_ms": avg_ms, "launches_timed": dom_cnt}
+    if dom == 1 and fb is None:
         ub = unfused_operand_bytes(n, N, s_bytes)
         roofline["unfused_operand_bytes_per_launch"] = ub
         roofline["unfused_operand_gbs"] = ub / (avg_ms * 1e-3) / 1e9
@@ -617,7 +647,8 @@ def run_cmg(args, world, rank, local):
                 "speedup_vs_plain_fp64": survey[plain]["time_to_tol_ms"] / statistics.median(times),
                 "forms": survey, "cycles_per_step": statistics.mean(cycles),
                 "roofline": roofline,
-                "kernel_time_share_level0": {KIND_NAMES[k]: v[0] for k, v in kind_time.items()},
+                "kernel_time_share_level0": {("rbgs_fused_kernel" if k == 1 and fb is not None else KIND_NAMES[k]): v[0]
+                                             for k, v in kind_time.items()},
                 "tuning_chunks_per_lane": tuned, "tol": tol,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
@@ -745,25 +776,58 @@ def run_batch(args, world, rank, local):
         stats, status = B.solve(opts, fs, xs, tol=TOL, maxit=200)
         return stats
 
+    def timed(k):
+        ts, cyc = [], []
+        for _ in range(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            stats = batch_step()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            cyc.append([s.cycles for s in stats])
+        return ts, cyc
+
+    # both forms of the batched solve, 2 untimed + 3 timed steps each
+    forms = {"persistent": P.BATCH_PERSISTENT, "branches": P.BATCH_BRANCHES}
+    survey = {}
+    for name, code in forms.items():
+        B.set_form(code)
+        for _ in range(2):
+            batch_step()
+        ts, cyc = timed(3)
+        survey[name] = {"time_to_tol_ms": statistics.median(ts), "form_used": B.form(),
+                        "cycles_min_max": [min(cyc[-1]), max(cyc[-1])]}
+    chosen = min(survey, key=lambda k: survey[k]["time_to_tol_ms"])
+    B.set_form(forms[chosen])
     for _ in range(args.warmup):
         batch_step()
     clocks = ClockSampler(local)
     launches0 = C.kernel_launches()
     torch.cuda.synchronize()
     clocks.start()
-    times, units = [], 0
-    for _ in range(args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        stats = batch_step()
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        units += sum(u * s.cycles for u, s in zip(unknowns, stats))
+    times, cycles = timed(args.steps)
     clk = clocks.stop()
     launches = C.kernel_launches() - launches0
+    units = sum(u * c for cyc in cycles for u, c in zip(unknowns, cyc))
     value = units / (sum(times) / 1e3)
+    stats = [type("S", (), {"iters": c})() for c in cycles[-1]]
+    # whole-solve roofline: the FP32 V(2,2) cycle's algorithmic bytes (about
+    # 203 B per fine node-sample, all grids, without the refinement passes)
+    # over the measured time
+    node_samples = [p.n * p.n * p.N for p in probs]
+    alg = sum(203.0 * ns * c for cyc in cycles for ns, c in zip(node_samples, cyc)) / len(cycles)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs") or 6800.0
+    achieved = alg / (statistics.mean(times) / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "whole batched solve (every kernel of the step)", "achieved": achieved,
+                "peak": peak, "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "algorithmic_bytes_per_step": alg,
+                "algorithmic_bytes_rule": "203 B per fine node-sample per FP32 V(2,2) cycle (all grids), refinement "
+                                          "passes not counted"}
     # plain FP64: the same instances one after another (FGMRES + FP64 V-cycle)
     lib = P.load_library()
     seq_ms = []
@@ -784,11 +848,13 @@ def run_batch(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": statistics.mean(times), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": workload_config("batch96", world), "form": "batched graph, fp32-ir per instance",
+                "config": workload_config("batch96", world),
+                "form": f"batched {chosen} form, FP32 V(2,2) cycles in FP64 refinement per instance",
+                "forms": survey,
                 "time_to_tol_ms": {"chosen": statistics.median(times), "plain_fp64_sequential": min(seq_ms)},
                 "speedup_vs_plain_fp64": min(seq_ms) / statistics.median(times),
                 "iterations": [min(s.iters for s in stats), max(s.iters for s in stats)],
-                "gpu_launches": launches, "clocks": clk}
+                "roofline": roofline, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     B.close()
 

@@ -327,17 +327,33 @@ const char* cmg_batch_last_error(const cmg_batch* b);
 cmg_handle* cmg_batch_instance(cmg_batch* b, int i);
 
 /* Solve every instance to its own tolerance (as cmg_solve with
- * CMG_METHOD_CYCLE).  Arguments are HOST arrays of `count` DEVICE pointers
- * (instance i's vectors sized by its own n_i, N_i); stats: host array of
- * `count`.  With opts->precision == CMG_FP32 all instances run in ONE graph
- * launch: per instance an independent branch whose device-side while node
- * runs FP64 refinement around FP32 cycles and stops that instance at its
- * tolerance or maxit (convergence is decided on the device, instance by
- * instance); the graph is captured on first use and reused while the
- * pointers and options stay the same.  Three synchronisations per call.
- * With CMG_FP64 the instances are solved one after another.
- * Returns CMG_ERR_NOT_CONVERGED if any instance missed its tolerance
- * (stats say which), CMG_ERR_NONFINITE if any norm is not finite. */
+ * CMG_METHOD_CYCLE: each instance runs FP64 refinement around FP32 cycles of
+ * Algorithm 1 and stops at its own tolerance or maxit, decided on the
+ * device).  Arguments are HOST arrays of `count` DEVICE pointers (instance
+ * i's vectors sized by its own n_i, N_i); stats: host array of `count`.
+ * With opts->precision == CMG_FP32, two forms:
+ *   CMG_BATCH_PERSISTENT (used when the options and instances allow it:
+ *     red-black V-cycles with n1, n2 >= 1 and the control updated, averaged
+ *     coarse grids, one coarsest size, N <= 128): the instances advance in
+ *     lockstep, their grids aligned by depth from the finest.  Per cycle, ONE
+ *     persistent cooperative launch per grid depth runs every instance's
+ *     down-leg (pre-smoothing from zero, residual, restriction) phase by
+ *     phase over a work list of (instance, warp of nodes) items with a
+ *     grid-wide barrier between phases, one launch runs every coarsest
+ *     solve (a CTA per instance), and one persistent launch per depth runs
+ *     the up-legs; the refinement steps are one launch each for all
+ *     instances.  Per-instance masks skip instances that have stopped.  The
+ *     loop is one CUDA graph with a while node that runs while any instance
+ *     iterates (eager, one synchronisation per iteration, while a profiling
+ *     window is open or graphs are off).  A barrier wait that exceeds its
+ *     poll limit (cmg_batch_set_wait_limit) aborts the solve with
+ *     CMG_ERR_TIMEOUT and leaves the batch usable.
+ *   CMG_BATCH_BRANCHES (otherwise): ONE graph launch in which every instance
+ *     is an independent branch with its own device-side while node.
+ * Graphs are captured on first use and reused while the pointers and
+ * options stay the same.  With CMG_FP64 the instances are solved one after
+ * another.  Returns CMG_ERR_NOT_CONVERGED if any instance missed its
+ * tolerance (stats say which), CMG_ERR_NONFINITE if any norm is not finite. */
 cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, double tol, int maxit,
                            const double* const* fy, const double* const* fu, const double* const* fp,
                            double* const* y, double* const* u, double* const* p, cmg_stats* stats);
@@ -352,7 +368,7 @@ cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, double tol, int 
  * even and at most 64 the layout with two samples per lane and N/2 lanes
  * (rounded up to a power of two) per node (CMG_TUNE_WIDE | 1), which applies
  * to every node kernel of that grid.  Each candidate is timed
- * with CUDA events on a few red+black half-sweep pairs on the handle's own
+ * with CUDA events on a few red+black sweeps on the handle's own
  * work vectors, three times in turn, and the one with the fastest median
  * time is kept in the handle.  chosen (host, may
  * be NULL) receives the target per grid (num_levels entries; the coarsest
@@ -362,10 +378,29 @@ cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
 /* Set the per-grid targets directly (e.g. from a cache of earlier
  * cmg_autotune runs): num_levels entries of 0 (size heuristic), 1, 2 or 4,
  * and for CMG_FP32 also CMG_TUNE_STAGED | 1, CMG_TUNE_STAGED | 2 or
- * CMG_TUNE_WIDE | 1 (ignored where N is odd or above 64); NULL resets all to
- * 0.  Other values return CMG_ERR_INVALID_ARG. */
+ * CMG_TUNE_WIDE | 1 (ignored where N is odd or above 64) or CMG_TUNE_FUSED |
+ * 1, 2 or 4, each possibly with CMG_TUNE_UNFUSED; NULL resets all to 0.  Other values return
+ * CMG_ERR_INVALID_ARG. */
 #define CMG_TUNE_STAGED 16
 #define CMG_TUNE_WIDE 32
+/* FP32 flag, combinable with any FP32 target: on this grid the cycle adds
+ * the prolonged coarse correction in its own pass and then runs the plain
+ * post-smoothing half-sweeps, instead of fusing the prolongation into the
+ * first of them (cmg_autotune times both and sets it where the pass is
+ * faster). */
+#define CMG_TUNE_UNFUSED 64
+/* FP32 flag with 1, 2 or 4 chunks per lane: each red-black sweep on this
+ * grid (colour 0, then colour 1; Eq. (13) per node) runs as one launch over
+ * tiles of the grid, reading the old iterate from one buffer and writing
+ * the new one to a second (allocated with the handle when N % 4 == 0), so
+ * the faces, f and old values are read once per sweep instead of once per
+ * half-sweep.  Sweeps run in pairs (into the second buffer and back); the
+ * results equal the half-sweeps' bit for bit.  Ignored where the shape is
+ * not covered (N % 4 != 0, a frozen control, fewer than two sweeps).  Set
+ * by cmg_set_tuning only: cmg_autotune does not choose it (its tiles walk
+ * their rows one after another, so a sweep that reads less, from the zero
+ * iterate, takes as long as a full one). */
+#define CMG_TUNE_FUSED 128
 /* The launch shape the node kernels use for N samples of elem_bytes (4 or 8)
  * over `items` nodes (0: as many lanes per node as allowed) with a tuning
  * target as above: *lanes_per_node (a power of two <= 32, consecutive lanes of
@@ -378,6 +413,29 @@ cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
 cmg_status cmg_sample_map(int N, int elem_bytes, long long items, int target, int* lanes_per_node, int* vec_width,
                           int* chunks_per_lane);
 cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets);
+
+/* Forms of cmg_batch_solve for FP32 cycles. */
+enum { CMG_BATCH_AUTO = 0, CMG_BATCH_PERSISTENT = 1, CMG_BATCH_BRANCHES = 2 };
+/* Choose the form: CMG_BATCH_AUTO (the default: the branches, which solve
+ * the 96-instance workload of n up to 255 and N in [16, 128] faster),
+ * CMG_BATCH_PERSISTENT (cmg_batch_solve returns CMG_ERR_UNSUPPORTED where it
+ * is not supported) or CMG_BATCH_BRANCHES. */
+cmg_status cmg_batch_set_form(cmg_batch* b, int form);
+/* The form the last FP32 cmg_batch_solve used (0 before any). */
+int cmg_batch_form(const cmg_batch* b);
+/* Persistent form, per grid depth: each leg (down or up) runs either as the
+ * persistent kernel (one cooperative launch, barriers between phases) or as
+ * one ordinary launch per phase and map class (no barrier; every SM's warps
+ * resident).  CMG_BATCH_LEGS_BY_WORK (default): the persistent kernel where
+ * a depth has fewer than 19,456 warp items (152 SMs x 32 warps x 4), one
+ * launch per phase elsewhere; CMG_BATCH_LEGS_PERSISTENT / _PHASES: that form
+ * at every depth.  Takes effect on the next solve. */
+enum { CMG_BATCH_LEGS_BY_WORK = -1, CMG_BATCH_LEGS_PERSISTENT = 0, CMG_BATCH_LEGS_PHASES = 1 };
+cmg_status cmg_batch_set_legs(cmg_batch* b, int legs);
+/* Polls per grid-wide barrier wait of the persistent form before the solve
+ * is abandoned with CMG_ERR_TIMEOUT (0 = the default, 2^26 polls of at
+ * least 64 ns, several seconds).  Takes effect on the next solve. */
+cmg_status cmg_batch_set_wait_limit(cmg_batch* b, long long polls);
 
 /* cmg_autotune on every instance of a batch (the batch graph is re-captured
  * on the next solve). */
@@ -419,6 +477,14 @@ cmg_status cmg_nn_gemm_bf16(const void* A, long long lda, const void* B, long lo
  *   adamw       AdamW step on FP32 master weights, BF16 copy refreshed;
  *   pack_input / pack_target / unpack_output  between solver grids
  *               ([B][n*n] FP64) and S x S network images. */
+/* Poll limit of the TMA kernel's waits for operands and accumulators
+ * (process-wide; 0 = the default of 2^22 polls).  A wait that runs out sets
+ * the call's status word to 1 and the CTA stops issuing work; it still
+ * drains the tensor-core operations and copies it has in flight (those
+ * waits keep the default limit), frees its tensor memory and returns, so the
+ * next call runs normally.  A tiny limit makes every call give up: a way to
+ * exercise that path.  Takes effect for calls enqueued after it. */
+cmg_status cmg_nn_set_wait_limit(long long polls);
 /* Split-K form of cmg_nn_gemm_bf16 for long reductions (weight gradients):
  * slice z of ksplit reads columns [z Kslice, (z+1) Kslice) of A and B and
  * writes the FP32 partial product to partials + z*M*ldc (sum the slices
@@ -447,6 +513,67 @@ cmg_status cmg_nn_pack_input(const double* f0, const double* f1, int B, int n, i
 cmg_status cmg_nn_unpack_output(const float* img, int B, int n, int S, double scale, double* out,
                                 void* stream);
 cmg_status cmg_nn_pack_target(const double* u, int B, int n, int S, double scale, float* img, void* stream);
+
+/* ---- Neumann boundary control ---------------------------------------------- */
+
+/* The control problem of Sec. 2 with the control acting as a Neumann
+ * condition on Gamma = (0,1) x {0} (the boundary-control test case of
+ * Sec. 3.2), solved by collective multigrid with Galerkin coarse operators
+ * (Sec. 3) and damped collective Jacobi (Eq. (11); each node's block by
+ * Eq. (13) on Gamma and Eq. (14) elsewhere), all FP64.
+ *
+ * Grid l has n_l interior columns (x = (ix+1) h, Dirichlet at x = 0, 1) and
+ * n_l + 1 rows (y = r h, row 0 on Gamma, Dirichlet at y = 1): (n_l + 1) n_l
+ * nodes, node r n_l + ix.  Vectors: y, p [(n_l+1) n_l][N] (sample fastest),
+ * u [n_l] on the row-0 nodes.  System (symmetric scaling):
+ *     (M/N) y_j + A_j p_j = f_y,j;  G u - B^T sum_j p_j = f_u;  A_j y_j - B u = f_p,j
+ * with, on the finest grid, A_j the dual-cell 5-point stiffness (harmonic-
+ * mean faces; the x-faces of row 0 halved and no south face there), lumped
+ * M = h^2 (h^2/2 on row 0), G = nu h I and B = h I on Gamma; coarse blocks
+ * P^T S P with P bilinear in x and, in y, keeping row 0 on Gamma (fine row
+ * 2R = coarse row R).  Pointers are DEVICE, 16-byte aligned, borrowed for
+ * the call; work is enqueued on the handle's stream (cmg_bnd_rhs and
+ * cmg_bnd_solve synchronise).  Errors as for cmg_handle. */
+typedef struct cmg_bnd cmg_bnd;
+/* n = 2^L - 1 columns (rows n + 1), N samples (<= 1024), K field modes
+ * (xi_host [N][K], host), coarsest_n 1, 3 or 7 (<= n).  Builds the field,
+ * the finest blocks, every Galerkin coarse block, the Jacobi diagonals and
+ * the coarsest factors; synchronises once.  INVALID_ARG, UNSUPPORTED (the
+ * coarsest factors above 200 KB of shared memory), OOM, CUDA. */
+cmg_status cmg_bnd_create(int n, int N, int K, double nu, double amp, int coarsest_n, const double* xi_host,
+                          void* stream, cmg_bnd** out);
+void cmg_bnd_destroy(cmg_bnd* h);
+const char* cmg_bnd_last_error(const cmg_bnd* h);
+int cmg_bnd_num_levels(const cmg_bnd* h);
+int cmg_bnd_level_n(const cmg_bnd* h, int level);   /* columns of grid `level`, -1 if out of range */
+/* f = ((M y_d)/N, 0, M f_src) on the finest grid; yd, fsrc [(n+1) n] (fsrc
+ * may be NULL: zero). */
+cmg_status cmg_bnd_rhs(cmg_bnd* h, const double* yd, const double* fsrc, double* fy, double* fu, double* fp);
+/* r = f - S_l x (r = S_l x when fy, fu, fp are all NULL) on grid `level`. */
+cmg_status cmg_bnd_residual(cmg_bnd* h, int level, const double* y, const double* u, const double* p,
+                            const double* fy, const double* fu, const double* fp, double* ry, double* ru,
+                            double* rp);
+/* `sweeps` damped collective Jacobi steps x += theta S~^{-1} (f - S x), theta in (0, 1]. */
+cmg_status cmg_bnd_smooth(cmg_bnd* h, int level, double theta, int sweeps, double* y, double* u, double* p,
+                          const double* fy, const double* fu, const double* fp);
+/* c = P^T r from grid `level` to `level`+1; x += P e from `level`+1 to `level`. */
+cmg_status cmg_bnd_restrict(cmg_bnd* h, int level, const double* ry, const double* ru, const double* rp, double* cy,
+                            double* cu, double* cp);
+cmg_status cmg_bnd_prolong_add(cmg_bnd* h, int level, const double* ey, const double* eu, const double* ep,
+                               double* y, double* u, double* p);
+/* x = S^{-1} f on the coarsest grid (block elimination: per-sample A_j^{-1},
+ * the control Schur system G + B^T (sum_j A_j^{-1} (M/N) A_j^{-1}) B). */
+cmg_status cmg_bnd_coarse_solve(cmg_bnd* h, const double* fy, const double* fu, const double* fp, double* y,
+                                double* u, double* p);
+/* One cycle of Algorithm 1 on the finest grid (gamma 1: V, 2: W), in place. */
+cmg_status cmg_bnd_cycle(cmg_bnd* h, double theta, int n1, int n2, int gamma, double* y, double* u, double* p,
+                         const double* fy, const double* fu, const double* fp);
+/* Repeated cycles until ||W (f - S x)|| <= tol ||W f|| (W = diag(N I, 1, 1):
+ * the relative residual of the paper's scaling, Sec. 3.2) or maxit; x in/out.
+ * CMG_ERR_NOT_CONVERGED / CMG_ERR_NONFINITE as cmg_solve. */
+cmg_status cmg_bnd_solve(cmg_bnd* h, double theta, int n1, int n2, int gamma, double tol, int maxit,
+                         const double* fy, const double* fu, const double* fp, double* y, double* u, double* p,
+                         cmg_stats* stats);
 
 /* ---- learned warm start: the network as one handle ------------------------ */
 

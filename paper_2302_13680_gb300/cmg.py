@@ -22,6 +22,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5:
           6: "TIMEOUT", 7: "UNSUPPORTED"}
 SMOOTH_RBGS, SMOOTH_JACOBI = 0, 1
 FP64, FP32 = 0, 1
+BATCH_AUTO, BATCH_PERSISTENT, BATCH_BRANCHES = 0, 1, 2
+BATCH_LEGS_BY_WORK, BATCH_LEGS_PERSISTENT, BATCH_LEGS_PHASES = -1, 0, 1
 METHOD_CYCLE, METHOD_FGMRES = 0, 1
 COARSE = {"averaged": 0, "nodal": 1, "galerkin": 2}
 
@@ -367,6 +369,112 @@ def sample_map(N: int, elem_bytes: int, items: int = 0, target: int = 0):
     return tuple(o.value for o in out)
 
 
+class BoundaryHierarchy:
+    """Neumann boundary control on (0,1) x {0} (cmg_bnd_*): grid l has
+    level_n[l] interior columns and level_n[l] + 1 rows (row 0 on Gamma).
+    Vectors are triples (y, u, p) of CUDA float64 tensors, y and p of shape
+    [(n_l+1) n_l, N], u of shape [n_l]."""
+
+    def __init__(self, n: int, N: int, xi, nu: float, amp: float, coarsest_n: int = 3, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libcmg needs a CUDA GPU; none is available")
+        self._lib = load_library()
+        xi = np.ascontiguousarray(np.asarray(xi, dtype=np.float64))
+        if xi.ndim != 2 or xi.shape[0] != N:
+            raise ValueError("xi must have shape [N, K]")
+        self.n, self.N = int(n), int(N)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        L = self._lib
+        L.cmg_bnd_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.cmg_bnd_last_error.restype = ctypes.c_char_p
+        L.cmg_bnd_last_error.argtypes = [ctypes.c_void_p]
+        st = L.cmg_bnd_create(self.n, self.N, xi.shape[1], float(nu), float(amp), int(coarsest_n),
+                              xi.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(self.stream.cuda_stream),
+                              ctypes.byref(h))
+        if st != CMG_OK:
+            raise CMGError(st, "cmg_bnd_create failed")
+        self._h = h
+        self.levels = L.cmg_bnd_num_levels(h)
+        self.level_n = [L.cmg_bnd_level_n(h, l) for l in range(self.levels)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cmg_bnd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != CMG_OK:
+            msg = self._lib.cmg_bnd_last_error(self._h)
+            raise CMGError(st, msg.decode() if msg else "")
+
+    def zeros(self, level: int = 0):
+        import torch
+
+        n = self.level_n[level]
+        m = (n + 1) * n
+        return (torch.zeros(m, self.N, dtype=torch.float64, device="cuda"),
+                torch.zeros(n, dtype=torch.float64, device="cuda"),
+                torch.zeros(m, self.N, dtype=torch.float64, device="cuda"))
+
+    def _vec(self, v, level):
+        import torch
+
+        if v is None:
+            return [None, None, None]
+        n = self.level_n[level]
+        m = (n + 1) * n
+        for t, shape in zip(v, ((m, self.N), (n,), (m, self.N))):
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.device.type != "cuda" \
+                    or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"expected contiguous CUDA float64 tensors of shapes {(m, self.N)}, {(n,)}")
+        return [_ptr(t) for t in v]
+
+    def rhs(self, yd, fsrc=None):
+        f = self.zeros(0)
+        self._check(self._lib.cmg_bnd_rhs(self._h, _ptr(yd), _ptr(fsrc), *[_ptr(t) for t in f]))
+        return f
+
+    def residual(self, level, x, f, r):
+        self._check(self._lib.cmg_bnd_residual(self._h, level, *self._vec(x, level), *self._vec(f, level),
+                                               *self._vec(r, level)))
+
+    def smooth(self, level, theta, sweeps, x, f):
+        self._check(self._lib.cmg_bnd_smooth(self._h, level, ctypes.c_double(theta), sweeps, *self._vec(x, level),
+                                             *self._vec(f, level)))
+
+    def restrict(self, level, r, c):
+        self._check(self._lib.cmg_bnd_restrict(self._h, level, *self._vec(r, level), *self._vec(c, level + 1)))
+
+    def prolong_add(self, level, e, x):
+        self._check(self._lib.cmg_bnd_prolong_add(self._h, level, *self._vec(e, level + 1), *self._vec(x, level)))
+
+    def coarse_solve(self, f, x):
+        L = self.levels - 1
+        self._check(self._lib.cmg_bnd_coarse_solve(self._h, *self._vec(f, L), *self._vec(x, L)))
+
+    def cycle(self, x, f, theta=0.5, n1=2, n2=2, gamma=1):
+        self._check(self._lib.cmg_bnd_cycle(self._h, ctypes.c_double(theta), n1, n2, gamma, *self._vec(x, 0),
+                                            *self._vec(f, 0)))
+
+    def solve(self, f, x, theta=0.5, n1=2, n2=2, gamma=1, tol=1e-10, maxit=100, raise_on_fail=True):
+        st = Stats()
+        status = self._lib.cmg_bnd_solve(self._h, ctypes.c_double(theta), n1, n2, gamma, ctypes.c_double(tol),
+                                         maxit, *self._vec(f, 0), *self._vec(x, 0), ctypes.byref(st))
+        if raise_on_fail:
+            self._check(status)
+        return st, status
+
+
 def kernel_launches() -> int:
     """Kernels launched by libcmg in this process so far."""
     return int(load_library().cmg_kernel_launches())
@@ -414,6 +522,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_form(self, form: int):
+        """BATCH_AUTO, BATCH_PERSISTENT or BATCH_BRANCHES (cmg_batch_set_form)."""
+        self._bcheck(self._lib.cmg_batch_set_form(self._b, int(form)))
+
+    def form(self) -> int:
+        """The form the last FP32 solve used (cmg_batch_form)."""
+        return int(self._lib.cmg_batch_form(self._b))
+
+    def set_legs(self, legs: int):
+        """Persistent form, per grid depth: BATCH_LEGS_BY_WORK (default),
+        BATCH_LEGS_PERSISTENT (the persistent kernel everywhere) or
+        BATCH_LEGS_PHASES (one launch per phase everywhere)."""
+        self._bcheck(self._lib.cmg_batch_set_legs(self._b, int(legs)))
+
+    def set_wait_limit(self, polls: int):
+        """Polls per grid-wide barrier wait (0 = default) (cmg_batch_set_wait_limit)."""
+        self._bcheck(self._lib.cmg_batch_set_wait_limit(self._b, ctypes.c_longlong(int(polls))))
+
+    def _bcheck(self, st):
+        if st != CMG_OK:
+            msg = self._lib.cmg_batch_last_error(self._b)
+            raise CMGError(st, msg.decode() if msg else "")
 
     def autotune(self, precision: int = FP32):
         st = self._lib.cmg_batch_autotune(self._b, precision)

@@ -242,13 +242,13 @@ size_t coarse_cta_smem(int N, int m) {
   return 2 * 64 * sizeof(double) + ((size_t)N * m * m + 4 * (size_t)N * m) * sizeof(C);
 }
 
+// The coarsest solve by one CTA (the body shared by the single-instance
+// kernel and the batched one, which runs one CTA per instance).
 template <typename T, typename C>
-__global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int N, const C* __restrict__ Ainv,
-                                                                     const double* __restrict__ Minv, double c,
-                                                                     double d, double e, Vec3c<T> f, Vec3<T> x,
-                                                                     int freeze_u, int nside, CtlBox ctl,
-                                                                     const float* __restrict__ dw) {
-  pdl_enter();
+__device__ __forceinline__ void coarse_cta_body(int m, int N, const C* __restrict__ Ainv,
+                                                const double* __restrict__ Minv, double c, double d, double e,
+                                                Vec3c<T> f, Vec3<T> x, int freeze_u, int nside, CtlBox ctl,
+                                                const float* __restrict__ dw) {
   extern __shared__ __align__(16) double sm[];
   const int mm = m * m, nm = N * m;
   double* rhs = sm;                  // [m] control right side
@@ -321,6 +321,27 @@ __global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int
   }
 }
 
+template <typename T, typename C>
+__global__ void __launch_bounds__(kCoarseCtaThreads) coarse_solve_cta(int m, int N, const C* __restrict__ Ainv,
+                                                                     const double* __restrict__ Minv, double c,
+                                                                     double d, double e, Vec3c<T> f, Vec3<T> x,
+                                                                     int freeze_u, int nside, CtlBox ctl,
+                                                                     const float* __restrict__ dw) {
+  pdl_enter();
+  coarse_cta_body<T, C>(m, N, Ainv, Minv, c, d, e, f, x, freeze_u, nside, ctl, dw);
+}
+
+// The coarsest solves of a batch of instances (FP32 cycles), CTA b for
+// instance b; instances whose flag act[b] is zero, or whose abort flag is
+// set, are skipped.
+__global__ void __launch_bounds__(kCoarseCtaThreads) batch_coarse_kernel(const BatchCoarse* __restrict__ bc,
+                                                                        const int* __restrict__ act,
+                                                                        const int* __restrict__ err) {
+  if (*err || !act[blockIdx.x]) return;
+  const BatchCoarse& q = bc[blockIdx.x];
+  coarse_cta_body<float, float>(q.m, q.N, q.Ainv32, q.Minv, q.c, q.d, q.e, q.f, q.x, 0, q.nside, q.ctl, q.dw);
+}
+
 // FP32 copy of the A_j^{-1} for the FP32 coarse solve.
 __global__ void cast_ainv_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -365,6 +386,24 @@ cudaError_t launch_coarse_solve(const CoarseData& C, double c, double d, double 
   if (C.m == 9) return coarse_solve_mm<T, 9>(C, c, d, e, f, x, s, freeze_u);
   if (C.m == 49) return coarse_solve_mm<T, 49>(C, c, d, e, f, x, s, freeze_u);
   return cudaErrorInvalidValue;
+}
+
+size_t batch_coarse_smem(int N_max, int m) { return coarse_cta_smem<float>(N_max, m); }
+
+cudaError_t launch_batch_coarse(const BatchCoarse* bc, int count, int N_max, int m, const int* act, const int* err,
+                                cudaStream_t s) {
+  const size_t smem = coarse_cta_smem<float>(N_max, m);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t ea = cudaFuncSetAttribute(batch_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                200 * 1024);
+    if (ea != cudaSuccess) return ea;
+    attr = true;
+  }
+  batch_coarse_kernel<<<count, kCoarseCtaThreads, smem, s>>>(bc, act, err);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_setup(const CoarseData& C, const double* kx, const double* ky, double c, double G,

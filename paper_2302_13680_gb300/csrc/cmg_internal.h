@@ -139,6 +139,13 @@ constexpr int kTuneStaged = 16;
 // a warp holds one node at N = 64 -- twice the warps of the 16-byte layout,
 // finer work for the last wave of a grid.  Low bits must be 1.
 constexpr int kTuneWide = 32;
+// Tuning target flag (FP32): the cycle on this grid prolongs the coarse
+// correction in its own pass and then runs the plain post-smoothing
+// half-sweeps, instead of fusing the prolongation into the first of them.
+constexpr int kTuneUnfused = 64;
+// Tuning target flag (FP32): the red-black sweeps on this grid run as one
+// launch per sweep (launch_rbgs_fused) in pairs through a second buffer.
+constexpr int kTuneFused = 128;
 inline bool wide_supported(int N) { return N % 2 == 0 && N <= 64; }
 bool staged_supported(int N, int spl);
 cudaError_t launch_rbgs_half_staged(const LevelView<float>& L, Vec3<float> x, Vec3c<float> f, int colour,
@@ -165,6 +172,24 @@ cudaError_t launch_residual_c0(const LevelView<T>& L, Vec3c<T> x, Vec3c<T> f, Ve
 // half-sweep overwrites them), so the prolongation pass is not run.
 template <typename T>
 cudaError_t launch_rbgs_prolong(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, Vec3c<T> e, int nc, cudaStream_t s);
+// One whole red-black sweep in one launch (FP32, cmg_fused.cu): the
+// colour-0 and colour-1 half-sweeps over tiles of the grid, reading the old
+// iterate from xa and writing the new one to xb (xb != xa; equal to the two
+// half-sweeps bit for bit).  Modes: kFusedPlain, kFusedZero (xa is zero and
+// not read), kFusedProlong (colour 0 reads xa + P e, e on the grid of nc
+// nodes per side).  cudaErrorNotSupported where the shape is not covered
+// (fused_plan) or the control is frozen.
+enum { kFusedPlain = 0, kFusedZero = 1, kFusedProlong = 2 };
+struct FusedPlan {
+  bool ok = false;
+  int lpn = 0, spl = 0;          // the half-sweeps' sample map (V = 4)
+  int W = 0, BH = 0;             // tile width (columns) and band height (rows)
+  int strips = 0, tiles = 0;     // tile columns; tiles in all
+  int threads = 0, grid = 0;     // CTA size; CTAs (each walks tiles grid apart)
+};
+FusedPlan fused_plan(int n, int N, int spl_target);
+cudaError_t launch_rbgs_fused(const LevelView<float>& L, Vec3c<float> xa, Vec3<float> xb, Vec3c<float> f,
+                              int mode, Vec3c<float> e, int nc, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict(int nf, int N, Vec3c<T> r, Vec3<T> c, cudaStream_t s,
                             Vec3<T> zx = Vec3<T>{nullptr, nullptr, nullptr}, int colour0 = 0);
@@ -239,6 +264,123 @@ cudaError_t launch_fold(const double* adev, const double* gate, Vec3<float> d, V
 cudaError_t launch_zero3(Vec3<float> v, size_t ny, size_t nu, cudaStream_t s);
 cudaError_t launch_axpy3(double a, const double* adev, Vec3c<float> e, Vec3<double> x, size_t ny, size_t nu,
                          cudaStream_t st);
+
+// State of the FP32 refinement loop of one instance (device doubles; see
+// the refinement loop in cmg_api.cu):
+enum IrState {
+  kSc = 0,       // scale for the next FP64 pass (1 / latest norm)
+  kInvSc = 1,    // 1 / scale of the current right side r^ (also of d)
+  kRho = 2,      // latest residual norm (recursive between anchors, true at one)
+  kIt = 3,       // cycles done
+  kMaxit = 4,
+  kTolAbs = 5,
+  kRhoAnchor = 6,   // true norm at the last anchor
+  kSince = 7,       // cycles since the last anchor
+  kAnchor = 8,      // 1: the anchor kernels of this iteration run
+  kGo = 9,          // 1: another iteration follows
+  kDrop = 10,       // anchor once the recursive norm is below kDrop times the last true one
+  kAmax = 11,       // ... or after kAmax cycles since the last anchor
+  kIrStateSize = 12
+};
+
+// ---- batched persistent form (cmg_batch.cu, batched coarsest solve in cmg_coarse.cu) ----
+// Many independent instances advance through the FP32 refinement loop in
+// lockstep.  Their grids are aligned by depth (depth 0 = each instance's
+// finest grid); a V-cycle is one persistent launch per depth for the
+// down-leg (pre-smoothing, residual, restriction), one launch for every
+// instance's coarsest solve, and one persistent launch per depth for the
+// up-leg (prolongation fused into the first post-smoothing half-sweep, the
+// remaining half-sweeps).  A persistent launch walks a work list of (instance,
+// warp of nodes) items phase by phase, with a grid-wide barrier between
+// phases; instances that have converged are skipped (act[i] = 0).
+
+// Sample maps of the batched FP32 node kernels: on depths run one launch
+// per phase and map class, 16 samples per lane (kBatchMapPhase: 16 / V chunks
+// of V; measured faster than 4 samples or 4 chunks per lane); in the
+// persistent kernels, whose map is chosen at run time, four samples per lane
+// (kBatchMapCoop: the registers of the widest variant stay within two CTAs
+// per SM).
+constexpr int kBatchMapCoop = 0;
+constexpr int kBatchMapPhase = 1;
+
+// One grid of one instance as the batched kernels see it.
+struct BatchLevel {
+  LevelView<float> L;     // FP32 operator of this grid
+  Vec3<float> x, f, r;    // iterate (a correction), right side, residual
+  int lpn, V, spl;        // sample map (by the rule BatchTables::maps of this depth)
+  int nc;                 // nodes per side of the next coarser grid (0 on the coarsest)
+};
+
+// Finest-grid data of one instance for the refinement steps.
+struct BatchInst {
+  LevelView<double> L64;  // FP64 operator (anchor residual)
+  Vec3c<double> f64;      // right side
+  Vec3<double> x64;       // solution
+  Vec3<float> d32;        // FP32 sum of the corrections since the last anchor
+  double* state;          // refinement state (the single-instance loop's layout)
+  float wy2;              // weight of the state block in ||W r||^2
+  int lpn64, V64, spl64;  // FP64 sample map
+  int levels;             // grids of this instance
+};
+
+// Coarsest grid of one instance (FP32 cycle).
+struct BatchCoarse {
+  int m, N, nside;
+  CtlBox ctl;
+  const float* Ainv32;
+  const double* Minv;
+  double c, d, e;
+  const float* dw;
+  Vec3c<float> f;
+  Vec3<float> x;
+};
+
+size_t batch_coarse_smem(int N_max, int m);
+cudaError_t launch_batch_coarse(const BatchCoarse* bc, int count, int N_max, int m, const int* act, const int* err,
+                                cudaStream_t s);
+
+// Device tables of a batch: per instance, kMaxLevels BatchLevel entries and
+// one BatchInst; item prefix counts per (depth, kind) of length count + 1.
+enum BatchKind { kBkColour0 = 0, kBkColour1 = 1, kBkCoarse = 2, kBkAll32 = 3, kBkAll64 = 4, kBkKinds = 5 };
+// Tables per map class: 0 = every instance, 1 / 2 / 3 = the instances whose
+// FP32 vectors are 4 / 2 / 1 samples wide.
+constexpr int kBkClasses = 4;
+struct BatchTables {
+  int count;
+  int depths;                   // the deepest instance's grid count
+  const BatchLevel* lev;        // [count][kMaxLevels]
+  const BatchInst* inst;        // [count]
+  const int* pre;               // [depths][kBkKinds][kBkClasses][count + 1]
+  int cls_mask[kMaxLevels];     // per depth: bit c-1 set when map class c has instances there
+  int maps[kMaxLevels];         // per depth: the map rule of its grids (kBatchMapCoop or kBatchMapPhase)
+  const int* act;               // [count] 1 = instance iterating
+  unsigned* bar;                // grid barrier words [2]
+  int* err;                     // 0 = fine, 1 = a barrier wait ran out (all kernels then return)
+  long long limit;              // polls per barrier wait before giving up
+  double* partial;              // per-item partial sums of the refinement norms
+  int n1, n2;                   // pre- and post-smoothing sweeps
+};
+// Item prefix counts of (depth, kind, map class) in a batch's tables.
+__host__ __device__ inline const int* batch_prefix(const BatchTables& T, int depth, int kind, int cls) {
+  return T.pre + (((size_t)depth * kBkKinds + kind) * kBkClasses + cls) * (T.count + 1);
+}
+// Largest persistent grid of the batched kernels (co-resident CTAs on this
+// GPU); per_sm > 0 caps the CTAs per SM.
+int batch_grid(int which, int per_sm);
+cudaError_t launch_batch_down(const BatchTables& T, int depth, int grid, cudaStream_t s);
+cudaError_t launch_batch_up(const BatchTables& T, int depth, int grid, cudaStream_t s);
+// The same legs as one ordinary launch per phase (no barrier; for the grids
+// with the most work, where the persistent kernel's registers would halve
+// the resident warps).
+cudaError_t launch_batch_down_phases(const BatchTables& T, int depth, int grid, cudaStream_t s);
+cudaError_t launch_batch_up_phases(const BatchTables& T, int depth, int grid, cudaStream_t s);
+cudaError_t launch_batch_recur(const BatchTables& T, int grid, cudaStream_t s);
+cudaError_t launch_batch_anchor(const BatchTables& T, int grid, cudaStream_t s);
+// Per-instance control of the refinement (same decisions as the single-
+// instance loop): after the recursion and after the anchor.
+cudaError_t launch_batch_recur_control(const BatchTables& T, cudaStream_t s);
+cudaError_t launch_batch_anchor_control(const BatchTables& T, cudaStream_t s);
+
 
 // ---- coarsest grid (cmg_coarse.cu) ----
 template <typename T>
@@ -350,6 +492,8 @@ cudaError_t launch_mean_log_kappa(int n, int N, int K, double amp, const double*
 // ldb; K % 8 == 0.
 // ksplit > 1: K is the slice length, slice z reads columns z*K.. and writes
 // C32 + z*M*ldc (FP32 partials, no bias / ReLU / C16).
+// Poll limit of the tensor-core GEMM's waits for work (0 = the default).
+void set_gemm_wait_limit(long long polls);
 cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb, int M, int N, int K,
                                 const float* bias, int relu, float* C32, void* C16, int ldc, int* status,
                                 cudaStream_t s, int ksplit = 1);

@@ -217,17 +217,18 @@ __device__ __forceinline__ vec<T, V> prolonged(const T* xv, const T* ev, int nf,
 // value and the colour-1 sweep after it every colour-1 value, reading only
 // colour-0 neighbours).  Same values as the plain sweep on a cleared x:
 // adding k * 0 leaves a sum unchanged, up to the sign of a zero.
+// rbgs_node: the node (iy, ix) (valid = false: no loads or stores, only the
+// group's shuffles) reading its neighbours (and a frozen u) from xs and
+// writing its new values to x; the half-sweeps pass xs = x, the one-launch
+// full sweep (cmg_fused.cu) reads the old iterate from one buffer and writes
+// another.
 template <typename T, int V, int SPL, bool CG, bool PRO = false, bool ZG = false>
-__device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& x, const Vec3c<T>& f, int colour,
-                                          long g, int lane, int lpn, const Vec3c<T> e = Vec3c<T>{nullptr, nullptr,
-                                                                                                   nullptr},
-                                          int nc = 0) {
+__device__ __forceinline__ void rbgs_node(const LevelView<T>& L, const Vec3c<T>& xs, const Vec3<T>& x,
+                                          const Vec3c<T>& f, bool valid, int iy, int ix, int lane, int lpn,
+                                          const Vec3c<T> e, int nc) {
   const int n = L.n, N = L.N;
   const size_t ld = (size_t)L.ld;
-  const bool valid = g < colour_count(n, colour);
   const T c = (T)L.c;
-  int iy = 0, ix = 0;
-  if (valid) colour_node(g, n, colour, iy, ix);
   const long node = (long)iy * n + ix;
   const bool ctl = L.ctl.inside(iy, ix);   // taken here so (iy, ix) need not stay live
   const size_t o = (size_t)node * ld;
@@ -236,7 +237,7 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
   double bu = 0.0, isg = 0.0;   // control-row right side (or the frozen u) and 1/sigma, loaded with the rest
   double dwv = 1.0;             // per-node factor on d (semismooth Newton systems only), loaded with them
   if (valid) {
-    bu = L.freeze_u ? (double)ld1<T, CG>(x.u + node) : (double)ld1<T, CG>(f.u + node);
+    bu = L.freeze_u ? (double)ld1<T, CG>(xs.u + node) : (double)ld1<T, CG>(f.u + node);
     isg = isigma_of<T>(L, node);
     if (L.dw) dwv = (double)L.dw[node];
     const T* kWp = L.kx + ((size_t)iy * (n + 1) + ix) * ld;
@@ -254,19 +255,19 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
           const auto nb = [&](bool h, const T* xv, const T* ev, int fy, int fx) {
             return h ? prolonged<T, V, CG>(xv, ev, n, nc, ld, fy, fx, j) : vzero<T, V>();
           };
-          fma_faces<T, V>(bp[s], kW, nb(hW, x.p, e.p, iy, ix - 1), kE, nb(hE, x.p, e.p, iy, ix + 1), kS,
-                          nb(hS, x.p, e.p, iy - 1, ix), kN, nb(hN, x.p, e.p, iy + 1, ix));
-          fma_faces<T, V>(by[s], kW, nb(hW, x.y, e.y, iy, ix - 1), kE, nb(hE, x.y, e.y, iy, ix + 1), kS,
-                          nb(hS, x.y, e.y, iy - 1, ix), kN, nb(hN, x.y, e.y, iy + 1, ix));
+          fma_faces<T, V>(bp[s], kW, nb(hW, xs.p, e.p, iy, ix - 1), kE, nb(hE, xs.p, e.p, iy, ix + 1), kS,
+                          nb(hS, xs.p, e.p, iy - 1, ix), kN, nb(hN, xs.p, e.p, iy + 1, ix));
+          fma_faces<T, V>(by[s], kW, nb(hW, xs.y, e.y, iy, ix - 1), kE, nb(hE, xs.y, e.y, iy, ix + 1), kS,
+                          nb(hS, xs.y, e.y, iy - 1, ix), kN, nb(hN, xs.y, e.y, iy + 1, ix));
         } else if constexpr (!ZG) {
-          fma_faces<T, V>(bp[s], kW, ldx_if<T, V, CG>(hW, x.p + o - ld + j), kE,
-                          ldx_if<T, V, CG>(hE, x.p + o + ld + j), kS,
-                          ldx_if<T, V, CG>(hS, x.p + o - (size_t)n * ld + j), kN,
-                          ldx_if<T, V, CG>(hN, x.p + o + (size_t)n * ld + j));
-          fma_faces<T, V>(by[s], kW, ldx_if<T, V, CG>(hW, x.y + o - ld + j), kE,
-                          ldx_if<T, V, CG>(hE, x.y + o + ld + j), kS,
-                          ldx_if<T, V, CG>(hS, x.y + o - (size_t)n * ld + j), kN,
-                          ldx_if<T, V, CG>(hN, x.y + o + (size_t)n * ld + j));
+          fma_faces<T, V>(bp[s], kW, ldx_if<T, V, CG>(hW, xs.p + o - ld + j), kE,
+                          ldx_if<T, V, CG>(hE, xs.p + o + ld + j), kS,
+                          ldx_if<T, V, CG>(hS, xs.p + o - (size_t)n * ld + j), kN,
+                          ldx_if<T, V, CG>(hN, xs.p + o + (size_t)n * ld + j));
+          fma_faces<T, V>(by[s], kW, ldx_if<T, V, CG>(hW, xs.y + o - ld + j), kE,
+                          ldx_if<T, V, CG>(hE, xs.y + o + ld + j), kS,
+                          ldx_if<T, V, CG>(hS, xs.y + o - (size_t)n * ld + j), kN,
+                          ldx_if<T, V, CG>(hN, xs.y + o + (size_t)n * ld + j));
         }
         ia[s] = inv_diag<T, V, CG>(L, o + j, kW, kE, kS, kN);
 #pragma unroll
@@ -301,6 +302,17 @@ __device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& 
       }
     }
   }
+}
+
+template <typename T, int V, int SPL, bool CG, bool PRO = false, bool ZG = false>
+__device__ __forceinline__ void rbgs_item(const LevelView<T>& L, const Vec3<T>& x, const Vec3c<T>& f, int colour,
+                                          long g, int lane, int lpn, const Vec3c<T> e = Vec3c<T>{nullptr, nullptr,
+                                                                                                   nullptr},
+                                          int nc = 0) {
+  const bool valid = g < colour_count(L.n, colour);
+  int iy = 0, ix = 0;
+  if (valid) colour_node(g, L.n, colour, iy, ix);
+  rbgs_node<T, V, SPL, CG, PRO, ZG>(L, cview(x), x, f, valid, iy, ix, lane, lpn, e, nc);
 }
 
 // Damped collective Jacobi, Eq. (11): x_i += theta S~_i^{-1} r_i.
@@ -599,6 +611,48 @@ __device__ __forceinline__ float residual_cast_item(const LevelView<double>& L, 
     const float ru = ctl ? (float)((f.u[node] - (L.G * x.u[node] + d_of(L, node) * psum)) * s) : 0.f;
     r.u[node] = ru;
     sq = fmaf(ru, ru, sq);
+  }
+  return sq;
+}
+
+// One node of the FP32 refinement between anchors (residual replacement):
+// the scaled residual r (the cycle's right side) is updated in place,
+// r <- r - S e (A e from neighbour differences, see residual_item), the
+// running correction d += e, and this lane's part of ||W r||^2 is returned
+// (squares in FP32; wy2 weights the state block).  Each lane reads its own r
+// entries before writing them, so the update in place is safe.
+template <int V, int SPL>
+__device__ __forceinline__ float recur_item(const LevelView<float>& L, const Vec3c<float>& e, const Vec3<float>& r,
+                                            const Vec3<float>& d, long node, int lane, int lpn, float wy2) {
+  residual_item<float, V, SPL, false, true>(L, e, cview(r), r, node, lane, lpn, 1.0f);
+  const int N = L.N;
+  const size_t ld = (size_t)L.ld;
+  float sq = 0.f;
+  if (node < (long)L.n * L.n) {
+    const size_t o = (size_t)node * ld;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+      const int j = (lane + s * lpn) * V;
+      if (j < N) {
+        const vec<float, V> ry = ldv<float, V>(r.y + o + j), rp = ldv<float, V>(r.p + o + j);
+        const vec<float, V> ey = ldv<float, V>(e.y + o + j), ep = ldv<float, V>(e.p + o + j);
+        vec<float, V> dy = ldv<float, V>(d.y + o + j), dp = ldv<float, V>(d.p + o + j);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          sq = fmaf(wy2 * ry.v[k], ry.v[k], sq);
+          sq = fmaf(rp.v[k], rp.v[k], sq);
+          dy.v[k] += ey.v[k];
+          dp.v[k] += ep.v[k];
+        }
+        stv<float, V>(d.y + o + j, dy);
+        stv<float, V>(d.p + o + j, dp);
+      }
+    }
+    if (lane == 0) {
+      const float ru = r.u[node];
+      sq = fmaf(ru, ru, sq);
+      d.u[node] += e.u[node];
+    }
   }
   return sq;
 }

@@ -42,3 +42,9 @@ extern "C" cmg_status cmg_nn_gemm_bf16_splitk(const void* A, long long lda, cons
   }
   return CMG_OK;
 }
+
+extern "C" cmg_status cmg_nn_set_wait_limit(long long polls) {
+  if (polls < 0) return CMG_ERR_INVALID_ARG;
+  set_gemm_wait_limit(polls);
+  return CMG_OK;
+}

@@ -45,6 +45,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 
@@ -104,9 +105,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 // Wait for phase `parity` of the mbarrier; false if the poll limit expires
 // or, when `abort` is given, once another thread has set it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort = nullptr) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort = nullptr,
+                                          long long limit = kSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (long i = 0; i < kSpinLimit; ++i) {
+  for (long long i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -386,7 +388,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     gemm_bf16_tn_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                             int N, int K, const float* __restrict__ bias, int relu, float* __restrict__ C32,
                             __nv_bfloat16* __restrict__ C16, int ldc, int* __restrict__ status, int vec16,
-                            int vec32, int mtiles, int ntiles, int tiles) {
+                            int vec32, int mtiles, int ntiles, int tiles, long long wlimit) {
+  // wlimit bounds the waits for work (operands, accumulators); the waits
+  // that drain MMAs and copies already in flight keep the fixed limit, so a
+  // CTA that gives up never leaves an asynchronous operation behind
   using T = TmaTile<BN, S>;
   extern __shared__ __align__(1024) unsigned char dyn_smem[];
   __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], drain;
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         const TileIdx ti = tile_of(t, mtiles, ntiles, BN);
         for (int kt = 0; kt < ksteps; ++kt, ++it) {
           const int s = it % S;
-          if (it >= S && !mbar_wait(&empty[s], (uint32_t)((it / S - 1) & 1), &failed)) {
+          if (it >= S && !mbar_wait(&empty[s], (uint32_t)((it / S - 1) & 1), &failed, wlimit)) {
             failed = 1;
             break;
           }
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       int it = 0, tc = 0;
       for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x, ++tc) {
         const int b = tc & 1;
-        if (tc >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((tc / 2 - 1) & 1), &failed)) {
+        if (tc >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((tc / 2 - 1) & 1), &failed, wlimit)) {
           failed = 1;
           break;
         }
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         bool ok = true;
         for (int kt = 0; kt < ksteps; ++kt, ++it) {
           const int s = it % S;
-          if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), &failed)) {
+          if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), &failed, wlimit)) {
             ok = false;
             break;
           }
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       const int b = tc & 1;
       // every lane waits; the outcome is made uniform over the warp before the
       // warp-collective TMEM loads
-      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((tc / 2) & 1), &failed))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((tc / 2) & 1), &failed, wlimit))) {
         failed = 1;
         break;
       }
@@ -678,6 +683,10 @@ int pick_bn(int M, int N) {
   return 64;
 }
 
+// Poll limit of the TMA kernel's work waits (0: kSpinLimit); see
+// cmg_nn_set_wait_limit.
+std::atomic<long long> g_wait_limit{0};
+
 template <int BN, int S>
 cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int N, int K, const float* bias, int relu,
                        float* C32, __nv_bfloat16* C16, int ldc, int* status, cudaStream_t s, int ksplit, int vec16,
@@ -694,12 +703,16 @@ cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int 
   if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
   const int sms = sm_count();
   const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));   // persistent: one CTA per SM
+  const long long wl = g_wait_limit.load(std::memory_order_relaxed);
   gemm_bf16_tn_tma_kernel<BN, S><<<grid, kTmaThreads, TmaTile<BN, S>::kSmem, s>>>(
-      mA, mB, M, N, K, bias, relu, C32, C16, ldc, status, vec16, vec32, mtiles, ntiles, (int)tiles);
+      mA, mB, M, N, K, bias, relu, C32, C16, ldc, status, vec16, vec32, mtiles, ntiles, (int)tiles,
+      wl > 0 ? wl : (long long)kSpinLimit);
   return cudaGetLastError();
 }
 
 }  // namespace nn
+
+void set_gemm_wait_limit(long long polls) { nn::g_wait_limit.store(polls, std::memory_order_relaxed); }
 
 cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb, int M, int N, int K,
                                 const float* bias, int relu, float* C32, void* C16, int ldc, int* status,

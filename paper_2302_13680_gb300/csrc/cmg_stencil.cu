@@ -130,36 +130,7 @@ __global__ void __launch_bounds__(kBlock) recur_kernel(LevelView<float> L, Vec3c
   __shared__ double sh[kBlock / 32];
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   const int lane = threadIdx.x & (lpn - 1);
-  residual_item<float, V, SPL, false, true>(L, e, cview(r), r, node, lane, lpn, 1.0f);
-  const int N = L.N;
-  const size_t ld = (size_t)L.ld;
-  float sq = 0.f;
-  if (node < (long)L.n * L.n) {
-    const size_t o = (size_t)node * ld;
-#pragma unroll
-    for (int s = 0; s < SPL; ++s) {
-      const int j = (lane + s * lpn) * V;
-      if (j < N) {
-        const vec<float, V> ry = ldv<float, V>(r.y + o + j), rp = ldv<float, V>(r.p + o + j);
-        const vec<float, V> ey = ldv<float, V>(e.y + o + j), ep = ldv<float, V>(e.p + o + j);
-        vec<float, V> dy = ldv<float, V>(d.y + o + j), dp = ldv<float, V>(d.p + o + j);
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-          sq = fmaf(wy2 * ry.v[k], ry.v[k], sq);
-          sq = fmaf(rp.v[k], rp.v[k], sq);
-          dy.v[k] += ey.v[k];
-          dp.v[k] += ep.v[k];
-        }
-        stv<float, V>(d.y + o + j, dy);
-        stv<float, V>(d.p + o + j, dp);
-      }
-    }
-    if (lane == 0) {
-      const float ru = r.u[node];
-      sq = fmaf(ru, ru, sq);
-      d.u[node] += e.u[node];
-    }
-  }
+  const float sq = recur_item<V, SPL>(L, e, r, d, node, lane, lpn, wy2);
   double v = (double)sq;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
@@ -172,24 +143,39 @@ __global__ void __launch_bounds__(kBlock) recur_kernel(LevelView<float> L, Vec3c
 }
 
 // Anchor of residual replacement: x += a d (a = *adev) and d = 0, when
-// *gate is nonzero.
+// *gate is nonzero.  The y and p blocks move as pairs (16-byte FP64 and
+// 8-byte FP32 vectors; the blocks start 16-byte aligned), one odd tail
+// element and the u block singly.
 __global__ void fold_kernel(const double* __restrict__ adev, const double* __restrict__ gate, Vec3<float> d,
                             Vec3<double> x, size_t ny, size_t nu) {
   pdl_enter();
   if (*gate == 0.0) return;
   const double a = *adev;
-  const size_t total = 2 * ny + nu;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    if (i < ny) {
-      x.y[i] = fma(a, (double)d.y[i], x.y[i]);
-      d.y[i] = 0.f;
-    } else if (i < ny + nu) {
-      x.u[i - ny] = fma(a, (double)d.u[i - ny], x.u[i - ny]);
-      d.u[i - ny] = 0.f;
-    } else {
-      x.p[i - ny - nu] = fma(a, (double)d.p[i - ny - nu], x.p[i - ny - nu]);
-      d.p[i - ny - nu] = 0.f;
-    }
+  const size_t np = ny / 2;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (size_t i = t0; i < 2 * np; i += stride) {
+    const bool isp = i >= np;
+    const size_t k = isp ? i - np : i;
+    double2* xv = reinterpret_cast<double2*>(isp ? x.p : x.y) + k;
+    float2* dv = reinterpret_cast<float2*>(isp ? d.p : d.y) + k;
+    double2 xx = *xv;
+    const float2 dd = *dv;
+    xx.x = fma(a, (double)dd.x, xx.x);
+    xx.y = fma(a, (double)dd.y, xx.y);
+    *xv = xx;
+    *dv = make_float2(0.f, 0.f);
+  }
+  for (size_t i = t0; i < nu; i += stride) {
+    x.u[i] = fma(a, (double)d.u[i], x.u[i]);
+    d.u[i] = 0.f;
+  }
+  if (t0 == 0 && (ny & 1)) {
+    const size_t k = ny - 1;
+    x.y[k] = fma(a, (double)d.y[k], x.y[k]);
+    d.y[k] = 0.f;
+    x.p[k] = fma(a, (double)d.p[k], x.p[k]);
+    d.p[k] = 0.f;
   }
 }
 
@@ -390,7 +376,7 @@ int launch_recur(const LevelView<float>& L, Vec3c<float> e, Vec3<float> r, Vec3<
 
 cudaError_t launch_fold(const double* adev, const double* gate, Vec3<float> d, Vec3<double> x, size_t ny, size_t nu,
                         cudaStream_t st) {
-  const size_t total = 2 * ny + nu;
+  const size_t total = ny + nu;
   size_t blocks = (total + kBlock - 1) / kBlock;
   if (blocks > 152 * 16) blocks = 152 * 16;
   const cudaError_t e_ = launch_k(fold_kernel, dim3((unsigned)blocks), dim3(kBlock), 0, st, adev, gate, d, x, ny, nu);

@@ -75,7 +75,7 @@ def test_binding_loads_and_rejects_bad_sizes(lib):
 def header_constants():
     text = open(os.path.join(ROOT, "include", "cmg.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    vals = {k: int(v) for k, v in re.findall(r"\b(CMG_\w+)\s*=\s*(\d+)", text)}
+    vals = {k: int(v) for k, v in re.findall(r"\b(CMG_\w+)\s*=\s*(-?\d+)", text)}
     vals.update({k: int(v) for k, v in re.findall(r"#define\s+(CMG_\w+)\s+(\d+)", text)})
     return vals
 
@@ -97,6 +97,11 @@ def test_binding_constants_match_the_header():
             cmg.KERNEL_TAIL) == tuple(c["CMG_KERNEL_" + k] for k in ("SMOOTH", "RESIDUAL", "RESTRICT", "PROLONG",
                                                                        "COARSE", "TAIL"))
     assert (c["CMG_TUNE_STAGED"], c["CMG_TUNE_WIDE"]) == (16, 32)   # the flags the tests and tuning cache use
+    assert c["CMG_TUNE_UNFUSED"] == 64 and c["CMG_TUNE_FUSED"] == 128
+    assert (cmg.BATCH_AUTO, cmg.BATCH_PERSISTENT, cmg.BATCH_BRANCHES) == \
+        (c["CMG_BATCH_AUTO"], c["CMG_BATCH_PERSISTENT"], c["CMG_BATCH_BRANCHES"])
+    assert (cmg.BATCH_LEGS_BY_WORK, cmg.BATCH_LEGS_PERSISTENT, cmg.BATCH_LEGS_PHASES) == \
+        (c["CMG_BATCH_LEGS_BY_WORK"], c["CMG_BATCH_LEGS_PERSISTENT"], c["CMG_BATCH_LEGS_PHASES"])
 
 
 def test_sample_map_covers_every_sample_and_matches_the_stated_limits(lib):

@@ -117,3 +117,41 @@ def test_gemm_row_stride_wider_than_k(gemm, path):
     got = C.cpu()
     assert (got[:, :N] - ref).abs().max().item() <= 1e-5 * K ** 0.5 * ref.abs().max().item() + 1e-6
     assert bool((got[:, N:] == 7.0).all())   # columns past N untouched
+
+
+def test_wait_limit_gives_up_cleanly_and_the_next_call_runs(gemm, monkeypatch):
+    """With the TMA kernel's work waits limited to one poll, a call gives up
+    (status word set; the kernel drains what it has in flight and frees its
+    tensor memory); with the default limit restored, the next call on the
+    same stream is exact again."""
+    import paper_2302_13680_gb300 as P
+
+    monkeypatch.setenv("CMG_GEMM_TMA", "1")
+    lib = P.load_library()
+    setl = lib.cmg_nn_set_wait_limit
+    setl.argtypes = [ctypes.c_longlong]
+    setl.restype = ctypes.c_int
+    g = torch.Generator().manual_seed(5)
+    M, N, K = 4096, 256, 512
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    ref = A.float().cpu() @ B.float().cpu().T
+    try:
+        assert setl(1) == 0
+        gave_up = False
+        for _ in range(3):
+            C = torch.zeros(M, N, device="cuda")
+            status = torch.zeros(1, dtype=torch.int32, device="cuda")
+            assert gemm(ptr(A), K, ptr(B), K, M, N, K, None, 0, ptr(C), None, N, ptr(status), None) == 0
+            torch.cuda.synchronize()
+            gave_up = gave_up or int(status.item()) == 1
+        assert gave_up
+    finally:
+        assert setl(0) == 0
+    C = torch.zeros(M, N, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert gemm(ptr(A), K, ptr(B), K, M, N, K, None, 0, ptr(C), None, N, ptr(status), None) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert float((C.cpu() - ref).abs().max()) <= 1e-3 * float(ref.abs().max())
+    assert setl(-1) == 1   # refused
