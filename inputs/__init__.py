@@ -103,6 +103,9 @@ CONFIGS = {
     "n255_N64": dict(n=255, N=64, K=16, nu=1e-6, amp=1.0, seed=2),
     # large mixed-precision instance, n=1023, N=256, 32 modes, nu=1e-5
     "n1023_N256": dict(n=1023, N=256, K=32, nu=1e-5, amp=1.0, seed=3),
+    # a grid whose finest launches still fit a profiler capture (a few GB on the
+    # device, five times the L2 per launch) with the large instance's sample map
+    "n511_N128": dict(n=511, N=128, K=32, nu=1e-5, amp=1.0, seed=5),
     # the n=255, N=64 instance with the control acting on (0.25, 0.75)^2 only
     "n255_N64_local": dict(n=255, N=64, K=16, nu=1e-6, amp=1.0, seed=2, control_box=(0.25, 0.75, 0.25, 0.75)),
 }

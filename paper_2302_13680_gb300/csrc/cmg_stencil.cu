@@ -42,9 +42,15 @@ __global__ void __launch_bounds__(kBlock) residual_c0_kernel(LevelView<T> L, Vec
   residual_item<T, V, SPL, false>(L, x, f, r, node, threadIdx.x & (lpn - 1), lpn, T(1));
 }
 
+// The widest FP32 variants (16 samples per lane) at more CTAs per SM than
+// their registers would allow: more warps in flight to cover the load latency
+// (a few spilled registers cost less).
 template <typename T, int V, int SPL>
-__global__ void __launch_bounds__(kBlock) rbgs_half_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, int colour,
-                                                           int lpn) {
+constexpr int wide_ctas(int k) { return (sizeof(T) == 4 && V * SPL == 16) ? k : 1; }
+
+template <typename T, int V, int SPL>
+__global__ void __launch_bounds__(kBlock, wide_ctas<T, V, SPL>(3))
+    rbgs_half_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, int colour, int lpn) {
   pdl_enter();
   const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   rbgs_item<T, V, SPL, false>(L, x, f, colour, g, threadIdx.x & (lpn - 1), lpn);
@@ -52,7 +58,8 @@ __global__ void __launch_bounds__(kBlock) rbgs_half_kernel(LevelView<T> L, Vec3<
 
 // Colour-0 half-sweep from a zero iterate (see rbgs_item, ZG).
 template <typename T, int V, int SPL>
-__global__ void __launch_bounds__(kBlock) rbgs_zero_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, int lpn) {
+__global__ void __launch_bounds__(kBlock, wide_ctas<T, V, SPL>(3))
+    rbgs_zero_kernel(LevelView<T> L, Vec3<T> x, Vec3c<T> f, int lpn) {
   pdl_enter();
   const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) / lpn;
   rbgs_item<T, V, SPL, false, false, true>(L, x, f, 0, g, threadIdx.x & (lpn - 1), lpn);
@@ -123,7 +130,7 @@ __global__ void __launch_bounds__(kBlock) residual_cast_kernel(LevelView<double>
 // written (squares in FP32, CTA sum in FP64).  Each lane reads its own f
 // entries before writing r at the same place, so the update in place is safe.
 template <int V, int SPL>
-__global__ void __launch_bounds__(kBlock) recur_kernel(LevelView<float> L, Vec3c<float> e, Vec3<float> r,
+__global__ void __launch_bounds__(kBlock, wide_ctas<float, V, SPL>(3)) recur_kernel(LevelView<float> L, Vec3c<float> e, Vec3<float> r,
                                                        Vec3<float> d, int lpn, float wy2,
                                                        double* __restrict__ partial) {
   pdl_enter();
