@@ -1800,7 +1800,6 @@ struct cmg_batch {
   std::vector<int> grid_down, grid_up;
   std::vector<int> leg_phases;       // per depth: 1 = one launch per phase, 0 = the persistent kernel
   int leg_force = -1;                // CMG_BATCH_LEG_* override (-1 = by the depth's work)
-  int grid_plain32 = 0, grid_plain64 = 0;
   int Nmax = 0, cm = 0;
   BatchCoarse* coarse = nullptr;
   cudaStream_t cap = nullptr;
@@ -2101,6 +2100,9 @@ cmg_status batch_build_tables(cmg_batch* b, const cmg_cycle& o, const double* co
   for (int d = 0; d < kMaxLevels; ++d) {
     T.cls_mask[d] = cls_mask[d];
     T.maps[d] = maps[d];
+    for (int k = 0; k < kBkKinds; ++k)
+      for (int c = 0; c < kBkClasses; ++c)
+        T.items[d][k][c] = d < D ? pre[(((size_t)d * kBkKinds + k) * kBkClasses + c) * (count + 1) + count] : 0;
   }
   b->act = dact;
   b->any = dany;
@@ -2110,13 +2112,11 @@ cmg_status batch_build_tables(cmg_batch* b, const cmg_cycle& o, const double* co
   if (cap_d < 1 || cap_u < 1) return bfail(b, CMG_ERR_UNSUPPORTED, "no co-resident grid for the persistent kernels");
   for (int d = 0; d < D; ++d) {
     const long want = std::max<long>(1, (max_depth[d] + 63) / 64);   // a chunk of 8 items per warp, 8 warps
-    // one launch per phase: a warp per item; persistent: chunks of 8 items per warp
-    const long per_item = std::max<long>(1, (max_depth[d] + 7) / 8);
-    b->grid_down[d] = b->leg_phases[d] ? (int)std::min<long>(per_item, 1L << 20) : (int)std::min<long>(want, cap_d);
-    b->grid_up[d] = b->leg_phases[d] ? (int)std::min<long>(per_item, 1L << 20) : (int)std::min<long>(want, cap_u);
+    // persistent legs (the per-phase launches size each class's grid to its
+    // items, one warp per item)
+    b->grid_down[d] = (int)std::min<long>(want, cap_d);
+    b->grid_up[d] = (int)std::min<long>(want, cap_u);
   }
-  b->grid_plain32 = (int)std::max<long>(1, std::min<long>((max_all + 7) / 8, 1L << 20));
-  b->grid_plain64 = b->grid_plain32;
   return CMG_OK;
 }
 
@@ -2127,15 +2127,15 @@ cmg_status batch_body(cmg_batch* b, cudaStream_t s, cudaGraphConditionalHandle c
   const BatchTables& T = b->T;
   const int D = T.depths;
   for (int d = 0; d + 1 < D; ++d)
-    BCK(b->leg_phases[d] ? launch_batch_down_phases(T, d, b->grid_down[d], s)
+    BCK(b->leg_phases[d] ? launch_batch_down_phases(T, d, s)
                          : launch_batch_down(T, d, b->grid_down[d], s));
   BCK(launch_batch_coarse(b->coarse, T.count, b->Nmax, b->cm, T.act, T.err, s));
   for (int d = D - 2; d >= 0; --d)
-    BCK(b->leg_phases[d] ? launch_batch_up_phases(T, d, b->grid_up[d], s)
+    BCK(b->leg_phases[d] ? launch_batch_up_phases(T, d, s)
                          : launch_batch_up(T, d, b->grid_up[d], s));
-  BCK(launch_batch_recur(T, b->grid_plain32, s));
+  BCK(launch_batch_recur(T, s));
   BCK(launch_batch_recur_control(T, s));
-  BCK(launch_batch_anchor(T, b->grid_plain64, s));
+  BCK(launch_batch_anchor(T, s));
   BCK(launch_batch_anchor_control(T, s));
   BCK(launch_k(batch_next_kernel, dim3(1), dim3(256), 0, s, T, b->act, b->any, cond, graph));
   count_launches(1);

@@ -411,66 +411,83 @@ cudaError_t launch_batch_up(const BatchTables& T, int depth, int grid, cudaStrea
 }
 
 namespace {
-// One launch per map class present at this depth (cls_mask bit c-1 = class c).
+// CTAs for one warp per item of (depth, kind, class).
+int class_grid(const BatchTables& T, int depth, int kind, int cls) {
+  return std::max(1, std::min((T.items[depth][kind][cls] + kBWarps - 1) / kBWarps, 1 << 20));
+}
+
+// The items a phase walks.
+constexpr int phase_kind(int ph, int colour) {
+  return ph == kPhRestrict ? kBkCoarse : ph == kPhProlongAdd ? kBkAll32 : (ph == kPhSweep && colour) ? kBkColour1
+                                                                                                      : kBkColour0;
+}
+
+// One launch per map class present at this depth (cls_mask bit c-1 = class
+// c), each sized to that class's items.
 template <int PH>
-cudaError_t launch_phase(const BatchTables& T, int depth, int colour, int grid, cudaStream_t s) {
-  const int mask = T.cls_mask[depth];
+cudaError_t launch_phase(const BatchTables& T, int depth, int colour, cudaStream_t s) {
+  const int mask = T.cls_mask[depth], kind = phase_kind(PH, colour);
   cudaError_t e = cudaSuccess;
-  if (mask & 1) e = launch_k(batch_phase_kernel<PH, 4>, dim3(grid), dim3(kBThreads), 0, s, T, depth, colour);
+  if (mask & 1)
+    e = launch_k(batch_phase_kernel<PH, 4>, dim3(class_grid(T, depth, kind, 1)), dim3(kBThreads), 0, s, T, depth,
+                 colour);
   if (e == cudaSuccess && (mask & 2))
-    e = launch_k(batch_phase_kernel<PH, 2>, dim3(grid), dim3(kBThreads), 0, s, T, depth, colour);
+    e = launch_k(batch_phase_kernel<PH, 2>, dim3(class_grid(T, depth, kind, 2)), dim3(kBThreads), 0, s, T, depth,
+                 colour);
   if (e == cudaSuccess && (mask & 4))
-    e = launch_k(batch_phase_kernel<PH, 1>, dim3(grid), dim3(kBThreads), 0, s, T, depth, colour);
+    e = launch_k(batch_phase_kernel<PH, 1>, dim3(class_grid(T, depth, kind, 3)), dim3(kBThreads), 0, s, T, depth,
+                 colour);
   count_launches(__builtin_popcount(mask));
   return e;
 }
 }  // namespace
 
-cudaError_t launch_batch_down_phases(const BatchTables& T, int depth, int grid, cudaStream_t s) {
-  cudaError_t e = launch_phase<kPhZero>(T, depth, 0, grid, s);
-  if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, grid, s);
+cudaError_t launch_batch_down_phases(const BatchTables& T, int depth, cudaStream_t s) {
+  cudaError_t e = launch_phase<kPhZero>(T, depth, 0, s);
+  if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, s);
   for (int k = 1; k < T.n1 && e == cudaSuccess; ++k) {
-    e = launch_phase<kPhSweep>(T, depth, 0, grid, s);
-    if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, grid, s);
+    e = launch_phase<kPhSweep>(T, depth, 0, s);
+    if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, s);
   }
-  if (e == cudaSuccess) e = launch_phase<kPhResidual>(T, depth, 0, grid, s);
-  if (e == cudaSuccess) e = launch_phase<kPhRestrict>(T, depth, 0, grid, s);
+  if (e == cudaSuccess) e = launch_phase<kPhResidual>(T, depth, 0, s);
+  if (e == cudaSuccess) e = launch_phase<kPhRestrict>(T, depth, 0, s);
   return e;
 }
 
-cudaError_t launch_batch_up_phases(const BatchTables& T, int depth, int grid, cudaStream_t s) {
+cudaError_t launch_batch_up_phases(const BatchTables& T, int depth, cudaStream_t s) {
   // the prolongation in its own pass, then the plain post-smoothing (on the
   // grids with much work the fused sweep's extra coarse loads cost more)
-  cudaError_t e = launch_phase<kPhProlongAdd>(T, depth, 0, grid, s);
-  if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 0, grid, s);
-  if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, grid, s);
+  cudaError_t e = launch_phase<kPhProlongAdd>(T, depth, 0, s);
+  if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 0, s);
+  if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, s);
   for (int k = 1; k < T.n2 && e == cudaSuccess; ++k) {
-    e = launch_phase<kPhSweep>(T, depth, 0, grid, s);
-    if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, grid, s);
+    e = launch_phase<kPhSweep>(T, depth, 0, s);
+    if (e == cudaSuccess) e = launch_phase<kPhSweep>(T, depth, 1, s);
   }
   return e;
 }
 
 namespace {
 template <int R>
-void recur_classes(const BatchTables& T, int grid, cudaStream_t s) {
+void recur_classes(const BatchTables& T, cudaStream_t s) {
   const int mask = T.cls_mask[0];
-  if (mask & 1) batch_recur_kernel<4, R><<<grid, kBThreads, 0, s>>>(T);
-  if (mask & 2) batch_recur_kernel<2, R><<<grid, kBThreads, 0, s>>>(T);
-  if (mask & 4) batch_recur_kernel<1, R><<<grid, kBThreads, 0, s>>>(T);
+  if (mask & 1) batch_recur_kernel<4, R><<<class_grid(T, 0, kBkAll32, 1), kBThreads, 0, s>>>(T);
+  if (mask & 2) batch_recur_kernel<2, R><<<class_grid(T, 0, kBkAll32, 2), kBThreads, 0, s>>>(T);
+  if (mask & 4) batch_recur_kernel<1, R><<<class_grid(T, 0, kBkAll32, 3), kBThreads, 0, s>>>(T);
   count_launches(__builtin_popcount(mask));
 }
 }  // namespace
 
 // The finest grids' maps follow the rule T.maps[0].
-cudaError_t launch_batch_recur(const BatchTables& T, int grid, cudaStream_t s) {
-  if (T.maps[0] == kBatchMapPhase) recur_classes<kBatchMapPhase>(T, grid, s);
-  else if (T.maps[0] == kBatchMapCoop) recur_classes<kBatchMapCoop>(T, grid, s);
+cudaError_t launch_batch_recur(const BatchTables& T, cudaStream_t s) {
+  if (T.maps[0] == kBatchMapPhase) recur_classes<kBatchMapPhase>(T, s);
+  else if (T.maps[0] == kBatchMapCoop) recur_classes<kBatchMapCoop>(T, s);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_anchor(const BatchTables& T, int grid, cudaStream_t s) {
+cudaError_t launch_batch_anchor(const BatchTables& T, cudaStream_t s) {
+  const int grid = class_grid(T, 0, kBkAll64, 0);
   batch_fold_kernel<<<grid, kBThreads, 0, s>>>(T);
   batch_cast_kernel<<<grid, kBThreads, 0, s>>>(T);
   count_launches(2);

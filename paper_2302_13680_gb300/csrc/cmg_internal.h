@@ -353,6 +353,7 @@ struct BatchTables {
   const int* pre;               // [depths][kBkKinds][kBkClasses][count + 1]
   int cls_mask[kMaxLevels];     // per depth: bit c-1 set when map class c has instances there
   int maps[kMaxLevels];         // per depth: the map rule of its grids (kBatchMapCoop or kBatchMapPhase)
+  int items[kMaxLevels][kBkKinds][kBkClasses];   // the prefix tables' totals (host copy: launch grids)
   const int* act;               // [count] 1 = instance iterating
   unsigned* bar;                // grid barrier words [2]
   int* err;                     // 0 = fine, 1 = a barrier wait ran out (all kernels then return)
@@ -372,10 +373,10 @@ cudaError_t launch_batch_up(const BatchTables& T, int depth, int grid, cudaStrea
 // The same legs as one ordinary launch per phase (no barrier; for the grids
 // with the most work, where the persistent kernel's registers would halve
 // the resident warps).
-cudaError_t launch_batch_down_phases(const BatchTables& T, int depth, int grid, cudaStream_t s);
-cudaError_t launch_batch_up_phases(const BatchTables& T, int depth, int grid, cudaStream_t s);
-cudaError_t launch_batch_recur(const BatchTables& T, int grid, cudaStream_t s);
-cudaError_t launch_batch_anchor(const BatchTables& T, int grid, cudaStream_t s);
+cudaError_t launch_batch_down_phases(const BatchTables& T, int depth, cudaStream_t s);
+cudaError_t launch_batch_up_phases(const BatchTables& T, int depth, cudaStream_t s);
+cudaError_t launch_batch_recur(const BatchTables& T, cudaStream_t s);
+cudaError_t launch_batch_anchor(const BatchTables& T, cudaStream_t s);
 // Per-instance control of the refinement (same decisions as the single-
 // instance loop): after the recursion and after the anchor.
 cudaError_t launch_batch_recur_control(const BatchTables& T, cudaStream_t s);
