@@ -485,6 +485,21 @@ cmg_status cmg_nn_gemm_bf16(const void* A, long long lda, const void* B, long lo
  * next call runs normally.  A tiny limit makes every call give up: a way to
  * exercise that path.  Takes effect for calls enqueued after it. */
 cmg_status cmg_nn_set_wait_limit(long long polls);
+/* 3x3 convolution with zero padding 1 as an implicit GEMM on the tensor
+ * cores: Y[p][co] = relu?(bias[co] + sum over taps t = 3 dy + dx and channels
+ * c of X[b][y + dy - 1][x + dx - 1][c] Wt[co][t C + c]) for output pixel
+ * p = (b, y, x); X NHWC BF16 [B][H][W][C], Wt [Cout][9 C] BF16 (both 16-byte
+ * aligned), bias FP32 [Cout] or NULL, Y [B H W][Cout] BF16, all device
+ * pointers.  The tensor cores read X directly through a TMA im2col map (no
+ * im2col matrix in memory); the result equals cmg_nn_im2col followed by
+ * cmg_nn_gemm_bf16 bit for bit.  Covers C a multiple of 32 (per K step of
+ * 64, one tensor-map load of 64 channels of a tap, or two of 32) and C = 8,
+ * 16, 24 (one load per 8 channels of a tap); returns CMG_ERR_UNSUPPORTED,
+ * with nothing enqueued, for other C, Cout > 64, where no tensor map can be
+ * made or with CMG_GEMM_TMA=0 (use im2col + GEMM then).  status as for cmg_nn_gemm_bf16.
+ * Enqueued on `stream`. */
+cmg_status cmg_nn_conv3x3_bf16(const void* X, int B, int H, int W, int C, const void* Wt, int Cout,
+                               const float* bias, int relu, void* Y, int* status, void* stream);
 /* Split-K form of cmg_nn_gemm_bf16 for long reductions (weight gradients):
  * slice z of ksplit reads columns [z Kslice, (z+1) Kslice) of A and B and
  * writes the FP32 partial product to partials + z*M*ldc (sum the slices

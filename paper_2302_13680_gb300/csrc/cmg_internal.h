@@ -495,6 +495,14 @@ cudaError_t launch_mean_log_kappa(int n, int N, int K, double amp, const double*
 // C32 + z*M*ldc (FP32 partials, no bias / ReLU / C16).
 // Poll limit of the tensor-core GEMM's waits for work (0 = the default).
 void set_gemm_wait_limit(long long polls);
+// 3x3 convolution with zero padding 1 as an implicit GEMM on the tensor cores:
+// Y[p][co] = sum_{t, c} X(pixel p shifted by tap t)[c] Wt[co][t C + c] (+
+// bias, ReLU), X NHWC BF16 [B][H][W][C], Wt [Cout][9 C], Y [B H W][Cout] BF16
+// (the im2col + GEMM result, bit for bit).  cudaErrorNotSupported where it
+// does not apply (C neither a multiple of 32 nor 8, 16 or 24; Cout > 64; no
+// tensor map; CMG_GEMM_TMA=0).
+cudaError_t launch_conv3x3_bf16(const void* X, int B, int H, int W, int C, const void* Wt, int Cout,
+                                const float* bias, int relu, void* Y16, int* status, cudaStream_t s);
 cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb, int M, int N, int K,
                                 const float* bias, int relu, float* C32, void* C16, int ldc, int* status,
                                 cudaStream_t s, int ksplit = 1);

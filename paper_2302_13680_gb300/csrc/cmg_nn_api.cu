@@ -26,6 +26,20 @@ extern "C" cmg_status cmg_nn_gemm_bf16(const void* A, long long lda, const void*
   return CMG_OK;
 }
 
+extern "C" cmg_status cmg_nn_conv3x3_bf16(const void* X, int B, int H, int W, int C, const void* Wt, int Cout,
+                                          const float* bias, int relu, void* Y, int* status, void* stream) {
+  if (!X || !Wt || !Y || !status || B < 1 || H < 1 || W < 1 || C < 1 || Cout < 1) return CMG_ERR_INVALID_ARG;
+  if (!aligned16(X) || !aligned16(Wt)) return CMG_ERR_INVALID_ARG;
+  const cudaError_t e = launch_conv3x3_bf16(X, B, H, W, C, Wt, Cout, bias, relu, Y, status,
+                                            static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorNotSupported) return CMG_ERR_UNSUPPORTED;
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return CMG_ERR_CUDA;
+  }
+  return CMG_OK;
+}
+
 extern "C" cmg_status cmg_nn_gemm_bf16_splitk(const void* A, long long lda, const void* B, long long ldb, int M,
                                               int N, int Kslice, int ksplit, float* partials, int ldc, int* status,
                                               void* stream) {

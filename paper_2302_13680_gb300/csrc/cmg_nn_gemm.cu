@@ -29,6 +29,11 @@
 // split-K form (slice z covers K columns [z Kslice, (z+1) Kslice)) reads
 // zeros past the end of its own slice.
 //
+// The same kernel also runs 3x3 convolutions as an implicit GEMM
+// (launch_conv3x3_bf16): the A tiles come straight from the NHWC activations
+// through an im2col tensor map (TMA im2col mode, one load per 8-channel chunk
+// of K, filter offsets per load), so no im2col matrix is written or read.
+//
 // gemm_bf16_tn_kernel (fallback when no tensor map can be made, or
 // CMG_GEMM_TMA=0): a 128 x 64 tile, every thread copying with cp.async into
 // the no-swizzle core-matrix layout, kStages - 1 K steps in flight, one
@@ -74,6 +79,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// K-major tile written by TMA with the 64-byte swizzle: rows of 64 bytes
+// (32 BF16 of K), 8-row groups 512 bytes apart, layout type 4 (64-byte
+// swizzle); the tile base is 512-byte aligned, so a K step of 16 inside the
+// 64-byte row advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
   return d;
 }
 
@@ -136,6 +155,20 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// TMA load in im2col mode of an NHWC tensor map: from the pixel at
+// coordinates (w, h, n) of the map's bounding box on, pixelsPerColumn pixels
+// in W, H, N order, each the box's channels from channel c at input pixel
+// (w + ow, h + oh); outside the tensor reads as zero.  c is a multiple of 8
+// BF16 (16-byte aligned).
+__device__ __forceinline__ void tma_load_im2col(void* dst, const CUtensorMap* map, int c, int w, int h, int n,
+                                                uint16_t ow, uint16_t oh, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.im2col.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6], {%7, %8};" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(w), "r"(h), "r"(n), "r"(smem_u32(bar)), "h"(ow), "h"(oh)
       : "memory");
 }
 
@@ -383,12 +416,29 @@ __device__ __forceinline__ TileIdx tile_of(int t, int mtiles, int ntiles, int bn
   return {(r / ntiles) * kBM, (r % ntiles) * bn, z};
 }
 
-template <int BN, int S>
+// A operand of a 3x3 convolution read straight from the NHWC activations
+// (implicit GEMM): row p of A is output pixel p, column t C + c is channel c
+// of input pixel (y + t / 3 - 1, x + t % 3 - 1).  H, W: image size; cpt = C / 8
+// chunks of 8 channels per tap; kchunks = 9 cpt.
+struct ConvGeom {
+  int H, W, cpt, kchunks;
+};
+
+// AM = 0: A through a tiled map (128-byte swizzle); AM = 1: A through an
+// im2col map of the activations (ConvGeom), one load per 8-channel chunk of
+// K into the no-swizzle core-matrix layout: chunk q of a K step fills bytes
+// q * 2048 .. + 2047 of the A tile (128 pixels x 16 bytes, eight 8 x 16-byte
+// core matrices along M), so the descriptor's K stride is 2048 bytes and its
+// M stride 128; AM = 2 (C a multiple of 64): one im2col load of 64 channels
+// of one tap per K step, with the 128-byte swizzle of the tiled layout;
+// AM = 3 (C a multiple of 32): two loads of 32 channels per K step, each a
+// 128 x 64-byte half of the tile with the 64-byte swizzle.
+template <int BN, int S, int AM>
 __global__ void __launch_bounds__(kTmaThreads, 1)
     gemm_bf16_tn_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                             int N, int K, const float* __restrict__ bias, int relu, float* __restrict__ C32,
                             __nv_bfloat16* __restrict__ C16, int ldc, int* __restrict__ status, int vec16,
-                            int vec32, int mtiles, int ntiles, int tiles, long long wlimit) {
+                            int vec32, int mtiles, int ntiles, int tiles, long long wlimit, ConvGeom geo) {
   // wlimit bounds the waits for work (operands, accumulators); the waits
   // that drain MMAs and copies already in flight keep the fixed limit, so a
   // CTA that gives up never leaves an asynchronous operation behind
@@ -448,7 +498,47 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
           }
           unsigned char* sa = ring + s * T::kStageBytes;
           mbar_expect_tx(&full[s], T::kStageBytes);
-          tma_load_3d(sa, &mapA, kt * kBK, ti.z, ti.m0, &full[s]);
+          if constexpr (AM == 0) {
+            tma_load_3d(sa, &mapA, kt * kBK, ti.z, ti.m0, &full[s]);
+          } else if constexpr (AM == 3) {
+            // 32 channels of a tap per half K step (C % 32 == 0): two loads of 128 pixels x 64 bytes, 64-byte swizzle
+            const int hw = geo.H * geo.W;
+            const int b0 = ti.m0 / hw, rem = ti.m0 - b0 * hw, h0 = rem / geo.W, w0 = rem - h0 * geo.W;
+            const int C = geo.cpt * 8;
+#pragma unroll 1
+            for (int j = 0; j < 2; ++j) {
+              const int k0 = kt * kBK + j * 32;
+              int cc = C, tap = 0;   // past K: a channel past the end, zero filled
+              if (k0 < 9 * C) {
+                tap = k0 / C;
+                cc = k0 - tap * C;
+              }
+              tma_load_im2col(sa + j * 8192, &mapA, cc, w0 - 1, h0 - 1, b0, (uint16_t)(tap % 3), (uint16_t)(tap / 3),
+                              &full[s]);
+            }
+          } else if constexpr (AM == 2) {
+            // 64 channels of one tap per K step (C % 64 == 0): one load, 128-byte swizzle
+            const int hw = geo.H * geo.W;
+            const int b0 = ti.m0 / hw, rem = ti.m0 - b0 * hw, h0 = rem / geo.W, w0 = rem - h0 * geo.W;
+            const int k0 = kt * kBK, C = geo.cpt * 8, tap = k0 / C;
+            tma_load_im2col(sa, &mapA, k0 - tap * C, w0 - 1, h0 - 1, b0, (uint16_t)(tap % 3), (uint16_t)(tap / 3),
+                            &full[s]);
+          } else {
+            // the tile's first output pixel (b0, h0, w0) is bounding-box pixel (w0 - 1, h0 - 1)
+            const int hw = geo.H * geo.W;
+            const int b0 = ti.m0 / hw, rem = ti.m0 - b0 * hw, h0 = rem / geo.W, w0 = rem - h0 * geo.W;
+#pragma unroll 1
+            for (int q = 0; q < kBK / 8; ++q) {
+              const int g = kt * (kBK / 8) + q;
+              int cc = geo.cpt * 8, tap = 0;   // past the last chunk: a channel past the end, zero filled
+              if (g < geo.kchunks) {
+                tap = g / geo.cpt;
+                cc = (g - tap * geo.cpt) * 8;
+              }
+              tma_load_im2col(sa + q * 2048, &mapA, cc, w0 - 1, h0 - 1, b0, (uint16_t)(tap % 3), (uint16_t)(tap / 3),
+                              &full[s]);
+            }
+          }
           tma_load_3d(sa + T::kABytes, &mapB, kt * kBK, ti.z, ti.n0, &full[s]);
         }
       }
@@ -479,9 +569,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(ring + s * T::kStageBytes), b0 = a0 + T::kABytes;
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk)
-            mma_bf16(acc, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
-                     (kt > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            // K = 16: 32 bytes into the swizzled 128-byte rows, or two 2048-byte chunks of the im2col tile
+            const uint64_t ad = AM == 1   ? smem_desc(a0 + kk * 4096, 2048, 128)
+                                : AM == 3 ? smem_desc_sw64(a0 + (kk >> 1) * 8192 + (kk & 1) * 32)
+                                          : smem_desc_sw128(a0 + kk * 32);
+            mma_bf16(acc, ad, smem_desc_sw128(b0 + kk * 32), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          }
           mma_commit(&empty[s]);
         }
         if (!ok) {
@@ -659,6 +753,49 @@ bool operand_map(CUtensorMap* map, const void* base, long ld, int rows, int ksli
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// cuTensorMapEncodeIm2col from the driver, looked up once.
+using EncodeIm2col = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const int*, const int*, cuuint32_t, cuuint32_t, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeIm2col encoder_im2col() {
+  static std::once_flag once;
+  static EncodeIm2col fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeIm2col", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeIm2col>(p);
+    (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+// im2col map of NHWC BF16 activations [B][H][W][C] for a 3x3 convolution with
+// zero padding 1: dimensions {C, W, H, B}; the starting pixels of the filter
+// window run over the bounding box [-1, W - 2] x [-1, H - 2] (both corners
+// -1), the filter offsets (0 .. 2) are added per load; cpp channels per
+// pixel (8: one K chunk, no swizzle; 32: half a K step, 64-byte swizzle; 64:
+// one K step, 128-byte swizzle) and
+// 128 pixels per load (one 128-row A tile), zero outside the tensor.
+bool im2col_map(CUtensorMap* map, const void* X, int B, int H, int W, int C, int cpp) {
+  const EncodeIm2col fn = encoder_im2col();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  const int lower[2] = {-1, -1}, upper[2] = {-1, -1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(X), dims, strides, lower, upper,
+            (cuuint32_t)cpp, (cuuint32_t)kBM, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            cpp == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
+            : cpp == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                        : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int sm_count() {
   static std::once_flag once;
   static int sms = 0;
@@ -687,14 +824,14 @@ int pick_bn(int M, int N) {
 // cmg_nn_set_wait_limit.
 std::atomic<long long> g_wait_limit{0};
 
-template <int BN, int S>
+template <int BN, int S, int AM = 0>
 cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int N, int K, const float* bias, int relu,
                        float* C32, __nv_bfloat16* C16, int ldc, int* status, cudaStream_t s, int ksplit, int vec16,
-                       int vec32) {
+                       int vec32, ConvGeom geo = ConvGeom{0, 0, 0, 0}) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(gemm_bf16_tn_tma_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(gemm_bf16_tn_tma_kernel<BN, S, AM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 TmaTile<BN, S>::kSmem);
   });
   if (attr != cudaSuccess) return attr;
@@ -704,15 +841,43 @@ cudaError_t launch_tma(const CUtensorMap& mA, const CUtensorMap& mB, int M, int 
   const int sms = sm_count();
   const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));   // persistent: one CTA per SM
   const long long wl = g_wait_limit.load(std::memory_order_relaxed);
-  gemm_bf16_tn_tma_kernel<BN, S><<<grid, kTmaThreads, TmaTile<BN, S>::kSmem, s>>>(
+  gemm_bf16_tn_tma_kernel<BN, S, AM><<<grid, kTmaThreads, TmaTile<BN, S>::kSmem, s>>>(
       mA, mB, M, N, K, bias, relu, C32, C16, ldc, status, vec16, vec32, mtiles, ntiles, (int)tiles,
-      wl > 0 ? wl : (long long)kSpinLimit);
+      wl > 0 ? wl : (long long)kSpinLimit, geo);
   return cudaGetLastError();
 }
 
 }  // namespace nn
 
 void set_gemm_wait_limit(long long polls) { nn::g_wait_limit.store(polls, std::memory_order_relaxed); }
+
+cudaError_t launch_conv3x3_bf16(const void* X, int B, int H, int W, int C, const void* Wt, int Cout,
+                                const float* bias, int relu, void* Y16, int* status, cudaStream_t s) {
+  const char* env = std::getenv("CMG_GEMM_TMA");
+  if (env && env[0] == '0') return cudaErrorNotSupported;
+  const long P = (long)B * H * W;
+  // loads per K step of 64: one (C a multiple of 64), two (of 32) or eight
+  // (C = 8, 16, 24: one per 8-channel chunk of a tap)
+  const int cpp = C % 64 == 0 ? 64 : C % 32 == 0 ? 32 : (C % 8 == 0 && C < 32) ? 8 : 0;
+  if (!cpp || Cout < 1 || Cout > 64 || P < 1 || P > 0x7fffffffL || 9L * C > 0x7fffffffL)
+    return cudaErrorNotSupported;
+  const int K = 9 * C;
+  CUtensorMap mA, mB;
+  if (!nn::im2col_map(&mA, X, B, H, W, C, cpp) || !nn::operand_map(&mB, Wt, K, Cout, K, 1, 64))
+    return cudaErrorNotSupported;
+  const int vec16 = (Cout % 8 == 0) && ((reinterpret_cast<uintptr_t>(Y16) & 15) == 0);
+  const nn::ConvGeom geo{H, W, C / 8, 9 * (C / 8)};
+  __nv_bfloat16* y16 = static_cast<__nv_bfloat16*>(Y16);
+  cudaError_t e;
+  if (cpp == 64)
+    e = nn::launch_tma<64, 7, 2>(mA, mB, (int)P, Cout, K, bias, relu, nullptr, y16, Cout, status, s, 1, vec16, 0, geo);
+  else if (cpp == 32)
+    e = nn::launch_tma<64, 7, 3>(mA, mB, (int)P, Cout, K, bias, relu, nullptr, y16, Cout, status, s, 1, vec16, 0, geo);
+  else
+    e = nn::launch_tma<64, 7, 1>(mA, mB, (int)P, Cout, K, bias, relu, nullptr, y16, Cout, status, s, 1, vec16, 0, geo);
+  count_launches(1);
+  return e;
+}
 
 cudaError_t launch_gemm_bf16_tn(const void* A, long lda, const void* B, long ldb, int M, int N, int K,
                                 const float* bias, int relu, float* C32, void* C16, int ldc, int* status,

@@ -167,6 +167,10 @@ cmg_status conv_forward(cmg_unet* u, int layer, const void* X, void* Y, int B) {
   const int H = u->S >> c.level;
   const long P = pixels(u, B, c.level);
   const Param& p = u->prm[layer];
+  // implicit GEMM (the tensor cores read X through an im2col tensor map);
+  // im2col + GEMM where it does not apply (same results)
+  const cmg_status st = cmg_nn_conv3x3_bf16(X, B, H, H, c.ci, p.w16, c.co, p.b, 1, Y, u->status, u->stream);
+  if (st != CMG_ERR_UNSUPPORTED) return st == CMG_OK ? CMG_OK : fail(u, st, "layer call: cmg_nn_conv3x3_bf16");
   NN(cmg_nn_im2col(X, u->col, B, H, H, c.ci, 0, u->stream));
   NN(cmg_nn_gemm_bf16(u->col, 9 * c.ci, p.w16, 9 * c.ci, (int)P, c.co, 9 * c.ci, p.b, 1, nullptr, Y, c.co, u->status,
                       u->stream));
