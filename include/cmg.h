@@ -511,6 +511,11 @@ cmg_status cmg_nn_outer(const void* a, const float* w, void* out, long long P, i
 cmg_status cmg_nn_im2col(const void* X, void* col, int B, int H, int W, int C, int transposed, void* stream);
 cmg_status cmg_nn_col2im(const float* dcol, void* dX, int B, int H, int W, int C, void* stream);
 cmg_status cmg_nn_transpose(const void* in, void* out, long long R, long long Cc, void* stream);
+/* Weights of the data-gradient convolution of a 3x3 layer: Wf [C][9 Cout]
+ * with Wf[c][t Cout + co] = W[co][(8 - t) C + c] (W [Cout][9 C]); then
+ * cmg_nn_conv3x3_bf16(dZ, ..., C = Cout, Wf, Cout = C, no bias, no ReLU)
+ * gives the gradient of the layer's input, the col2im of dZ W. */
+cmg_status cmg_nn_flip3x3(const void* W, void* Wf, int Cout, int C, void* stream);
 cmg_status cmg_nn_relu_bwd(const void* y, const void* dy, void* dz, long long n, void* stream);
 cmg_status cmg_nn_avgpool(const void* X, void* Y, int B, int H, int W, int C, int backward, void* stream);
 cmg_status cmg_nn_upsample_add(const void* X, const void* S, void* Y, int B, int H, int W, int C, void* stream);

@@ -83,6 +83,19 @@ __global__ void col2im_kernel(const float* __restrict__ dcol, bf16* __restrict__
   }
 }
 
+// Weights of the data-gradient convolution: Wf[c][t Cout + co] =
+// W[co][(8 - t) C + c] (taps turned by 180 degrees, channels exchanged), so
+// that dX = conv3x3(dZ, Wf) equals col2im of dZ W.
+__global__ void flip3x3_kernel(const bf16* __restrict__ W, bf16* __restrict__ Wf, int Cout, int C) {
+  const long total = 9L * C * Cout;
+  GRID_STRIDE(i, total) {
+    const int co = (int)(i % Cout);
+    const long r = i / Cout;
+    const int t = (int)(r % 9), c = (int)(r / 9);
+    Wf[i] = W[(long)co * 9 * C + (8 - t) * C + c];
+  }
+}
+
 __global__ void transpose_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, long R, long Cc) {
   GRID_STRIDE(i, R * Cc) {
     const long r = i % R, c = i / R;
@@ -302,6 +315,12 @@ cmg_status cmg_nn_col2im(const float* dcol, void* dX, int B, int H, int W, int C
 cmg_status cmg_nn_transpose(const void* in, void* out, long long R, long long Cc, void* stream) {
   if (!in || !out || R < 1 || Cc < 1) return CMG_ERR_INVALID_ARG;
   transpose_kernel<<<blocks(R * Cc), kT, 0, st(stream)>>>((const bf16*)in, (bf16*)out, R, Cc);
+  return done(1);
+}
+
+cmg_status cmg_nn_flip3x3(const void* W, void* Wf, int Cout, int C, void* stream) {
+  if (!W || !Wf || Cout < 1 || C < 1) return CMG_ERR_INVALID_ARG;
+  flip3x3_kernel<<<blocks(9L * C * Cout), kT, 0, st(stream)>>>((const bf16*)W, (bf16*)Wf, Cout, C);
   return done(1);
 }
 

@@ -194,6 +194,11 @@ cmg_status conv_backward(cmg_unet* u, int layer, const void* X, const void* Y, c
                              u->stream));
   NN(cmg_nn_sum_slices(u->part, nsl, p.gw, (long long)c.co * 9 * c.ci, u->stream));
   if (!dX) return CMG_OK;
+  // dX as a 3x3 convolution of dZ with the turned weights (implicit GEMM, no
+  // patch-gradient matrix); else dZ W into patches and col2im
+  NN(cmg_nn_flip3x3(p.w16, u->WT, c.co, c.ci, u->stream));
+  const cmg_status st = cmg_nn_conv3x3_bf16(u->dZ, B, H, H, c.co, u->WT, c.ci, nullptr, 0, dX, u->status, u->stream);
+  if (st != CMG_ERR_UNSUPPORTED) return st == CMG_OK ? CMG_OK : fail(u, st, "layer call: cmg_nn_conv3x3_bf16");
   NN(cmg_nn_transpose(p.w16, u->WT, c.co, 9 * c.ci, u->stream));
   NN(cmg_nn_gemm_bf16(u->dZ, c.co, u->WT, c.co, (int)P, 9 * c.ci, c.co, nullptr, 0, u->dcol, nullptr, 9 * c.ci,
                       u->status, u->stream));
