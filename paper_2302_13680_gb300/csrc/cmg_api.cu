@@ -2063,16 +2063,33 @@ cmg_status batch_build_tables(cmg_batch* b, const cmg_cycle& o, const double* co
         if (k <= kBkAll32) max_depth[d] = std::max<long>(max_depth[d], row[count]);
         if (d == 0 && k >= kBkAll32) max_all = std::max<long>(max_all, row[count]);
       }
+  // per row, the instance of every 8th item (the first item of each CTA of
+  // a one-item-per-warp launch)
+  std::vector<int> first;
+  int first_off[kMaxLevels][kBkKinds][kBkClasses] = {};
+  for (int d = 0; d < D; ++d)
+    for (int k = 0; k < kBkKinds; ++k)
+      for (int c = 0; c < kBkClasses; ++c) {
+        const int* row = &pre[(((size_t)d * kBkKinds + k) * kBkClasses + c) * (count + 1)];
+        first_off[d][k][c] = (int)first.size();
+        int i = 0;
+        for (int it = 0; it < row[count]; it += 8) {
+          while (row[i + 1] <= it) ++i;
+          first.push_back(i);
+        }
+      }
+  if (first.empty()) first.push_back(0);
   // one allocation per table
   BatchLevel* dlev;
   BatchInst* dinst;
-  int *dpre, *dact, *derr, *dany;
+  int *dpre, *dact, *derr, *dany, *dfirst;
   unsigned* dbar;
   double* dpart;
   BCK(palloc(b, &dlev, lev.size()));
   BCK(palloc(b, &dinst, inst.size()));
   BCK(palloc(b, &b->coarse, co.size()));
   BCK(palloc(b, &dpre, pre.size()));
+  BCK(palloc(b, &dfirst, first.size()));
   BCK(palloc(b, &dact, (size_t)count));
   BCK(palloc(b, &derr, 1));
   BCK(palloc(b, &dany, 1));
@@ -2083,6 +2100,7 @@ cmg_status batch_build_tables(cmg_batch* b, const cmg_cycle& o, const double* co
   BCK(cudaMemcpyAsync(dinst, inst.data(), inst.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->coarse, co.data(), co.size() * sizeof(BatchCoarse), cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(dpre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaMemcpyAsync(dfirst, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
   BatchTables& T = b->T;
   T.count = count;
@@ -2090,6 +2108,7 @@ cmg_status batch_build_tables(cmg_batch* b, const cmg_cycle& o, const double* co
   T.lev = dlev;
   T.inst = dinst;
   T.pre = dpre;
+  T.first = dfirst;
   T.act = dact;
   T.bar = dbar;
   T.err = derr;
@@ -2101,8 +2120,10 @@ cmg_status batch_build_tables(cmg_batch* b, const cmg_cycle& o, const double* co
     T.cls_mask[d] = cls_mask[d];
     T.maps[d] = maps[d];
     for (int k = 0; k < kBkKinds; ++k)
-      for (int c = 0; c < kBkClasses; ++c)
+      for (int c = 0; c < kBkClasses; ++c) {
         T.items[d][k][c] = d < D ? pre[(((size_t)d * kBkKinds + k) * kBkClasses + c) * (count + 1) + count] : 0;
+        T.first_off[d][k][c] = first_off[d][k][c];
+      }
   }
   b->act = dact;
   b->any = dany;

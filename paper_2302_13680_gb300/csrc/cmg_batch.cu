@@ -117,6 +117,13 @@ __device__ __forceinline__ void walk(const BatchTables& T, int depth, int kind, 
   const int lane = threadIdx.x & 31;
   for (int c0 = (blockIdx.x * kBWarps + (threadIdx.x >> 5)) * kChunk; c0 < total; c0 += wtot * kChunk) {
     int lo = 0, hi = T.count;   // pre[lo] <= c0 < pre[hi]
+    if (kChunk == 1 && c0 / kBWarps < T.items[depth][kind][cls] / kBWarps + 1) {
+      // one item per warp: start from the instance of the CTA's first item
+      // (host table) and step forward; a CTA's items span few instances
+      lo = T.first[T.first_off[depth][kind][cls] + c0 / kBWarps];
+      while (pre[lo + 1] <= c0) ++lo;
+      hi = lo + 1;
+    }
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (pre[mid] <= c0) lo = mid;

@@ -354,6 +354,10 @@ struct BatchTables {
   int cls_mask[kMaxLevels];     // per depth: bit c-1 set when map class c has instances there
   int maps[kMaxLevels];         // per depth: the map rule of its grids (kBatchMapCoop or kBatchMapPhase)
   int items[kMaxLevels][kBkKinds][kBkClasses];   // the prefix tables' totals (host copy: launch grids)
+  // per (depth, kind, class): the instance of item 8 b (the first item of
+  // CTA b of a one-item-per-warp launch), at first + first_off[..]
+  const int* first;
+  int first_off[kMaxLevels][kBkKinds][kBkClasses];
   const int* act;               // [count] 1 = instance iterating
   unsigned* bar;                // grid barrier words [2]
   int* err;                     // 0 = fine, 1 = a barrier wait ran out (all kernels then return)
