@@ -2331,7 +2331,7 @@ extern "C" cmg_status cmg_batch_solve(cmg_batch* b, const cmg_cycle* opts, doubl
   // iteration, while a profiling window is open or graphs are off)
   std::string why;
   // CMG_BATCH_AUTO takes the branches: on the 96-instance workload (n up to
-  // 255, N in [16, 128]) they solve in 429-447 ms against 558 ms persistent
+  // 255, N in [16, 128]) they solve in 429-447 ms against 548 ms persistent
   const bool persistent = b->force == CMG_BATCH_PERSISTENT;
   if (persistent) {
     if (!batch_persistent_ok(b, *opts, &why)) return bfail(b, CMG_ERR_UNSUPPORTED, "persistent form: " + why);
