@@ -79,13 +79,15 @@ typedef struct {
                        CMG_COARSE_GALERKIN: no rediscretisation -- the coarse matrices are the
                        Galerkin products S_l = P^T S_{l-1} P of Sec. 3 (the operator of the
                        paper's experiments): 9-point A_j and a 9-point mass M_l on every grid
-                       below the finest.  FP64 cycles only (cmg_cycle.precision = CMG_FP64,
-                       freeze_u = 0; tail_n is ignored); CMG_SMOOTH_JACOBI as on any grid, and
-                       CMG_SMOOTH_RBGS = red-black Gauss-Seidel on the finest grid and four-colour
-                       (iy mod 2, ix mod 2) collective Gauss-Seidel on the 9-point grids;
-                       distributed control only (ctl_box all zero), no
-                       semismooth Newton and no batches: those return CMG_ERR_UNSUPPORTED, as do
-                       the _f32 level operations on such a handle */
+                       below the finest.  Cycles in FP64 or FP32 with the control updated
+                       (freeze_u = 0; FP32 with ctl32 = 0: on the 9-point grids the per-sample
+                       arithmetic is FP32 on FP32 copies of the FP64 Galerkin planes, the control
+                       row and the coarsest elimination FP64; tail_n is ignored);
+                       CMG_SMOOTH_JACOBI as on any grid, and CMG_SMOOTH_RBGS = red-black
+                       Gauss-Seidel on the finest grid and four-colour (iy mod 2, ix mod 2)
+                       collective Gauss-Seidel on the 9-point grids; distributed control only
+                       (ctl_box all zero), no semismooth Newton and no batches: those return
+                       CMG_ERR_UNSUPPORTED */
   double ctl_box[4]; /* local control (Sec. 3.1 after Eq. (13); the local-control test case of
                        Sec. 3.2): the closed region [x0, x1] x [y0, y1] = {ctl_box[0], ctl_box[1],
                        ctl_box[2], ctl_box[3]} inside the unit square.  Nodes of every grid inside
@@ -178,7 +180,8 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc,
 /* r = f - S x on grid `level` (Eq. (2) with this problem's blocks).  With
  * fy, fu, fp all NULL the call computes r = S x (operator apply).  On a
  * CMG_COARSE_GALERKIN handle S on the grids below the finest is the Galerkin
- * product P^T S P (9-point blocks); the _f32 variant is refused there. */
+ * product P^T S P (9-point blocks); the _f32 variant reads FP32 copies of
+ * its planes and forms the control row's sums in FP64. */
 cmg_status cmg_residual(cmg_handle* h, int level,
                         const double* y, const double* u, const double* p,
                         const double* fy, const double* fu, const double* fp,
@@ -226,7 +229,7 @@ cmg_status cmg_prolong_add_f32(cmg_handle* h, int level,
  * n_c^2 x n_c^2 Schur system for u is solved with its precomputed inverse.
  * Always computed in FP64 (the f32 variant converts on load and store).  On
  * a CMG_COARSE_GALERKIN handle the elimination carries the non-diagonal
- * Galerkin mass (FP64 only; x and f must not overlap). */
+ * Galerkin mass (x and f must not overlap). */
 cmg_status cmg_coarse_solve(cmg_handle* h, const double* fy, const double* fu, const double* fp,
                             double* y, double* u, double* p);
 cmg_status cmg_coarse_solve_f32(cmg_handle* h, const float* fy, const float* fu, const float* fp,

@@ -48,6 +48,8 @@ struct Lev {
   double* a9 = nullptr;
   double* psum = nullptr;
   Stencil9 m9{};
+  float* a9f = nullptr;     // FP32 copies of the planes and of 1/(A_j)_ii for the FP32 cycle
+  float* invaf = nullptr;
   float* f32[3] = {nullptr, nullptr, nullptr};
   float* r32[3] = {nullptr, nullptr, nullptr};
 };
@@ -78,6 +80,7 @@ struct cmg_handle {
   CoarseData coarse32{};   // from the FP32 operators (FP32 cycles; averaged coarse grids only)
   double* cface64 = nullptr;   // coarsest FP32 faces promoted to FP64 for coarse32's set-up
   bool fp64_ready = false;     // FP64 operators below the finest faces are current
+  bool g32_ready = false;      // Galerkin handles: the FP32 copies of the coarse planes are current
   CoarseData& c32() { return prob.coarse_coeff == CMG_COARSE_NODAL ? coarse : coarse32; }
   bool galerkin() const { return prob.coarse_coeff == CMG_COARSE_GALERKIN; }
   double* xi = nullptr;       // [N][K] device
@@ -217,6 +220,7 @@ cudaError_t setup_coefficients(cmg_handle* h) {
     return launch_coarse_setup(h->coarse, cl.kx64, cl.ky64, cl.c, cl.G, cl.d, cl.e, h->stream);
   }
   h->fp64_ready = false;
+  h->g32_ready = false;
   Lev& v0 = h->lv[0];
   cudaError_t e = launch_field_faces(v0.n, P.N, P.K, P.amp, h->xi, h->kap, v0.kx64, v0.ky64, v0.kx32, v0.ky32,
                                      h->stream);
@@ -281,6 +285,29 @@ cudaError_t ensure_fp64(cmg_handle* h) {
   return e;
 }
 
+// Galerkin handles, FP32 cycles: FP32 copies of the coarse grids' planes and
+// 1/(A_j)_ii, from the FP64 operators (built first); 1/sigma and the coarsest
+// solve stay FP64.
+cudaError_t ensure_galerkin32(cmg_handle* h) {
+  if (!h->galerkin() || h->g32_ready) return cudaSuccess;
+  cudaError_t e = ensure_fp64(h);
+  const size_t N = (size_t)h->prob.N;
+  for (int l = 1; l < h->L && e == cudaSuccess; ++l) {
+    Lev& v = h->lv[l];
+    e = launch_scale_cast<double, float>(1.0, v.a9, v.a9f, 9 * v.nodes * N, h->stream);
+    if (e == cudaSuccess) e = launch_scale_cast<double, float>(1.0, v.inva, v.invaf, v.nodes * N, h->stream);
+  }
+  if (e == cudaSuccess) h->g32_ready = true;
+  return e;
+}
+
+// The operators a call in precision T reads.
+template <typename T>
+cudaError_t ensure_ops(cmg_handle* h) {
+  if constexpr (sizeof(T) == 8) return ensure_fp64(h);
+  else return ensure_galerkin32(h);
+}
+
 // After the finest grid's per-node factor on d changed: inject it to the
 // coarse grids and rebuild what depends on it (1/sigma on every grid, the
 // coarsest control Schur inverse), for the FP32 operators and, where built,
@@ -318,12 +345,13 @@ cudaError_t refresh_dw(cmg_handle* h) {
 // operator on the coarse grids of a Galerkin hierarchy, else the 5-point one.
 template <typename T>
 cudaError_t level_residual(cmg_handle* h, int l, Vec3c<T> x, Vec3c<T> f, Vec3<T> r) {
-  if constexpr (sizeof(T) == 8) {
-    if (h->galerkin() && l > 0) {
-      const Lev& v = h->lv[l];
-      const Lev& f0 = h->lv[0];
-      return launch_residual9(v.n, h->prob.N, v.a9, v.m9, f0.c, f0.G, f0.d, f0.e, x, f, r, v.psum, h->stream);
-    }
+  if (h->galerkin() && l > 0) {
+    const Lev& v = h->lv[l];
+    const Lev& f0 = h->lv[0];
+    const T* a9 = nullptr;
+    if constexpr (sizeof(T) == 8) a9 = v.a9;
+    else a9 = v.a9f;
+    return launch_residual9<T>(v.n, h->prob.N, a9, v.m9, f0.c, f0.G, f0.d, f0.e, x, f, r, v.psum, h->stream);
   }
   return launch_residual<T>(view<T>(h, l), x, f, r, h->stream);
 }
@@ -367,15 +395,41 @@ cudaError_t smooth(cmg_handle* h, const cmg_cycle& o, int l, int sweeps, Vec3<T>
       }
     }
   }
-  if constexpr (sizeof(T) == 8) {
-    if (h->galerkin() && l > 0 && o.smoother == CMG_SMOOTH_RBGS) {
+  if (h->galerkin() && l > 0) {
+    const Lev& v = h->lv[l];
+    const Lev& f0 = h->lv[0];
+    const T *a9 = nullptr, *inva = nullptr;
+    if constexpr (sizeof(T) == 8) {
+      a9 = v.a9;
+      inva = v.inva;
+    } else {
+      a9 = v.a9f;
+      inva = v.invaf;
+    }
+    if (o.smoother == CMG_SMOOTH_RBGS) {
       // Gauss-Seidel on a 9-point grid: four colours instead of two
-      const Lev& v = h->lv[l];
-      const Lev& f0 = h->lv[0];
       for (int s = 0; s < sweeps; ++s) {
         ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
-        const cudaError_t e = launch_gs4_sweep(v.n, h->prob.N, v.a9, v.m9, f0.c, f0.G, f0.d, f0.e, v.inva, v.isigma,
-                                               x, f, v.psum, h->stream);
+        const cudaError_t e = launch_gs4_sweep<T>(v.n, h->prob.N, a9, v.m9, f0.c, f0.G, f0.d, f0.e, inva, v.isigma,
+                                                  x, f, v.psum, h->stream);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    if constexpr (sizeof(T) == 4) {
+      // damped Jacobi with the 9-point diagonal entries (the FP64 cycle takes
+      // the 5-point update below, which reads the stored 1/a)
+      Vec3<T> r = Work<T>::r(h->lv[l]);
+      for (int s = 0; s < sweeps; ++s) {
+        cudaError_t e;
+        {
+          ProfScope ps(h, CMG_KERNEL_RESIDUAL, l);
+          e = level_residual<T>(h, l, cview(x), f, r);
+        }
+        if (e != cudaSuccess) return e;
+        ProfScope ps(h, CMG_KERNEL_SMOOTH, l);
+        e = launch_galerkin_jacobi<T>(v.n, h->prob.N, v.m9, f0.c, f0.d, f0.e, o.theta, inva, v.isigma, x, cview(r),
+                                      h->stream);
         if (e != cudaSuccess) return e;
       }
       return cudaSuccess;
@@ -483,11 +537,9 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
   }
   if (l == h->L - 1) {
     ProfScope ps(h, CMG_KERNEL_COARSE, l);
-    if constexpr (sizeof(T) == 8) {
-      if (h->galerkin()) {
-        const Lev& f0 = h->lv[0];
-        return launch_galerkin_coarse_solve(h->coarse, v.m9, f0.c, f0.d, f0.e, f, x, h->stream);
-      }
+    if (h->galerkin()) {
+      const Lev& f0 = h->lv[0];
+      return launch_galerkin_coarse_solve<T>(h->coarse, v.m9, f0.c, f0.d, f0.e, f, x, h->stream);
     }
     return launch_coarse_solve<T>(coarse_for<T>(h), v.c, v.d, v.e, f, x, h->stream, o.freeze_u);
   }
@@ -544,7 +596,7 @@ cudaError_t cycle(cmg_handle* h, const cmg_cycle& o, int l, Vec3<T> x, Vec3c<T> 
     return e;
   }
   if (sizeof(T) == 4 && o.smoother == CMG_SMOOTH_RBGS && o.n2 >= 1 && !o.freeze_u &&
-      !(v.spl_target[1] & kTuneUnfused)) {
+      !(v.spl_target[1] & kTuneUnfused) && !(h->galerkin() && l > 0)) {
     // FP32: prolongation fused into the first post-smoothing half-sweep
     // (colour 0); identical results, one pass over x fewer.  (In FP64 the
     // fused sweep is bound by the FP64 pipe and costs more than the pass.)
@@ -581,8 +633,10 @@ cmg_status check_cycle(cmg_handle* h, const cmg_cycle* o) {
   if (o->ctl32 != 0 && o->ctl32 != 1) return fail(h, CMG_ERR_INVALID_ARG, "ctl32 must be 0 or 1");
   if (o->smoother == CMG_SMOOTH_JACOBI && !(o->theta > 0.0 && o->theta <= 1.0))
     return fail(h, CMG_ERR_INVALID_ARG, "theta must be in (0, 1]");
-  if (h && h->galerkin() && (o->precision != CMG_FP64 || o->freeze_u))
-    return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin coarse operators: FP64 cycles, control updated");
+  if (h && h->galerkin() && o->freeze_u)
+    return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin coarse operators: the control is updated in every sweep");
+  if (h && h->galerkin() && o->precision != CMG_FP64 && o->ctl32)
+    return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin coarse operators: the control row is FP64");
   return CMG_OK;
 }
 
@@ -717,6 +771,8 @@ cmg_status cmg_create(const cmg_problem* prob, const double* xi_host, void* stre
     for (int l = 1; l < L; ++l) {
       AL(h->lv[l].a9, 9 * h->lv[l].nodes * N);
       AL(h->lv[l].psum, 2 * h->lv[l].nodes);
+      AL(h->lv[l].a9f, 9 * h->lv[l].nodes * N);
+      AL(h->lv[l].invaf, h->lv[l].nodes * N);
     }
   const size_t g = (size_t)P.n + 2;
   AL(h->kap, g * g * N + g * N);
@@ -821,8 +877,7 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!level_ok(h, level)) return fail(h, CMG_ERR_INVALID_ARG, "level out of range");                        \
     if (!vec_ok(y, u, p) || !vec_ok(ry, ru, rp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
     if ((fy || fu || fp) && !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "partial rhs");           \
-    if (sizeof(T) == 4 && h->galerkin()) return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin operators are FP64");   \
-    if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
+    CK(ensure_ops<T>(h));                                                                                       \
     CK(level_residual<T>(h, level, Vec3c<T>{y, u, p}, Vec3c<T>{fy, fu, fp}, Vec3<T>{ry, ru, rp}));             \
     return CMG_OK;                                                                                              \
   }                                                                                                             \
@@ -836,7 +891,7 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     o.n1 = o.n2 = 0; o.gamma = 1; o.precision = sizeof(T) == 8 ? CMG_FP64 : CMG_FP32;                           \
     const cmg_status st = check_cycle(h, &o);                                                                   \
     if (st != CMG_OK) return st;                                                                                \
-    if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
+    CK(ensure_ops<T>(h));                                                                                       \
     CK(smooth<T>(h, o, level, sweeps, Vec3<T>{y, u, p}, Vec3c<T>{fy, fu, fp}));                                \
     return CMG_OK;                                                                                              \
   }                                                                                                             \
@@ -862,12 +917,10 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (!vec_ok(fy, fu, fp) || !vec_ok(y, u, p)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
     const Lev& v = h->lv[h->L - 1];                                                                             \
     if (h->galerkin()) {                                                                                        \
-      if (sizeof(T) == 4) return fail(h, CMG_ERR_UNSUPPORTED, "Galerkin operators are FP64");                  \
       CK(ensure_fp64(h));                                                                                       \
       const Lev& f0 = h->lv[0];                                                                                 \
-      CK(launch_galerkin_coarse_solve(h->coarse, v.m9, f0.c, f0.d, f0.e,                                        \
-                                      Vec3c<double>{(const double*)fy, (const double*)fu, (const double*)fp},   \
-                                      Vec3<double>{(double*)y, (double*)u, (double*)p}, h->stream));            \
+      CK(launch_galerkin_coarse_solve<T>(h->coarse, v.m9, f0.c, f0.d, f0.e, Vec3c<T>{fy, fu, fp},              \
+                                         Vec3<T>{y, u, p}, h->stream));                                         \
       return CMG_OK;                                                                                            \
     }                                                                                                           \
     if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
@@ -883,7 +936,7 @@ cmg_status cmg_rhs(cmg_handle* h, const double* yd, const double* fsrc, double* 
     if (opts->precision != (sizeof(T) == 8 ? CMG_FP64 : CMG_FP32))                                              \
       return fail(h, CMG_ERR_INVALID_ARG, "precision does not match the vector type");                         \
     if (!vec_ok(y, u, p) || !vec_ok(fy, fu, fp)) return fail(h, CMG_ERR_INVALID_ARG, "null pointer");          \
-    if (sizeof(T) == 8) CK(ensure_fp64(h));                                                                     \
+    CK(ensure_ops<T>(h));                                                                                       \
     CK(cycle<T>(h, *opts, 0, Vec3<T>{y, u, p}, Vec3c<T>{fy, fu, fp}));                                          \
     return CMG_OK;                                                                                              \
   }
@@ -1019,7 +1072,7 @@ cmg_status autotune_levels(cmg_handle* h, int* chosen) {
   const int k = sizeof(T) == 8 ? 0 : 1;
   for (int l = 0; l + 1 < h->L; ++l) {
     Lev& v = h->lv[l];
-    if (sizeof(T) == 8 && h->galerkin() && l > 0) {
+    if (h->galerkin() && l > 0) {
       // Galerkin grids have no face arrays and never run the timed sweeps
       v.spl_target[k] = 0;
       if (chosen) chosen[l] = 0;
@@ -1640,7 +1693,7 @@ extern "C" cmg_status cmg_solve(cmg_handle* h, const cmg_cycle* opts, int method
     CK(cudaStreamSynchronize(h->stream));
     return CMG_OK;
   }
-  if (opts->precision == CMG_FP64) CK(ensure_fp64(h));
+  CK(opts->precision == CMG_FP64 ? ensure_fp64(h) : ensure_galerkin32(h));
   if (method == CMG_METHOD_CYCLE) return solve_cycle(h, *opts, tol, maxit, f, x, fnorm, st);
   return solve_fgmres(h, *opts, tol, maxit, restart, f, x, fnorm, st);
 }
@@ -2223,7 +2276,7 @@ extern "C" cmg_status cmg_batch_create(const cmg_problem* probs, const double* c
   *out = nullptr;
   if (!probs || !xi_host || count < 1 || count > 4096) return CMG_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i)
-    if (probs[i].coarse_coeff == CMG_COARSE_GALERKIN) return CMG_ERR_UNSUPPORTED;   // the batch runs FP32 cycles
+    if (probs[i].coarse_coeff == CMG_COARSE_GALERKIN) return CMG_ERR_UNSUPPORTED;   // the batch kernels are 5-point
   cmg_batch* b = new (std::nothrow) cmg_batch();
   if (!b) return CMG_ERR_OOM;
   b->stream = static_cast<cudaStream_t>(stream);

@@ -540,9 +540,11 @@ __global__ void galerkin_schur_inv_kernel(int n, const double* __restrict__ Q, S
 
 // One CTA, a thread per sample for the per-sample products and a thread per
 // node for the control system.  wz: [2][N][m] scratch (w_j, then y_j; z_j).
+// f and x in the cycle's precision T; the elimination itself runs in FP64.
+template <typename T>
 __global__ void galerkin_coarse_solve_kernel(int n, int N, const double* __restrict__ Ainv,
                                              const double* __restrict__ Minv, Stencil9 M, double c, double d,
-                                             double e, Vec3c<double> f, Vec3<double> x, double* __restrict__ wz) {
+                                             double e, Vec3c<T> f, Vec3<T> x, double* __restrict__ wz) {
   __shared__ double s_sum[kMaxCoarseM], s_rhs[kMaxCoarseM], s_u[kMaxCoarseM];
   const int m = n * n;
   double* W = wz;
@@ -554,10 +556,10 @@ __global__ void galerkin_coarse_solve_kernel(int n, int N, const double* __restr
     double* z = Z + (size_t)j * m;
     for (int r = 0; r < m; ++r) {
       double s = 0.0;
-      for (int k = 0; k < m; ++k) s = fma(A[r * m + k], f.p[(size_t)k * N + j], s);
+      for (int k = 0; k < m; ++k) s = fma(A[r * m + k], (double)f.p[(size_t)k * N + j], s);
       w[r] = s;
     }
-    for (int r = 0; r < m; ++r) t[r] = f.y[(size_t)r * N + j] - c * mass_apply(M, w, n, r);
+    for (int r = 0; r < m; ++r) t[r] = (double)f.y[(size_t)r * N + j] - c * mass_apply(M, w, n, r);
     for (int r = 0; r < m; ++r) {
       double s = 0.0;
       for (int k = 0; k < m; ++k) s = fma(A[r * m + k], t[k], s);
@@ -571,13 +573,13 @@ __global__ void galerkin_coarse_solve_kernel(int n, int N, const double* __restr
     s_sum[r] = s;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < m; r += blockDim.x) s_rhs[r] = f.u[r] - d * mass_apply(M, s_sum, n, r);
+  for (int r = threadIdx.x; r < m; r += blockDim.x) s_rhs[r] = (double)f.u[r] - d * mass_apply(M, s_sum, n, r);
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     double s = 0.0;
     for (int k = 0; k < m; ++k) s = fma(Minv[r * m + k], s_rhs[k], s);
     s_u[r] = s;
-    x.u[r] = s;
+    x.u[r] = (T)s;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) s_rhs[r] = mass_apply(M, s_u, n, r);   // M u
@@ -589,13 +591,13 @@ __global__ void galerkin_coarse_solve_kernel(int n, int N, const double* __restr
       double s = 0.0;
       for (int k = 0; k < m; ++k) s = fma(A[r * m + k], s_rhs[k], s);
       w[r] -= e * s;
-      x.y[(size_t)r * N + j] = w[r];
+      x.y[(size_t)r * N + j] = (T)w[r];
     }
-    for (int r = 0; r < m; ++r) t[r] = f.y[(size_t)r * N + j] - c * mass_apply(M, w, n, r);
+    for (int r = 0; r < m; ++r) t[r] = (double)f.y[(size_t)r * N + j] - c * mass_apply(M, w, n, r);
     for (int r = 0; r < m; ++r) {
       double s = 0.0;
       for (int k = 0; k < m; ++k) s = fma(A[r * m + k], t[k], s);
-      x.p[(size_t)r * N + j] = s;
+      x.p[(size_t)r * N + j] = (T)s;
     }
   }
 }
@@ -613,14 +615,20 @@ cudaError_t launch_galerkin_coarse_setup(const CoarseData& C, const double* a9, 
   return cudaGetLastError();
 }
 
+template <typename T>
 cudaError_t launch_galerkin_coarse_solve(const CoarseData& C, const Stencil9& M, double c, double d, double e,
-                                         Vec3c<double> f, Vec3<double> x, cudaStream_t s) {
+                                         Vec3c<T> f, Vec3<T> x, cudaStream_t s) {
   if (C.m > kMaxCoarseM || C.N > 1024) return cudaErrorInvalidValue;
   const int threads = std::max(32, std::min(1024, (std::max(C.N, C.m) + 31) / 32 * 32));
-  galerkin_coarse_solve_kernel<<<1, threads, 0, s>>>(C.n, C.N, C.Ainv, C.Minv, M, c, d, e, f, x, C.wz);
+  galerkin_coarse_solve_kernel<T><<<1, threads, 0, s>>>(C.n, C.N, C.Ainv, C.Minv, M, c, d, e, f, x, C.wz);
   count_launches(1);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_galerkin_coarse_solve<double>(const CoarseData&, const Stencil9&, double, double, double,
+                                                          Vec3c<double>, Vec3<double>, cudaStream_t);
+template cudaError_t launch_galerkin_coarse_solve<float>(const CoarseData&, const Stencil9&, double, double, double,
+                                                         Vec3c<float>, Vec3<float>, cudaStream_t);
 
 template cudaError_t launch_coarse_solve<double>(const CoarseData&, double, double, double, Vec3c<double>,
                                                  Vec3<double>, cudaStream_t, int);

@@ -109,16 +109,20 @@ __global__ void galerkin_diag_kernel(long nodes, int N, const double* __restrict
 
 // The three kernels of the 9-point residual run as a programmatic-dependent
 // chain: the sums over samples of p, then the control row (which also leaves
-// (M u)_i for the others), then the state and adjoint rows.
+// (M u)_i for the others), then the state and adjoint rows.  T is the
+// vectors' and the per-sample arithmetic's precision (FP64, or FP32 for the
+// FP32 cycle on FP32 copies of the planes); the sums over samples and the
+// control row stay FP64 in both.
 
-// psum[i] = sum_j p[i][j]: one warp per node, fixed-order shuffle reduction.
-__global__ void galerkin_psum_kernel(long nodes, int N, const double* __restrict__ p, double* __restrict__ psum) {
+// psum[i] = sum_j p[i][j] (FP64): one warp per node, fixed-order shuffle reduction.
+template <typename T>
+__global__ void galerkin_psum_kernel(long nodes, int N, const T* __restrict__ p, double* __restrict__ psum) {
   pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (node >= nodes) return;   // whole warp
   double s = 0.0;
-  for (int j = lane; j < N; j += 32) s += p[(size_t)node * N + j];
+  for (int j = lane; j < N; j += 32) s += (double)p[(size_t)node * N + j];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) psum[node] = s;
 }
@@ -126,9 +130,9 @@ __global__ void galerkin_psum_kernel(long nodes, int N, const double* __restrict
 // State and adjoint rows, one thread per (node, sample):
 //   r_y = f_y - (c (M y_j)_i + (A_j p_j)_i),  r_p = f_p - ((A_j y_j)_i + e (M u)_i),
 // with (M u)_i from the control-row kernel (mu).
-__global__ void residual9_yp_kernel(int n, int N, const double* __restrict__ a9, Stencil9 M, double c, double e,
-                                    const double* __restrict__ mu, Vec3c<double> x, Vec3c<double> f,
-                                    Vec3<double> r) {
+template <typename T>
+__global__ void residual9_yp_kernel(int n, int N, const T* __restrict__ a9, Stencil9 M, double c, double e,
+                                    const double* __restrict__ mu, Vec3c<T> x, Vec3c<T> f, Vec3<T> r) {
   pdl_enter();
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nodes = (size_t)n * n;
@@ -136,28 +140,29 @@ __global__ void residual9_yp_kernel(int n, int N, const double* __restrict__ a9,
   const int j = (int)(t % N);
   const long i = t / N;
   const int iy = (int)(i / n), ix = (int)(i - (long)iy * n);
-  double Ap = 0.0, Ay = 0.0, My = 0.0;
+  T Ap = 0, Ay = 0, My = 0;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int ny = iy + k / 3 - 1, nx = ix + k % 3 - 1;
     if (ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
     const size_t nb = (size_t)ny * n + nx;
-    const double a = a9[((size_t)k * nodes + i) * N + j];
-    const double yv = x.y[nb * N + j], pv = x.p[nb * N + j];
+    const T a = a9[((size_t)k * nodes + i) * N + j];
+    const T yv = x.y[nb * N + j], pv = x.p[nb * N + j];
     Ap = fma(a, pv, Ap);
     Ay = fma(a, yv, Ay);
-    My = fma(M.w[k], yv, My);
+    My = fma((T)M.w[k], yv, My);
   }
-  const double sy = c * My + Ap, sp = Ay + e * mu[i];
+  const T sy = (T)c * My + Ap, sp = Ay + (T)e * (T)mu[i];
   const size_t o = (size_t)i * N + j;
   r.y[o] = f.y ? f.y[o] - sy : sy;
   r.p[o] = f.y ? f.p[o] - sp : sp;
 }
 
-// Control row, one thread per node: r_u = f_u - (G (M u)_i + d (M sum_j p_j)_i);
+// Control row, one thread per node (FP64): r_u = f_u - (G (M u)_i + d (M sum_j p_j)_i);
 // (M u)_i is also left in mu.
+template <typename T>
 __global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stencil9 M, double G, double d,
-                                   Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* __restrict__ mu) {
+                                   Vec3c<T> x, Vec3c<T> f, Vec3<T> r, double* __restrict__ mu) {
   pdl_enter();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)n * n) return;
@@ -169,11 +174,11 @@ __global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stenc
       if (ny < 0 || ny >= n || nx < 0 || nx >= n) continue;
       const int k = (dy + 1) * 3 + (dx + 1);
       const size_t nb = (size_t)ny * n + nx;
-      Mu = fma(M.w[k], x.u[nb], Mu);
+      Mu = fma(M.w[k], (double)x.u[nb], Mu);
       Mp = fma(M.w[k], psum[nb], Mp);
     }
   const double su = G * Mu + d * Mp;
-  r.u[i] = f.y ? f.u[i] - su : su;
+  r.u[i] = f.y ? (T)((double)f.u[i] - su) : (T)su;
   mu[i] = Mu;
 }
 
@@ -189,9 +194,12 @@ __global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stenc
 // during this colour); pass 2 writes the solution and the node's new sum
 // over samples of p.  c, G, d, e: the finest grid's; the diagonal entries are
 // these times m_centre, a = (A_j)_ii; inva, isigma from galerkin_diag_kernel.
-__global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const double* __restrict__ a9, Stencil9 M, double c,
-                                  double G, double d, double e, const double* __restrict__ inva,
-                                  const double* __restrict__ isigma, Vec3<double> x, Vec3c<double> f,
+// The per-sample work is in T; B_u, the sum over samples for u (the lanes'
+// partial sums converted once), 1/sigma and u are FP64.
+template <typename T>
+__global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const T* __restrict__ a9, Stencil9 M, double c,
+                                  double G, double d, double e, const T* __restrict__ inva,
+                                  const double* __restrict__ isigma, Vec3<T> x, Vec3c<T> f,
                                   double* __restrict__ psum) {
   pdl_enter();
   const int nbx = (n - cx + 1) / 2, nby = (n - cy + 1) / 2;
@@ -202,7 +210,8 @@ __global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const double* __
   const size_t nodes = (size_t)n * n;
   const size_t i = (size_t)iy * n + ix;
   const double mc = M.w[4];
-  const double cd = c * mc, dd = d * mc, ed = e * mc;   // diagonal entries of the mass blocks
+  const T cd = (T)(c * mc), ed = (T)(e * mc);   // diagonal entries of the mass blocks
+  const double dd = d * mc;
   // the eight neighbours (unrolled, predicated: all loads of a sample issue together)
   bool ok[9];
   size_t nbr[9];
@@ -214,50 +223,87 @@ __global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const double* __
   }
   double Bu = 0.0;
   if (lane == 0) {
-    double s = f.u[i];
+    double s = (double)f.u[i];
 #pragma unroll
     for (int k = 0; k < 9; ++k)
-      if (ok[k]) s -= M.w[k] * (G * x.u[nbr[k]] + d * psum[nbr[k]]);
+      if (ok[k]) s -= M.w[k] * (G * (double)x.u[nbr[k]] + d * psum[nbr[k]]);
     Bu = s;
   }
   double eMu = 0.0;   // e (M u)_i off the centre: the same for every sample
 #pragma unroll
   for (int k = 0; k < 9; ++k)
-    if (ok[k]) eMu += e * M.w[k] * x.u[nbr[k]];
-  double tacc = 0.0;
+    if (ok[k]) eMu += e * M.w[k] * (double)x.u[nbr[k]];
+  const T eMuT = (T)eMu, cT = (T)c;
+  T tacc = 0;
   for (int j = lane; j < N; j += 32) {
-    double By = f.y[i * N + j], Bp = f.p[i * N + j] - eMu;
+    T By = f.y[i * N + j], Bp = f.p[i * N + j] - eMuT;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       if (!ok[k]) continue;
-      const double a = a9[((size_t)k * nodes + i) * N + j];
-      const double yv = x.y[nbr[k] * N + j], pv = x.p[nbr[k] * N + j];
-      By -= c * M.w[k] * yv + a * pv;
+      const T a = a9[((size_t)k * nodes + i) * N + j];
+      const T yv = x.y[nbr[k] * N + j], pv = x.p[nbr[k] * N + j];
+      By -= cT * (T)M.w[k] * yv + a * pv;
       Bp -= a * yv;
     }
-    const double ia = inva[i * N + j];
+    const T ia = inva[i * N + j];
     tacc += (cd * ia) * (ia * Bp) - ia * By;
     x.y[i * N + j] = Bp;   // parked until pass 2
     x.p[i * N + j] = By;
   }
-  for (int o = 16; o > 0; o >>= 1) tacc += __shfl_xor_sync(0xffffffffu, tacc, o);
+  double ts = (double)tacc;
+  for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
   Bu = __shfl_sync(0xffffffffu, Bu, 0);
-  const double u = (Bu + dd * tacc) * isigma[i];
+  const double u = (Bu + dd * ts) * isigma[i];
+  const T uT = (T)u;
   double ps = 0.0;
   for (int j = lane; j < N; j += 32) {
-    const double ia = inva[i * N + j];
-    const double Bp = x.y[i * N + j], By = x.p[i * N + j];
-    const double y = ia * (Bp - ed * u);
-    const double p = ia * (By - cd * y);
+    const T ia = inva[i * N + j];
+    const T Bp = x.y[i * N + j], By = x.p[i * N + j];
+    const T y = ia * (Bp - ed * uT);
+    const T p = ia * (By - cd * y);
     x.y[i * N + j] = y;
     x.p[i * N + j] = p;
-    ps += p;
+    ps += (double)p;
   }
   for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
   if (lane == 0) {
-    x.u[i] = u;
+    x.u[i] = uT;
     psum[i] = ps;
   }
+}
+
+// Damped collective Jacobi on a 9-point grid: x_i += theta S~_i^{-1} r_i with
+// S~_i the node's block with the Galerkin diagonal entries (Eq. (11), Eq. (13)
+// on the residual).  One warp per node, lanes over samples; per-sample work
+// in T, the sum over samples and the u correction in FP64.
+template <typename T>
+__global__ void galerkin_jacobi_kernel(long nodes, int N, Stencil9 M, double c, double d, double e, double theta,
+                                       const T* __restrict__ inva, const double* __restrict__ isigma, Vec3<T> x,
+                                       Vec3c<T> r) {
+  pdl_enter();
+  const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= nodes) return;   // whole warp
+  const double mc = M.w[4];
+  const T cd = (T)(c * mc), ed = (T)(e * mc);
+  T tacc = 0;
+  for (int j = lane; j < N; j += 32) {
+    const T ia = inva[(size_t)i * N + j];
+    tacc += (cd * ia) * (ia * r.p[(size_t)i * N + j]) - ia * r.y[(size_t)i * N + j];
+  }
+  double ts = (double)tacc;
+  for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+  const double du = ((double)r.u[i] + d * mc * ts) * isigma[i];
+  const T duT = (T)du, th = (T)theta;
+  for (int j = lane; j < N; j += 32) {
+    const size_t o = (size_t)i * N + j;
+    const T ia = inva[o];
+    const T dy = ia * (r.p[o] - ed * duT);
+    const T dp = ia * (r.y[o] - cd * dy);
+    x.y[o] += th * dy;
+    x.p[o] += th * dp;
+  }
+  if (lane == 0) x.u[i] += (T)(theta * du);
 }
 
 unsigned blocks_for(long threads) { return (unsigned)((threads + kGBlock - 1) / kGBlock); }
@@ -303,36 +349,63 @@ cudaError_t launch_galerkin_diag(int n, int N, const double* a9, double* inva, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
-                             double e, Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* psum,
-                             cudaStream_t s) {
+template <typename T>
+cudaError_t launch_residual9(int n, int N, const T* a9, const Stencil9& M, double c, double G, double d, double e,
+                             Vec3c<T> x, Vec3c<T> f, Vec3<T> r, double* psum, cudaStream_t s) {
   const long nodes = (long)n * n;
   double* mu = psum + nodes;
-  cudaError_t err = launch_k(galerkin_psum_kernel, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N, x.p, psum);
+  cudaError_t err = launch_k(galerkin_psum_kernel<T>, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N, x.p, psum);
   if (err == cudaSuccess)
-    err = launch_k(residual9_u_kernel, blocks_for(nodes), kGBlock, 0, s, n, (const double*)psum, M, G, d, x, f, r, mu);
+    err = launch_k(residual9_u_kernel<T>, blocks_for(nodes), kGBlock, 0, s, n, (const double*)psum, M, G, d, x, f, r,
+                   mu);
   if (err == cudaSuccess)
-    err = launch_k(residual9_yp_kernel, blocks_for(nodes * N), kGBlock, 0, s, n, N, a9, M, c, e, (const double*)mu,
-                   x, f, r);
+    err = launch_k(residual9_yp_kernel<T>, blocks_for(nodes * N), kGBlock, 0, s, n, N, a9, M, c, e,
+                   (const double*)mu, x, f, r);
   count_launches(3);
   return err != cudaSuccess ? err : cudaGetLastError();
 }
 
-cudaError_t launch_gs4_sweep(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
-                             double e, const double* inva, const double* isigma, Vec3<double> x, Vec3c<double> f,
-                             double* psum, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_gs4_sweep(int n, int N, const T* a9, const Stencil9& M, double c, double G, double d, double e,
+                             const T* inva, const double* isigma, Vec3<T> x, Vec3c<T> f, double* psum,
+                             cudaStream_t s) {
   const long nodes = (long)n * n;
-  cudaError_t err = launch_k(galerkin_psum_kernel, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N,
-                             (const double*)x.p, psum);
+  cudaError_t err = launch_k(galerkin_psum_kernel<T>, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N,
+                             (const T*)x.p, psum);
   for (int col = 0; col < 4 && err == cudaSuccess; ++col) {
     const int cy = col >> 1, cx = col & 1;
     const long groups = (long)((n - cx + 1) / 2) * ((n - cy + 1) / 2);
     if (groups == 0) continue;
-    err = launch_k(gs4_colour_kernel, blocks_for(groups * 32), kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva,
-                   isigma, x, f, psum);
+    err = launch_k(gs4_colour_kernel<T>, blocks_for(groups * 32), kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e,
+                   inva, isigma, x, f, psum);
   }
   count_launches(5);
   return err != cudaSuccess ? err : cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_galerkin_jacobi(int n, int N, const Stencil9& M, double c, double d, double e, double theta,
+                                   const T* inva, const double* isigma, Vec3<T> x, Vec3c<T> r, cudaStream_t s) {
+  const long nodes = (long)n * n;
+  const cudaError_t err = launch_k(galerkin_jacobi_kernel<T>, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N, M, c,
+                                   d, e, theta, inva, isigma, x, r);
+  count_launches(1);
+  return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+template cudaError_t launch_residual9<double>(int, int, const double*, const Stencil9&, double, double, double,
+                                              double, Vec3c<double>, Vec3c<double>, Vec3<double>, double*,
+                                              cudaStream_t);
+template cudaError_t launch_residual9<float>(int, int, const float*, const Stencil9&, double, double, double, double,
+                                             Vec3c<float>, Vec3c<float>, Vec3<float>, double*, cudaStream_t);
+template cudaError_t launch_gs4_sweep<double>(int, int, const double*, const Stencil9&, double, double, double,
+                                              double, const double*, const double*, Vec3<double>, Vec3c<double>,
+                                              double*, cudaStream_t);
+template cudaError_t launch_gs4_sweep<float>(int, int, const float*, const Stencil9&, double, double, double, double,
+                                             const float*, const double*, Vec3<float>, Vec3c<float>, double*,
+                                             cudaStream_t);
+template cudaError_t launch_galerkin_jacobi<float>(int, int, const Stencil9&, double, double, double, double,
+                                                   const float*, const double*, Vec3<float>, Vec3c<float>,
+                                                   cudaStream_t);
 
 }  // namespace cmg

@@ -470,24 +470,35 @@ cudaError_t launch_galerkin_setup(int nf, int N, const double* kx, const double*
 cudaError_t launch_galerkin_diag(int n, int N, const double* a9, double* inva, double* isigma, double dce, double G,
                                  cudaStream_t s);
 // r = f - S_l x (r = S_l x when f.y == nullptr) with 9-point blocks; psum:
-// scratch [2 n*n] (the sums over samples of x.p, then (M u)_i).
-cudaError_t launch_residual9(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
-                             double e, Vec3c<double> x, Vec3c<double> f, Vec3<double> r, double* psum,
-                             cudaStream_t s);
+// scratch [2 n*n] FP64 (the sums over samples of x.p, then (M u)_i).  T =
+// double, or float for the FP32 cycle on FP32 copies of the planes (the
+// control row and the sums over samples stay FP64).
+template <typename T>
+cudaError_t launch_residual9(int n, int N, const T* a9, const Stencil9& M, double c, double G, double d, double e,
+                             Vec3c<T> x, Vec3c<T> f, Vec3<T> r, double* psum, cudaStream_t s);
 // One collective Gauss-Seidel sweep in four colours (iy mod 2, ix mod 2) on
 // a 9-point grid (Eq. (13) per node with the Galerkin diagonal entries);
 // psum: scratch [n*n] (sums over samples of p, kept current by the sweep).
-cudaError_t launch_gs4_sweep(int n, int N, const double* a9, const Stencil9& M, double c, double G, double d,
-                             double e, const double* inva, const double* isigma, Vec3<double> x, Vec3c<double> f,
-                             double* psum, cudaStream_t s);
+// FP32: per-sample work in FP32, the Schur scalar of Eq. (13) in FP64.
+template <typename T>
+cudaError_t launch_gs4_sweep(int n, int N, const T* a9, const Stencil9& M, double c, double G, double d, double e,
+                             const T* inva, const double* isigma, Vec3<T> x, Vec3c<T> f, double* psum,
+                             cudaStream_t s);
+// Damped collective Jacobi update x += theta S~^{-1} r on a 9-point grid
+// (FP32; the FP64 cycle uses the 5-point update with the stored 1/a).
+template <typename T>
+cudaError_t launch_galerkin_jacobi(int n, int N, const Stencil9& M, double c, double d, double e, double theta,
+                                   const T* inva, const double* isigma, Vec3<T> x, Vec3c<T> r, cudaStream_t s);
 // Coarsest grid: A_j^{-1} per sample from the 9-point stencil, and the
 // inverse of the control Schur matrix G M + d c e M (sum_j A_j^{-1} M A_j^{-1}) M.
 cudaError_t launch_galerkin_coarse_setup(const CoarseData& C, const double* a9, const Stencil9& M, double c,
                                          double G, double d, double e, cudaStream_t s);
 // x = S_L^{-1} f on the coarsest grid by block elimination with the
-// non-diagonal mass (x and f must not overlap).
+// non-diagonal mass (x and f must not overlap), in FP64 whatever T (the
+// cycle's precision) f and x are stored in.
+template <typename T>
 cudaError_t launch_galerkin_coarse_solve(const CoarseData& C, const Stencil9& M, double c, double d, double e,
-                                         Vec3c<double> f, Vec3<double> x, cudaStream_t s);
+                                         Vec3c<T> f, Vec3<T> x, cudaStream_t s);
 
 // ---- warm-start network kernels (cmg_nn_*.cu) ----
 // mean over samples of log kappa_j at the n x n interior nodes of the finest grid.

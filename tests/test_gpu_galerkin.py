@@ -183,19 +183,18 @@ def test_converged_solution(case, method, smoother):
 
 
 def test_unsupported_combinations_are_refused(P):
+    """A frozen control (the 9-point sweeps update u in every colour) and the
+    FP32 control row (the Galerkin control row sums in FP64) are refused."""
     xi = inputs.draw_xi(7, 4, 3)
     H = P.Hierarchy(15, 4, xi, 1e-3, 0.8, coarse="galerkin")
     try:
         f = H.zeros(0)
-        for o in (P.CycleOptions(smoother=P.SMOOTH_RBGS, precision=P.FP32),
-                  P.CycleOptions(smoother=P.SMOOTH_JACOBI, precision=P.FP32),
+        for o in (P.CycleOptions(smoother=P.SMOOTH_RBGS, precision=P.FP32, ctl32=1),
+                  P.CycleOptions(smoother=P.SMOOTH_JACOBI, precision=P.FP32, freeze_u=1),
                   P.CycleOptions(smoother=P.SMOOTH_JACOBI, precision=P.FP64, freeze_u=1)):
             with pytest.raises(P.CMGError) as ei:
                 H.solve(o, f, H.zeros(0))
             assert ei.value.status == 7
-        with pytest.raises(P.CMGError) as ei:
-            H.residual(1, H.zeros(1, torch.float32), H.zeros(1, torch.float32), H.zeros(1, torch.float32))
-        assert ei.value.status == 7
     finally:
         H.close()
     with pytest.raises(P.CMGError):
@@ -216,5 +215,136 @@ def test_fp64_autotune_skips_galerkin_grids(P):
         x = H.zeros(0)
         st, _ = H.solve(jacobi(), dev(f, 15, 5), x, tol=1e-12, maxit=100)
         assert_blocks(host(x), spla.spsolve(S[0].tocsc(), f), 15, 5, 1e-7, "solution after autotune")
+    finally:
+        H.close()
+
+
+# ---- FP32 cycles on the Galerkin grids ----------------------------------
+# The per-sample arithmetic runs in FP32 on FP32 copies of the FP64 Galerkin
+# planes; the control row's sums over samples, Eq. (13)'s Schur scalar and
+# the coarsest elimination stay FP64.  Inputs are FP32-representable, the
+# oracle FP64; errors relative to each block's largest entry.  Measured
+# maxima over these cases: apply 1.6e-7 (FP32 planes, 9-term sums), one
+# sweep 3.7e-7, the coarsest solve 5.7e-8 (FP64 elimination, FP32 results),
+# one V-cycle from a random iterate 2.0e-5 (the cycle shrinks the iterate's
+# rough part, so the rounding of the input is large against the output);
+# the bars leave a factor of 5 or more.  FP64 refinement around FP32 cycles
+# to 1e-11 lands where FP64 cycles do (1.5e-8 from the sparse direct
+# solution at worst, the control block's sensitivity): bar 1e-7.
+RES32, SWEEP32, COARSE32, CYCLE32 = 1e-6, 2e-6, 3e-7, 1e-4
+
+
+def f32(z):
+    return np.asarray(z, dtype=np.float32).astype(np.float64)
+
+
+def dev32(z, n, N):
+    return tuple(t.float() for t in dev(z, n, N))
+
+
+def opts32(smoother="jacobi", gamma=1):
+    import paper_2302_13680_gb300 as P
+
+    o = opts(smoother, gamma)
+    o.precision = P.FP32
+    return o
+
+
+def test_fp32_residual_every_level(case):
+    H, levels, S = case
+    N = levels[0].N
+    rng = np.random.default_rng(31)
+    for l, lv in enumerate(levels):
+        dim = S[l].shape[0]
+        z, f = f32(rng.standard_normal(dim)), f32(rng.standard_normal(dim))
+        r = H.zeros(l, torch.float32)
+        H.residual(l, dev32(z, lv.n, N), dev32(f, lv.n, N), r)
+        assert_blocks(host(r), f - S[l] @ z, lv.n, N, RES32, f"FP32 residual level {l}")
+        H.residual(l, dev32(z, lv.n, N), None, r)
+        assert_blocks(host(r), S[l] @ z, lv.n, N, RES32, f"FP32 apply level {l}")
+
+
+@pytest.mark.parametrize("smoother", SMOOTHERS)
+def test_fp32_one_sweep_every_grid(case, smoother):
+    H, levels, S = case
+    ns = [lv.n for lv in levels]
+    N = levels[0].N
+    fine = levels[0]
+    rng = np.random.default_rng(32)
+    for l, lv in enumerate(levels[:-1]):
+        m = lv.n * lv.n
+        z = f32(rng.standard_normal(S[l].shape[0]))
+        f = rng.standard_normal(S[l].shape[0])
+        f[: m * N] *= fine.c
+        f[m * N: m * N + m] *= fine.G
+        f[m * N + m:] *= fine.h ** 2
+        f = f32(f)
+        x = dev32(z, lv.n, N)
+        H.smooth(l, opts32(smoother), 1, x, dev32(f, lv.n, N))
+        ref = G.smooth(S, ns, N, l, z, f, smoother, 0.5)
+        assert_blocks(host(x), ref, lv.n, N, SWEEP32, f"FP32 {smoother} level {l}")
+
+
+def test_fp32_coarse_solve(case):
+    H, levels, S = case
+    N = levels[0].N
+    lv = levels[-1]
+    f = f32(np.random.default_rng(33).standard_normal(S[-1].shape[0]))
+    x = H.zeros(len(levels) - 1, torch.float32)
+    H.coarse_solve(dev32(f, lv.n, N), x)
+    assert_blocks(host(x), spla.spsolve(S[-1].tocsc(), f), lv.n, N, COARSE32, "FP32 coarse solve")
+
+
+@pytest.mark.parametrize("smoother", SMOOTHERS)
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_fp32_cycle_iterate(case, gamma, smoother):
+    H, levels, S = case
+    N, n = levels[0].N, levels[0].n
+    ns = [lv.n for lv in levels]
+    rng = np.random.default_rng(34)
+    z = f32(rng.standard_normal(S[0].shape[0]))
+    f = f32(O.pack(O.fine_rhs(levels[0], inputs.target_sinsin(n))))
+    x = dev32(z, n, N)
+    H.cycle(opts32(smoother, gamma), x, dev32(f, n, N))
+    ref = G.cycle(S, ns, N, 0, z, f, n1=2, n2=2, theta=0.5, gamma=gamma, smoother=smoother)
+    assert_blocks(host(x), ref, n, N, CYCLE32, "FP32 cycle")
+
+
+@pytest.mark.parametrize("smoother", SMOOTHERS)
+@pytest.mark.parametrize("method", ["cycle", "fgmres"])
+def test_fp32_refined_solution(case, method, smoother):
+    """FP64 refinement around FP32 cycles (stationary, or FGMRES with the
+    FP32 cycle as preconditioner) to 1e-11: the sparse direct solution, in
+    as many cycles (within one) as FP64 cycles take."""
+    H, levels, S = case
+    import paper_2302_13680_gb300 as P
+
+    N, n = levels[0].N, levels[0].n
+    f = O.pack(O.fine_rhs(levels[0], inputs.target_sinsin(n)))
+    x = H.zeros(0)
+    m = P.METHOD_CYCLE if method == "cycle" else P.METHOD_FGMRES
+    st, _ = H.solve(opts32(smoother), dev(f, n, N), x, method=m, tol=1e-11, maxit=200, restart=30)
+    assert st.relres <= 1e-11
+    st64, _ = H.solve(opts(smoother), dev(f, n, N), H.zeros(0), method=m, tol=1e-11, maxit=200, restart=30)
+    assert abs(st.cycles - st64.cycles) <= 1
+    assert_blocks(host(x), spla.spsolve(S[0].tocsc(), f), n, N, 1e-7, f"FP32-refined {method} solution")
+
+
+def test_fp32_autotune_skips_galerkin_grids(P):
+    """The FP32 autotuner times red-black half-sweeps of the 5-point grids:
+    the Galerkin grids are left at the size heuristic, and FP32-refined
+    solves after it converge."""
+    xi = inputs.draw_xi(7, 8, 3)
+    H = P.Hierarchy(31, 8, xi, 1e-4, 0.8, coarse="galerkin")
+    try:
+        chosen = H.autotune(P.FP32)
+        assert chosen[0] != 0 and all(t == 0 for t in chosen[1:])
+        levels = O.make_hierarchy(31, 8, 1e-4, O.sine_mode_field(xi, 0.8))
+        S = G.hierarchy(levels)
+        f = O.pack(O.fine_rhs(levels[0], inputs.target_sinsin(31)))
+        x = H.zeros(0)
+        st, _ = H.solve(opts32("gs"), dev(f, 31, 8), x, tol=1e-11, maxit=200)
+        assert st.relres <= 1e-11
+        assert_blocks(host(x), spla.spsolve(S[0].tocsc(), f), 31, 8, 1e-7, "FP32 solution after autotune")
     finally:
         H.close()
