@@ -16,6 +16,10 @@ namespace cmg {
 namespace {
 
 constexpr int kGBlock = 256;
+// grids up to this side take the one-launch residual (FP32, FP64: the
+// one-launch form's extra FMAs per node-sample cost more in the FP64 pipe)
+constexpr int kResidual9OnePass32 = 63, kResidual9OnePass64 = 31;
+constexpr int kGsMaxR = 8;   // four-colour sweep: samples per lane held in registers (N <= 256)
 
 // The coarse nodes that a fine node 2C+1+g (one axis, g in [-2, 2]) takes
 // its bilinear interpolant from, as offsets from C, with their weights: g
@@ -107,14 +111,24 @@ __global__ void galerkin_diag_kernel(long nodes, int N, const double* __restrict
   if (lane == 0) isigma[node] = 1.0 / (G + dce * s);
 }
 
-// The three kernels of the 9-point residual run as a programmatic-dependent
-// chain: the sums over samples of p, then the control row (which also leaves
-// (M u)_i for the others), then the state and adjoint rows.  T is the
-// vectors' and the per-sample arithmetic's precision (FP64, or FP32 for the
-// FP32 cycle on FP32 copies of the planes); the sums over samples and the
-// control row stay FP64 in both.
+// T is the vectors' and the per-sample arithmetic's precision (FP64, or
+// FP32 for the FP32 cycle on FP32 copies of the planes); the sums over
+// samples and the control row are FP64 in both (for FP32: the lanes' partial
+// sums over their own samples in FP32, converted once).
 
-// psum[i] = sum_j p[i][j] (FP64): one warp per node, fixed-order shuffle reduction.
+// The neighbours of node (iy, ix) in stencil order k = (dy+1)*3 + (dx+1);
+// ok[k] false off the grid (Dirichlet: no entry), nb[k] then the node itself.
+__device__ __forceinline__ void nine_neighbours(int n, int iy, int ix, bool* ok, int* nb) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ny = iy + k / 3 - 1, nx = ix + k % 3 - 1;
+    ok[k] = ny >= 0 && ny < n && nx >= 0 && nx < n;
+    nb[k] = ok[k] ? ny * n + nx : iy * n + ix;
+  }
+}
+
+// psum[i] = sum_j p[i][j] (FP64): one warp per node, fixed-order shuffle
+// reduction (the four-colour sweep for N above 32 kGsMaxR samples).
 template <typename T>
 __global__ void galerkin_psum_kernel(long nodes, int N, const T* __restrict__ p, double* __restrict__ psum) {
   pdl_enter();
@@ -127,6 +141,10 @@ __global__ void galerkin_psum_kernel(long nodes, int N, const T* __restrict__ p,
   if (lane == 0) psum[node] = s;
 }
 
+// Large grids: the residual as three launches in a programmatic-dependent
+// chain (the per-node sums of p; the control row, which leaves (M u)_i in
+// mu; the state and adjoint rows), one thread per (node, sample) for the
+// last, whose FP64 pipe (27 FMAs per node-sample) sets the time there.
 // State and adjoint rows, one thread per (node, sample):
 //   r_y = f_y - (c (M y_j)_i + (A_j p_j)_i),  r_p = f_p - ((A_j y_j)_i + e (M u)_i),
 // with (M u)_i from the control-row kernel (mu).
@@ -180,6 +198,60 @@ __global__ void residual9_u_kernel(int n, const double* __restrict__ psum, Stenc
   const double su = G * Mu + d * Mp;
   r.u[i] = f.y ? (T)((double)f.u[i] - su) : (T)su;
   mu[i] = Mu;
+}
+
+// Small grids (launch-bound): the 9-point residual in one pass, one warp
+// per node, lanes over samples:
+//   r_y = f_y - (c (M y_j)_i + (A_j p_j)_i),
+//   r_p = f_p - ((A_j y_j)_i + e (M u)_i),
+//   r_u = f_u - (G (M u)_i + d sum_j (M p_j)_i).
+// (M u)_i in FP64 by every lane (the same nine loads); the control row's
+// sum over samples is formed from the p values the state rows load.
+// r = S x when f.y == nullptr.
+template <typename T>
+__global__ void residual9_kernel(int n, int N, const T* __restrict__ a9, Stencil9 M, double c, double G, double d,
+                                 double e, Vec3c<T> x, Vec3c<T> f, Vec3<T> r) {
+  pdl_enter();
+  const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const size_t nodes = (size_t)n * n;
+  if (i >= (long)nodes) return;   // whole warp
+  const int iy = (int)(i / n), ix = (int)(i - (long)iy * n);
+  bool ok[9];
+  int nb[9];
+  nine_neighbours(n, iy, ix, ok, nb);
+  double Mu = 0.0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    if (ok[k]) Mu = fma(M.w[k], (double)x.u[nb[k]], Mu);
+  const T eMu = (T)(e * Mu), cT = (T)c;
+  T pm = 0;   // this lane's share of sum_j (M p_j)_i
+#pragma unroll 1
+  for (int j = lane; j < N; j += 32) {
+    T Ap = 0, Ay = 0, My = 0, Mp = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      if (!ok[k]) continue;
+      const T a = a9[((size_t)k * nodes + i) * N + j];
+      const T yv = x.y[(size_t)nb[k] * N + j], pv = x.p[(size_t)nb[k] * N + j];
+      const T m = (T)M.w[k];
+      Ap = fma(a, pv, Ap);
+      Ay = fma(a, yv, Ay);
+      My = fma(m, yv, My);
+      Mp = fma(m, pv, Mp);
+    }
+    const T sy = cT * My + Ap, sp = Ay + eMu;
+    const size_t o = (size_t)i * N + j;
+    r.y[o] = f.y ? f.y[o] - sy : sy;
+    r.p[o] = f.y ? f.p[o] - sp : sp;
+    pm += Mp;
+  }
+  double ps = (double)pm;
+  for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
+  if (lane == 0) {
+    const double su = G * Mu + d * ps;
+    r.u[i] = f.y ? (T)((double)f.u[i] - su) : (T)su;
+  }
 }
 
 // Collective Gauss-Seidel on a 9-point grid, one colour (iy mod 2, ix mod 2)
@@ -272,6 +344,83 @@ __global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const T* __restr
   }
 }
 
+// The same colour sweep with each lane's samples (j = lane + 32 q, q < R,
+// N <= 32 R) held in registers between the two passes, and the control
+// row's sum over samples of the neighbours' (M p_j) formed from the p values
+// the state rows load (no per-node sums kept between launches):
+//   B_u = f_u - G (M u)_i - d sum_j (M p_j)_i   (off-centre entries, FP64).
+template <typename T, int R>
+__global__ void __launch_bounds__(kGBlock) gs4_colour_reg_kernel(int n, int N, int cy, int cx,
+                                                                 const T* __restrict__ a9, Stencil9 M, double c,
+                                                                 double G, double d, double e,
+                                                                 const T* __restrict__ inva,
+                                                                 const double* __restrict__ isigma, Vec3<T> x,
+                                                                 Vec3c<T> f) {
+  pdl_enter();
+  const int nbx = (n - cx + 1) / 2, nby = (n - cy + 1) / 2;
+  const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= (long)nbx * nby) return;   // whole warp
+  const int iy = cy + 2 * (int)(g / nbx), ix = cx + 2 * (int)(g % nbx);
+  const size_t nodes = (size_t)n * n;
+  const size_t i = (size_t)iy * n + ix;
+  const double mc = M.w[4];
+  const T cd = (T)(c * mc), ed = (T)(e * mc);   // diagonal entries of the mass blocks
+  bool ok[9];
+  int nb[9];
+  nine_neighbours(n, iy, ix, ok, nb);
+  ok[4] = false;
+  double Mu = 0.0;   // off-centre (M u)_i
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    if (ok[k]) Mu = fma(M.w[k], (double)x.u[nb[k]], Mu);
+  const T eMu = (T)(e * Mu), cT = (T)c;
+  T By[R], Bp[R], ia[R];
+  T tacc = 0, pm = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int j = lane + 32 * q;
+    By[q] = Bp[q] = ia[q] = 0;
+    if (j < N) {
+      T by = f.y[i * N + j], bp = f.p[i * N + j] - eMu, mp = 0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        if (!ok[k]) continue;
+        const T a = a9[((size_t)k * nodes + i) * N + j];
+        const T yv = x.y[(size_t)nb[k] * N + j], pv = x.p[(size_t)nb[k] * N + j];
+        const T m = (T)M.w[k];
+        by -= cT * m * yv + a * pv;
+        bp -= a * yv;
+        mp = fma(m, pv, mp);
+      }
+      const T iq = inva[i * N + j];
+      tacc += (cd * iq) * (iq * bp) - iq * by;
+      pm += mp;
+      By[q] = by;
+      Bp[q] = bp;
+      ia[q] = iq;
+    }
+  }
+  double ts = (double)tacc, ps = (double)pm;
+  for (int o = 16; o > 0; o >>= 1) {
+    ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    ps += __shfl_xor_sync(0xffffffffu, ps, o);
+  }
+  const double Bu = (double)f.u[i] - G * Mu - d * ps;
+  const double u = (Bu + d * mc * ts) * isigma[i];
+  const T uT = (T)u;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int j = lane + 32 * q;
+    if (j < N) {
+      const T y = ia[q] * (Bp[q] - ed * uT);
+      x.y[i * N + j] = y;
+      x.p[i * N + j] = ia[q] * (By[q] - cd * y);
+    }
+  }
+  if (lane == 0) x.u[i] = uT;
+}
+
 // Damped collective Jacobi on a 9-point grid: x_i += theta S~_i^{-1} r_i with
 // S~_i the node's block with the Galerkin diagonal entries (Eq. (11), Eq. (13)
 // on the residual).  One warp per node, lanes over samples; per-sample work
@@ -353,6 +502,12 @@ template <typename T>
 cudaError_t launch_residual9(int n, int N, const T* a9, const Stencil9& M, double c, double G, double d, double e,
                              Vec3c<T> x, Vec3c<T> f, Vec3<T> r, double* psum, cudaStream_t s) {
   const long nodes = (long)n * n;
+  if (n <= (sizeof(T) == 4 ? kResidual9OnePass32 : kResidual9OnePass64)) {
+    const cudaError_t err =
+        launch_k(residual9_kernel<T>, blocks_for(nodes * 32), kGBlock, 0, s, n, N, a9, M, c, G, d, e, x, f, r);
+    count_launches(1);
+    return err != cudaSuccess ? err : cudaGetLastError();
+  }
   double* mu = psum + nodes;
   cudaError_t err = launch_k(galerkin_psum_kernel<T>, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N, x.p, psum);
   if (err == cudaSuccess)
@@ -370,6 +525,33 @@ cudaError_t launch_gs4_sweep(int n, int N, const T* a9, const Stencil9& M, doubl
                              const T* inva, const double* isigma, Vec3<T> x, Vec3c<T> f, double* psum,
                              cudaStream_t s) {
   const long nodes = (long)n * n;
+  if (N <= 32 * kGsMaxR) {
+    // samples in registers: four launches, nothing kept between them
+    const int R = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : 8;
+    cudaError_t err = cudaSuccess;
+    for (int col = 0; col < 4 && err == cudaSuccess; ++col) {
+      const int cy = col >> 1, cx = col & 1;
+      const long groups = (long)((n - cx + 1) / 2) * ((n - cy + 1) / 2);
+      if (groups == 0) continue;
+      const unsigned grid = blocks_for(groups * 32);
+      if (R == 1)
+        err = launch_k(gs4_colour_reg_kernel<T, 1>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
+                       x, f);
+      else if (R == 2)
+        err = launch_k(gs4_colour_reg_kernel<T, 2>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
+                       x, f);
+      else if (R == 4)
+        err = launch_k(gs4_colour_reg_kernel<T, 4>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
+                       x, f);
+      else
+        err = launch_k(gs4_colour_reg_kernel<T, 8>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
+                       x, f);
+    }
+    count_launches(4);
+    return err != cudaSuccess ? err : cudaGetLastError();
+  }
+  // more samples: park the local right sides in x between the two passes,
+  // with the per-node sums over samples of p in psum
   cudaError_t err = launch_k(galerkin_psum_kernel<T>, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N,
                              (const T*)x.p, psum);
   for (int col = 0; col < 4 && err == cudaSuccess; ++col) {

@@ -469,16 +469,18 @@ cudaError_t launch_galerkin_setup(int nf, int N, const double* kx, const double*
 // denominator of Eq. (13) with the diagonal entries of the blocks).
 cudaError_t launch_galerkin_diag(int n, int N, const double* a9, double* inva, double* isigma, double dce, double G,
                                  cudaStream_t s);
-// r = f - S_l x (r = S_l x when f.y == nullptr) with 9-point blocks; psum:
-// scratch [2 n*n] FP64 (the sums over samples of x.p, then (M u)_i).  T =
-// double, or float for the FP32 cycle on FP32 copies of the planes (the
-// control row and the sums over samples stay FP64).
+// r = f - S_l x (r = S_l x when f.y == nullptr) with 9-point blocks: one
+// launch on small grids; on larger ones three, with psum (scratch [2 n*n]
+// FP64) holding the sums over samples of x.p, then (M u)_i.  T = double, or
+// float for the FP32 cycle on FP32 copies of the planes (the control row
+// and the sums over samples stay FP64).
 template <typename T>
 cudaError_t launch_residual9(int n, int N, const T* a9, const Stencil9& M, double c, double G, double d, double e,
                              Vec3c<T> x, Vec3c<T> f, Vec3<T> r, double* psum, cudaStream_t s);
 // One collective Gauss-Seidel sweep in four colours (iy mod 2, ix mod 2) on
-// a 9-point grid (Eq. (13) per node with the Galerkin diagonal entries);
-// psum: scratch [n*n] (sums over samples of p, kept current by the sweep).
+// a 9-point grid (Eq. (13) per node with the Galerkin diagonal entries):
+// four launches for N <= 256; above, psum (scratch [n*n], the sums over
+// samples of p) is filled first and kept current by the sweep.
 // FP32: per-sample work in FP32, the Schur scalar of Eq. (13) in FP64.
 template <typename T>
 cudaError_t launch_gs4_sweep(int n, int N, const T* a9, const Stencil9& M, double c, double G, double d, double e,

@@ -348,3 +348,68 @@ def test_fp32_autotune_skips_galerkin_grids(P):
         assert_blocks(host(x), spla.spsolve(S[0].tocsc(), f), 31, 8, 1e-7, "FP32 solution after autotune")
     finally:
         H.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_residual_large_grid(P, dtype):
+    """The residual on a 9-point grid above the one-launch size (n = 127 below
+    n = 255: the three-launch form with the per-node sums of p) and on the
+    grids below it, in FP64 and FP32, against the sparse Galerkin product."""
+    n, N = 255, 4
+    xi = inputs.draw_xi(13, N, 3)
+    H = P.Hierarchy(n, N, xi, 1e-4, 0.8, coarse="galerkin")
+    try:
+        levels = O.make_hierarchy(n, N, 1e-4, O.sine_mode_field(xi, 0.8))
+        S = G.hierarchy(levels)
+        rng = np.random.default_rng(35)
+        tol = 1e-12 if dtype == torch.float64 else RES32
+        for l in (1, 2):
+            lv = levels[l]
+            dim = S[l].shape[0]
+            z, f = f32(rng.standard_normal(dim)), f32(rng.standard_normal(dim))
+            cast = (lambda v: v) if dtype == torch.float64 else (lambda v: tuple(t.float() for t in v))
+            r = H.zeros(l, dtype)
+            H.residual(l, cast(dev(z, lv.n, N)), cast(dev(f, lv.n, N)), r)
+            assert_blocks(host(r), f - S[l] @ z, lv.n, N, tol, f"residual level {l} (n = {lv.n})")
+    finally:
+        H.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_gs_above_256_samples(P, dtype):
+    """N = 260, above the 256 samples the four-colour sweep keeps in
+    registers: the sweep then parks each node's local right sides in its own
+    y, p slots between its two passes, with the per-node sums of p kept in a
+    scratch array.  One sweep on the 9-point grid, and one V-cycle, against
+    the oracle (FP64 bars as above; FP32 as SWEEP32 and CYCLE32)."""
+    n, N = 15, 260
+    xi = inputs.draw_xi(12, N, 4)
+    H = P.Hierarchy(n, N, xi, 1e-3, 0.8, coarse="galerkin")
+    try:
+        levels = O.make_hierarchy(n, N, 1e-3, O.sine_mode_field(xi, 0.8))
+        S = G.hierarchy(levels)
+        ns = [lv.n for lv in levels]
+        fine, lv = levels[0], levels[1]
+        m = lv.n * lv.n
+        rng = np.random.default_rng(36)
+        z = f32(rng.standard_normal(S[1].shape[0]))
+        f = rng.standard_normal(S[1].shape[0])
+        f[: m * N] *= fine.c
+        f[m * N: m * N + m] *= fine.G
+        f[m * N + m:] *= fine.h ** 2
+        f = f32(f)
+        cast = (lambda v: v) if dtype == torch.float64 else (lambda v: tuple(t.float() for t in v))
+        o = opts("gs") if dtype == torch.float64 else opts32("gs")
+        x = cast(dev(z, lv.n, N))
+        H.smooth(1, o, 1, x, cast(dev(f, lv.n, N)))
+        tol = 1e-10 if dtype == torch.float64 else SWEEP32
+        assert_blocks(host(x), G.smooth(S, ns, N, 1, z, f, "gs", 0.5), lv.n, N, tol, "gs sweep, N = 260")
+        z0 = f32(rng.standard_normal(S[0].shape[0]))
+        f0 = f32(O.pack(O.fine_rhs(fine, inputs.target_sinsin(n))))
+        x = cast(dev(z0, n, N))
+        H.cycle(o, x, cast(dev(f0, n, N)))
+        ref = G.cycle(S, ns, N, 0, z0, f0, n1=2, n2=2, theta=0.5, gamma=1, smoother="gs")
+        tol = 1e-9 if dtype == torch.float64 else CYCLE32
+        assert_blocks(host(x), ref, n, N, tol, "gs cycle, N = 260")
+    finally:
+        H.close()
