@@ -21,26 +21,36 @@ def conv_weight(w, cin):
     return w.reshape(co, 9, cin).permute(0, 2, 1).reshape(co, cin, 3, 3)
 
 
-def forward(params, x_nhwc):
+def forward(params, x_nhwc, q=None):
     """params: name -> (w, b) float64 tensors (requires_grad as wanted);
-    x_nhwc [B][S][S][8] -> prediction [B][S][S]."""
-    x = x_nhwc.permute(0, 3, 1, 2)
+    x_nhwc [B][S][S][8] -> prediction [B][S][S].
+
+    q, if given, is applied to every activation the network stores between
+    layers (the input, each convolution's output after ReLU, each pooled
+    and each upsampled-plus-skip tensor; not the prediction): with q the
+    rounding to the storage precision of an implementation, the result is
+    that implementation's up to the order of its sums."""
+    r = q if q is not None else (lambda t: t)
+    x = r(x_nhwc).permute(0, 3, 1, 2)
     cin = dict((n, ci) for n, ci, _ in CONVS)
 
     def conv(name, t):
         w, b = params[name]
-        return F.relu(F.conv2d(t, conv_weight(w, cin[name]), b, padding=1))
+        return r(F.relu(F.conv2d(t, conv_weight(w, cin[name]), b, padding=1)))
 
-    def up(t):
-        return F.interpolate(t, scale_factor=2, mode="nearest")
+    def pool(t):
+        return r(F.avg_pool2d(t, 2))
+
+    def up_add(t, skip):
+        return r(F.interpolate(t, scale_factor=2, mode="nearest") + skip)
 
     s0 = conv("c0b", conv("c0a", x))
-    s1 = conv("c1b", conv("c1a", F.avg_pool2d(s0, 2)))
-    s2 = conv("c2b", conv("c2a", F.avg_pool2d(s1, 2)))
-    b3 = conv("c3b", conv("c3a", F.avg_pool2d(s2, 2)))
-    e2 = conv("d2", up(b3) + s2)
-    e1 = conv("d1", up(e2) + s1)
-    e0 = conv("d0", up(e1) + s0)
+    s1 = conv("c1b", conv("c1a", pool(s0)))
+    s2 = conv("c2b", conv("c2a", pool(s1)))
+    b3 = conv("c3b", conv("c3a", pool(s2)))
+    e2 = conv("d2", up_add(b3, s2))
+    e1 = conv("d1", up_add(e2, s1))
+    e0 = conv("d0", up_add(e1, s0))
     w, b = params["head"]
     return F.conv2d(e0, w.reshape(1, -1, 1, 1), b)[:, 0]
 

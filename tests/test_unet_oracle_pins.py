@@ -64,3 +64,45 @@ def test_network_gradients_match_finite_differences():
             fd = (loss_at(h) - loss_at(-h)) / (2 * h)
             ad = float((w.grad * vw).sum() + (b.grad * vb).sum())
             assert abs(fd - ad) <= 1e-6 * max(1e-3, abs(ad)), (name, fd, ad)
+
+
+def test_storage_rounding_hook_sees_every_stored_activation_in_order():
+    """forward(..., q) applies q to the input and to every tensor the network
+    stores between layers, in layer order: the 11 convolution outputs, the 3
+    pooled and the 3 upsampled-plus-skip tensors (18 in all), never to the
+    prediction; q = identity leaves the result unchanged, and with q the
+    BF16 rounding each stored tensor is BF16-representable."""
+    g = torch.Generator().manual_seed(2)
+    S = 16
+    params = {name: (torch.randn(co, 9 * ci, generator=g, dtype=torch.float64) * (2.0 / (9 * ci)) ** 0.5,
+                     torch.randn(co, generator=g, dtype=torch.float64) * 0.1) for name, ci, co in U.CONVS}
+    params["head"] = (torch.randn(1, 32, generator=g, dtype=torch.float64) * 0.3, torch.zeros(1, dtype=torch.float64))
+    x = torch.randn(2, S, S, 8, generator=g, dtype=torch.float64)
+    seen = []
+
+    def record(t):
+        seen.append(tuple(t.shape))
+        return t
+
+    base = U.forward(params, x)
+    assert torch.equal(U.forward(params, x, q=record), base)
+    # NHWC input, then NCHW activations: level-0 convs, pool, level-1 convs, ...
+    expect = [(2, S, S, 8), (2, 32, S, S), (2, 32, S, S), (2, 32, S // 2, S // 2), (2, 64, S // 2, S // 2),
+              (2, 64, S // 2, S // 2), (2, 64, S // 4, S // 4), (2, 64, S // 4, S // 4), (2, 64, S // 4, S // 4),
+              (2, 64, S // 8, S // 8), (2, 64, S // 8, S // 8), (2, 64, S // 8, S // 8),
+              (2, 64, S // 4, S // 4), (2, 64, S // 4, S // 4),      # up + skip, d2
+              (2, 64, S // 2, S // 2), (2, 32, S // 2, S // 2),      # up + skip, d1
+              (2, 32, S, S), (2, 32, S, S)]                          # up + skip, d0
+    assert seen == expect
+
+    def bf16(t):
+        r = t.to(torch.bfloat16).to(torch.float64)
+        seen.append(bool(torch.equal(r.to(torch.bfloat16).to(torch.float64), r)))
+        return r
+
+    seen.clear()
+    rounded = U.forward(params, x, q=bf16)
+    assert len(seen) == 18 and all(seen)
+    # rounding every stored tensor to 8 significant bits moves the prediction
+    # by a few tenths of a percent of its scale, not more
+    assert 0 < float((rounded - base).abs().max()) <= 2e-2 * float(base.abs().max())
