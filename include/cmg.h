@@ -382,7 +382,7 @@ cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
  * cmg_autotune runs): num_levels entries of 0 (size heuristic), 1, 2 or 4,
  * and for CMG_FP32 also CMG_TUNE_STAGED | 1, CMG_TUNE_STAGED | 2 or
  * CMG_TUNE_WIDE | 1 (ignored where N is odd or above 64) or CMG_TUNE_FUSED |
- * 1, 2 or 4, each possibly with CMG_TUNE_UNFUSED; NULL resets all to 0.  Other values return
+ * 1, 2 or 4 or CMG_TUNE_TMA | 1, 2 or 4, each possibly with CMG_TUNE_UNFUSED; NULL resets all to 0.  Other values return
  * CMG_ERR_INVALID_ARG. */
 #define CMG_TUNE_STAGED 16
 #define CMG_TUNE_WIDE 32
@@ -404,6 +404,24 @@ cmg_status cmg_autotune(cmg_handle* h, int precision, int* chosen);
  * their rows one after another, so a sweep that reads less, from the zero
  * iterate, takes as long as a full one). */
 #define CMG_TUNE_FUSED 128
+/* FP32 flag with 1, 2 or 4 chunks per lane (N % 4 == 0, N <= 256): the
+ * plain red-black half-sweeps on this grid bring their operands into a ring
+ * of shared-memory stages by TMA tensor loads that gather every other node
+ * of a grid row (a segment of one colour's nodes, its neighbours in the
+ * rows above and below, its left/right neighbours, its faces and right
+ * sides); one producer thread per CTA issues them and consumer warps
+ * update the nodes from there, so the bytes in flight are set by the ring,
+ * not by registers.  The results equal the direct half-sweep's bit for
+ * bit.  Ignored where the shape is not covered (frozen control, 16-byte
+ * misaligned arrays); the zero-iterate and prolongation-fused sweeps keep
+ * their direct kernels. */
+#define CMG_TUNE_TMA 256
+/* The TMA half-sweep (CMG_TUNE_TMA) bounds every wait on its shared-memory
+ * barriers; a wait that runs out (never, unless a load or a warp fails to
+ * complete) adds one to a process-wide counter and returns.  *count = that
+ * counter for the current device (synchronises the device).
+ * CMG_ERR_INVALID_ARG for a null pointer, CMG_ERR_CUDA if the read fails. */
+cmg_status cmg_sweep_wait_timeouts(unsigned int* count);
 /* The launch shape the node kernels use for N samples of elem_bytes (4 or 8)
  * over `items` nodes (0: as many lanes per node as allowed) with a tuning
  * target as above: *lanes_per_node (a power of two <= 32, consecutive lanes of

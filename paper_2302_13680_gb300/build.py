@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libcmg.so")
 
 SOURCES = ["cmg_api.cu", "cmg_stencil.cu", "cmg_setup.cu", "cmg_coarse.cu", "cmg_blas.cu", "cmg_noalloc.cu",
            "cmg_tail_f32.cu", "cmg_tail_f64.cu", "cmg_nn_gemm.cu", "cmg_nn_api.cu", "cmg_nn_ops.cu",
-           "cmg_staged.cu", "cmg_ssn.cu", "cmg_galerkin.cu", "cmg_unet.cu",
+           "cmg_staged.cu", "cmg_tma_sweep.cu", "cmg_ssn.cu", "cmg_galerkin.cu", "cmg_unet.cu",
            "cmg_batch.cu", "cmg_boundary.cu", "cmg_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

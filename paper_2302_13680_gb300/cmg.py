@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cmg_kernel_launches": (ctypes.c_longlong, []),
         "cmg_autotune": (_I, [H, _I, ctypes.POINTER(ctypes.c_int)]),
         "cmg_set_tuning": (_I, [H, _I, ctypes.POINTER(ctypes.c_int)]),
+        "cmg_sweep_wait_timeouts": (_I, [ctypes.POINTER(ctypes.c_uint)]),
         "cmg_batch_autotune": (_I, [_P, _I]),
         "cmg_batch_create": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p), _I, _P,
                                   ctypes.POINTER(ctypes.c_void_p)]),

@@ -1162,13 +1162,15 @@ cmg_status cmg_set_tuning(cmg_handle* h, int precision, const int* spl_targets) 
   const int k = precision == CMG_FP64 ? 0 : 1;
   for (int l = 0; l < h->L; ++l) {
     const int t = spl_targets ? spl_targets[l] : 0;
-    const int c = t & ~(kTuneStaged | kTuneWide | kTuneUnfused | kTuneFused);
+    const int c = t & ~(kTuneStaged | kTuneWide | kTuneUnfused | kTuneFused | kTuneTma);
     const bool staged = t & kTuneStaged, wide = t & kTuneWide, unfused = t & kTuneUnfused, fused = t & kTuneFused;
-    if ((c != 0 && c != 1 && c != 2 && c != 4) || ((staged || wide || unfused || fused) && k == 0) ||
-        (staged && c != 1 && c != 2) || (wide && (staged || c != 1)) || (fused && (staged || wide || c == 0)))
+    const bool tma = t & kTuneTma;
+    if ((c != 0 && c != 1 && c != 2 && c != 4) || ((staged || wide || unfused || fused || tma) && k == 0) ||
+        (staged && c != 1 && c != 2) || (wide && (staged || c != 1)) || (fused && (staged || wide || c == 0)) ||
+        (tma && (staged || wide || fused || c == 0)))
       return fail(h, CMG_ERR_INVALID_ARG,
                   "target must be 0, 1, 2 or 4 (FP32: or CMG_TUNE_STAGED | 1 or 2, or CMG_TUNE_WIDE | 1, or "
-                  "CMG_TUNE_FUSED | 1, 2 or 4; any of them | CMG_TUNE_UNFUSED)");
+                  "CMG_TUNE_FUSED | 1, 2 or 4, or CMG_TUNE_TMA | 1, 2 or 4; any of them | CMG_TUNE_UNFUSED)");
   }
   for (int l = 0; l < h->L; ++l) h->lv[l].spl_target[k] = spl_targets ? spl_targets[l] : 0;
   h->ir_opts.n1 = -1;   // captured graphs bake the launch shapes: force a re-capture

@@ -146,10 +146,19 @@ constexpr int kTuneUnfused = 64;
 // Tuning target flag (FP32): the red-black sweeps on this grid run as one
 // launch per sweep (launch_rbgs_fused) in pairs through a second buffer.
 constexpr int kTuneFused = 128;
+// Tuning target flag (FP32, N % 4 == 0 and N <= 256, with 1, 2 or 4 chunks
+// per lane): the plain half-sweeps on this grid bring their rows into
+// shared memory by TMA loads that gather every other node of a grid row
+// (launch_rbgs_half_tma, cmg_tma_sweep.cu); the same bits as the direct
+// half-sweep.
+constexpr int kTuneTma = 256;
 inline bool wide_supported(int N) { return N % 2 == 0 && N <= 64; }
 bool staged_supported(int N, int spl);
 cudaError_t launch_rbgs_half_staged(const LevelView<float>& L, Vec3<float> x, Vec3c<float> f, int colour,
                                     const SampleMap& m, cudaStream_t s);
+// cudaErrorNotSupported (nothing enqueued) where the shape is not covered.
+cudaError_t launch_rbgs_half_tma(const LevelView<float>& L, Vec3<float> x, Vec3c<float> f, int colour,
+                                 const SampleMap& m, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int colour, cudaStream_t s);
 // Colour-0 half-sweep of a cycle that starts from a zero iterate: x is not

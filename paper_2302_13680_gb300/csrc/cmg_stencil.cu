@@ -284,6 +284,10 @@ cudaError_t launch_rbgs_half(const LevelView<T>& L, Vec3<T> x, Vec3c<T> f, int c
       const cudaError_t e = launch_rbgs_half_staged(L, x, f, colour, m, st);
       if (e != cudaErrorNotSupported) return e;
     }
+    if (L.spl_target & kTuneTma) {
+      const cudaError_t e = launch_rbgs_half_tma(L, x, f, colour, m, st);
+      if (e != cudaErrorNotSupported) return e;
+    }
   }
   const unsigned grid = grid_for(colour_count(L.n, colour), m.lpn);
   cudaError_t e_ = cudaSuccess;
