@@ -20,6 +20,7 @@ constexpr int kGBlock = 256;
 // one-launch form's extra FMAs per node-sample cost more in the FP64 pipe)
 constexpr int kResidual9OnePass32 = 63, kResidual9OnePass64 = 31;
 constexpr int kGsMaxR = 8;   // four-colour sweep: samples per lane held in registers (N <= 256)
+constexpr long kGsHalfWarpNodes = 2048;   // FP32 grids from this many nodes per colour: 16 lanes per node
 
 // The coarse nodes that a fine node 2C+1+g (one axis, g in [-2, 2]) takes
 // its bilinear interpolant from, as offsets from C, with their weights: g
@@ -344,12 +345,16 @@ __global__ void gs4_colour_kernel(int n, int N, int cy, int cx, const T* __restr
   }
 }
 
-// The same colour sweep with each lane's samples (j = lane + 32 q, q < R,
-// N <= 32 R) held in registers between the two passes, and the control
-// row's sum over samples of the neighbours' (M p_j) formed from the p values
-// the state rows load (no per-node sums kept between launches):
+// The same colour sweep with each node's samples spread over LPN lanes
+// (j = l + LPN q, q < R, N <= LPN R) and held in registers between the two
+// passes, and the control row's sum over samples of the neighbours' (M p_j)
+// formed from the p values the state rows load (no per-node sums kept
+// between launches):
 //   B_u = f_u - G (M u)_i - d sum_j (M p_j)_i   (off-centre entries, FP64).
-template <typename T, int R>
+// A warp takes 32 / LPN nodes, so each warp instruction of the node's FP64
+// work (the off-centre (M u)_i, the two group sums, u_i) serves as many
+// nodes: on this GPU the FP64 pipe, not memory, bounds a warp per node.
+template <typename T, int R, int LPN>
 __global__ void __launch_bounds__(kGBlock) gs4_colour_reg_kernel(int n, int N, int cy, int cx,
                                                                  const T* __restrict__ a9, Stencil9 M, double c,
                                                                  double G, double d, double e,
@@ -358,10 +363,13 @@ __global__ void __launch_bounds__(kGBlock) gs4_colour_reg_kernel(int n, int N, i
                                                                  Vec3c<T> f) {
   pdl_enter();
   const int nbx = (n - cx + 1) / 2, nby = (n - cy + 1) / 2;
-  const long g = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (g >= (long)nbx * nby) return;   // whole warp
-  const int iy = cy + 2 * (int)(g / nbx), ix = cx + 2 * (int)(g % nbx);
+  const long count = (long)nbx * nby;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((t & ~31L) / LPN >= count) return;   // the warp's first node is past the end: whole warp
+  const long g = t / LPN;
+  const int l = (int)(threadIdx.x & (LPN - 1));
+  const bool valid = g < count;
+  const int iy = valid ? cy + 2 * (int)(g / nbx) : 0, ix = valid ? cx + 2 * (int)(g % nbx) : 0;
   const size_t nodes = (size_t)n * n;
   const size_t i = (size_t)iy * n + ix;
   const double mc = M.w[4];
@@ -371,17 +379,19 @@ __global__ void __launch_bounds__(kGBlock) gs4_colour_reg_kernel(int n, int N, i
   nine_neighbours(n, iy, ix, ok, nb);
   ok[4] = false;
   double Mu = 0.0;   // off-centre (M u)_i
+  if (valid) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k)
-    if (ok[k]) Mu = fma(M.w[k], (double)x.u[nb[k]], Mu);
+    for (int k = 0; k < 9; ++k)
+      if (ok[k]) Mu = fma(M.w[k], (double)x.u[nb[k]], Mu);
+  }
   const T eMu = (T)(e * Mu), cT = (T)c;
   T By[R], Bp[R], ia[R];
   T tacc = 0, pm = 0;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int j = lane + 32 * q;
+    const int j = l + LPN * q;
     By[q] = Bp[q] = ia[q] = 0;
-    if (j < N) {
+    if (valid && j < N) {
       T by = f.y[i * N + j], bp = f.p[i * N + j] - eMu, mp = 0;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
@@ -402,23 +412,24 @@ __global__ void __launch_bounds__(kGBlock) gs4_colour_reg_kernel(int n, int N, i
     }
   }
   double ts = (double)tacc, ps = (double)pm;
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = LPN / 2; o > 0; o >>= 1) {
     ts += __shfl_xor_sync(0xffffffffu, ts, o);
     ps += __shfl_xor_sync(0xffffffffu, ps, o);
   }
+  if (!valid) return;
   const double Bu = (double)f.u[i] - G * Mu - d * ps;
   const double u = (Bu + d * mc * ts) * isigma[i];
   const T uT = (T)u;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int j = lane + 32 * q;
+    const int j = l + LPN * q;
     if (j < N) {
       const T y = ia[q] * (Bp[q] - ed * uT);
       x.y[i * N + j] = y;
       x.p[i * N + j] = ia[q] * (By[q] - cd * y);
     }
   }
-  if (lane == 0) x.u[i] = uT;
+  if (l == 0) x.u[i] = uT;
 }
 
 // Damped collective Jacobi on a 9-point grid: x_i += theta S~_i^{-1} r_i with
@@ -526,26 +537,35 @@ cudaError_t launch_gs4_sweep(int n, int N, const T* a9, const Stencil9& M, doubl
                              cudaStream_t s) {
   const long nodes = (long)n * n;
   if (N <= 32 * kGsMaxR) {
-    // samples in registers: four launches, nothing kept between them
-    const int R = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : 8;
+    // samples in registers: four launches, nothing kept between them.  FP32
+    // on grids of at least kGsHalfWarpNodes nodes per colour, up to 64
+    // samples: 16 lanes per node (two nodes per warp share the FP64 work);
+    // elsewhere a warp per node (smaller grids want the warps, and in FP64
+    // the per-sample work outweighs the per-node)
+    const long colour_nodes = (long)((n + 1) / 2) * ((n + 1) / 2);
+    const int lpn = (sizeof(T) == 4 && N <= 64 && colour_nodes >= kGsHalfWarpNodes) ? 16 : 32;
+    const int need = (N + lpn - 1) / lpn;
+    const int R = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
     cudaError_t err = cudaSuccess;
     for (int col = 0; col < 4 && err == cudaSuccess; ++col) {
       const int cy = col >> 1, cx = col & 1;
       const long groups = (long)((n - cx + 1) / 2) * ((n - cy + 1) / 2);
       if (groups == 0) continue;
-      const unsigned grid = blocks_for(groups * 32);
-      if (R == 1)
-        err = launch_k(gs4_colour_reg_kernel<T, 1>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
-                       x, f);
-      else if (R == 2)
-        err = launch_k(gs4_colour_reg_kernel<T, 2>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
-                       x, f);
-      else if (R == 4)
-        err = launch_k(gs4_colour_reg_kernel<T, 4>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
-                       x, f);
-      else
-        err = launch_k(gs4_colour_reg_kernel<T, 8>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, isigma,
-                       x, f);
+      const unsigned grid = blocks_for(groups * lpn);
+#define CMG_GS4(RR, LL)                                                                                         \
+  err = launch_k(gs4_colour_reg_kernel<T, RR, LL>, grid, kGBlock, 0, s, n, N, cy, cx, a9, M, c, G, d, e, inva, \
+                 isigma, x, f)
+      if (lpn == 16) {
+        if (R == 1) CMG_GS4(1, 16);
+        else if (R == 2) CMG_GS4(2, 16);
+        else CMG_GS4(4, 16);
+      } else {
+        if (R == 1) CMG_GS4(1, 32);
+        else if (R == 2) CMG_GS4(2, 32);
+        else if (R == 4) CMG_GS4(4, 32);
+        else CMG_GS4(8, 32);
+      }
+#undef CMG_GS4
     }
     count_launches(4);
     return err != cudaSuccess ? err : cudaGetLastError();
