@@ -128,16 +128,18 @@ __device__ __forceinline__ void nine_neighbours(int n, int iy, int ix, bool* ok,
   }
 }
 
-// psum[i] = sum_j p[i][j] (FP64): one warp per node, fixed-order shuffle
-// reduction (the four-colour sweep for N above 32 kGsMaxR samples).
+// psum[i] = sum_j p[i][j]: the lanes' parts in T, then a fixed-order FP64
+// shuffle reduction; one warp per node (the three-launch residual and the
+// four-colour sweep above 32 kGsMaxR samples).
 template <typename T>
 __global__ void galerkin_psum_kernel(long nodes, int N, const T* __restrict__ p, double* __restrict__ psum) {
   pdl_enter();
   const long node = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (node >= nodes) return;   // whole warp
-  double s = 0.0;
-  for (int j = lane; j < N; j += 32) s += (double)p[(size_t)node * N + j];
+  T sl = 0;   // this lane's part in T (FP32: converted once, as the sweeps' sums)
+  for (int j = lane; j < N; j += 32) sl += p[(size_t)node * N + j];
+  double s = (double)sl;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) psum[node] = s;
 }
@@ -434,28 +436,34 @@ __global__ void __launch_bounds__(kGBlock) gs4_colour_reg_kernel(int n, int N, i
 
 // Damped collective Jacobi on a 9-point grid: x_i += theta S~_i^{-1} r_i with
 // S~_i the node's block with the Galerkin diagonal entries (Eq. (11), Eq. (13)
-// on the residual).  One warp per node, lanes over samples; per-sample work
-// in T, the sum over samples and the u correction in FP64.
-template <typename T>
+// on the residual).  LPN lanes per node (32, or 16 on large FP32 grids, as
+// the colour kernel), lanes over samples; per-sample work in T, the sum over
+// samples and the u correction in FP64.
+template <typename T, int LPN>
 __global__ void galerkin_jacobi_kernel(long nodes, int N, Stencil9 M, double c, double d, double e, double theta,
                                        const T* __restrict__ inva, const double* __restrict__ isigma, Vec3<T> x,
                                        Vec3c<T> r) {
   pdl_enter();
-  const long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= nodes) return;   // whole warp
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((t & ~31L) / LPN >= nodes) return;   // the warp's first node is past the end: whole warp
+  const long i = t / LPN;
+  const int l = (int)(threadIdx.x & (LPN - 1));
+  const bool valid = i < nodes;
   const double mc = M.w[4];
   const T cd = (T)(c * mc), ed = (T)(e * mc);
   T tacc = 0;
-  for (int j = lane; j < N; j += 32) {
-    const T ia = inva[(size_t)i * N + j];
-    tacc += (cd * ia) * (ia * r.p[(size_t)i * N + j]) - ia * r.y[(size_t)i * N + j];
+  if (valid) {
+    for (int j = l; j < N; j += LPN) {
+      const T ia = inva[(size_t)i * N + j];
+      tacc += (cd * ia) * (ia * r.p[(size_t)i * N + j]) - ia * r.y[(size_t)i * N + j];
+    }
   }
   double ts = (double)tacc;
-  for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+  for (int o = LPN / 2; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+  if (!valid) return;
   const double du = ((double)r.u[i] + d * mc * ts) * isigma[i];
   const T duT = (T)du, th = (T)theta;
-  for (int j = lane; j < N; j += 32) {
+  for (int j = l; j < N; j += LPN) {
     const size_t o = (size_t)i * N + j;
     const T ia = inva[o];
     const T dy = ia * (r.p[o] - ed * duT);
@@ -463,7 +471,7 @@ __global__ void galerkin_jacobi_kernel(long nodes, int N, Stencil9 M, double c, 
     x.y[o] += th * dy;
     x.p[o] += th * dp;
   }
-  if (lane == 0) x.u[i] += (T)(theta * du);
+  if (l == 0) x.u[i] += (T)(theta * du);
 }
 
 unsigned blocks_for(long threads) { return (unsigned)((threads + kGBlock - 1) / kGBlock); }
@@ -589,8 +597,14 @@ template <typename T>
 cudaError_t launch_galerkin_jacobi(int n, int N, const Stencil9& M, double c, double d, double e, double theta,
                                    const T* inva, const double* isigma, Vec3<T> x, Vec3c<T> r, cudaStream_t s) {
   const long nodes = (long)n * n;
-  const cudaError_t err = launch_k(galerkin_jacobi_kernel<T>, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N, M, c,
-                                   d, e, theta, inva, isigma, x, r);
+  // two nodes per warp where the colour kernel takes them (its node count
+  // per colour is a quarter of the grid's)
+  const int lpn = (sizeof(T) == 4 && N <= 64 && nodes >= 4 * kGsHalfWarpNodes) ? 16 : 32;
+  const cudaError_t err =
+      lpn == 16 ? launch_k(galerkin_jacobi_kernel<T, 16>, blocks_for(nodes * 16), kGBlock, 0, s, nodes, N, M, c, d, e,
+                           theta, inva, isigma, x, r)
+                : launch_k(galerkin_jacobi_kernel<T, 32>, blocks_for(nodes * 32), kGBlock, 0, s, nodes, N, M, c, d, e,
+                           theta, inva, isigma, x, r);
   count_launches(1);
   return err != cudaSuccess ? err : cudaGetLastError();
 }

@@ -355,7 +355,8 @@ def test_residual_large_grid(P, dtype):
     """The residual on a 9-point grid above the one-launch size (n = 127 below
     n = 255: the three-launch form with the per-node sums of p) and on the
     grids below it, in FP64 and FP32, against the sparse Galerkin product;
-    and one four-colour sweep on the n = 127 grid against the oracle's."""
+    and one sweep of either smoother on the n = 127 grid against the
+    oracle's."""
     n, N = 255, 4
     xi = inputs.draw_xi(13, N, 3)
     H = P.Hierarchy(n, N, xi, 1e-4, 0.8, coarse="galerkin")
@@ -372,8 +373,9 @@ def test_residual_large_grid(P, dtype):
             r = H.zeros(l, dtype)
             H.residual(l, cast(dev(z, lv.n, N)), cast(dev(f, lv.n, N)), r)
             assert_blocks(host(r), f - S[l] @ z, lv.n, N, tol, f"residual level {l} (n = {lv.n})")
-        # one Gauss-Seidel sweep on the n = 127 grid: in FP32 its 4,096 nodes
-        # per colour take the two-nodes-per-warp form of the colour kernel
+        # one sweep of either smoother on the n = 127 grid: in FP32 its 4,096
+        # nodes per colour (16,129 in all) take the two-nodes-per-warp forms of
+        # the colour and Jacobi kernels
         fine, lv = levels[0], levels[1]
         m = lv.n * lv.n
         z = f32(rng.standard_normal(S[1].shape[0]))
@@ -382,10 +384,11 @@ def test_residual_large_grid(P, dtype):
         fr[m * N: m * N + m] *= fine.G
         fr[m * N + m:] *= fine.h ** 2
         fr = f32(fr)
-        x = cast(dev(z, lv.n, N))
-        H.smooth(1, opts("gs") if dtype == torch.float64 else opts32("gs"), 1, x, cast(dev(fr, lv.n, N)))
-        ref = G.smooth(S, [v.n for v in levels], N, 1, z, fr, "gs", 0.5)
-        assert_blocks(host(x), ref, lv.n, N, 1e-10 if dtype == torch.float64 else SWEEP32, "gs sweep, n = 127")
+        for sm in SMOOTHERS:
+            x = cast(dev(z, lv.n, N))
+            H.smooth(1, opts(sm) if dtype == torch.float64 else opts32(sm), 1, x, cast(dev(fr, lv.n, N)))
+            ref = G.smooth(S, [v.n for v in levels], N, 1, z, fr, sm, 0.5)
+            assert_blocks(host(x), ref, lv.n, N, 1e-10 if dtype == torch.float64 else SWEEP32, f"{sm} sweep, n = 127")
     finally:
         H.close()
 
